@@ -1,0 +1,370 @@
+"""Benchmark: screened ACE builds per second (128 orbitals, 96^3 grid, rho_cut 1e-3) on one GB300.
+
+One step = one whole ACE build through the C ABI (pair screen, pair-potential chain, M,
+Cholesky/L^-1/E_x, xi) on the 32-water-like synthetic input, plus the host read of E_x.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Our arm prints one JSON line with the mixed-form builds/s (value), the plain FP64 form for
+comparison, an end-to-end figure through host buffers, the roofline of the pair chain, sampled
+clocks and the FP64 CPU oracle timed on a bounded sample.  ``--impl reference`` times the oracle
+alone (the CPU program written from the paper) on the same workload.  Under torchrun every rank
+builds its own replica (weak scaling) and rank 0 prints.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "water32_128orb_96c_rhocut1e-3"
+METRIC = "ACE builds/s (128 orb, 96^3), mixed vs FP64 GPU form; E_x err <=1e-6 Ha/orb"
+UNIT = "builds/s"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_values.json")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _golden():
+    try:
+        with open(GOLDEN) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"ace_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.remove(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle on a bounded sample (baseline leg and reference arm)
+# ------------------------------------------------------------------------------------------
+
+def oracle_sample(w, mask, target_s: float, include_dense: bool):
+    """Time the FP64 oracle on part of one build and scale to a whole build.
+
+    The pair work (Eq. vx row by row) is timed for the first rows whose (i, j) evaluations add up to
+    about `target_s` seconds and scaled by total/sampled evaluations; with include_dense the screen
+    and the M / Cholesky / xi step (value-independent cost, timed on a stand-in W) are timed whole.
+    """
+    import oracle
+
+    n = w.norb
+    counts = mask.sum(axis=1)
+    t_screen = t_dense = 0.0
+    if include_dense:
+        t0 = time.perf_counter()
+        oracle.screen(w.phi, w.lattice, w.rho_cut)
+        t_screen = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.ace_from_w(w.phi, w.phi, w.dV, want_xi=True)
+        t_dense = time.perf_counter() - t0
+    # calibrate with one row, then take enough rows for ~target_s
+    t0 = time.perf_counter()
+    oracle.exchange_w(w.phi, w.lattice, mask=mask, rows=[0])
+    t_row0 = time.perf_counter() - t0
+    per_eval = t_row0 / max(int(counts[0]), 1) * oracle.max_threads()  # single-thread cost per v_ij
+    nthreads = oracle.max_threads()
+    rows, evals = [], 0
+    for i in range(1, n):
+        rows.append(i)
+        evals += int(counts[i])
+        if evals * per_eval / nthreads >= target_s and len(rows) >= nthreads:
+            break
+    t0 = time.perf_counter()
+    oracle.exchange_w(w.phi, w.lattice, mask=mask, rows=rows)
+    t_rows = time.perf_counter() - t0
+    total_evals = int(counts.sum())
+    t_pair_full = t_rows * total_evals / max(evals, 1)
+    t_build = t_pair_full + t_screen + t_dense
+    return {
+        "builds_per_s": 1.0 / t_build,
+        "seconds_per_build": t_build,
+        "sample_rows": len(rows),
+        "sample_evals": evals,
+        "total_evals": total_evals,
+        "cores": nthreads,
+        "t_rows": t_rows,
+        "t_screen": t_screen,
+        "t_dense": t_dense,
+    }
+
+
+def _workload():
+    from workloads.generators import config2
+
+    return config2()
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    w = _workload()
+    _, mask = oracle.screen(w.phi, w.lattice, w.rho_cut)
+    for _ in range(args.warmup):
+        oracle_sample(w, mask, target_s=args.ref_step_s, include_dense=False)
+    t_all = []
+    info = None
+    for _ in range(args.steps):
+        info = oracle_sample(w, mask, target_s=args.ref_step_s, include_dense=False)
+        t_all.append(info["seconds_per_build"])
+    spb = statistics.mean(t_all)
+    value = 1.0 / spb
+    sample = (f"per step: Eq. vx rows 1..{info['sample_rows']} ({info['sample_evals']} of {info['total_evals']} "
+              f"v_ij evaluations, FP64, OpenMP) scaled by evaluations to one screened build")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * spb, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "norb": w.norb, "grid": list(w.grid), "rho_cut": w.rho_cut},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+
+def _timed_builds(ace, desc, phi, stream, steps, collect):
+    import torch
+
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for _ in range(steps):
+        op = ace.ace_build(desc, phi, stream)
+        e = ace.exchange_energy(op)
+        collect(op, e)
+        op.close()
+    end.record(stream)
+    torch.cuda.synchronize()
+    return start.elapsed_time(end)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2101_03155_gb300 as ace
+    from paper_2101_03155_gb300 import build as cuda_build
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(local)
+    if rank == 0:
+        cuda_build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    cuda_build.build()
+    ace.ace.load()
+
+    w = _workload()
+    n, N = w.norb, w.npts
+    golden = _golden().get(WORKLOAD, {})
+    stream = torch.cuda.current_stream()
+    phi32 = torch.from_numpy(w.phi.astype(np.float32)).cuda()
+    desc = ace.make_desc(w.grid, w.lattice, n, rho_cut=w.rho_cut, spin_factor=w.spin_factor, prec=ace.ACE_MIXED)
+
+    rec = {"E": [], "chain_ms": [], "stage": [], "launches": 0, "npairs": None}
+
+    def collect(op, e):
+        rec["E"].append(e)
+        st = ace.ace_stage_times(op)
+        rec["stage"].append(st)
+        rec["chain_ms"].append(st["pair_chain"])
+        rec["launches"] += ace.ace.ace_kernel_launches(op)
+        rec["npairs"] = ace.ace_pair_count(op)
+
+    for _ in range(args.warmup):
+        op = ace.ace_build(desc, phi32, stream)
+        op.close()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ms = _timed_builds(ace, desc, phi32, stream, args.steps, collect)
+    clk = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        torch.distributed.barrier()
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+
+    # end to end: host (pinned) orbitals through the same C ABI call; copies inside the timed region
+    host32 = torch.from_numpy(w.phi.astype(np.float32)).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    rec_e2e = {"E": []}
+    ms_e2e = _timed_builds(ace, desc, host32, stream, e2e_steps, lambda op, e: rec_e2e["E"].append(e))
+    e2e_value = world * e2e_steps / (ms_e2e / 1e3)
+
+    # plain FP64 GPU form, same workload
+    phi64 = torch.from_numpy(w.phi).cuda()
+    desc64 = ace.make_desc(w.grid, w.lattice, n, rho_cut=w.rho_cut, spin_factor=w.spin_factor, prec=ace.ACE_FP64)
+    op = ace.ace_build(desc64, phi64, stream)
+    op.close()
+    rec64 = {"E": []}
+    ms64 = _timed_builds(ace, desc64, phi64, stream, args.fp64_steps, lambda op, e: rec64["E"].append(e))
+    fp64_value = args.fp64_steps / (ms64 / 1e3)
+    del phi64
+
+    peaks, peak_kind = _peaks()
+    npairs = rec["npairs"]
+    chain_s = statistics.mean(rec["chain_ms"]) / 1e3
+    alg_bytes = 24.0 * N * npairs  # read phi_i, phi_j; read+write W_i, W_j in FP32, per grid point per pair
+    achieved = alg_bytes / chain_s / 1e9
+    stage_mean = {k: statistics.mean(s[k] for s in rec["stage"]) for k in rec["stage"][0]}
+
+    e_ref = golden.get("E_x")
+    ex_err = None if e_ref is None else abs(statistics.mean(rec["E"]) - e_ref) / n
+    ex_err64 = None if e_ref is None else abs(statistics.mean(rec64["E"]) - e_ref) / n
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "norb": n, "grid": list(w.grid), "rho_cut": w.rho_cut,
+                   "precision": "mixed", "npairs": npairs,
+                   "l2": "inputs larger than L2 (orbitals 453 MB FP32, W and xi 453 MB each)"},
+        "accuracy": {"E_x": statistics.mean(rec["E"]), "E_x_oracle": e_ref, "ex_err_ha_per_orb": ex_err},
+        "fp64_form": {"value": fp64_value, "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps,
+                      "steps": args.fp64_steps, "ex_err_ha_per_orb": ex_err64,
+                      "speedup_mixed_over_fp64": value / world / fp64_value},
+        "stage_ms": stage_mean,
+        "roofline": {"kernel": "pair chain (5 pencil passes per pack batch)", "bound": "hbm",
+                     "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                     "frac": achieved / peaks.get("hbm_gbs"), "traffic": None,
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes": f"24 B x N x npairs = {alg_bytes:.4g} B per build"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n * N, "d2h_bytes_per_step": 16,
+                "steps": e2e_steps},
+        "gpu_launches": rec["launches"],
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        _, mask = oracle.screen(w.phi, w.lattice, w.rho_cut)
+        info = oracle_sample(w, mask, target_s=args.cpu_sample_s, include_dense=True)
+        line["cpu_baseline"] = {
+            "value": info["builds_per_s"], "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+            "sample": (f"FP64 oracle: full screen ({info['t_screen']:.1f} s) + M/Cholesky/xi on a stand-in W "
+                       f"({info['t_dense']:.1f} s) + Eq. vx rows 1..{info['sample_rows']} "
+                       f"({info['sample_evals']}/{info['total_evals']} v_ij, {info['t_rows']:.1f} s) scaled "
+                       f"to all rows"),
+        }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    ap.add_argument("--ref-step-s", type=float, default=8.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,142 @@
+/*
+ * ace.h -- C ABI of the GB300 (sm_103a) screened adaptively-compressed-exchange (s-ACE) library.
+ *
+ * Method: arXiv:2101.03155 (s-MTACE).  The library builds the ACE operator from a set of real,
+ * Gamma-point, orthonormal (typically localized) orbitals on a periodic grid and applies it:
+ *
+ *   pair screen (section II, display after Eq. unit): keep pair (i,j) iff int |phi_i phi_j| >= rho_cut
+ *   pair potential (Eq. e:vij): v_ij = <phi_j | 1/r12 | phi_i>, by FFT with the 4 pi/|G|^2 kernel
+ *   exchange action (Eq. vx):  W_i = sum_j v_ij phi_j            (W = -V_X phi)
+ *   Appendix A:                M = -dV Phi^T W, -M = L L^T, xi = W L^-T   (xi = -P of App. A)
+ *   ACE application (section II): K psi = -xi (dV xi^T psi) = V_X^ACE psi
+ *   exchange energy:           E_x = (f/2) tr M
+ *
+ * Conventions (all entry points):
+ *   - grid index r = (i1, i2, i3), i3 fastest; point x_r = sum_k (i_k/N_k) a_k; N = N1 N2 N3;
+ *     dV = Omega / N with Omega = |det(lattice)|.
+ *   - orbital arrays are [count][N1][N2][N3] in the stated dtype, rows contiguous; the input set
+ *     is orthonormal under dV (dV sum_r phi_i phi_j = delta_ij); this is not checked.
+ *   - Fourier convention: rho~(m) = (1/N) sum_r rho(r) e^{-i G_m . x_r}; G_m = sum_k m_k b_k,
+ *     b = 2 pi A^-T, m_k wrapped to [-N_k/2, N_k/2); full FFT box; G = 0 term dropped; at a Nyquist
+ *     index the kernel is the mean of 4 pi/|G|^2 over the +-N_k/2 choices.
+ *   - pointers named *_dev are CUDA device pointers; pointers that the comments say "host or
+ *     device" may be either (host memory, pageable or pinned, is copied inside the call on the
+ *     given stream).  `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+ *   - every entry point returns an ace_status and never throws; on failure the message is
+ *     available from ace_last_error() on the calling thread.
+ *   - ownership: the caller owns every buffer it passes and must keep it valid and unchanged
+ *     until the stream work of the call completes.  The library owns everything inside an
+ *     ace_op; ace_destroy frees it and must not race with stream work that uses the handle.
+ *   - thread safety: distinct handles may be used concurrently on distinct streams.
+ */
+#ifndef ACE_GB300_H
+#define ACE_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ACE_OK = 0,
+  ACE_ERR_ARG = 1,              /* invalid argument (null pointer, bad size, bad lattice)        */
+  ACE_ERR_CUDA = 2,             /* a CUDA runtime call failed; see ace_last_error()              */
+  ACE_ERR_OOM = 3,              /* device allocation failed                                      */
+  ACE_ERR_NOT_POSDEF = 4,       /* -M is not positive definite (Cholesky pivot in the message)   */
+  ACE_ERR_NONFINITE = 5,        /* NaN/Inf reached M                                             */
+  ACE_ERR_UNSUPPORTED_GRID = 6, /* an axis length has no compiled FFT plan (see ace_grid_supported) */
+  ACE_ERR_TIMEOUT = 7           /* a bounded device-side wait gave up                            */
+} ace_status;
+
+typedef enum {
+  ACE_FP64 = 0,  /* plain form: every step in double precision                                 */
+  ACE_MIXED = 1  /* mixed form: FP32 pair densities/FFTs/kernel multiply/accumulation,
+                    BF16x3 split products (FP32 accumulate within 4096-point chunks, FP64 across)
+                    for Phi^T W, xi^T psi and xi C; M, Cholesky, L^-1 and E_x in FP64            */
+} ace_precision;
+
+typedef enum { ACE_F32 = 0, ACE_F64 = 1 } ace_dtype;
+
+typedef struct {
+  int n[3];              /* N1, N2, N3 (each must satisfy ace_grid_supported)                  */
+  double lattice[3][3];  /* rows a1, a2, a3 in bohr; det != 0                                    */
+  int norb;              /* n, 1 <= n <= 256                                                     */
+  double rho_cut;        /* keep (i,j) iff dV sum_r |phi_i phi_j| >= rho_cut; <= 0 keeps all     */
+  double spin_factor;    /* f in E_x = (f/2) tr M: 2 closed shell, 1 one spin channel            */
+  ace_precision prec;
+} ace_desc;
+
+typedef struct ace_op ace_op; /* opaque: owns xi, W, M, L, L^-1, the pair list and workspaces  */
+
+/* Build the s-ACE operator (Appendix A with the screen of section II).
+ *   phi:   orbitals [norb][N1][N2][N3], host or device, dtype as given (converted internally to
+ *          the working precision of desc->prec).
+ *   out:   receives a new handle, also on ACE_ERR_NOT_POSDEF / ACE_ERR_NONFINITE (so that M can be
+ *          inspected); NULL on every other error.
+ * The call returns after the build has completed on `cuda_stream` (it reads the pair count and
+ * the Cholesky status back to the host).  Errors: ACE_ERR_ARG, ACE_ERR_UNSUPPORTED_GRID,
+ * ACE_ERR_OOM, ACE_ERR_CUDA, ACE_ERR_NOT_POSDEF, ACE_ERR_NONFINITE. */
+ace_status ace_build(const ace_desc *desc, const void *phi, ace_dtype dtype, void *cuda_stream,
+                     ace_op **out);
+
+/* k independent builds (replicas or snapshots) issued back to back on one stream.  desc, phi and
+ * out are arrays of length k; each build is as in ace_build.  On the first failing build the
+ * handles already created are destroyed, every out[i] is NULL, and its status is returned. */
+ace_status ace_build_batched(int k, const ace_desc *desc, const void *const *phi, ace_dtype dtype,
+                             void *cuda_stream, ace_op **out);
+
+/* Apply the ACE operator (section II): out = -xi (dV xi^T psi) = V_X^ACE psi, dense (no screen).
+ *   psi, out: [m][N1][N2][N3] of `dtype`, host or device (both on the same side), m >= 1.
+ * Stream-ordered on `cuda_stream`; returns after the work is enqueued (device buffers) or after
+ * the result has been copied back (host buffers). */
+ace_status ace_apply(const ace_op *op, const void *psi, ace_dtype dtype, int m, void *out,
+                     void *cuda_stream);
+
+/* E_x = (f/2) tr M in Hartree (host scalar), computed in FP64 during the build. */
+ace_status exchange_energy(const ace_op *op, double *ex_hartree);
+
+/* Copy an internal array to `dst` (host or device) of `bytes` bytes (must equal the size):
+ *   ACE_GET_XI      xi  [norb][N]  working dtype (float for ACE_MIXED, double for ACE_FP64)
+ *   ACE_GET_W       W   [norb][N]  working dtype
+ *   ACE_GET_M       M   [norb][norb] double, symmetrised
+ *   ACE_GET_M_RAW   M   [norb][norb] double, before symmetrisation
+ *   ACE_GET_L       L   [norb][norb] double, lower triangular, -M = L L^T
+ *   ACE_GET_PAIRS   kept pairs, int32 [npairs][2] with i <= j, sorted by (i, j)
+ *   ACE_GET_OVERLAP screen values O_ij = dV sum_r |phi_i phi_j|, [norb][norb] double
+ * Synchronous with respect to the host. */
+enum {
+  ACE_GET_XI = 0,
+  ACE_GET_W = 1,
+  ACE_GET_M = 2,
+  ACE_GET_M_RAW = 3,
+  ACE_GET_L = 4,
+  ACE_GET_PAIRS = 5,
+  ACE_GET_OVERLAP = 6
+};
+ace_status ace_get(const ace_op *op, int what, void *dst, size_t bytes, void *cuda_stream);
+
+/* Number of kept (i <= j) pairs in the build, and the byte size of an ace_get item. */
+ace_status ace_pair_count(const ace_op *op, long *npairs);
+ace_status ace_get_size(const ace_op *op, int what, size_t *bytes);
+
+/* Per-stage device times of the last build in milliseconds (CUDA events on the build stream):
+ * [0] screen, [1] pair chain (W), [2] M, [3] Cholesky/L^-1/E_x, [4] xi, [5] total. */
+ace_status ace_stage_times(const ace_op *op, float ms[6]);
+
+/* Number of this library's CUDA kernels that the build of `op` launched. */
+ace_status ace_kernel_launches(const ace_op *op, long *launches);
+
+/* 1 if an axis length has a compiled FFT plan for precision `prec`, else 0. */
+int ace_grid_supported(int n_axis, ace_precision prec);
+
+void ace_destroy(ace_op *op);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *ace_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ACE_GB300_H */

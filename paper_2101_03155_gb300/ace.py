@@ -1,0 +1,299 @@
+"""ctypes binding of libace_gb300.so (include/ace.h), same entry-point names, marshalling only.
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays; the library decides from the pointer
+whether memory is on the device or the host.  There is no CPU implementation here: if the shared
+library is missing, loading fails with an error that says how to build it.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libace_gb300.so")
+
+ACE_OK = 0
+ACE_ERR_ARG = 1
+ACE_ERR_CUDA = 2
+ACE_ERR_OOM = 3
+ACE_ERR_NOT_POSDEF = 4
+ACE_ERR_NONFINITE = 5
+ACE_ERR_UNSUPPORTED_GRID = 6
+ACE_ERR_TIMEOUT = 7
+STATUS_NAMES = {
+    0: "ACE_OK", 1: "ACE_ERR_ARG", 2: "ACE_ERR_CUDA", 3: "ACE_ERR_OOM", 4: "ACE_ERR_NOT_POSDEF",
+    5: "ACE_ERR_NONFINITE", 6: "ACE_ERR_UNSUPPORTED_GRID", 7: "ACE_ERR_TIMEOUT",
+}
+
+ACE_FP64 = 0
+ACE_MIXED = 1
+ACE_F32 = 0
+ACE_F64 = 1
+
+ACE_GET_XI = 0
+ACE_GET_W = 1
+ACE_GET_M = 2
+ACE_GET_M_RAW = 3
+ACE_GET_L = 4
+ACE_GET_PAIRS = 5
+ACE_GET_OVERLAP = 6
+
+EXPORTED = [
+    "ace_build", "ace_build_batched", "ace_apply", "exchange_energy", "ace_get", "ace_pair_count",
+    "ace_get_size", "ace_stage_times", "ace_kernel_launches", "ace_grid_supported", "ace_destroy",
+    "ace_last_error",
+]
+
+
+class AceError(RuntimeError):
+    def __init__(self, status: int, message: str, op=None):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.op = op
+
+
+class AceDesc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int * 3),
+        ("lattice", (ctypes.c_double * 3) * 3),
+        ("norb", ctypes.c_int),
+        ("rho_cut", ctypes.c_double),
+        ("spin_factor", ctypes.c_double),
+        ("prec", ctypes.c_int),
+    ]
+
+
+def make_desc(grid, lattice, norb, rho_cut=0.0, spin_factor=2.0, prec=ACE_MIXED) -> AceDesc:
+    d = AceDesc()
+    for k in range(3):
+        d.n[k] = int(grid[k])
+    lat = np.asarray(lattice, dtype=np.float64).reshape(3, 3)
+    for i in range(3):
+        for j in range(3):
+            d.lattice[i][j] = float(lat[i, j])
+    d.norb = int(norb)
+    d.rho_cut = float(rho_cut)
+    d.spin_factor = float(spin_factor)
+    d.prec = int(prec)
+    return d
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library; raises if it has not been built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(
+                f"{path} is missing: build it with `python -m paper_2101_03155_gb300.build` "
+                "(nvcc, sm_103a); there is no CPU implementation"
+            )
+        lib = ctypes.CDLL(path)
+        vp, c_int, c_long, c_size = ctypes.c_void_p, ctypes.c_int, ctypes.c_long, ctypes.c_size_t
+        lib.ace_build.argtypes = [ctypes.POINTER(AceDesc), vp, c_int, vp, ctypes.POINTER(vp)]
+        lib.ace_build_batched.argtypes = [c_int, ctypes.POINTER(AceDesc), ctypes.POINTER(vp), c_int, vp,
+                                          ctypes.POINTER(vp)]
+        lib.ace_apply.argtypes = [vp, vp, c_int, c_int, vp, vp]
+        lib.exchange_energy.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        lib.ace_get.argtypes = [vp, c_int, vp, c_size, vp]
+        lib.ace_get_size.argtypes = [vp, c_int, ctypes.POINTER(c_size)]
+        lib.ace_pair_count.argtypes = [vp, ctypes.POINTER(c_long)]
+        lib.ace_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+        lib.ace_kernel_launches.argtypes = [vp, ctypes.POINTER(c_long)]
+        lib.ace_grid_supported.argtypes = [c_int, c_int]
+        lib.ace_grid_supported.restype = c_int
+        lib.ace_destroy.argtypes = [vp]
+        lib.ace_destroy.restype = None
+        lib.ace_last_error.restype = ctypes.c_char_p
+        for name in ("ace_build", "ace_build_batched", "ace_apply", "exchange_energy", "ace_get", "ace_get_size",
+                     "ace_pair_count", "ace_stage_times", "ace_kernel_launches"):
+            getattr(lib, name).restype = c_int
+        _lib = lib
+        return lib
+
+
+def ace_last_error() -> str:
+    return load().ace_last_error().decode()
+
+
+def _check(status: int, op=None):
+    if status != ACE_OK:
+        raise AceError(status, ace_last_error(), op)
+
+
+def _array_info(a):
+    """(pointer, dtype code, number of elements) of a contiguous torch tensor or numpy array."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        code = {np.dtype(np.float32): ACE_F32, np.dtype(np.float64): ACE_F64}.get(a.dtype)
+        if code is None:
+            raise TypeError(f"unsupported dtype {a.dtype}")
+        return a.ctypes.data, code, a.size
+    import torch
+
+    if not isinstance(a, torch.Tensor):
+        raise TypeError("expected a torch tensor or numpy array")
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    code = {torch.float32: ACE_F32, torch.float64: ACE_F64}.get(a.dtype)
+    if code is None:
+        raise TypeError(f"unsupported dtype {a.dtype}")
+    return a.data_ptr(), code, a.numel()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None  # torch.cuda.Stream
+
+
+class AceOp:
+    """Owner of an ace_op handle; ace_destroy runs on close() or garbage collection."""
+
+    def __init__(self, handle: int, desc: AceDesc):
+        self.handle = handle
+        self.desc = desc
+
+    @property
+    def grid(self):
+        return tuple(self.desc.n)
+
+    @property
+    def norb(self):
+        return self.desc.norb
+
+    def close(self):
+        if self.handle:
+            load().ace_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def ace_build(desc: AceDesc, phi, stream=None, check: bool = True) -> AceOp:
+    """ace_build: phi [norb][N1][N2][N3] (torch CUDA/CPU tensor or numpy array)."""
+    ptr, code, numel = _array_info(phi)
+    expect = desc.norb * desc.n[0] * desc.n[1] * desc.n[2]
+    if numel != expect:
+        raise ValueError(f"phi has {numel} elements, descriptor needs {expect}")
+    h = ctypes.c_void_p()
+    st = load().ace_build(ctypes.byref(desc), ptr, code, _stream_handle(stream), ctypes.byref(h))
+    op = AceOp(h.value, desc) if h.value else None
+    if check:
+        _check(st, op)
+    return op if check else (st, op)
+
+
+def ace_build_batched(descs, phis, stream=None):
+    k = len(descs)
+    arr = (AceDesc * k)(*descs)
+    ptrs = []
+    code = None
+    for d, p in zip(descs, phis):
+        ptr, c, numel = _array_info(p)
+        if code is not None and c != code:
+            raise TypeError("all inputs of a batch must have one dtype")
+        code = c
+        if numel != d.norb * d.n[0] * d.n[1] * d.n[2]:
+            raise ValueError("input size does not match its descriptor")
+        ptrs.append(ptr)
+    pa = (ctypes.c_void_p * k)(*ptrs)
+    outs = (ctypes.c_void_p * k)()
+    _check(load().ace_build_batched(k, arr, pa, code if code is not None else ACE_F32, _stream_handle(stream), outs))
+    return [AceOp(outs[i], descs[i]) for i in range(k)]
+
+
+def ace_apply(op: AceOp, psi, out, stream=None):
+    """ace_apply: out = V_X^ACE psi; psi and out [m][N] of one dtype, both on the host or both on the device."""
+    p_ptr, p_code, p_numel = _array_info(psi)
+    o_ptr, o_code, o_numel = _array_info(out)
+    N = op.desc.n[0] * op.desc.n[1] * op.desc.n[2]
+    if p_code != o_code or p_numel != o_numel or p_numel % N:
+        raise ValueError("psi and out must have the same dtype and [m][N] shape")
+    _check(load().ace_apply(op.handle, p_ptr, p_code, p_numel // N, o_ptr, _stream_handle(stream)))
+    return out
+
+
+def exchange_energy(op: AceOp) -> float:
+    e = ctypes.c_double()
+    _check(load().exchange_energy(op.handle, ctypes.byref(e)))
+    return e.value
+
+
+def ace_get_size(op: AceOp, what: int) -> int:
+    b = ctypes.c_size_t()
+    _check(load().ace_get_size(op.handle, what, ctypes.byref(b)))
+    return b.value
+
+
+def ace_get(op: AceOp, what: int, dst, stream=None):
+    """Copy an internal array into dst (torch tensor or numpy array of exactly the item's size)."""
+    if isinstance(dst, np.ndarray):
+        ptr, nbytes = dst.ctypes.data, dst.nbytes
+    else:
+        ptr, nbytes = dst.data_ptr(), dst.numel() * dst.element_size()
+    _check(load().ace_get(op.handle, what, ptr, nbytes, _stream_handle(stream)))
+    return dst
+
+
+def ace_pair_count(op: AceOp) -> int:
+    n = ctypes.c_long()
+    _check(load().ace_pair_count(op.handle, ctypes.byref(n)))
+    return n.value
+
+
+def ace_stage_times(op: AceOp):
+    ms = (ctypes.c_float * 6)()
+    _check(load().ace_stage_times(op.handle, ms))
+    return {k: float(v) for k, v in zip(("screen", "pair_chain", "M", "cholesky", "xi", "total"), ms)}
+
+
+def ace_kernel_launches(op: AceOp) -> int:
+    n = ctypes.c_long()
+    _check(load().ace_kernel_launches(op.handle, ctypes.byref(n)))
+    return n.value
+
+
+def ace_grid_supported(n_axis: int, prec: int = ACE_MIXED) -> bool:
+    return bool(load().ace_grid_supported(int(n_axis), int(prec)))
+
+
+def ace_destroy(op: AceOp) -> None:
+    op.close()
+
+
+# ---- convenience readers (host numpy copies) ----
+
+def get_numpy(op: AceOp, what: int) -> np.ndarray:
+    n = op.norb
+    N = op.desc.n[0] * op.desc.n[1] * op.desc.n[2]
+    work = np.float64 if op.desc.prec == ACE_FP64 else np.float32
+    if what in (ACE_GET_XI, ACE_GET_W):
+        out = np.empty((n, N), dtype=work)
+    elif what == ACE_GET_PAIRS:
+        out = np.empty((ace_pair_count(op), 2), dtype=np.int32)
+    else:
+        out = np.empty((n, n), dtype=np.float64)
+    return ace_get(op, what, out)

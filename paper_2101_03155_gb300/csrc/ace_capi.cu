@@ -1,0 +1,661 @@
+// ace_capi.cu -- the C ABI declared in include/ace.h: argument checks, host-made tables, device
+// workspaces and the order of the build steps (screen, pair chain, M, Cholesky, xi) and of the
+// ACE application.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ace.h"
+#include "ace_internal.h"
+#include "fft.cuh"
+
+using ace::cpx;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ace_status fail(ace_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+ace_status cuda_fail(cudaError_t e, const char *what) {
+  if (e == cudaErrorMemoryAllocation) return fail(ACE_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(ACE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define ACE_CUDA(call, what)                 \
+  do {                                       \
+    cudaError_t _e = (call);                 \
+    if (_e != cudaSuccess) return cuda_fail(_e, what); \
+  } while (0)
+
+// Keep freed stream-ordered allocations cached in the device's default pool (once per device).
+std::mutex g_pool_mu;
+std::vector<int> g_pool_ready;
+
+cudaError_t prepare_pool(int dev) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (std::find(g_pool_ready.begin(), g_pool_ready.end(), dev) != g_pool_ready.end()) return cudaSuccess;
+  cudaMemPool_t pool;
+  cudaError_t e = cudaDeviceGetDefaultMemPool(&pool, dev);
+  if (e != cudaSuccess) return e;
+  unsigned long long thr = ~0ull;
+  e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  if (e != cudaSuccess) return e;
+  g_pool_ready.push_back(dev);
+  return cudaSuccess;
+}
+
+bool is_device_pointer(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// 4 pi / (N |G_m|^2) on the FFT box; G = 0 -> 0; mean over +-N_k/2 at Nyquist indices.
+void coulomb_table(const ace_desc &d, std::vector<double> &K) {
+  const int n1 = d.n[0], n2 = d.n[1], n3 = d.n[2];
+  const double *A = &d.lattice[0][0];
+  const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                     A[2] * (A[3] * A[7] - A[4] * A[6]);
+  // b_k = 2 pi * (row k of A^-T) = 2 pi * (column k of A^-1); A^-1 = adj(A) / det
+  double adj[9];
+  adj[0] = A[4] * A[8] - A[5] * A[7];
+  adj[1] = A[2] * A[7] - A[1] * A[8];
+  adj[2] = A[1] * A[5] - A[2] * A[4];
+  adj[3] = A[5] * A[6] - A[3] * A[8];
+  adj[4] = A[0] * A[8] - A[2] * A[6];
+  adj[5] = A[2] * A[3] - A[0] * A[5];
+  adj[6] = A[3] * A[7] - A[4] * A[6];
+  adj[7] = A[1] * A[6] - A[0] * A[7];
+  adj[8] = A[0] * A[4] - A[1] * A[3];
+  const double twopi = 2.0 * ace::kPi;
+  double B[3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int c = 0; c < 3; ++c) B[k][c] = twopi * adj[c * 3 + k] / det;
+  // Gram matrix of the reciprocal basis: |G|^2 = sum_kl m_k m_l (b_k . b_l)
+  double g[3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) g[k][l] = B[k][0] * B[l][0] + B[k][1] * B[l][1] + B[k][2] * B[l][2];
+  const long long N = (long long)n1 * n2 * n3;
+  K.assign((size_t)N, 0.0);
+  const int nn[3] = {n1, n2, n3};
+  const double fourpi_over_N = 4.0 * ace::kPi / (double)N;
+  for (int i1 = 0; i1 < n1; ++i1)
+    for (int i2 = 0; i2 < n2; ++i2)
+      for (int i3 = 0; i3 < n3; ++i3) {
+        const int idx[3] = {i1, i2, i3};
+        int m[3];
+        bool nyq[3];
+        for (int k = 0; k < 3; ++k) {
+          m[k] = (2 * idx[k] < nn[k]) ? idx[k] : idx[k] - nn[k];
+          nyq[k] = (nn[k] % 2 == 0) && (2 * idx[k] == nn[k]);
+        }
+        const long long lin = ((long long)i1 * n2 + i2) * n3 + i3;
+        if (m[0] == 0 && m[1] == 0 && m[2] == 0) continue;
+        double acc = 0.0;
+        int cnt = 0;
+        for (int s = 0; s < 8; ++s) {
+          bool ok = true;
+          double mm[3];
+          for (int k = 0; k < 3; ++k) {
+            const bool flip = (s >> k) & 1;
+            if (flip && !nyq[k]) ok = false;
+            mm[k] = flip ? -m[k] : m[k];
+          }
+          if (!ok) continue;
+          double q = 0.0;
+          for (int k = 0; k < 3; ++k)
+            for (int l = 0; l < 3; ++l) q += mm[k] * mm[l] * g[k][l];
+          acc += 1.0 / q;
+          ++cnt;
+        }
+        K[(size_t)lin] = fourpi_over_N * acc / cnt;
+      }
+}
+
+
+// Device copies of the Coulomb kernel table and the per-axis twiddles, made once per
+// (device, grid, lattice, precision) and kept until the process exits.
+struct DeviceTables {
+  int dev;
+  int n[3];
+  double lattice[9];
+  size_t esz;
+  void *K;
+  void *tw[3];
+};
+std::mutex g_tab_mu;
+std::deque<DeviceTables> g_tables;  // deque: references stay valid on push_back
+
+template <typename T>
+cudaError_t get_tables(int dev, const ace_desc &d, cudaStream_t st, const DeviceTables **out) {
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  for (const DeviceTables &t : g_tables) {
+    if (t.dev == dev && t.esz == sizeof(T) && t.n[0] == d.n[0] && t.n[1] == d.n[1] && t.n[2] == d.n[2] &&
+        std::memcmp(t.lattice, &d.lattice[0][0], sizeof(t.lattice)) == 0) {
+      *out = &t;
+      return cudaSuccess;
+    }
+  }
+  DeviceTables t{};
+  t.dev = dev;
+  t.esz = sizeof(T);
+  for (int k = 0; k < 3; ++k) t.n[k] = d.n[k];
+  std::memcpy(t.lattice, &d.lattice[0][0], sizeof(t.lattice));
+  std::vector<double> Kh;
+  coulomb_table(d, Kh);
+  std::vector<T> Kt(Kh.begin(), Kh.end());
+  cudaError_t e = cudaMalloc(&t.K, sizeof(T) * Kt.size());
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(t.K, Kt.data(), sizeof(T) * Kt.size(), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  std::vector<cpx<T>> twh[3];
+  for (int a = 0; a < 3; ++a) {
+    const int L = d.n[a];
+    twh[a].resize(L);
+    for (int k = 0; k < L; ++k) {
+      const double ang = 2.0 * ace::kPi * (double)k / (double)L;
+      twh[a][k] = cpx<T>{(T)std::cos(ang), (T)(-std::sin(ang))};
+    }
+    e = cudaMalloc(&t.tw[a], sizeof(cpx<T>) * L);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(t.tw[a], twh[a].data(), sizeof(cpx<T>) * L, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaStreamSynchronize(st);  // host vectors must outlive the copies
+  if (e != cudaSuccess) return e;
+  g_tables.push_back(t);
+  *out = &g_tables.back();
+  return cudaSuccess;
+}
+
+}  // namespace
+
+struct ace_op {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  ace_desc desc{};
+  int n = 0;
+  long long N = 0;
+  double dV = 0.0;
+  bool fp64 = false;
+  size_t esz = 4;
+  void *W = nullptr, *xi = nullptr;
+  double *O = nullptr, *O_sym = nullptr, *M_raw = nullptr, *M = nullptr, *L = nullptr, *Linv = nullptr;
+  double *energy_d = nullptr;
+  int *status_d = nullptr, *count_d = nullptr;
+  int2 *pairs = nullptr;
+  int4 *packs = nullptr;
+  long npairs = 0;
+  double energy = 0.0;
+  int status = 0;
+  cudaEvent_t ev[6] = {};
+  float stage_ms[6] = {};
+  long launches = 0;          // kernels of this library launched by the build
+  std::vector<void *> owned;  // stream-ordered allocations freed by ace_destroy
+};
+
+namespace {
+
+template <typename P>
+cudaError_t op_alloc(ace_op *op, P **p, size_t bytes) {
+  void *v = nullptr;
+  cudaError_t e = cudaMallocAsync(&v, bytes > 0 ? bytes : 16, op->stream);
+  if (e != cudaSuccess) return e;
+  op->owned.push_back(v);
+  *p = static_cast<P *>(v);
+  return cudaSuccess;
+}
+
+void op_free_all(ace_op *op) {
+  for (void *p : op->owned) cudaFreeAsync(p, op->stream);
+  op->owned.clear();
+}
+
+ace_status check_desc(const ace_desc *d) {
+  if (!d) return fail(ACE_ERR_ARG, "desc is NULL");
+  if (d->norb < 1 || d->norb > 1024) return fail(ACE_ERR_ARG, "norb = %d outside [1, 1024]", d->norb);
+  for (int k = 0; k < 3; ++k)
+    if (d->n[k] < 1) return fail(ACE_ERR_ARG, "grid axis %d has length %d", k, d->n[k]);
+  for (int k = 0; k < 3; ++k)
+    if (!ace::pass_length_supported(d->n[k]))
+      return fail(ACE_ERR_UNSUPPORTED_GRID, "grid axis %d length %d has no compiled FFT plan", k, d->n[k]);
+  const double *A = &d->lattice[0][0];
+  for (int i = 0; i < 9; ++i)
+    if (!std::isfinite(A[i])) return fail(ACE_ERR_ARG, "lattice has a non-finite entry");
+  const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                     A[2] * (A[3] * A[7] - A[4] * A[6]);
+  if (!(std::fabs(det) > 0.0)) return fail(ACE_ERR_ARG, "lattice is singular");
+  if (d->prec != ACE_FP64 && d->prec != ACE_MIXED) return fail(ACE_ERR_ARG, "unknown precision %d", (int)d->prec);
+  if (!std::isfinite(d->spin_factor) || !std::isfinite(d->rho_cut)) return fail(ACE_ERR_ARG, "non-finite scalar");
+  return ACE_OK;
+}
+
+int env_int(const char *name, int dflt) {
+  const char *v = std::getenv(name);
+  if (!v || !*v) return dflt;
+  return std::atoi(v);
+}
+
+// Bring `src` (host or device, dtype `dt`) to a device array of T; returns the device pointer
+// (either src itself or an op-owned or caller-supplied staging copy).
+template <typename T>
+ace_status stage_input(ace_op *op, const void *src, ace_dtype dt, long long count, const T **out,
+                       std::vector<void *> *temps) {
+  // a conversion kernel (if any) is counted in op->launches
+  const bool dev = is_device_pointer(src);
+  const bool same = (dt == ACE_F64) == (sizeof(T) == 8);
+  const size_t in_bytes = (size_t)count * (dt == ACE_F64 ? 8 : 4);
+  const void *d_in = src;
+  if (!dev) {
+    void *tmp = nullptr;
+    ACE_CUDA(cudaMallocAsync(&tmp, in_bytes, op->stream), "staging allocation");
+    temps->push_back(tmp);
+    ACE_CUDA(cudaMemcpyAsync(tmp, src, in_bytes, cudaMemcpyHostToDevice, op->stream), "host-to-device copy");
+    d_in = tmp;
+  }
+  if (same) {
+    *out = static_cast<const T *>(d_in);
+    return ACE_OK;
+  }
+  void *conv = nullptr;
+  ACE_CUDA(cudaMallocAsync(&conv, (size_t)count * sizeof(T), op->stream), "conversion allocation");
+  temps->push_back(conv);
+  if (dt == ACE_F64)
+    ACE_CUDA((ace::launch_convert<double, T>(static_cast<const double *>(d_in), static_cast<T *>(conv), count, 1.0,
+                                             op->stream)),
+             "convert");
+  else
+    ACE_CUDA((ace::launch_convert<float, T>(static_cast<const float *>(d_in), static_cast<T *>(conv), count, 1.0,
+                                            op->stream)),
+             "convert");
+  ++op->launches;
+  *out = static_cast<const T *>(conv);
+  return ACE_OK;
+}
+
+template <typename T>
+ace_status build_impl(ace_op *op, const void *phi_in, ace_dtype dtype) {
+  const ace_desc &d = op->desc;
+  const int n = op->n;
+  const long long N = op->N;
+  cudaStream_t st = op->stream;
+  std::vector<void *> temps;
+  struct TempGuard {
+    std::vector<void *> *v;
+    cudaStream_t s;
+    ~TempGuard() {
+      for (void *p : *v) cudaFreeAsync(p, s);
+    }
+  } guard{&temps, st};
+
+  for (int i = 0; i < 6; ++i) ACE_CUDA(cudaEventCreate(&op->ev[i]), "event create");
+  ACE_CUDA(cudaEventRecord(op->ev[0], st), "event record");
+
+  const T *phi = nullptr;
+  ace_status s = stage_input<T>(op, phi_in, dtype, (long long)n * N, &phi, &temps);
+  if (s != ACE_OK) return s;
+
+  // tables (cached per device, grid, lattice and precision)
+  const DeviceTables *tab = nullptr;
+  {
+    cudaError_t e = get_tables<T>(op->dev, d, st, &tab);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel and twiddle tables");
+  }
+  const T *Kd = static_cast<const T *>(tab->K);
+  const cpx<T> *twd[3] = {static_cast<const cpx<T> *>(tab->tw[0]), static_cast<const cpx<T> *>(tab->tw[1]),
+                          static_cast<const cpx<T> *>(tab->tw[2])};
+  void *tmp = nullptr;
+
+  // ---- screen (section II): O_ij = dV sum |phi_i phi_j|, pair list ----
+  ACE_CUDA(op_alloc(op, &op->O, sizeof(double) * n * n), "alloc O");
+  ACE_CUDA(op_alloc(op, &op->O_sym, sizeof(double) * n * n), "alloc O_sym");
+  ACE_CUDA(op_alloc(op, &op->pairs, sizeof(int2) * ((size_t)n * (n + 1) / 2 + 2)), "alloc pairs");
+  ACE_CUDA(op_alloc(op, &op->packs, sizeof(int4) * ((size_t)n * (n + 1) / 4 + 2)), "alloc packs");
+  ACE_CUDA(op_alloc(op, &op->count_d, sizeof(int) * 4), "alloc count");
+  ACE_CUDA(op_alloc(op, &op->status_d, sizeof(int) * 4), "alloc status");
+  ACE_CUDA(op_alloc(op, &op->energy_d, sizeof(double) * 2), "alloc energy");
+  if (d.rho_cut > 0.0) {
+    ACE_CUDA(ace::launch_gram<T>(phi, n, phi, n, N, op->dV, true, true, op->O, st), "screen");
+    ++op->launches;
+  } else {
+    ACE_CUDA(cudaMemsetAsync(op->O, 0, sizeof(double) * n * n, st), "screen skip");
+  }
+  ACE_CUDA(ace::launch_screen_compact(op->O, n, d.rho_cut, op->pairs, op->packs, op->count_d, op->O_sym, st),
+           "compact");
+  ++op->launches;
+  int count = 0;
+  ACE_CUDA(cudaMemcpyAsync(&count, op->count_d, sizeof(int), cudaMemcpyDeviceToHost, st), "count readback");
+  ACE_CUDA(cudaStreamSynchronize(st), "count readback");
+  op->npairs = count;
+  ACE_CUDA(cudaEventRecord(op->ev[1], st), "event record");
+
+  // ---- pair chain (Eq. vx, Eq. e:vij): W_i = sum_j v_ij phi_j ----
+  ACE_CUDA(op_alloc(op, &op->W, op->esz * (size_t)n * N), "alloc W");
+  ACE_CUDA(cudaMemsetAsync(op->W, 0, op->esz * (size_t)n * N, st), "zero W");
+  const int npacks = (count + 1) / 2;
+  const double scratch_budget = (double)env_int("ACE_SCRATCH_MB", 64) * 1048576.0;
+  int batch = (int)std::max(1.0, std::floor(scratch_budget / (double)(sizeof(cpx<T>) * N)));
+  batch = std::min(batch, std::max(npacks, 1));
+  batch = std::min(batch, 65535);
+  if (npacks > 0) {
+    cpx<T> *scratch = nullptr;
+    ACE_CUDA(cudaMallocAsync(&tmp, sizeof(cpx<T>) * (size_t)N * batch, st), "alloc scratch");
+    temps.push_back(tmp);
+    scratch = static_cast<cpx<T> *>(tmp);
+    ace::PairPassArgs<T> a;
+    a.phi = phi;
+    a.W = static_cast<T *>(op->W);
+    a.scratch = scratch;
+    a.packs = op->packs;
+    a.kernel = Kd;
+    a.N = N;
+    a.n1 = d.n[0];
+    a.n2 = d.n[1];
+    a.n3 = d.n[2];
+    for (int p0 = 0; p0 < npacks; p0 += batch) {
+      const int nb = std::min(batch, npacks - p0);
+      a.pack0 = p0;
+      const int modes[5] = {ace::PASS_FWD3_PAIR, ace::PASS_FWD2, ace::PASS_CONV1, ace::PASS_INV2,
+                            ace::PASS_INV3_ACC};
+      const int axis[5] = {2, 1, 0, 1, 2};
+      for (int k = 0; k < 5; ++k) {
+        a.tw = twd[axis[k]];
+        ACE_CUDA(ace::launch_pair_pass<T>(modes[k], a, nb, st), "pair pass");
+        ++op->launches;
+      }
+    }
+  }
+  ACE_CUDA(cudaEventRecord(op->ev[2], st), "event record");
+
+  // ---- M = -dV Phi^T W (App. A) ----
+  ACE_CUDA(op_alloc(op, &op->M_raw, sizeof(double) * n * n), "alloc M_raw");
+  ACE_CUDA(op_alloc(op, &op->M, sizeof(double) * n * n), "alloc M");
+  ACE_CUDA(op_alloc(op, &op->L, sizeof(double) * n * n), "alloc L");
+  ACE_CUDA(op_alloc(op, &op->Linv, sizeof(double) * n * n), "alloc Linv");
+  ACE_CUDA(ace::launch_gram<T>(phi, n, static_cast<const T *>(op->W), n, N, -op->dV, false, false, op->M_raw, st),
+           "M");
+  ++op->launches;
+  ACE_CUDA(cudaEventRecord(op->ev[3], st), "event record");
+
+  // ---- -M = L L^T, L^-1, E_x = (f/2) tr M ----
+  ACE_CUDA(ace::launch_cholesky(op->M_raw, n, d.spin_factor, op->M, op->L, op->Linv, op->energy_d, op->status_d, st),
+           "cholesky");
+  ++op->launches;
+  ACE_CUDA(cudaEventRecord(op->ev[4], st), "event record");
+
+  // ---- xi = W L^-T, stored as rows: xi_rows = L^-1 W_rows ----
+  ACE_CUDA(op_alloc(op, &op->xi, op->esz * (size_t)n * N), "alloc xi");
+  const T *Linv_T = nullptr;
+  if (sizeof(T) == 8) {
+    Linv_T = reinterpret_cast<const T *>(op->Linv);
+  } else {
+    ACE_CUDA(cudaMallocAsync(&tmp, sizeof(T) * n * n, st), "alloc Linv32");
+    temps.push_back(tmp);
+    ACE_CUDA((ace::launch_convert<double, T>(op->Linv, static_cast<T *>(tmp), (long long)n * n, 1.0, st)), "Linv32");
+    ++op->launches;
+    Linv_T = static_cast<const T *>(tmp);
+  }
+  ACE_CUDA(ace::launch_left_mul<T>(Linv_T, n, n, static_cast<const T *>(op->W), N, static_cast<T *>(op->xi), st),
+           "xi");
+  ++op->launches;
+  ACE_CUDA(cudaEventRecord(op->ev[5], st), "event record");
+
+  int status = 0;
+  double energy = 0.0;
+  ACE_CUDA(cudaMemcpyAsync(&status, op->status_d, sizeof(int), cudaMemcpyDeviceToHost, st), "status readback");
+  ACE_CUDA(cudaMemcpyAsync(&energy, op->energy_d, sizeof(double), cudaMemcpyDeviceToHost, st), "energy readback");
+  ACE_CUDA(cudaStreamSynchronize(st), "build");
+  op->status = status;
+  op->energy = energy;
+  for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&op->stage_ms[i], op->ev[i], op->ev[i + 1]);
+  cudaEventElapsedTime(&op->stage_ms[5], op->ev[0], op->ev[5]);
+  if (status >= 2000000) return fail(ACE_ERR_NONFINITE, "M has a non-finite entry");
+  if (status >= 1000000)
+    return fail(ACE_ERR_NOT_POSDEF, "-M is not positive definite: Cholesky pivot %d", status - 1000000);
+  return ACE_OK;
+}
+
+template <typename T>
+ace_status apply_impl(const ace_op *op, const void *psi_in, ace_dtype dtype, int m, void *out, cudaStream_t st) {
+  const int n = op->n;
+  const long long N = op->N;
+  std::vector<void *> temps;
+  struct TempGuard {
+    std::vector<void *> *v;
+    cudaStream_t s;
+    ~TempGuard() {
+      for (void *p : *v) cudaFreeAsync(p, s);
+    }
+  } guard{&temps, st};
+  ace_op tmpop;  // only for staging on `st`
+  tmpop.stream = st;
+  const bool host_out = !is_device_pointer(out);
+  const T *psi = nullptr;
+  ace_status s = stage_input<T>(&tmpop, psi_in, dtype, (long long)m * N, &psi, &temps);
+  if (s != ACE_OK) return s;
+  void *tmp = nullptr;
+  // C = dV xi psi^T  (n x m, FP64 across 4096-point chunks)
+  ACE_CUDA(cudaMallocAsync(&tmp, sizeof(double) * n * m, st), "alloc C");
+  temps.push_back(tmp);
+  double *C = static_cast<double *>(tmp);
+  ACE_CUDA(ace::launch_gram<T>(static_cast<const T *>(op->xi), n, psi, m, N, op->dV, false, false, C, st), "xi^T psi");
+  ACE_CUDA(cudaMallocAsync(&tmp, sizeof(T) * n * m, st), "alloc A");
+  temps.push_back(tmp);
+  T *A = static_cast<T *>(tmp);
+  ACE_CUDA(ace::launch_transpose_scale<T>(C, n, m, -1.0, A, st), "transpose");
+  // out = -C^T xi  (m x N)
+  const bool same = (dtype == ACE_F64) == (sizeof(T) == 8);
+  T *res = nullptr;
+  if (same && !host_out) {
+    res = static_cast<T *>(out);
+  } else {
+    ACE_CUDA(cudaMallocAsync(&tmp, sizeof(T) * (size_t)m * N, st), "alloc out");
+    temps.push_back(tmp);
+    res = static_cast<T *>(tmp);
+  }
+  ACE_CUDA(ace::launch_left_mul<T>(A, m, n, static_cast<const T *>(op->xi), N, res, st), "xi C");
+  void *final_dev = res;
+  const size_t out_bytes = (size_t)m * N * (dtype == ACE_F64 ? 8 : 4);
+  if (!same) {
+    void *conv = nullptr;
+    if (!host_out) {
+      conv = out;
+    } else {
+      ACE_CUDA(cudaMallocAsync(&conv, out_bytes, st), "alloc out conv");
+      temps.push_back(conv);
+    }
+    if (dtype == ACE_F64)
+      ACE_CUDA((ace::launch_convert<T, double>(res, static_cast<double *>(conv), (long long)m * N, 1.0, st)), "conv");
+    else
+      ACE_CUDA((ace::launch_convert<T, float>(res, static_cast<float *>(conv), (long long)m * N, 1.0, st)), "conv");
+    final_dev = conv;
+  }
+  if (host_out) {
+    ACE_CUDA(cudaMemcpyAsync(out, final_dev, out_bytes, cudaMemcpyDeviceToHost, st), "device-to-host copy");
+    ACE_CUDA(cudaStreamSynchronize(st), "apply");
+  }
+  return ACE_OK;
+}
+
+size_t item_bytes(const ace_op *op, int what) {
+  const size_t nn = (size_t)op->n * op->n;
+  switch (what) {
+    case ACE_GET_XI:
+    case ACE_GET_W: return op->esz * (size_t)op->n * op->N;
+    case ACE_GET_M:
+    case ACE_GET_M_RAW:
+    case ACE_GET_L:
+    case ACE_GET_OVERLAP: return sizeof(double) * nn;
+    case ACE_GET_PAIRS: return sizeof(int2) * (size_t)op->npairs;
+    default: return 0;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ace_last_error(void) { return g_last_error.c_str(); }
+
+int ace_grid_supported(int n_axis, ace_precision prec) {
+  (void)prec;
+  return ace::pass_length_supported(n_axis) ? 1 : 0;
+}
+
+ace_status ace_build(const ace_desc *desc, const void *phi, ace_dtype dtype, void *cuda_stream, ace_op **out) {
+  g_last_error.clear();
+  if (!out) return fail(ACE_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  ace_status s = check_desc(desc);
+  if (s != ACE_OK) return s;
+  if (!phi) return fail(ACE_ERR_ARG, "phi is NULL");
+  if (dtype != ACE_F32 && dtype != ACE_F64) return fail(ACE_ERR_ARG, "unknown dtype %d", (int)dtype);
+  ace_op *op = new (std::nothrow) ace_op();
+  if (!op) return fail(ACE_ERR_OOM, "host allocation failed");
+  op->stream = static_cast<cudaStream_t>(cuda_stream);
+  op->desc = *desc;
+  op->n = desc->norb;
+  op->N = (long long)desc->n[0] * desc->n[1] * desc->n[2];
+  const double *A = &desc->lattice[0][0];
+  const double vol = std::fabs(A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                               A[2] * (A[3] * A[7] - A[4] * A[6]));
+  op->dV = vol / (double)op->N;
+  op->fp64 = desc->prec == ACE_FP64;
+  op->esz = op->fp64 ? 8 : 4;
+  cudaError_t e = cudaGetDevice(&op->dev);
+  if (e == cudaSuccess) e = prepare_pool(op->dev);
+  if (e != cudaSuccess) {
+    delete op;
+    return cuda_fail(e, "device setup");
+  }
+  s = op->fp64 ? build_impl<double>(op, phi, dtype) : build_impl<float>(op, phi, dtype);
+  if (s == ACE_OK || s == ACE_ERR_NOT_POSDEF || s == ACE_ERR_NONFINITE) {
+    *out = op;
+    return s;
+  }
+  cudaStreamSynchronize(op->stream);
+  ace_destroy(op);
+  return s;
+}
+
+ace_status ace_build_batched(int k, const ace_desc *desc, const void *const *phi, ace_dtype dtype, void *cuda_stream,
+                             ace_op **out) {
+  g_last_error.clear();
+  if (k < 0 || (k > 0 && (!desc || !phi || !out))) return fail(ACE_ERR_ARG, "bad batched arguments");
+  for (int i = 0; i < k; ++i) out[i] = nullptr;
+  for (int i = 0; i < k; ++i) {
+    ace_status s = ace_build(&desc[i], phi[i], dtype, cuda_stream, &out[i]);
+    if (s != ACE_OK) {
+      std::string msg = g_last_error;
+      for (int j = 0; j <= i; ++j) {
+        if (out[j]) ace_destroy(out[j]);
+        out[j] = nullptr;
+      }
+      return fail(s, "build %d of %d: %s", i, k, msg.c_str());
+    }
+  }
+  return ACE_OK;
+}
+
+ace_status ace_apply(const ace_op *op, const void *psi, ace_dtype dtype, int m, void *out, void *cuda_stream) {
+  g_last_error.clear();
+  if (!op || !psi || !out) return fail(ACE_ERR_ARG, "NULL argument");
+  if (m < 1) return fail(ACE_ERR_ARG, "m = %d < 1", m);
+  if (dtype != ACE_F32 && dtype != ACE_F64) return fail(ACE_ERR_ARG, "unknown dtype %d", (int)dtype);
+  if (op->status != 0) return fail(ACE_ERR_NOT_POSDEF, "operator build did not complete (status %d)", op->status);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  return op->fp64 ? apply_impl<double>(op, psi, dtype, m, out, st) : apply_impl<float>(op, psi, dtype, m, out, st);
+}
+
+ace_status exchange_energy(const ace_op *op, double *ex_hartree) {
+  g_last_error.clear();
+  if (!op || !ex_hartree) return fail(ACE_ERR_ARG, "NULL argument");
+  *ex_hartree = op->energy;
+  return ACE_OK;
+}
+
+ace_status ace_get_size(const ace_op *op, int what, size_t *bytes) {
+  g_last_error.clear();
+  if (!op || !bytes) return fail(ACE_ERR_ARG, "NULL argument");
+  const size_t b = item_bytes(op, what);
+  if (b == 0 && what != ACE_GET_PAIRS) return fail(ACE_ERR_ARG, "unknown item %d", what);
+  *bytes = b;
+  return ACE_OK;
+}
+
+ace_status ace_get(const ace_op *op, int what, void *dst, size_t bytes, void *cuda_stream) {
+  g_last_error.clear();
+  if (!op || (!dst && bytes)) return fail(ACE_ERR_ARG, "NULL argument");
+  const size_t want = item_bytes(op, what);
+  if (want == 0 && what != ACE_GET_PAIRS) return fail(ACE_ERR_ARG, "unknown item %d", what);
+  if (bytes != want) return fail(ACE_ERR_ARG, "item %d has %zu bytes, %zu given", what, want, bytes);
+  if (bytes == 0) return ACE_OK;
+  const void *src = nullptr;
+  switch (what) {
+    case ACE_GET_XI: src = op->xi; break;
+    case ACE_GET_W: src = op->W; break;
+    case ACE_GET_M: src = op->M; break;
+    case ACE_GET_M_RAW: src = op->M_raw; break;
+    case ACE_GET_L: src = op->L; break;
+    case ACE_GET_PAIRS: src = op->pairs; break;
+    case ACE_GET_OVERLAP: src = op->O_sym; break;
+  }
+  if (!src) return fail(ACE_ERR_ARG, "item %d is not available", what);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  ACE_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st), "ace_get copy");
+  ACE_CUDA(cudaStreamSynchronize(st), "ace_get");
+  return ACE_OK;
+}
+
+ace_status ace_pair_count(const ace_op *op, long *npairs) {
+  g_last_error.clear();
+  if (!op || !npairs) return fail(ACE_ERR_ARG, "NULL argument");
+  *npairs = op->npairs;
+  return ACE_OK;
+}
+
+ace_status ace_kernel_launches(const ace_op *op, long *launches) {
+  g_last_error.clear();
+  if (!op || !launches) return fail(ACE_ERR_ARG, "NULL argument");
+  *launches = op->launches;
+  return ACE_OK;
+}
+
+ace_status ace_stage_times(const ace_op *op, float ms[6]) {
+  g_last_error.clear();
+  if (!op || !ms) return fail(ACE_ERR_ARG, "NULL argument");
+  for (int i = 0; i < 6; ++i) ms[i] = op->stage_ms[i];
+  return ACE_OK;
+}
+
+void ace_destroy(ace_op *op) {
+  if (!op) return;
+  op_free_all(op);
+  for (int i = 0; i < 6; ++i)
+    if (op->ev[i]) cudaEventDestroy(op->ev[i]);
+  delete op;
+}
+
+}  // extern "C"

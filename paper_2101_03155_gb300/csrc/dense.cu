@@ -1,0 +1,378 @@
+// dense.cu -- CUDA-core dense steps of the ACE build and application.
+//
+//   gram:      G[i][j] = scale * sum_r f(X_i(r)) f(Y_j(r)),  f = |.| for the pair screen
+//              (section II: int |phi_i phi_j| dr) or identity for M = -dV Phi^T W (App. A) and
+//              C = dV xi^T psi.  Products and the sum inside one 4096-point chunk are in T; the
+//              chunks are added into the FP64 result.
+//   left_mul:  Z = A Y with A small (m x n) and Y (n x K): xi = L^-1 W (xi = W L^-T, App. A) and
+//              the ACE application out = -C^T xi (section II).
+//   cholesky:  M = (M_raw + M_raw^T)/2; -M = L L^T; L^-1; E_x = (f/2) tr M, all FP64 (App. A).
+//   compact:   pair list of the screen (i <= j, sorted) and packs of two pairs.
+#include <cuda_runtime.h>
+
+#include "ace_internal.h"
+#include "fft.cuh"
+
+namespace ace {
+
+// ----------------------------------------------------------------------------------------
+// Gram: 64 x 64 output tile per CTA, 256 threads with 4 x 4 register tiles, K chunk per CTA.
+// ----------------------------------------------------------------------------------------
+constexpr int GR_BM = 64, GR_BK = 32, GR_CHUNK = 4096, GR_NT = 256;
+
+template <typename T, bool ABS>
+__global__ void __launch_bounds__(GR_NT) gram_kernel(const T *__restrict__ X, int nx, const T *__restrict__ Y, int ny,
+                                                     long long K, double scale, bool upper_only, int nbx,
+                                                     double *__restrict__ G) {
+  __shared__ T xs[GR_BK][GR_BM + 1];
+  __shared__ T ys[GR_BK][GR_BM + 1];
+  int bi, bj;
+  if (upper_only) {
+    // blockIdx.x enumerates tile pairs (bi <= bj) row by row
+    int idx = blockIdx.x;
+    bi = 0;
+    while (idx >= nbx - bi) {
+      idx -= nbx - bi;
+      ++bi;
+    }
+    bj = bi + idx;
+  } else {
+    bi = blockIdx.x % nbx;
+    bj = blockIdx.x / nbx;
+  }
+  const int i0 = bi * GR_BM, j0 = bj * GR_BM;
+  const long long k0 = (long long)blockIdx.y * GR_CHUNK;
+  const long long k1 = min(K, k0 + GR_CHUNK);
+  const int tid = threadIdx.x;
+  const int ty = tid / 16, tx = tid % 16;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+
+  for (long long kk = k0; kk < k1; kk += GR_BK) {
+    // load 64 rows x 32 k of X and of Y (coalesced along k)
+    for (int e = tid; e < GR_BM * GR_BK; e += GR_NT) {
+      const int r = e / GR_BK, c = e % GR_BK;
+      const long long k = kk + c;
+      T xv = (T)0, yv = (T)0;
+      if (k < k1) {
+        if (i0 + r < nx) xv = X[(long long)(i0 + r) * K + k];
+        if (j0 + r < ny) yv = Y[(long long)(j0 + r) * K + k];
+      }
+      if (ABS) {
+        xv = xv < (T)0 ? -xv : xv;
+        yv = yv < (T)0 ? -yv : yv;
+      }
+      xs[c][r] = xv;
+      ys[c][r] = yv;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int c = 0; c < GR_BK; ++c) {
+      T xr[4], yr[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) xr[a] = xs[c][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) yr[b] = ys[c][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] += xr[a] * yr[b];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * b;
+      if (i < nx && j < ny) atomicAdd(G + (long long)i * ny + j, scale * (double)acc[a][b]);
+    }
+}
+
+template <typename T>
+cudaError_t launch_gram(const T *X, int nx, const T *Y, int ny, long long K, double scale, bool abs_values,
+                        bool upper_only, double *G, cudaStream_t st) {
+  const int nbx = (nx + GR_BM - 1) / GR_BM, nby = (ny + GR_BM - 1) / GR_BM;
+  const int tiles = upper_only ? nbx * (nbx + 1) / 2 : nbx * nby;
+  const long long chunks = (K + GR_CHUNK - 1) / GR_CHUNK;
+  if (chunks > 65535) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(G, 0, sizeof(double) * (size_t)nx * ny, st);
+  if (e != cudaSuccess) return e;
+  dim3 grid(tiles, (unsigned)chunks);
+  if (abs_values)
+    gram_kernel<T, true><<<grid, GR_NT, 0, st>>>(X, nx, Y, ny, K, scale, upper_only, nbx, G);
+  else
+    gram_kernel<T, false><<<grid, GR_NT, 0, st>>>(X, nx, Y, ny, K, scale, upper_only, nbx, G);
+  return cudaGetLastError();
+}
+template cudaError_t launch_gram<float>(const float *, int, const float *, int, long long, double, bool, bool,
+                                        double *, cudaStream_t);
+template cudaError_t launch_gram<double>(const double *, int, const double *, int, long long, double, bool, bool,
+                                         double *, cudaStream_t);
+
+// ----------------------------------------------------------------------------------------
+// Left multiply Z (m x K) = A (m x n) * Y (n x K); 64 x 64 tile, k-step 16, 4 x 4 per thread.
+// ----------------------------------------------------------------------------------------
+constexpr int LM_BM = 64, LM_BN = 64, LM_BK = 16, LM_NT = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(LM_NT) left_mul_kernel(const T *__restrict__ A, int m, int n,
+                                                         const T *__restrict__ Y, long long K, T *__restrict__ Z) {
+  __shared__ T as[LM_BK][LM_BM + 1];
+  __shared__ T ys[LM_BK][LM_BN];
+  const int i0 = blockIdx.y * LM_BM;
+  const long long c0 = (long long)blockIdx.x * LM_BN;
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+  for (int l0 = 0; l0 < n; l0 += LM_BK) {
+    for (int e = tid; e < LM_BM * LM_BK; e += LM_NT) {
+      const int r = e / LM_BK, c = e % LM_BK;
+      as[c][r] = (i0 + r < m && l0 + c < n) ? A[(long long)(i0 + r) * n + l0 + c] : (T)0;
+    }
+    for (int e = tid; e < LM_BK * LM_BN; e += LM_NT) {
+      const int r = e / LM_BN, c = e % LM_BN;
+      ys[r][c] = (l0 + r < n && c0 + c < K) ? Y[(long long)(l0 + r) * K + c0 + c] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < LM_BK; ++c) {
+      T ar[4], yr[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) ar[a] = as[c][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) yr[b] = ys[c][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] += ar[a] * yr[b];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = i0 + ty + 16 * a;
+      const long long c = c0 + tx + 16 * b;
+      if (i < m && c < K) Z[(long long)i * K + c] = acc[a][b];
+    }
+}
+
+template <typename T>
+cudaError_t launch_left_mul(const T *A, int m, int n, const T *Y, long long K, T *Z, cudaStream_t st) {
+  dim3 grid((unsigned)((K + LM_BN - 1) / LM_BN), (unsigned)((m + LM_BM - 1) / LM_BM));
+  left_mul_kernel<T><<<grid, LM_NT, 0, st>>>(A, m, n, Y, K, Z);
+  return cudaGetLastError();
+}
+template cudaError_t launch_left_mul<float>(const float *, int, int, const float *, long long, float *, cudaStream_t);
+template cudaError_t launch_left_mul<double>(const double *, int, int, const double *, long long, double *,
+                                             cudaStream_t);
+
+// ----------------------------------------------------------------------------------------
+// Cholesky of -M (one CTA, right-looking, FP64 in global memory), L^-1, E_x.
+// status: 0 ok; 1000000 + j: pivot j of -M not positive; 2000000: non-finite entry in M.
+// ----------------------------------------------------------------------------------------
+constexpr int CH_NT = 1024;
+
+__global__ void __launch_bounds__(CH_NT) cholesky_kernel(const double *__restrict__ M_raw, int n, double spin_factor,
+                                                         double *__restrict__ M, double *__restrict__ L,
+                                                         double *__restrict__ Linv, double *__restrict__ energy,
+                                                         int *__restrict__ status) {
+  __shared__ int bad;
+  __shared__ double red[CH_NT / 32];
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  // symmetrise; A = -M kept in L's storage (lower part used), upper part cleared at the end
+  for (int e = tid; e < n * n; e += CH_NT) {
+    const int i = e / n, j = e % n;
+    const double v = 0.5 * (M_raw[(long long)i * n + j] + M_raw[(long long)j * n + i]);
+    M[e] = v;
+    L[e] = -v;
+    if (!isfinite(v)) atomicExch(&bad, 2000000);
+  }
+  __syncthreads();
+  // E_x = (f/2) tr M
+  double part = 0.0;
+  for (int k = tid; k < n; k += CH_NT) part += M[(long long)k * n + k];
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+  if ((tid & 31) == 0) red[tid >> 5] = part;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int w = 0; w < CH_NT / 32; ++w) s += red[w];
+    *energy = 0.5 * spin_factor * s;
+  }
+  if (bad) {
+    if (tid == 0) *status = bad;
+    return;
+  }
+  for (int j = 0; j < n; ++j) {
+    const double d = L[(long long)j * n + j];
+    if (!(d > 0.0) || !isfinite(d)) {
+      if (tid == 0) *status = 1000000 + j;
+      return;  // uniform: every thread read the same d
+    }
+    const double ljj = sqrt(d);
+    __syncthreads();
+    for (int i = j + 1 + tid; i < n; i += CH_NT) L[(long long)i * n + j] /= ljj;
+    if (tid == 0) L[(long long)j * n + j] = ljj;
+    __syncthreads();
+    // trailing update of the lower triangle: A[i][k] -= L[i][j] L[k][j], j < k <= i
+    const int m = n - j - 1;
+    const long long cnt = (long long)m * (m + 1) / 2;
+    for (long long e = tid; e < cnt; e += CH_NT) {
+      // e -> (ii, kk) with 0 <= kk <= ii < m
+      int ii = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+      while ((long long)ii * (ii + 1) / 2 > e) --ii;
+      while ((long long)(ii + 1) * (ii + 2) / 2 <= e) ++ii;
+      const int kk = (int)(e - (long long)ii * (ii + 1) / 2);
+      const int i = j + 1 + ii, k = j + 1 + kk;
+      L[(long long)i * n + k] -= L[(long long)i * n + j] * L[(long long)k * n + j];
+    }
+    __syncthreads();
+  }
+  // clear the strict upper triangle
+  for (int e = tid; e < n * n; e += CH_NT) {
+    const int i = e / n, j = e % n;
+    if (j > i) L[e] = 0.0;
+  }
+  __syncthreads();
+  // L^-1 by forward substitution, one column per thread
+  for (int c = tid; c < n; c += CH_NT) {
+    for (int i = 0; i < n; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      if (i >= c) {
+        for (int l = c; l < i; ++l) s -= L[(long long)i * n + l] * Linv[(long long)l * n + c];
+        s /= L[(long long)i * n + i];
+      } else {
+        s = 0.0;
+      }
+      Linv[(long long)i * n + c] = s;
+    }
+  }
+  if (tid == 0) *status = 0;
+}
+
+cudaError_t launch_cholesky(const double *M_raw, int n, double spin_factor, double *M, double *L, double *Linv,
+                            double *energy, int *status, cudaStream_t st) {
+  cholesky_kernel<<<1, CH_NT, 0, st>>>(M_raw, n, spin_factor, M, L, Linv, energy, status);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------------
+// Screen compaction (one CTA): keep (i <= j) iff i == j or rho_cut <= 0 or O_ij >= rho_cut,
+// in lexicographic order; packs = consecutive pairs two at a time.  Also writes the symmetric O.
+// ----------------------------------------------------------------------------------------
+constexpr int CP_NT = 1024;
+
+__global__ void __launch_bounds__(CP_NT) compact_kernel(const double *__restrict__ O, int n, double rho_cut,
+                                                        int2 *__restrict__ pairs, int4 *__restrict__ packs,
+                                                        int *__restrict__ count, double *__restrict__ O_sym) {
+  __shared__ int warp_sums[CP_NT / 32];
+  __shared__ int running;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) running = 0;
+  for (int e = tid; e < n * n; e += CP_NT) {
+    const int i = e / n, j = e % n;
+    O_sym[e] = (i <= j) ? O[e] : O[(long long)j * n + i];
+  }
+  __syncthreads();
+  const long long total = (long long)n * (n + 1) / 2;
+  for (long long base = 0; base < total; base += CP_NT) {
+    const long long e = base + tid;
+    int keep = 0, i = 0, j = 0;
+    if (e < total) {
+      // row-major enumeration of the upper triangle: row i holds n - i entries
+      // row i starts at s(i) = i (2n - i + 1) / 2; take the largest i with s(i) <= e
+      const double b = 2.0 * n + 1.0;
+      i = (int)((b - sqrt(b * b - 8.0 * (double)e)) * 0.5);
+      if (i < 0) i = 0;
+      while (i > 0 && (long long)i * (2 * n - i + 1) / 2 > e) --i;
+      while ((long long)(i + 1) * (2 * n - i) / 2 <= e) ++i;
+      j = i + (int)(e - (long long)i * (2 * n - i + 1) / 2);
+      const double o = O[(long long)i * n + j];
+      keep = (i == j) || (rho_cut <= 0.0) || (o >= rho_cut);
+    }
+    const unsigned ballot = __ballot_sync(0xffffffffu, keep);
+    const int prefix = __popc(ballot & ((1u << lane) - 1u));
+    if (lane == 0) warp_sums[wid] = __popc(ballot);
+    __syncthreads();
+    int off = running;
+    for (int w = 0; w < wid; ++w) off += warp_sums[w];
+    if (keep) pairs[off + prefix] = make_int2(i, j);
+    __syncthreads();
+    if (tid == 0) {
+      int s = 0;
+      for (int w = 0; w < CP_NT / 32; ++w) s += warp_sums[w];
+      running += s;
+    }
+    __syncthreads();
+  }
+  const int np = running;
+  const int nk = (np + 1) / 2;
+  for (int p = tid; p < nk; p += CP_NT) {
+    const int2 a = pairs[2 * p];
+    const int2 b = (2 * p + 1 < np) ? pairs[2 * p + 1] : make_int2(-1, -1);
+    packs[p] = make_int4(a.x, a.y, b.x, b.y);
+  }
+  if (tid == 0) *count = np;
+}
+
+cudaError_t launch_screen_compact(const double *O, int n, double rho_cut, int2 *pairs, int4 *packs, int *count,
+                                  double *O_sym, cudaStream_t st) {
+  compact_kernel<<<1, CP_NT, 0, st>>>(O, n, rho_cut, pairs, packs, count, O_sym);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------------
+// Elementwise precision conversion with scale.
+// ----------------------------------------------------------------------------------------
+template <typename Tin, typename Tout>
+__global__ void convert_kernel(const Tin *__restrict__ in, Tout *__restrict__ out, long long count, double scale) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (Tout)(scale * (double)in[i]);
+}
+
+template <typename Tin, typename Tout>
+cudaError_t launch_convert(const Tin *in, Tout *out, long long count, double scale, cudaStream_t st) {
+  const int nt = 256;
+  const long long blocks = min((count + nt - 1) / nt, (long long)152 * 16);
+  if (count == 0) return cudaSuccess;
+  convert_kernel<Tin, Tout><<<(unsigned)blocks, nt, 0, st>>>(in, out, count, scale);
+  return cudaGetLastError();
+}
+template cudaError_t launch_convert<double, float>(const double *, float *, long long, double, cudaStream_t);
+template cudaError_t launch_convert<float, double>(const float *, double *, long long, double, cudaStream_t);
+template cudaError_t launch_convert<double, double>(const double *, double *, long long, double, cudaStream_t);
+template cudaError_t launch_convert<float, float>(const float *, float *, long long, double, cudaStream_t);
+
+}  // namespace ace
+
+namespace ace {
+// A[c][k] = scale * C[k][c] (C is n x m FP64, A is m x n in T)
+template <typename T>
+__global__ void transpose_scale_kernel(const double *__restrict__ C, int n, int m, double scale, T *__restrict__ A) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * m; e += gridDim.x * blockDim.x) {
+    const int c = e / n, k = e % n;
+    A[e] = (T)(scale * C[(long long)k * m + c]);
+  }
+}
+template <typename T>
+cudaError_t launch_transpose_scale(const double *C, int n, int m, double scale, T *A, cudaStream_t st) {
+  const int nt = 256;
+  const int blocks = (int)min((long long)(n * m + nt - 1) / nt, 4096LL);
+  transpose_scale_kernel<T><<<blocks > 0 ? blocks : 1, nt, 0, st>>>(C, n, m, scale, A);
+  return cudaGetLastError();
+}
+template cudaError_t launch_transpose_scale<float>(const double *, int, int, double, float *, cudaStream_t);
+template cudaError_t launch_transpose_scale<double>(const double *, int, int, double, double *, cudaStream_t);
+}  // namespace ace

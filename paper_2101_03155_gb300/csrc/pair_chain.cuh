@@ -1,0 +1,267 @@
+// pair_chain.cuh -- the five pencil passes that turn packed orbital pairs into W contributions.
+//
+// For each pack (a,b),(c,d):  z = phi_a phi_b + i phi_c phi_d          (pair densities, Eq. vx)
+//   z~ = FFT3(z);  z~ *= 4 pi / (N |G|^2)  (G = 0 dropped)               (Eq. e:vij in reciprocal space)
+//   z = IFFT3(z~) = v_ab + i v_cd                                        (kernel real and even)
+//   W_a += v_ab phi_b, W_b += v_ab phi_a, W_c += v_cd phi_d, W_d += v_cd phi_c   (Eq. vx; i = j once)
+//
+// The 3D transform is three sets of 1D pencils.  Each CTA owns TILE lines of one axis of one
+// pack, stages them in shared memory (odd pitch), and runs a two-stage transform L = R1 * R2
+// with both factors as register DFTs:
+//   stage 1, task (t, n2): DFT_R1 over n1 of line[n1 R2 + n2], twiddle w_L^{n2 k1}, store at k1 R2 + n2
+//   stage 2, task (t, k1): DFT_R2 over n2 of line[k1 R2 + n2]; X[k1 + R1 k2] stored at k1 R2 + k2
+// so natural index k sits at pos(k) = (k % R1) R2 + k / R1; the copy-out undoes that.  The axis-1
+// pass keeps stage-2 results in registers, multiplies by the kernel, and runs the inverse stages
+// (inverse DFT_R2, conjugate twiddle, then inverse DFT_R1) which return natural order.
+// Global accesses are coalesced: axis-3 tiles are TILE whole rows (contiguous), axis-1/2 tiles are
+// TILE neighbouring columns, read and written as TILE-wide contiguous runs.
+#pragma once
+
+#include "ace_internal.h"
+#include "fft.cuh"
+
+namespace ace {
+
+template <int L>
+struct PassShape {
+  static constexpr int R1 = Factor<L>::R1;
+  static constexpr int R2 = Factor<L>::R2;
+  static constexpr int TILE = 16;
+  static constexpr int LP = L + 1;  // odd pitch: lanes over lines hit distinct banks
+  static constexpr int NT = TILE * (R1 > R2 ? R1 : R2);
+};
+
+template <typename T>
+__device__ __forceinline__ cpx<T> conjc(cpx<T> a) {
+  return {a.x, -a.y};
+}
+
+// stage 1 of the two-stage transform in direction D (twiddled unless TWIDDLE is false)
+template <typename T, int L, int D, bool TWIDDLE>
+__device__ __forceinline__ void pencil_stage1(cpx<T> *s, const cpx<T> *tw, int tvalid) {
+  using S = PassShape<L>;
+  for (int task = threadIdx.x; task < S::TILE * S::R2; task += S::NT) {
+    const int t = task % S::TILE, n2 = task / S::TILE;
+    if (t >= tvalid) continue;
+    cpx<T> *line = s + t * S::LP;
+    cpx<T> x[S::R1];
+#pragma unroll
+    for (int n1 = 0; n1 < S::R1; ++n1) x[n1] = line[n1 * S::R2 + n2];
+    Dft<S::R1, D, T>::run(x);
+#pragma unroll
+    for (int k1 = 0; k1 < S::R1; ++k1) {
+      cpx<T> v = x[k1];
+      if (TWIDDLE && k1 > 0) {
+        const cpx<T> w = tw[n2 * k1];
+        v = cmul(v, D < 0 ? w : conjc(w));
+      }
+      line[k1 * S::R2 + n2] = v;
+    }
+  }
+}
+
+template <typename T, int L, int D>
+__device__ __forceinline__ void pencil_stage2(cpx<T> *s, int tvalid) {
+  using S = PassShape<L>;
+  for (int task = threadIdx.x; task < S::TILE * S::R1; task += S::NT) {
+    const int t = task % S::TILE, k1 = task / S::TILE;
+    if (t >= tvalid) continue;
+    cpx<T> *line = s + t * S::LP + k1 * S::R2;
+    cpx<T> x[S::R2];
+#pragma unroll
+    for (int n2 = 0; n2 < S::R2; ++n2) x[n2] = line[n2];
+    Dft<S::R2, D, T>::run(x);
+#pragma unroll
+    for (int k2 = 0; k2 < S::R2; ++k2) line[k2] = x[k2];
+  }
+}
+
+template <int L>
+__device__ __forceinline__ int perm_pos(int k) {
+  using S = PassShape<L>;
+  return (k % S::R1) * S::R2 + k / S::R1;
+}
+
+template <typename T, int L, int MODE>
+__global__ void __launch_bounds__(PassShape<L>::NT) pair_pass_kernel(PairPassArgs<T> a) {
+  using S = PassShape<L>;
+  constexpr int TILE = S::TILE, LP = S::LP, NT = S::NT;
+  __shared__ cpx<T> s[TILE * LP];
+  __shared__ cpx<T> tw[L];
+
+  const int tid = threadIdx.x;
+  const int4 pk = a.packs[a.pack0 + blockIdx.y];
+  cpx<T> *z = a.scratch + (long long)blockIdx.y * a.N;
+
+  for (int e = tid; e < L; e += NT) tw[e] = a.tw[e];
+
+  constexpr bool AXIS3 = (MODE == PASS_FWD3_PAIR || MODE == PASS_INV3_ACC);
+  long long base, Ns;
+  int tvalid;
+  if (AXIS3) {
+    const long long rows = (long long)a.n1 * a.n2;
+    const long long row0 = (long long)blockIdx.x * TILE;
+    tvalid = (int)min((long long)TILE, rows - row0);
+    base = row0 * L;
+    Ns = 1;
+  } else if (MODE == PASS_CONV1) {
+    const long long cols = (long long)a.n2 * a.n3;
+    const long long c0 = (long long)blockIdx.x * TILE;
+    tvalid = (int)min((long long)TILE, cols - c0);
+    base = c0;
+    Ns = cols;
+  } else {  // axis 2
+    const int tpi = (a.n3 + TILE - 1) / TILE;
+    const int i1 = blockIdx.x / tpi;
+    const int i30 = (blockIdx.x % tpi) * TILE;
+    tvalid = min(TILE, a.n3 - i30);
+    base = (long long)i1 * a.n2 * a.n3 + i30;
+    Ns = a.n3;
+  }
+
+  // ---- copy in ----
+  if (MODE == PASS_FWD3_PAIR) {
+    const T *pa = a.phi + (long long)pk.x * a.N + base;
+    const T *pb = a.phi + (long long)pk.y * a.N + base;
+    const bool two = pk.z >= 0;
+    const T *pc = a.phi + (long long)(two ? pk.z : 0) * a.N + base;
+    const T *pd = a.phi + (long long)(two ? pk.w : 0) * a.N + base;
+    for (int e = tid; e < tvalid * L; e += NT) {
+      const int t = e / L, n = e - t * L;
+      const T re = pa[e] * pb[e];
+      const T im = two ? pc[e] * pd[e] : (T)0;
+      s[t * LP + n] = cpx<T>{re, im};
+    }
+  } else if (AXIS3) {
+    const cpx<T> *src = z + base;
+    for (int e = tid; e < tvalid * L; e += NT) {
+      const int t = e / L, n = e - t * L;
+      s[t * LP + n] = src[e];
+    }
+  } else {
+    const cpx<T> *src = z + base;
+    for (int e = tid; e < TILE * L; e += NT) {
+      const int n = e / TILE, t = e - n * TILE;
+      if (t < tvalid) s[t * LP + n] = src[(long long)n * Ns + t];
+    }
+  }
+  __syncthreads();
+
+  // ---- transform ----
+  if (MODE == PASS_CONV1) {
+    pencil_stage1<T, L, -1, true>(s, tw, tvalid);
+    __syncthreads();
+    for (int task = tid; task < TILE * S::R1; task += NT) {
+      const int t = task % TILE, k1 = task / TILE;
+      if (t >= tvalid) continue;
+      cpx<T> *line = s + t * LP + k1 * S::R2;
+      cpx<T> x[S::R2];
+#pragma unroll
+      for (int n2 = 0; n2 < S::R2; ++n2) x[n2] = line[n2];
+      Dft<S::R2, -1, T>::run(x);
+      const T *kcol = a.kernel + base + t;
+#pragma unroll
+      for (int k2 = 0; k2 < S::R2; ++k2) {
+        const T kv = kcol[(long long)(k1 + S::R1 * k2) * Ns];
+        x[k2] = cscale(x[k2], kv);
+      }
+      Dft<S::R2, +1, T>::run(x);
+#pragma unroll
+      for (int n2 = 0; n2 < S::R2; ++n2) {
+        cpx<T> v = x[n2];
+        if (n2 > 0 && k1 > 0) v = cmul(v, conjc(tw[n2 * k1]));
+        line[n2] = v;
+      }
+    }
+    __syncthreads();
+    pencil_stage1<T, L, +1, false>(s, tw, tvalid);  // inverse DFT_R1: natural order out
+    __syncthreads();
+  } else {
+    constexpr int D = (MODE == PASS_INV2 || MODE == PASS_INV3_ACC) ? +1 : -1;
+    pencil_stage1<T, L, D, true>(s, tw, tvalid);
+    __syncthreads();
+    pencil_stage2<T, L, D>(s, tvalid);
+    __syncthreads();
+  }
+
+  // ---- copy out ----
+  if (MODE == PASS_INV3_ACC) {
+    const long long oa = (long long)pk.x * a.N + base, ob = (long long)pk.y * a.N + base;
+    const bool two = pk.z >= 0;
+    const long long oc = (long long)(two ? pk.z : 0) * a.N + base, od = (long long)(two ? pk.w : 0) * a.N + base;
+    const bool diag1 = pk.x == pk.y, diag2 = pk.z == pk.w;
+    for (int e = tid; e < tvalid * L; e += NT) {
+      const int t = e / L, k = e - t * L;
+      const cpx<T> v = s[t * LP + perm_pos<L>(k)];
+      atomicAdd(a.W + oa + e, v.x * a.phi[ob + e]);
+      if (!diag1) atomicAdd(a.W + ob + e, v.x * a.phi[oa + e]);
+      if (two) {
+        atomicAdd(a.W + oc + e, v.y * a.phi[od + e]);
+        if (!diag2) atomicAdd(a.W + od + e, v.y * a.phi[oc + e]);
+      }
+    }
+  } else if (MODE == PASS_FWD3_PAIR) {
+    cpx<T> *dst = z + base;
+    for (int e = tid; e < tvalid * L; e += NT) {
+      const int t = e / L, k = e - t * L;
+      dst[e] = s[t * LP + perm_pos<L>(k)];
+    }
+  } else if (MODE == PASS_CONV1) {
+    cpx<T> *dst = z + base;
+    for (int e = tid; e < TILE * L; e += NT) {
+      const int k = e / TILE, t = e - k * TILE;
+      if (t < tvalid) dst[(long long)k * Ns + t] = s[t * LP + k];
+    }
+  } else {
+    cpx<T> *dst = z + base;
+    for (int e = tid; e < TILE * L; e += NT) {
+      const int k = e / TILE, t = e - k * TILE;
+      if (t < tvalid) dst[(long long)k * Ns + t] = s[t * LP + perm_pos<L>(k)];
+    }
+  }
+}
+
+template <typename T, int L>
+cudaError_t launch_pass_L(int mode, const PairPassArgs<T> &a, int npacks, cudaStream_t st) {
+  using S = PassShape<L>;
+  dim3 grid;
+  if (mode == PASS_FWD3_PAIR || mode == PASS_INV3_ACC) {
+    grid.x = (unsigned)(((long long)a.n1 * a.n2 + S::TILE - 1) / S::TILE);
+  } else if (mode == PASS_CONV1) {
+    grid.x = (unsigned)(((long long)a.n2 * a.n3 + S::TILE - 1) / S::TILE);
+  } else {
+    grid.x = (unsigned)(a.n1 * ((a.n3 + S::TILE - 1) / S::TILE));
+  }
+  grid.y = npacks;
+  switch (mode) {
+    case PASS_FWD3_PAIR: pair_pass_kernel<T, L, PASS_FWD3_PAIR><<<grid, S::NT, 0, st>>>(a); break;
+    case PASS_FWD2: pair_pass_kernel<T, L, PASS_FWD2><<<grid, S::NT, 0, st>>>(a); break;
+    case PASS_CONV1: pair_pass_kernel<T, L, PASS_CONV1><<<grid, S::NT, 0, st>>>(a); break;
+    case PASS_INV2: pair_pass_kernel<T, L, PASS_INV2><<<grid, S::NT, 0, st>>>(a); break;
+    case PASS_INV3_ACC: pair_pass_kernel<T, L, PASS_INV3_ACC><<<grid, S::NT, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+#define ACE_PASS_LENGTHS(X) X(8) X(12) X(16) X(20) X(24) X(32) X(48) X(64) X(72) X(96) X(108) X(128) X(144) X(160)
+
+template <typename T>
+cudaError_t launch_pair_pass_impl(int mode, const PairPassArgs<T> &a, int npacks, cudaStream_t st) {
+  int L;
+  switch (mode) {
+    case PASS_FWD3_PAIR:
+    case PASS_INV3_ACC: L = a.n3; break;
+    case PASS_CONV1: L = a.n1; break;
+    default: L = a.n2; break;
+  }
+  switch (L) {
+#define ACE_CASE(L_) \
+  case L_: return launch_pass_L<T, L_>(mode, a, npacks, st);
+    ACE_PASS_LENGTHS(ACE_CASE)
+#undef ACE_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ace

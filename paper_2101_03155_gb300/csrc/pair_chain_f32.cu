@@ -1,0 +1,20 @@
+// FP32 instantiation of the pair-potential chain (mixed form).
+#include "pair_chain.cuh"
+
+namespace ace {
+template <>
+cudaError_t launch_pair_pass<float>(int mode, const PairPassArgs<float> &a, int npacks, cudaStream_t st) {
+  return launch_pair_pass_impl<float>(mode, a, npacks, st);
+}
+
+bool pass_length_supported(int L) {
+  switch (L) {
+#define ACE_CASE(L_) case L_:
+    ACE_PASS_LENGTHS(ACE_CASE)
+#undef ACE_CASE
+    return true;
+    default:
+      return false;
+  }
+}
+}  // namespace ace

