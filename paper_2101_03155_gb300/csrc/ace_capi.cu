@@ -525,7 +525,6 @@ int ace_grid_supported(int n_axis, ace_precision prec) {
 }
 
 ace_status ace_build(const ace_desc *desc, const void *phi, ace_dtype dtype, void *cuda_stream, ace_op **out) {
-  g_last_error.clear();
   if (!out) return fail(ACE_ERR_ARG, "out is NULL");
   *out = nullptr;
   ace_status s = check_desc(desc);
@@ -562,7 +561,6 @@ ace_status ace_build(const ace_desc *desc, const void *phi, ace_dtype dtype, voi
 
 ace_status ace_build_batched(int k, const ace_desc *desc, const void *const *phi, ace_dtype dtype, void *cuda_stream,
                              ace_op **out) {
-  g_last_error.clear();
   if (k < 0 || (k > 0 && (!desc || !phi || !out))) return fail(ACE_ERR_ARG, "bad batched arguments");
   for (int i = 0; i < k; ++i) out[i] = nullptr;
   for (int i = 0; i < k; ++i) {
@@ -580,7 +578,6 @@ ace_status ace_build_batched(int k, const ace_desc *desc, const void *const *phi
 }
 
 ace_status ace_apply(const ace_op *op, const void *psi, ace_dtype dtype, int m, void *out, void *cuda_stream) {
-  g_last_error.clear();
   if (!op || !psi || !out) return fail(ACE_ERR_ARG, "NULL argument");
   if (m < 1) return fail(ACE_ERR_ARG, "m = %d < 1", m);
   if (dtype != ACE_F32 && dtype != ACE_F64) return fail(ACE_ERR_ARG, "unknown dtype %d", (int)dtype);
@@ -590,14 +587,12 @@ ace_status ace_apply(const ace_op *op, const void *psi, ace_dtype dtype, int m, 
 }
 
 ace_status exchange_energy(const ace_op *op, double *ex_hartree) {
-  g_last_error.clear();
   if (!op || !ex_hartree) return fail(ACE_ERR_ARG, "NULL argument");
   *ex_hartree = op->energy;
   return ACE_OK;
 }
 
 ace_status ace_get_size(const ace_op *op, int what, size_t *bytes) {
-  g_last_error.clear();
   if (!op || !bytes) return fail(ACE_ERR_ARG, "NULL argument");
   const size_t b = item_bytes(op, what);
   if (b == 0 && what != ACE_GET_PAIRS) return fail(ACE_ERR_ARG, "unknown item %d", what);
@@ -606,7 +601,6 @@ ace_status ace_get_size(const ace_op *op, int what, size_t *bytes) {
 }
 
 ace_status ace_get(const ace_op *op, int what, void *dst, size_t bytes, void *cuda_stream) {
-  g_last_error.clear();
   if (!op || (!dst && bytes)) return fail(ACE_ERR_ARG, "NULL argument");
   const size_t want = item_bytes(op, what);
   if (want == 0 && what != ACE_GET_PAIRS) return fail(ACE_ERR_ARG, "unknown item %d", what);
@@ -630,21 +624,18 @@ ace_status ace_get(const ace_op *op, int what, void *dst, size_t bytes, void *cu
 }
 
 ace_status ace_pair_count(const ace_op *op, long *npairs) {
-  g_last_error.clear();
   if (!op || !npairs) return fail(ACE_ERR_ARG, "NULL argument");
   *npairs = op->npairs;
   return ACE_OK;
 }
 
 ace_status ace_kernel_launches(const ace_op *op, long *launches) {
-  g_last_error.clear();
   if (!op || !launches) return fail(ACE_ERR_ARG, "NULL argument");
   *launches = op->launches;
   return ACE_OK;
 }
 
 ace_status ace_stage_times(const ace_op *op, float ms[6]) {
-  g_last_error.clear();
   if (!op || !ms) return fail(ACE_ERR_ARG, "NULL argument");
   for (int i = 0; i < 6; ++i) ms[i] = op->stage_ms[i];
   return ACE_OK;

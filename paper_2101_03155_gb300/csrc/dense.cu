@@ -45,11 +45,12 @@ __global__ void __launch_bounds__(GR_NT) gram_kernel(const T *__restrict__ X, in
   const long long k1 = min(K, k0 + GR_CHUNK);
   const int tid = threadIdx.x;
   const int ty = tid / 16, tx = tid % 16;
-  T acc[4][4];
+  // acc + comp is a compensated (Kahan) running sum of the 32-point partial sums of each tile
+  T acc[4][4], comp[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+    for (int b = 0; b < 4; ++b) acc[a][b] = comp[a][b] = (T)0;
 
   for (long long kk = k0; kk < k1; kk += GR_BK) {
     // load 64 rows x 32 k of X and of Y (coalesced along k)
@@ -69,6 +70,11 @@ __global__ void __launch_bounds__(GR_NT) gram_kernel(const T *__restrict__ X, in
       ys[c][r] = yv;
     }
     __syncthreads();
+    T part[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) part[a][b] = (T)0;
 #pragma unroll 8
     for (int c = 0; c < GR_BK; ++c) {
       T xr[4], yr[4];
@@ -79,8 +85,17 @@ __global__ void __launch_bounds__(GR_NT) gram_kernel(const T *__restrict__ X, in
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] += xr[a] * yr[b];
+        for (int b = 0; b < 4; ++b) part[a][b] += xr[a] * yr[b];
     }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const T y = part[a][b] - comp[a][b];
+        const T t = acc[a][b] + y;
+        comp[a][b] = (t - acc[a][b]) - y;
+        acc[a][b] = t;
+      }
     __syncthreads();
   }
 #pragma unroll

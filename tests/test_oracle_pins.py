@@ -253,11 +253,11 @@ def test_exchange_w_row_subset(oracle_mod, cfg1_build):
 
 
 def test_not_posdef_reported(oracle_mod):
-    """A duplicated orbital makes -M singular: the Cholesky reports the failing pivot."""
+    """A zero orbital makes pivot 3 of -M exactly zero: the Cholesky reports it (status = pivot + 1)."""
     rng = np.random.default_rng(8)
     lat, grid = np.diag([8.0, 8.0, 8.0]), (10, 10, 10)
     phi, _, _ = gaussian_orbitals(grid, lat, 3, 1, rng)
-    phi = np.concatenate([phi, phi[:1]])
+    phi = np.concatenate([phi, np.zeros_like(phi[:1])])
     W = oracle_mod.exchange_w(phi, lat)
     res = oracle_mod.ace_from_w(phi, W, 512.0 / 1000, want_xi=False)
     assert res["status"] == 4
