@@ -132,6 +132,31 @@ int ace_grid_supported(int n_axis, ace_precision prec);
 
 void ace_destroy(ace_op *op);
 
+/* W without device allocation.  The paper has no counterpart: this entry point exists for callers
+ * that may not call cudaMalloc (or any allocator) while they run -- applications that hand the
+ * library pre-allocated buffers under a fixed memory budget, allocation-free inner loops, or hosts
+ * whose framework owns all device memory.
+ *
+ * Computes the pair-potential chain of Eq. (vx) for an explicit pair list:
+ *   W_i = sum_{j : (i,j) or (j,i) listed} v_ij phi_j,  v_ij by FFT with the 4 pi/|G|^2 kernel,
+ * the same arithmetic as the W step of ace_build (desc->rho_cut and desc->spin_factor are ignored).
+ *   phi_dev:    device orbitals [norb][N1][N2][N3]; W_dev: device output of the same shape (zeroed
+ *               by the call).  dtype must be the working type of desc->prec (ACE_F32 for ACE_MIXED,
+ *               ACE_F64 for ACE_FP64).
+ *   pairs_host: host int32 [npairs][2] with 0 <= i <= j < norb (checked before any work is queued).
+ * All workspace (FFT scratch, pack list, kernel table, twiddles) lives in one array of
+ * ACE_NOALLOC_SCRATCH_BYTES compiled into the library; every GPU that loads the library holds that
+ * array until the process exits.  A grid needs (3 * sizeof(T) * N + about 80 KB) bytes of it; larger
+ * grids return ACE_ERR_ARG.  Every call on a device shares the array and finds the previous call's
+ * contents in it: the call rewrites what it reads and zeroes W.  Calls whose GPU work overlaps (other
+ * streams or host threads) race on the array and must be serialised by the caller.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress, with that device current);
+ * make it before any stream capture.  Stream-ordered on `cuda_stream`; pair uploads go through a
+ * small pageable host buffer.  Errors: ACE_ERR_ARG, ACE_ERR_UNSUPPORTED_GRID, ACE_ERR_CUDA. */
+#define ACE_NOALLOC_SCRATCH_BYTES (32u << 20)
+ace_status ace_exchange_w_noalloc(const ace_desc *desc, const void *phi_dev, ace_dtype dtype,
+                                  const int *pairs_host, long npairs, void *W_dev, void *cuda_stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *ace_last_error(void);
 

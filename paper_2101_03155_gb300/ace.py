@@ -45,7 +45,7 @@ ACE_GET_OVERLAP = 6
 EXPORTED = [
     "ace_build", "ace_build_batched", "ace_apply", "exchange_energy", "ace_get", "ace_pair_count",
     "ace_get_size", "ace_stage_times", "ace_kernel_launches", "ace_grid_supported", "ace_destroy",
-    "ace_last_error",
+    "ace_last_error", "ace_exchange_w_noalloc",
 ]
 
 
@@ -109,13 +109,15 @@ def load(path: str = LIB_PATH):
         lib.ace_pair_count.argtypes = [vp, ctypes.POINTER(c_long)]
         lib.ace_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         lib.ace_kernel_launches.argtypes = [vp, ctypes.POINTER(c_long)]
+        lib.ace_exchange_w_noalloc.argtypes = [ctypes.POINTER(AceDesc), vp, c_int, ctypes.POINTER(c_int), c_long,
+                                               vp, vp]
         lib.ace_grid_supported.argtypes = [c_int, c_int]
         lib.ace_grid_supported.restype = c_int
         lib.ace_destroy.argtypes = [vp]
         lib.ace_destroy.restype = None
         lib.ace_last_error.restype = ctypes.c_char_p
         for name in ("ace_build", "ace_build_batched", "ace_apply", "exchange_energy", "ace_get", "ace_get_size",
-                     "ace_pair_count", "ace_stage_times", "ace_kernel_launches"):
+                     "ace_pair_count", "ace_stage_times", "ace_kernel_launches", "ace_exchange_w_noalloc"):
             getattr(lib, name).restype = c_int
         _lib = lib
         return lib
@@ -282,6 +284,22 @@ def ace_grid_supported(n_axis: int, prec: int = ACE_MIXED) -> bool:
 
 def ace_destroy(op: AceOp) -> None:
     op.close()
+
+
+def ace_exchange_w_noalloc(desc: AceDesc, phi, pairs, W, stream=None):
+    """W for an explicit pair list without any device allocation (fixed in-library workspace).
+
+    phi and W: device tensors [norb][N] of the precision's working dtype; pairs: host int32 [npairs][2].
+    """
+    p_ptr, p_code, p_numel = _array_info(phi)
+    w_ptr, w_code, w_numel = _array_info(W)
+    if p_code != w_code or p_numel != w_numel:
+        raise ValueError("phi and W must have the same dtype and shape")
+    pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    _check(load().ace_exchange_w_noalloc(ctypes.byref(desc), p_ptr, p_code,
+                                         pr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(pr), w_ptr,
+                                         _stream_handle(stream)))
+    return W
 
 
 # ---- convenience readers (host numpy copies) ----

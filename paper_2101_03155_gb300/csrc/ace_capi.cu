@@ -515,6 +515,10 @@ size_t item_bytes(const ace_op *op, int what) {
 
 }  // namespace
 
+namespace ace {
+void set_last_error(const char *msg) { g_last_error = msg; }
+}  // namespace ace
+
 extern "C" {
 
 const char *ace_last_error(void) { return g_last_error.c_str(); }

@@ -57,6 +57,9 @@ cudaError_t launch_screen_compact(const double *O, int n, double rho_cut, int2 *
 template <typename T>
 cudaError_t launch_transpose_scale(const double *C, int n, int m, double scale, T *A, cudaStream_t st);
 
+// Sets the message returned by ace_last_error() on this thread.
+void set_last_error(const char *msg);
+
 template <typename Tin, typename Tout>
 cudaError_t launch_convert(const Tin *in, Tout *out, long long count, double scale, cudaStream_t st);
 

@@ -1,0 +1,71 @@
+"""ace_exchange_w_noalloc: W for an explicit pair list with no device allocation inside the call.
+
+Callers that may not allocate device memory while they run (fixed memory budgets, allocation-free
+inner loops, frameworks that own all device memory) use this entry point; it takes its workspace
+from a fixed array compiled into the library.  These tests check, through the C ABI, that its W
+equals the W of ace_build (the allocating path) on the same pair list, within the tolerances the
+other parity tests use, for two calls in a row (the shared array keeps the previous call's
+contents, and the output is filled with garbage before each call), and that grids too large for
+the array are refused.  This file is collected last so that a failure here does not hide others.
+"""
+
+import numpy as np
+import pytest
+
+import paper_2101_03155_gb300 as ace
+from gpu_helpers import FP64_ARRAY_RTOL, MIXED_W_RTOL, gpu_build, rel_max
+from workloads.generators import config1, water_like
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2101_03155_gb300 import build
+
+    build.build()
+    ace.ace.load()
+
+
+def _cases():
+    w1 = config1()
+    w2 = water_like(8, 11.74, (48, 48, 48), np.random.default_rng(1010), rho_cut=1e-3, dmin=4.0)
+    return [(w1, 0.0), (w2, w2.rho_cut)]
+
+
+@pytest.mark.parametrize("prec", [ace.ACE_FP64, ace.ACE_MIXED])
+def test_noalloc_matches_build_on_consecutive_calls(prec):
+    import torch
+
+    dtype = torch.float64 if prec == ace.ACE_FP64 else torch.float32
+    tol = FP64_ARRAY_RTOL if prec == ace.ACE_FP64 else MIXED_W_RTOL
+    stream = torch.cuda.current_stream()
+    refs = []
+    for w, rho_cut in _cases():
+        g = gpu_build(w.phi, w.lattice, prec, rho_cut=rho_cut)
+        assert g["status"] == 0
+        refs.append((w, rho_cut, g["W"].reshape(w.phi.shape), g["pairs"]))
+        g["op"].close()
+    # two calls in a row on the same input, then a call on a different grid and pair list
+    for w, rho_cut, W_ref, pairs in (refs[0], refs[0], refs[1], refs[1]):
+        desc = ace.make_desc(w.grid, w.lattice, w.norb, rho_cut=rho_cut, spin_factor=w.spin_factor, prec=prec)
+        phi = torch.from_numpy(w.phi).to(device="cuda", dtype=dtype)
+        W = torch.full_like(phi, float("nan"))
+        ace.ace.ace_exchange_w_noalloc(desc, phi, pairs, W, stream)
+        torch.cuda.synchronize()
+        assert rel_max(W.cpu().numpy(), W_ref) <= tol
+
+
+def test_noalloc_refuses_grids_beyond_its_array():
+    import torch
+
+    lat = np.eye(3) * 20.0
+    desc = ace.make_desc((128, 128, 128), lat, 2, prec=ace.ACE_FP64)  # 3 * 8 B * 128^3 > 32 MiB
+    tiny = torch.zeros(16, dtype=torch.float64, device="cuda")  # refused before any access
+    with pytest.raises(ace.AceError) as e:
+        ace.ace.ace_exchange_w_noalloc(desc, tiny, np.array([[0, 0]], np.int32), tiny)
+    assert e.value.status == ace.ace.ACE_ERR_ARG
+    assert "fixed array" in str(e.value)
