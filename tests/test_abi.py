@@ -1,0 +1,76 @@
+"""The C-ABI library builds, loads and exports every entry point include/ace.h declares (no GPU)."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ace.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "return")))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2101_03155_gb300 import build
+
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_parses():
+    names = declared_functions()
+    for must in ("ace_build", "ace_apply", "exchange_energy", "ace_build_batched", "ace_get", "ace_destroy",
+                 "ace_last_error", "ace_pair_count"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"declared in include/ace.h but not exported: {missing}"
+
+
+def test_binding_covers_the_abi():
+    from paper_2101_03155_gb300 import ace
+
+    assert sorted(ace.EXPORTED) == declared_functions()
+    for n in ace.EXPORTED:
+        assert callable(getattr(ace, n))
+
+
+def test_host_side_checks_without_gpu(lib):
+    """Argument checks that run before any CUDA call return ACE_ERR_ARG / UNSUPPORTED_GRID."""
+    from paper_2101_03155_gb300 import ace
+
+    ace.load()
+    assert ace.ace_grid_supported(96) and ace.ace_grid_supported(160) and not ace.ace_grid_supported(97)
+    d = ace.make_desc((96, 96, 97), np.eye(3) * 10, 4)
+    with pytest.raises(ace.AceError) as e:
+        ace.ace_build(d, np.zeros((4, 96, 96, 97), np.float32))
+    assert e.value.status == ace.ACE_ERR_UNSUPPORTED_GRID
+    d = ace.make_desc((16, 16, 16), np.zeros((3, 3)), 4)
+    with pytest.raises(ace.AceError) as e:
+        ace.ace_build(d, np.zeros((4, 16, 16, 16), np.float32))
+    assert e.value.status == ace.ACE_ERR_ARG
+    assert "singular" in ace.ace_last_error()
+    h = ctypes.c_void_p()
+    assert lib.ace_build(None, None, 0, None, ctypes.byref(h)) == ace.ACE_ERR_ARG
+    lib.ace_destroy(None)  # no-op
+
+
+def test_product_path_does_not_import_oracle():
+    import subprocess
+    import sys
+
+    code = ("import sys; import paper_2101_03155_gb300 as p; p.ace.load(); "
+            "bad=[m for m in sys.modules if m == 'oracle' or m.startswith('oracle.')]; "
+            "assert not bad, bad")
+    subprocess.run([sys.executable, "-c", code], cwd=ROOT, check=True)
