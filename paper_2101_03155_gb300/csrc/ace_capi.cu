@@ -143,6 +143,7 @@ struct DeviceTables {
   double lattice[9];
   size_t esz;
   void *K;
+  void *Kperm;  // K[m1][k2(p2)][k3(p3)]: axes 2 and 3 in the plane passes' output positions
   void *tw[3];
 };
 std::mutex g_tab_mu;
@@ -169,6 +170,25 @@ cudaError_t get_tables(int dev, const ace_desc &d, cudaStream_t st, const Device
   cudaError_t e = cudaMalloc(&t.K, sizeof(T) * Kt.size());
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(t.K, Kt.data(), sizeof(T) * Kt.size(), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  std::vector<T> Kp(Kt.size());
+  {
+    int a2, b2, a3, b3;
+    ace::axis_factors(d.n[1], &a2, &b2);
+    ace::axis_factors(d.n[2], &a3, &b3);
+    const int n2 = d.n[1], n3 = d.n[2];
+    for (int m1 = 0; m1 < d.n[0]; ++m1)
+      for (int p2 = 0; p2 < n2; ++p2) {
+        const int k2 = p2 / b2 + a2 * (p2 % b2);
+        for (int p3 = 0; p3 < n3; ++p3) {
+          const int k3 = p3 / b3 + a3 * (p3 % b3);
+          Kp[((size_t)m1 * n2 + p2) * n3 + p3] = Kt[((size_t)m1 * n2 + k2) * n3 + k3];
+        }
+      }
+  }
+  e = cudaMalloc(&t.Kperm, sizeof(T) * Kp.size());
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(t.Kperm, Kp.data(), sizeof(T) * Kp.size(), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
   std::vector<cpx<T>> twh[3];
   for (int a = 0; a < 3; ++a) {
@@ -214,6 +234,7 @@ struct ace_op {
   float stage_ms[6] = {};
   long launches = 0;          // kernels of this library launched by the build
   std::vector<void *> owned;  // stream-ordered allocations freed by ace_destroy
+  std::vector<int2> pairs_h;  // host copy of the kept pairs
 };
 
 namespace {
@@ -296,6 +317,153 @@ ace_status stage_input(ace_op *op, const void *src, ace_dtype dt, long long coun
 }
 
 template <typename T>
+bool find_plane_ops(int n2, int n3, ace::PlaneOps<T> *out);
+template <>
+bool find_plane_ops<float>(int n2, int n3, ace::PlaneOps<float> *out) {
+  return ace::plane_ops_f32_small(n2, n3, out) || ace::plane_ops_f32_large(n2, n3, out);
+}
+template <>
+bool find_plane_ops<double>(int n2, int n3, ace::PlaneOps<double> *out) {
+  return ace::plane_ops_f64(n2, n3, out);
+}
+
+// Five pencil passes per batch of packs (any compiled grid).
+template <typename T>
+ace_status run_chain_pencil(ace_op *op, const T *phi, const T *Kd, const cpx<T> *const *twd, int count,
+                            std::vector<void *> &temps) {
+  const ace_desc &d = op->desc;
+  const long long N = op->N;
+  cudaStream_t st = op->stream;
+  const int npacks = (count + 1) / 2;
+  const double scratch_budget = (double)env_int("ACE_SCRATCH_MB", 64) * 1048576.0;
+  int batch = (int)std::max(1.0, std::floor(scratch_budget / (double)(sizeof(cpx<T>) * N)));
+  batch = std::min(batch, std::max(npacks, 1));
+  batch = std::min(batch, 65535);
+  void *tmp = nullptr;
+  ACE_CUDA(cudaMallocAsync(&tmp, sizeof(cpx<T>) * (size_t)N * batch, st), "alloc scratch");
+  temps.push_back(tmp);
+  ace::PairPassArgs<T> a;
+  a.phi = phi;
+  a.W = static_cast<T *>(op->W);
+  a.scratch = static_cast<cpx<T> *>(tmp);
+  a.packs = op->packs;
+  a.kernel = Kd;
+  a.N = N;
+  a.n1 = d.n[0];
+  a.n2 = d.n[1];
+  a.n3 = d.n[2];
+  for (int p0 = 0; p0 < npacks; p0 += batch) {
+    const int nb = std::min(batch, npacks - p0);
+    a.pack0 = p0;
+    const int modes[5] = {ace::PASS_FWD3_PAIR, ace::PASS_FWD2, ace::PASS_CONV1, ace::PASS_INV2, ace::PASS_INV3_ACC};
+    const int axis[5] = {2, 1, 0, 1, 2};
+    for (int k = 0; k < 5; ++k) {
+      a.tw = twd[axis[k]];
+      ACE_CUDA(ace::launch_pair_pass<T>(modes[k], a, nb, st), "pair pass");
+      ++op->launches;
+    }
+  }
+  return ACE_OK;
+}
+
+// Plane, pencil, plane per batch; packs grouped by their shared first orbital.
+template <typename T>
+ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, const ace::PlaneOps<T> &pops,
+                           int count, std::vector<void *> &temps) {
+  const ace_desc &d = op->desc;
+  const long long N = op->N;
+  cudaStream_t st = op->stream;
+  const int G = std::max(1, env_int("ACE_GROUP", 2));
+  const int B = std::max(G, env_int("ACE_PLANE_BATCH", 8));
+  const bool acc = pops.acc_fits && G > 1;
+  // packs: two pairs of one row (i, j1), (i, j2); leftover single pairs of different rows are
+  // packed together at the end as mixed packs
+  std::vector<int4> packs;
+  std::vector<int4> groups;
+  std::vector<int2> left;
+  const std::vector<int2> &pr = op->pairs_h;
+  size_t r0 = 0;
+  while (r0 < pr.size()) {
+    size_t r1 = r0;
+    while (r1 < pr.size() && pr[r1].x == pr[r0].x) ++r1;
+    const int row = pr[r0].x;
+    size_t k = r0;
+    const int gfirst = (int)packs.size();
+    for (; k + 1 < r1; k += 2) packs.push_back(make_int4(row, pr[k].y, row, pr[k + 1].y));
+    if (k < r1) left.push_back(pr[k]);
+    for (int g0 = gfirst; g0 < (int)packs.size(); g0 += G)
+      groups.push_back(make_int4(g0, std::min(G, (int)packs.size() - g0), acc ? row : -1, 0));
+    r0 = r1;
+  }
+  for (size_t k = 0; k < left.size(); k += 2) {
+    const int2 p = left[k];
+    const int2 q = (k + 1 < left.size()) ? left[k + 1] : make_int2(-1, -1);
+    groups.push_back(make_int4((int)packs.size(), 1, -1, 0));
+    packs.push_back(make_int4(p.x, p.y, q.x, q.y));
+  }
+  // batches of whole groups holding at most B packs
+  std::vector<int2> batches;  // (first group, end group)
+  {
+    int gb = 0, cnt = 0;
+    for (int g = 0; g < (int)groups.size(); ++g) {
+      if (cnt + groups[g].y > B && g > gb) {
+        batches.push_back(make_int2(gb, g));
+        gb = g;
+        cnt = 0;
+      }
+      cnt += groups[g].y;
+    }
+    if (gb < (int)groups.size()) batches.push_back(make_int2(gb, (int)groups.size()));
+  }
+  void *tmp = nullptr;
+  ACE_CUDA(cudaMallocAsync(&tmp, sizeof(int4) * (packs.size() + groups.size()), st), "alloc packs");
+  temps.push_back(tmp);
+  int4 *packs_d = static_cast<int4 *>(tmp);
+  int4 *groups_d = packs_d + packs.size();
+  std::vector<int4> up(packs);
+  up.insert(up.end(), groups.begin(), groups.end());
+  ACE_CUDA(cudaMemcpyAsync(packs_d, up.data(), sizeof(int4) * up.size(), cudaMemcpyHostToDevice, st), "pack upload");
+  ACE_CUDA(cudaMallocAsync(&tmp, sizeof(cpx<T>) * (size_t)N * B, st), "alloc scratch");
+  temps.push_back(tmp);
+  cpx<T> *scratch = static_cast<cpx<T> *>(tmp);
+
+  ace::PlaneArgs<T> pa;
+  pa.phi = phi;
+  pa.W = static_cast<T *>(op->W);
+  pa.scratch = scratch;
+  pa.packs = packs_d;
+  pa.groups = groups_d;
+  pa.tw2 = static_cast<const cpx<T> *>(tab->tw[1]);
+  pa.tw3 = static_cast<const cpx<T> *>(tab->tw[2]);
+  pa.N = N;
+  pa.n1 = d.n[0];
+  ace::PairPassArgs<T> ca;
+  ca.phi = phi;
+  ca.W = static_cast<T *>(op->W);
+  ca.scratch = scratch;
+  ca.packs = packs_d;
+  ca.kernel = static_cast<const T *>(tab->Kperm);
+  ca.tw = static_cast<const cpx<T> *>(tab->tw[0]);
+  ca.N = N;
+  ca.n1 = d.n[0];
+  ca.n2 = d.n[1];
+  ca.n3 = d.n[2];
+  for (const int2 &b : batches) {
+    const int p0 = groups[b.x].x;
+    const int p1 = groups[b.y - 1].x + groups[b.y - 1].y;
+    pa.pack0 = p0;
+    pa.batch0 = p0;
+    pa.group0 = b.x;
+    ca.pack0 = p0;
+    ACE_CUDA(pops.fwd(pa, p1 - p0, st), "plane forward");
+    ACE_CUDA(ace::launch_pair_pass<T>(ace::PASS_CONV1, ca, p1 - p0, st), "pencil pass");
+    ACE_CUDA(pops.inv(pa, b.y - b.x, acc, st), "plane inverse");
+    op->launches += 3;
+  }
+  return ACE_OK;
+}
+
+template <typename T>
 ace_status build_impl(ace_op *op, const void *phi_in, ace_dtype dtype) {
   const ace_desc &d = op->desc;
   const int n = op->n;
@@ -346,47 +514,27 @@ ace_status build_impl(ace_op *op, const void *phi_in, ace_dtype dtype) {
            "compact");
   ++op->launches;
   int count = 0;
+  op->pairs_h.resize((size_t)n * (n + 1) / 2);
   ACE_CUDA(cudaMemcpyAsync(&count, op->count_d, sizeof(int), cudaMemcpyDeviceToHost, st), "count readback");
+  ACE_CUDA(cudaMemcpyAsync(op->pairs_h.data(), op->pairs, sizeof(int2) * op->pairs_h.size(), cudaMemcpyDeviceToHost,
+                           st),
+           "pair readback");
   ACE_CUDA(cudaStreamSynchronize(st), "count readback");
   op->npairs = count;
+  op->pairs_h.resize(count);
   ACE_CUDA(cudaEventRecord(op->ev[1], st), "event record");
 
   // ---- pair chain (Eq. vx, Eq. e:vij): W_i = sum_j v_ij phi_j ----
   ACE_CUDA(op_alloc(op, &op->W, op->esz * (size_t)n * N), "alloc W");
   ACE_CUDA(cudaMemsetAsync(op->W, 0, op->esz * (size_t)n * N, st), "zero W");
-  const int npacks = (count + 1) / 2;
-  const double scratch_budget = (double)env_int("ACE_SCRATCH_MB", 64) * 1048576.0;
-  int batch = (int)std::max(1.0, std::floor(scratch_budget / (double)(sizeof(cpx<T>) * N)));
-  batch = std::min(batch, std::max(npacks, 1));
-  batch = std::min(batch, 65535);
-  if (npacks > 0) {
-    cpx<T> *scratch = nullptr;
-    ACE_CUDA(cudaMallocAsync(&tmp, sizeof(cpx<T>) * (size_t)N * batch, st), "alloc scratch");
-    temps.push_back(tmp);
-    scratch = static_cast<cpx<T> *>(tmp);
-    ace::PairPassArgs<T> a;
-    a.phi = phi;
-    a.W = static_cast<T *>(op->W);
-    a.scratch = scratch;
-    a.packs = op->packs;
-    a.kernel = Kd;
-    a.N = N;
-    a.n1 = d.n[0];
-    a.n2 = d.n[1];
-    a.n3 = d.n[2];
-    for (int p0 = 0; p0 < npacks; p0 += batch) {
-      const int nb = std::min(batch, npacks - p0);
-      a.pack0 = p0;
-      const int modes[5] = {ace::PASS_FWD3_PAIR, ace::PASS_FWD2, ace::PASS_CONV1, ace::PASS_INV2,
-                            ace::PASS_INV3_ACC};
-      const int axis[5] = {2, 1, 0, 1, 2};
-      for (int k = 0; k < 5; ++k) {
-        a.tw = twd[axis[k]];
-        ACE_CUDA(ace::launch_pair_pass<T>(modes[k], a, nb, st), "pair pass");
-        ++op->launches;
-      }
-    }
+  ace::PlaneOps<T> pops{};
+  const bool plane = find_plane_ops<T>(d.n[1], d.n[2], &pops) && env_int("ACE_FORCE_PENCIL", 0) == 0;
+  if (count > 0 && plane) {
+    s = run_chain_plane<T>(op, phi, tab, pops, count, temps);
+  } else if (count > 0) {
+    s = run_chain_pencil<T>(op, phi, Kd, twd, count, temps);
   }
+  if (s != ACE_OK) return s;
   ACE_CUDA(cudaEventRecord(op->ev[2], st), "event record");
 
   // ---- M = -dV Phi^T W (App. A) ----
@@ -400,7 +548,14 @@ ace_status build_impl(ace_op *op, const void *phi_in, ace_dtype dtype) {
   ACE_CUDA(cudaEventRecord(op->ev[3], st), "event record");
 
   // ---- -M = L L^T, L^-1, E_x = (f/2) tr M ----
-  ACE_CUDA(ace::launch_cholesky(op->M_raw, n, d.spin_factor, op->M, op->L, op->Linv, op->energy_d, op->status_d, st),
+  double *chol_work = nullptr;
+  if (n > 128) {
+    ACE_CUDA(cudaMallocAsync(&tmp, sizeof(double) * ((size_t)n * n + n), st), "alloc cholesky workspace");
+    temps.push_back(tmp);
+    chol_work = static_cast<double *>(tmp);
+  }
+  ACE_CUDA(ace::launch_cholesky(op->M_raw, n, d.spin_factor, op->M, op->L, op->Linv, op->energy_d, op->status_d,
+                                chol_work, st),
            "cholesky");
   ++op->launches;
   ACE_CUDA(cudaEventRecord(op->ev[4], st), "event record");

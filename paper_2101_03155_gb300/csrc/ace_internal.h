@@ -35,12 +35,43 @@ struct PairPassArgs {
   int n1, n2, n3;
 };
 
+// Arguments of the three-pass (plane, pencil, plane) chain.
+template <typename T>
+struct PlaneArgs {
+  const T *phi;        // [norb][N]
+  T *W;                // [norb][N]
+  cpx<T> *scratch;     // [batch][N], pack p of the launch at p - batch0
+  const int4 *packs;   // all packs of the build
+  const int4 *groups;  // (first pack, pack count, shared first orbital or -1, 0)
+  int pack0;           // forward pass: first pack of this launch
+  int group0;          // inverse pass: first group of this launch
+  int batch0;          // first pack of the batch held in the scratch
+  const cpx<T> *tw2;   // [N2] e^{-2 pi i e / N2}
+  const cpx<T> *tw3;   // [N3] e^{-2 pi i e / N3}
+  long long N;
+  int n1;
+};
+
+// Plane passes for one (N2, N3) plane shape; absent shapes fall back to the five pencil passes.
+template <typename T>
+struct PlaneOps {
+  cudaError_t (*fwd)(const PlaneArgs<T> &, int npacks, cudaStream_t);
+  cudaError_t (*inv)(const PlaneArgs<T> &, int ngroups, bool acc, cudaStream_t);
+  bool acc_fits;  // the inverse pass can keep a plane of W_i partial sums in shared memory
+};
+bool plane_ops_f32_small(int n2, int n3, PlaneOps<float> *out);
+bool plane_ops_f32_large(int n2, int n3, PlaneOps<float> *out);
+bool plane_ops_f64(int n2, int n3, PlaneOps<double> *out);
+
 // Launch one pass over `npacks` packs (grid.y); returns cudaErrorInvalidValue if the axis
 // length has no compiled plan.
 template <typename T>
 cudaError_t launch_pair_pass(int mode, const PairPassArgs<T> &a, int npacks, cudaStream_t st);
 
 bool pass_length_supported(int L);
+// Two-stage factorisation L = r1 * r2 of a compiled axis length (output index k sits at
+// position (k % r1) * r2 + k / r1 after a forward transform).
+bool axis_factors(int L, int *r1, int *r2);
 
 // Dense steps.
 template <typename T>
@@ -49,8 +80,9 @@ cudaError_t launch_gram(const T *X, int nx, const T *Y, int ny, long long K, dou
 template <typename T>
 cudaError_t launch_left_mul(const T *A, int m, int n, const T *Y, long long K, T *Z, cudaStream_t st);
 
+// gwork: n*n + n doubles of device workspace, needed when n > 128 (else may be NULL)
 cudaError_t launch_cholesky(const double *M_raw, int n, double spin_factor, double *M, double *L, double *Linv,
-                            double *energy, int *status, cudaStream_t st);
+                            double *energy, int *status, double *gwork, cudaStream_t st);
 cudaError_t launch_screen_compact(const double *O, int n, double rho_cut, int2 *pairs, int4 *packs,
                                   int *count, double *O_sym, cudaStream_t st);
 

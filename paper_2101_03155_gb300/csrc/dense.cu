@@ -191,30 +191,36 @@ template cudaError_t launch_left_mul<double>(const double *, int, int, const dou
                                              cudaStream_t);
 
 // ----------------------------------------------------------------------------------------
-// Cholesky of -M (one CTA, right-looking, FP64 in global memory), L^-1, E_x.
+// Cholesky of -M, L^-1 and E_x in one CTA (FP64).  A = -M lives in shared memory when n <= 128
+// (n^2 doubles), else in a global workspace.  Right-looking factorisation, then the in-place
+// inversion of the lower triangle column by column from the last (each column is a triangular
+// matrix-vector product with the already inverted trailing block).
 // status: 0 ok; 1000000 + j: pivot j of -M not positive; 2000000: non-finite entry in M.
 // ----------------------------------------------------------------------------------------
 constexpr int CH_NT = 1024;
+constexpr int CH_SMEM_MAX_N = 128;
 
 __global__ void __launch_bounds__(CH_NT) cholesky_kernel(const double *__restrict__ M_raw, int n, double spin_factor,
                                                          double *__restrict__ M, double *__restrict__ L,
                                                          double *__restrict__ Linv, double *__restrict__ energy,
-                                                         int *__restrict__ status) {
+                                                         int *__restrict__ status, double *__restrict__ gwork) {
+  extern __shared__ double dyn[];
   __shared__ int bad;
   __shared__ double red[CH_NT / 32];
+  const bool in_smem = n <= CH_SMEM_MAX_N;
+  double *A = in_smem ? dyn : gwork;                       // n * n
+  double *tmp = in_smem ? dyn + n * n : gwork + n * n;     // n
   const int tid = threadIdx.x;
   if (tid == 0) bad = 0;
   __syncthreads();
-  // symmetrise; A = -M kept in L's storage (lower part used), upper part cleared at the end
   for (int e = tid; e < n * n; e += CH_NT) {
     const int i = e / n, j = e % n;
     const double v = 0.5 * (M_raw[(long long)i * n + j] + M_raw[(long long)j * n + i]);
     M[e] = v;
-    L[e] = -v;
-    if (!isfinite(v)) atomicExch(&bad, 2000000);
+    A[e] = -v;
+    if (!isfinite(v)) bad = 2000000;
   }
   __syncthreads();
-  // E_x = (f/2) tr M
   double part = 0.0;
   for (int k = tid; k < n; k += CH_NT) part += M[(long long)k * n + k];
   for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
@@ -229,56 +235,63 @@ __global__ void __launch_bounds__(CH_NT) cholesky_kernel(const double *__restric
     if (tid == 0) *status = bad;
     return;
   }
+  // factorisation, lower triangle of A
   for (int j = 0; j < n; ++j) {
-    const double d = L[(long long)j * n + j];
+    const double d = A[j * n + j];
     if (!(d > 0.0) || !isfinite(d)) {
       if (tid == 0) *status = 1000000 + j;
-      return;  // uniform: every thread read the same d
+      return;  // every thread read the same d
     }
-    const double ljj = sqrt(d);
+    const double r = sqrt(d);
+    const double rinv = 1.0 / r;
+    for (int i = j + 1 + tid; i < n; i += CH_NT) A[i * n + j] *= rinv;
     __syncthreads();
-    for (int i = j + 1 + tid; i < n; i += CH_NT) L[(long long)i * n + j] /= ljj;
-    if (tid == 0) L[(long long)j * n + j] = ljj;
-    __syncthreads();
-    // trailing update of the lower triangle: A[i][k] -= L[i][j] L[k][j], j < k <= i
+    if (tid == 0) A[j * n + j] = r;
     const int m = n - j - 1;
-    const long long cnt = (long long)m * (m + 1) / 2;
-    for (long long e = tid; e < cnt; e += CH_NT) {
-      // e -> (ii, kk) with 0 <= kk <= ii < m
-      int ii = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
-      while ((long long)ii * (ii + 1) / 2 > e) --ii;
-      while ((long long)(ii + 1) * (ii + 2) / 2 <= e) ++ii;
-      const int kk = (int)(e - (long long)ii * (ii + 1) / 2);
-      const int i = j + 1 + ii, k = j + 1 + kk;
-      L[(long long)i * n + k] -= L[(long long)i * n + j] * L[(long long)k * n + j];
+    for (int e = tid; e < m * m; e += CH_NT) {
+      const int ii = e / m, kk = e - ii * m;
+      if (kk <= ii) {
+        const int i = j + 1 + ii, k = j + 1 + kk;
+        A[i * n + k] -= A[i * n + j] * A[k * n + j];
+      }
     }
     __syncthreads();
   }
-  // clear the strict upper triangle
   for (int e = tid; e < n * n; e += CH_NT) {
     const int i = e / n, j = e % n;
-    if (j > i) L[e] = 0.0;
+    L[e] = (j <= i) ? A[e] : 0.0;
   }
   __syncthreads();
-  // L^-1 by forward substitution, one column per thread
-  for (int c = tid; c < n; c += CH_NT) {
-    for (int i = 0; i < n; ++i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      if (i >= c) {
-        for (int l = c; l < i; ++l) s -= L[(long long)i * n + l] * Linv[(long long)l * n + c];
-        s /= L[(long long)i * n + i];
-      } else {
-        s = 0.0;
-      }
-      Linv[(long long)i * n + c] = s;
+  // in-place inverse of the lower triangle: for j = n-1 .. 0,
+  //   A[j][j] = 1 / L[j][j];  A[j+1:, j] = -A[j][j] * (Linv_trailing * L[j+1:, j])
+  for (int j = n - 1; j >= 0; --j) {
+    const double ajj = 1.0 / A[j * n + j];
+    for (int i = j + 1 + tid; i < n; i += CH_NT) {
+      double s = 0.0;
+      for (int k = j + 1; k <= i; ++k) s += A[i * n + k] * A[k * n + j];
+      tmp[i] = -ajj * s;
     }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < n; i += CH_NT) A[i * n + j] = tmp[i];
+    if (tid == 0) A[j * n + j] = ajj;
+    __syncthreads();
+  }
+  for (int e = tid; e < n * n; e += CH_NT) {
+    const int i = e / n, j = e % n;
+    Linv[e] = (j <= i) ? A[e] : 0.0;
   }
   if (tid == 0) *status = 0;
 }
 
 cudaError_t launch_cholesky(const double *M_raw, int n, double spin_factor, double *M, double *L, double *Linv,
-                            double *energy, int *status, cudaStream_t st) {
-  cholesky_kernel<<<1, CH_NT, 0, st>>>(M_raw, n, spin_factor, M, L, Linv, energy, status);
+                            double *energy, int *status, double *gwork, cudaStream_t st) {
+  const size_t smem = n <= CH_SMEM_MAX_N ? sizeof(double) * ((size_t)n * n + n) : 0;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (n > CH_SMEM_MAX_N && gwork == nullptr) return cudaErrorInvalidValue;
+  cholesky_kernel<<<1, CH_NT, smem, st>>>(M_raw, n, spin_factor, M, L, Linv, energy, status, gwork);
   return cudaGetLastError();
 }
 

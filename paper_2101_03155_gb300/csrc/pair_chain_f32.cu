@@ -7,6 +7,20 @@ cudaError_t launch_pair_pass<float>(int mode, const PairPassArgs<float> &a, int 
   return launch_pair_pass_impl<float>(mode, a, npacks, st);
 }
 
+bool axis_factors(int L, int *r1, int *r2) {
+  switch (L) {
+#define ACE_CASE(L_)        \
+  case L_:                  \
+    *r1 = Factor<L_>::R1;   \
+    *r2 = Factor<L_>::R2;   \
+    return true;
+    ACE_PASS_LENGTHS(ACE_CASE)
+#undef ACE_CASE
+    default:
+      return false;
+  }
+}
+
 bool pass_length_supported(int L) {
   switch (L) {
 #define ACE_CASE(L_) case L_:

@@ -1,0 +1,329 @@
+// plane_chain.cuh -- three-pass pair-potential chain: forward plane FFT (axes 3 and 2 of one
+// N2 x N3 plane in shared memory), the axis-1 pencil pass (forward, kernel multiply, inverse), and
+// the inverse plane FFT fused with the accumulation of W (Eq. vx, Eq. e:vij in reciprocal space).
+//
+// Spectrum layout in the scratch: [pack][i1][p2][p3] where p2, p3 are the positions the two-stage
+// transform leaves its output in (natural index k = k1 + R1 k2 sits at p = k1 R2 + k2).  The
+// axis-1 pass reads the Coulomb table in the same permuted layout, and the inverse plane pass
+// starts from permuted input and returns natural order, so no reordering pass is needed.
+//
+// The inverse pass handles a group of packs whose pairs all share the first orbital i (pairs
+// (i, j1), (i, j2), ...): the W_i contributions v_ij phi_j are summed in shared memory over the
+// group and added to W_i once; W_j += v_ij phi_i uses 16-byte vector atomics (FP32).
+#pragma once
+
+#include "ace_internal.h"
+#include "fft.cuh"
+
+namespace ace {
+
+template <int N2, int N3>
+struct PlaneShape {
+  static constexpr int R1c = Factor<N2>::R1, R2c = Factor<N2>::R2;  // axis 2 (columns of the plane)
+  static constexpr int R1r = Factor<N3>::R1, R2r = Factor<N3>::R2;  // axis 3 (rows of the plane)
+  static constexpr int PP = N3 + 1;                                  // odd pitch (complex elements)
+  static constexpr int NPTS = N2 * N3;
+  static_assert(N3 % 4 == 0, "rows are processed in groups of four points");
+};
+
+template <typename T, int NT>
+struct PlaneStages {
+  // stage 1 over NL lines of length L (element p of line l at s[l*LS + p*PS]):
+  //   tasks (l, n2): DFT_R1 over n1 of x[n1 R2 + n2]; optional twiddle w_L^{D n2 k1}; result k1 at k1 R2 + n2
+  template <int L, int NL, int LS, int PS, int D, bool TW>
+  static __device__ __forceinline__ void stage1(cpx<T> *s, const cpx<T> *tw) {
+    constexpr int R1 = Factor<L>::R1, R2 = Factor<L>::R2;
+    for (int task = threadIdx.x; task < NL * R2; task += NT) {
+      const int l = task % NL, n2 = task / NL;
+      cpx<T> *line = s + l * LS + n2 * PS;
+      cpx<T> x[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) x[n1] = line[n1 * R2 * PS];
+      Dft<R1, D, T>::run(x);
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) {
+        cpx<T> v = x[k1];
+        if (TW && k1 > 0) {
+          const cpx<T> w = tw[n2 * k1];
+          v = cmul(v, D < 0 ? w : cpx<T>{w.x, -w.y});
+        }
+        line[k1 * R2 * PS] = v;
+      }
+    }
+  }
+  // stage 2: tasks (l, k1): DFT_R2 of the contiguous block k1 R2 + n2; output k2 at k1 R2 + k2
+  template <int L, int NL, int LS, int PS, int D>
+  static __device__ __forceinline__ void stage2(cpx<T> *s) {
+    constexpr int R1 = Factor<L>::R1, R2 = Factor<L>::R2;
+    for (int task = threadIdx.x; task < NL * R1; task += NT) {
+      const int l = task % NL, k1 = task / NL;
+      cpx<T> *blk = s + l * LS + k1 * R2 * PS;
+      cpx<T> x[R2];
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) x[n2] = blk[n2 * PS];
+      Dft<R2, D, T>::run(x);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) blk[k2 * PS] = x[k2];
+    }
+  }
+  // inverse stage A (permuted input): tasks (l, k1): inverse DFT_R2 over k2 of the block
+  // k1 R2 + k2, conjugate twiddle w_L^{+n2 k1}; result n2 at k1 R2 + n2
+  template <int L, int NL, int LS, int PS>
+  static __device__ __forceinline__ void inv_stageA(cpx<T> *s, const cpx<T> *tw) {
+    constexpr int R1 = Factor<L>::R1, R2 = Factor<L>::R2;
+    for (int task = threadIdx.x; task < NL * R1; task += NT) {
+      const int l = task % NL, k1 = task / NL;
+      cpx<T> *blk = s + l * LS + k1 * R2 * PS;
+      cpx<T> x[R2];
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) x[k2] = blk[k2 * PS];
+      Dft<R2, +1, T>::run(x);
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) {
+        cpx<T> v = x[n2];
+        if (n2 > 0 && k1 > 0) {
+          const cpx<T> w = tw[n2 * k1];
+          v = cmul(v, cpx<T>{w.x, -w.y});
+        }
+        blk[n2 * PS] = v;
+      }
+    }
+  }
+};
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  static __device__ __forceinline__ void load(const float *p, float (&v)[4]) {
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+  }
+  static __device__ __forceinline__ void add(float *p, const float (&v)[4]) {
+    atomicAdd(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+  }
+};
+template <>
+struct Vec4<double> {
+  static __device__ __forceinline__ void load(const double *p, double (&v)[4]) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+  }
+  static __device__ __forceinline__ void add(double *p, const double (&v)[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) atomicAdd(p + k, v[k]);
+  }
+};
+
+// ---------------------------------------------------------------------------------------
+// Forward plane pass: one CTA per (plane i1, pack).
+// ---------------------------------------------------------------------------------------
+template <typename T, int N2, int N3, int NT>
+__global__ void __launch_bounds__(NT) plane_fwd_kernel(PlaneArgs<T> a) {
+  using S = PlaneShape<N2, N3>;
+  using F = PlaneStages<T, NT>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T> *s = reinterpret_cast<cpx<T> *>(smem_raw);
+  cpx<T> *tw2 = s + N2 * S::PP;
+  cpx<T> *tw3 = tw2 + N2;
+  const int tid = threadIdx.x;
+  const int i1 = blockIdx.x;
+  const int pidx = a.pack0 + blockIdx.y;
+  const int4 pk = a.packs[pidx];
+  for (int e = tid; e < N2; e += NT) tw2[e] = a.tw2[e];
+  for (int e = tid; e < N3; e += NT) tw3[e] = a.tw3[e];
+
+  const long long off = (long long)i1 * S::NPTS;
+  const T *pa = a.phi + (long long)pk.x * a.N + off;
+  const T *pb = a.phi + (long long)pk.y * a.N + off;
+  const bool two = pk.z >= 0;
+  const T *pc = a.phi + (long long)(two ? pk.z : 0) * a.N + off;
+  const T *pd = a.phi + (long long)(two ? pk.w : 0) * a.N + off;
+  for (int e4 = tid; e4 < S::NPTS / 4; e4 += NT) {
+    const int e = 4 * e4, i2 = e / N3, i3 = e - i2 * N3;
+    T va[4], vb[4], vc[4] = {0, 0, 0, 0}, vd[4] = {0, 0, 0, 0};
+    Vec4<T>::load(pa + e, va);
+    Vec4<T>::load(pb + e, vb);
+    if (two) {
+      Vec4<T>::load(pc + e, vc);
+      Vec4<T>::load(pd + e, vd);
+    }
+    cpx<T> *row = s + i2 * S::PP + i3;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) row[k] = cpx<T>{va[k] * vb[k], vc[k] * vd[k]};
+  }
+  __syncthreads();
+  // axis 3 (rows): natural -> permuted
+  F::template stage1<N3, N2, S::PP, 1, -1, true>(s, tw3);
+  __syncthreads();
+  F::template stage2<N3, N2, S::PP, 1, -1>(s);
+  __syncthreads();
+  // axis 2 (columns): stage 1 in shared memory, stage 2 straight to the scratch plane
+  F::template stage1<N2, N3, 1, S::PP, -1, true>(s, tw2);
+  __syncthreads();
+  cpx<T> *dst = a.scratch + (long long)(pidx - a.batch0) * a.N + off;
+  for (int task = tid; task < N3 * S::R1c; task += NT) {
+    const int p3 = task % N3, k1 = task / N3;
+    cpx<T> x[S::R2c];
+#pragma unroll
+    for (int n2 = 0; n2 < S::R2c; ++n2) x[n2] = s[(k1 * S::R2c + n2) * S::PP + p3];
+    Dft<S::R2c, -1, T>::run(x);
+#pragma unroll
+    for (int k2 = 0; k2 < S::R2c; ++k2) dst[(k1 * S::R2c + k2) * N3 + p3] = x[k2];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Inverse plane pass fused with the W accumulation: one CTA per (plane i1, group).
+// Group g covers packs [gstart, gstart + glen); grow >= 0 means every pair of the group has
+// first orbital grow (accumulated in shared memory), grow < 0 a single mixed pack.
+// ---------------------------------------------------------------------------------------
+template <typename T, int N2, int N3, int NT, bool ACC>
+__global__ void __launch_bounds__(NT) plane_inv_kernel(PlaneArgs<T> a) {
+  using S = PlaneShape<N2, N3>;
+  using F = PlaneStages<T, NT>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T> *s = reinterpret_cast<cpx<T> *>(smem_raw);
+  cpx<T> *tw2 = s + N2 * S::PP;
+  cpx<T> *tw3 = tw2 + N2;
+  T *acc = reinterpret_cast<T *>(tw3 + N3);  // NPTS values when ACC
+  const int tid = threadIdx.x;
+  const int i1 = blockIdx.x;
+  const int4 grp = a.groups[a.group0 + blockIdx.y];  // (start pack, count, row, unused)
+  const int grow = grp.z;
+  for (int e = tid; e < N2; e += NT) tw2[e] = a.tw2[e];
+  for (int e = tid; e < N3; e += NT) tw3[e] = a.tw3[e];
+  const bool use_acc = ACC && grow >= 0;
+  if (use_acc)
+    for (int e = tid; e < S::NPTS; e += NT) acc[e] = (T)0;
+  const long long off = (long long)i1 * S::NPTS;
+
+  for (int q = 0; q < grp.y; ++q) {
+    const int pidx = grp.x + q;
+    const int4 pk = a.packs[pidx];
+    const cpx<T> *src = a.scratch + (long long)(pidx - a.batch0) * a.N + off;
+    __syncthreads();  // previous pack's epilogue has finished reading s
+    // axis 2 inverse, stage A straight from the scratch plane (permuted rows p2 = k1 R2c + k2)
+    for (int task = tid; task < N3 * S::R1c; task += NT) {
+      const int p3 = task % N3, k1 = task / N3;
+      cpx<T> x[S::R2c];
+#pragma unroll
+      for (int k2 = 0; k2 < S::R2c; ++k2) x[k2] = src[(k1 * S::R2c + k2) * N3 + p3];
+      Dft<S::R2c, +1, T>::run(x);
+#pragma unroll
+      for (int n2 = 0; n2 < S::R2c; ++n2) {
+        cpx<T> v = x[n2];
+        if (n2 > 0 && k1 > 0) {
+          const cpx<T> w = tw2[n2 * k1];
+          v = cmul(v, cpx<T>{w.x, -w.y});
+        }
+        s[(k1 * S::R2c + n2) * S::PP + p3] = v;
+      }
+    }
+    __syncthreads();
+    F::template stage1<N2, N3, 1, S::PP, +1, false>(s, tw2);  // inverse stage B: natural rows
+    __syncthreads();
+    F::template inv_stageA<N3, N2, S::PP, 1>(s, tw3);
+    __syncthreads();
+    F::template stage1<N3, N2, S::PP, 1, +1, false>(s, tw3);  // natural columns
+    __syncthreads();
+    // epilogue: v = v_ab + i v_cd at natural points
+    const bool two = pk.z >= 0;
+    const long long ga = (long long)pk.x * a.N + off, gb = (long long)pk.y * a.N + off;
+    const long long gc = (long long)(two ? pk.z : 0) * a.N + off, gd = (long long)(two ? pk.w : 0) * a.N + off;
+    for (int e4 = tid; e4 < S::NPTS / 4; e4 += NT) {
+      const int e = 4 * e4, i2 = e / N3, i3 = e - i2 * N3;
+      const cpx<T> *row = s + i2 * S::PP + i3;
+      T vab[4], vcd[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        vab[k] = row[k].x;
+        vcd[k] = row[k].y;
+      }
+      T fa[4], fb[4], fc[4], fd[4], t[4];
+      Vec4<T>::load(a.phi + ga + e, fa);
+      Vec4<T>::load(a.phi + gb + e, fb);
+      if (two) {
+        Vec4<T>::load(a.phi + gc + e, fc);
+        Vec4<T>::load(a.phi + gd + e, fd);
+      }
+      if (use_acc) {
+        // W_row += v_ab phi_b + v_cd phi_d  (pk.x == pk.z == grow)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[e + k] += vab[k] * fb[k] + (two ? vcd[k] * fd[k] : (T)0);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t[k] = vab[k] * fb[k];
+        Vec4<T>::add(a.W + ga + e, t);
+        if (two) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) t[k] = vcd[k] * fd[k];
+          Vec4<T>::add(a.W + gc + e, t);
+        }
+      }
+      if (pk.y != pk.x) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t[k] = vab[k] * fa[k];
+        Vec4<T>::add(a.W + gb + e, t);
+      }
+      if (two && pk.w != pk.z) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t[k] = vcd[k] * fc[k];
+        Vec4<T>::add(a.W + gd + e, t);
+      }
+    }
+  }
+  if (use_acc) {
+    __syncthreads();
+    T *wr = a.W + (long long)grow * a.N + off;
+    for (int e4 = tid; e4 < S::NPTS / 4; e4 += NT) {
+      const int e = 4 * e4;
+      T t[4] = {acc[e], acc[e + 1], acc[e + 2], acc[e + 3]};
+      Vec4<T>::add(wr + e, t);
+    }
+  }
+}
+
+template <typename T, int N2, int N3>
+struct PlaneLaunch {
+  static constexpr int NT = 384;
+  static size_t fwd_smem() { return sizeof(cpx<T>) * (N2 * PlaneShape<N2, N3>::PP + N2 + N3); }
+  static size_t inv_smem(bool acc) {
+    return fwd_smem() + (acc ? sizeof(T) * (size_t)N2 * N3 : 0);
+  }
+  static bool fits(bool acc) { return inv_smem(acc) <= 227 * 1024 && fwd_smem() <= 227 * 1024; }
+
+  static cudaError_t fwd(const PlaneArgs<T> &a, int npacks, cudaStream_t st) {
+    const size_t sm = fwd_smem();
+    cudaError_t e = cudaFuncSetAttribute(plane_fwd_kernel<T, N2, N3, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    plane_fwd_kernel<T, N2, N3, NT><<<dim3(a.n1, npacks), NT, sm, st>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t inv(const PlaneArgs<T> &a, int ngroups, bool acc, cudaStream_t st) {
+    const size_t sm = inv_smem(acc);
+    cudaError_t e;
+    if (acc) {
+      e = cudaFuncSetAttribute(plane_inv_kernel<T, N2, N3, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sm);
+      if (e != cudaSuccess) return e;
+      plane_inv_kernel<T, N2, N3, NT, true><<<dim3(a.n1, ngroups), NT, sm, st>>>(a);
+    } else {
+      e = cudaFuncSetAttribute(plane_inv_kernel<T, N2, N3, NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sm);
+      if (e != cudaSuccess) return e;
+      plane_inv_kernel<T, N2, N3, NT, false><<<dim3(a.n1, ngroups), NT, sm, st>>>(a);
+    }
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace ace

@@ -1,0 +1,17 @@
+// Instantiations of the plane passes (float) for the plane shapes listed below.
+#include "plane_chain.cuh"
+
+namespace ace {
+bool plane_ops_f32_large(int n2, int n3, PlaneOps<float> *out) {
+#define X(A, B)                                                   \
+  if (n2 == A && n3 == B && PlaneLaunch<float, A, B>::fits(false)) { \
+    out->fwd = &PlaneLaunch<float, A, B>::fwd;                       \
+    out->inv = &PlaneLaunch<float, A, B>::inv;                       \
+    out->acc_fits = PlaneLaunch<float, A, B>::fits(true);            \
+    return true;                                                  \
+  }
+  X(96,96) X(108,108) X(128,128) X(144,128) X(144,144)
+#undef X
+  return false;
+}
+}  // namespace ace
