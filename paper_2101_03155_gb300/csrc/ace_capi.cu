@@ -316,6 +316,21 @@ ace_status stage_input(ace_op *op, const void *src, ace_dtype dt, long long coun
   return ACE_OK;
 }
 
+// Per-device side streams of the pair chain (created once, non-blocking, kept until exit).
+std::mutex g_side_mu;
+cudaStream_t g_side[64][4] = {};
+
+cudaError_t get_side_stream(int dev, int k, cudaStream_t *out) {
+  if (dev < 0 || dev >= 64 || k < 0 || k >= 4) return cudaErrorInvalidValue;
+  std::lock_guard<std::mutex> lk(g_side_mu);
+  if (!g_side[dev][k]) {
+    cudaError_t e = cudaStreamCreateWithFlags(&g_side[dev][k], cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
+  *out = g_side[dev][k];
+  return cudaSuccess;
+}
+
 template <typename T>
 bool find_plane_ops(int n2, int n3, ace::PlaneOps<T> *out);
 template <>
@@ -373,8 +388,9 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   const ace_desc &d = op->desc;
   const long long N = op->N;
   cudaStream_t st = op->stream;
-  const int G = std::max(1, env_int("ACE_GROUP", 2));
-  const int B = std::max(G, env_int("ACE_PLANE_BATCH", 8));
+  const int G = std::max(1, env_int("ACE_GROUP", 1));
+  const int B = std::max(G, env_int("ACE_PLANE_BATCH", 4));
+  const int nstreams = std::min(4, std::max(1, env_int("ACE_STREAMS", 2)));
   const bool acc = pops.acc_fits && G > 1;
   // packs: two pairs of one row (i, j1), (i, j2); leftover single pairs of different rows are
   // packed together at the end as mixed packs
@@ -423,14 +439,26 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   std::vector<int4> up(packs);
   up.insert(up.end(), groups.begin(), groups.end());
   ACE_CUDA(cudaMemcpyAsync(packs_d, up.data(), sizeof(int4) * up.size(), cudaMemcpyHostToDevice, st), "pack upload");
-  ACE_CUDA(cudaMallocAsync(&tmp, sizeof(cpx<T>) * (size_t)N * B, st), "alloc scratch");
+  ACE_CUDA(cudaMallocAsync(&tmp, sizeof(cpx<T>) * (size_t)N * B * nstreams, st), "alloc scratch");
   temps.push_back(tmp);
-  cpx<T> *scratch = static_cast<cpx<T> *>(tmp);
+  cpx<T> *scratch_all = static_cast<cpx<T> *>(tmp);
+  // consecutive batches alternate between side streams (own scratch each) so that one batch's
+  // kernels fill the tail of the previous one; W is only touched by atomic adds
+  cudaStream_t side[4] = {st, st, st, st};
+  cudaEvent_t fork = nullptr;
+  if (nstreams > 1) {
+    ACE_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "event");
+    ACE_CUDA(cudaEventRecord(fork, st), "event");
+    for (int k = 0; k < nstreams; ++k) {
+      ACE_CUDA(get_side_stream(op->dev, k, &side[k]), "side stream");
+      ACE_CUDA(cudaStreamWaitEvent(side[k], fork, 0), "wait");
+    }
+  }
 
   ace::PlaneArgs<T> pa;
   pa.phi = phi;
   pa.W = static_cast<T *>(op->W);
-  pa.scratch = scratch;
+  pa.scratch = scratch_all;
   pa.packs = packs_d;
   pa.groups = groups_d;
   pa.tw2 = static_cast<const cpx<T> *>(tab->tw[1]);
@@ -440,7 +468,7 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   ace::PairPassArgs<T> ca;
   ca.phi = phi;
   ca.W = static_cast<T *>(op->W);
-  ca.scratch = scratch;
+  ca.scratch = scratch_all;
   ca.packs = packs_d;
   ca.kernel = static_cast<const T *>(tab->Kperm);
   ca.tw = static_cast<const cpx<T> *>(tab->tw[0]);
@@ -448,17 +476,28 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   ca.n1 = d.n[0];
   ca.n2 = d.n[1];
   ca.n3 = d.n[2];
-  for (const int2 &b : batches) {
+  for (size_t bi = 0; bi < batches.size(); ++bi) {
+    const int2 b = batches[bi];
+    const int k = (int)(bi % nstreams);
     const int p0 = groups[b.x].x;
     const int p1 = groups[b.y - 1].x + groups[b.y - 1].y;
+    pa.scratch = scratch_all + (size_t)k * B * N;
+    ca.scratch = pa.scratch;
     pa.pack0 = p0;
     pa.batch0 = p0;
     pa.group0 = b.x;
     ca.pack0 = p0;
-    ACE_CUDA(pops.fwd(pa, p1 - p0, st), "plane forward");
-    ACE_CUDA(ace::launch_pair_pass<T>(ace::PASS_CONV1, ca, p1 - p0, st), "pencil pass");
-    ACE_CUDA(pops.inv(pa, b.y - b.x, acc, st), "plane inverse");
+    ACE_CUDA(pops.fwd(pa, p1 - p0, side[k]), "plane forward");
+    ACE_CUDA(ace::launch_pair_pass<T>(ace::PASS_CONV1, ca, p1 - p0, side[k]), "pencil pass");
+    ACE_CUDA(pops.inv(pa, b.y - b.x, acc, side[k]), "plane inverse");
     op->launches += 3;
+  }
+  if (nstreams > 1) {
+    for (int k = 0; k < nstreams; ++k) {
+      ACE_CUDA(cudaEventRecord(fork, side[k]), "event");
+      ACE_CUDA(cudaStreamWaitEvent(st, fork, 0), "join");
+    }
+    cudaEventDestroy(fork);
   }
   return ACE_OK;
 }

@@ -7,9 +7,11 @@
 // axis-1 pass reads the Coulomb table in the same permuted layout, and the inverse plane pass
 // starts from permuted input and returns natural order, so no reordering pass is needed.
 //
-// The inverse pass handles a group of packs whose pairs all share the first orbital i (pairs
-// (i, j1), (i, j2), ...): the W_i contributions v_ij phi_j are summed in shared memory over the
-// group and added to W_i once; W_j += v_ij phi_i uses 16-byte vector atomics (FP32).
+// The inverse pass handles a group of packs whose pairs share the first orbital i (pairs (i, j1),
+// (i, j2), ...).  With one pack per group (the default) the two W_i contributions of the pack are
+// added with one atomic per point; with larger groups they are summed in shared memory over the
+// group first.  W_j += v_ij phi_i are atomic adds.  Global accesses go one point per lane
+// (coalesced) so that the shared-memory side stays free of bank conflicts.
 #pragma once
 
 #include "ace_internal.h"
@@ -146,18 +148,12 @@ __global__ void __launch_bounds__(NT) plane_fwd_kernel(PlaneArgs<T> a) {
   const bool two = pk.z >= 0;
   const T *pc = a.phi + (long long)(two ? pk.z : 0) * a.N + off;
   const T *pd = a.phi + (long long)(two ? pk.w : 0) * a.N + off;
-  for (int e4 = tid; e4 < S::NPTS / 4; e4 += NT) {
-    const int e = 4 * e4, i2 = e / N3, i3 = e - i2 * N3;
-    T va[4], vb[4], vc[4] = {0, 0, 0, 0}, vd[4] = {0, 0, 0, 0};
-    Vec4<T>::load(pa + e, va);
-    Vec4<T>::load(pb + e, vb);
-    if (two) {
-      Vec4<T>::load(pc + e, vc);
-      Vec4<T>::load(pd + e, vd);
-    }
-    cpx<T> *row = s + i2 * S::PP + i3;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) row[k] = cpx<T>{va[k] * vb[k], vc[k] * vd[k]};
+#pragma unroll 4
+  for (int e = tid; e < S::NPTS; e += NT) {
+    const int i2 = e / N3, i3 = e - i2 * N3;
+    const T re = __ldg(pa + e) * __ldg(pb + e);
+    const T im = two ? __ldg(pc + e) * __ldg(pd + e) : (T)0;
+    s[i2 * S::PP + i3] = cpx<T>{re, im};
   }
   __syncthreads();
   // axis 3 (rows): natural -> permuted
@@ -234,60 +230,38 @@ __global__ void __launch_bounds__(NT) plane_inv_kernel(PlaneArgs<T> a) {
     __syncthreads();
     F::template stage1<N3, N2, S::PP, 1, +1, false>(s, tw3);  // natural columns
     __syncthreads();
-    // epilogue: v = v_ab + i v_cd at natural points
+    // epilogue: v = v_ab + i v_cd at natural points, one point per lane
     const bool two = pk.z >= 0;
-    const long long ga = (long long)pk.x * a.N + off, gb = (long long)pk.y * a.N + off;
-    const long long gc = (long long)(two ? pk.z : 0) * a.N + off, gd = (long long)(two ? pk.w : 0) * a.N + off;
-    for (int e4 = tid; e4 < S::NPTS / 4; e4 += NT) {
-      const int e = 4 * e4, i2 = e / N3, i3 = e - i2 * N3;
-      const cpx<T> *row = s + i2 * S::PP + i3;
-      T vab[4], vcd[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        vab[k] = row[k].x;
-        vcd[k] = row[k].y;
-      }
-      T fa[4], fb[4], fc[4], fd[4], t[4];
-      Vec4<T>::load(a.phi + ga + e, fa);
-      Vec4<T>::load(a.phi + gb + e, fb);
-      if (two) {
-        Vec4<T>::load(a.phi + gc + e, fc);
-        Vec4<T>::load(a.phi + gd + e, fd);
-      }
+    const bool same_a = two && pk.z == pk.x;
+    const T *fa = a.phi + (long long)pk.x * a.N + off;
+    const T *fb = a.phi + (long long)pk.y * a.N + off;
+    const T *fc = a.phi + (long long)(two ? pk.z : 0) * a.N + off;
+    const T *fd = a.phi + (long long)(two ? pk.w : 0) * a.N + off;
+    T *wa = a.W + (long long)pk.x * a.N + off;
+    T *wb = a.W + (long long)pk.y * a.N + off;
+    T *wc = a.W + (long long)(two ? pk.z : 0) * a.N + off;
+    T *wd = a.W + (long long)(two ? pk.w : 0) * a.N + off;
+#pragma unroll 2
+    for (int e = tid; e < S::NPTS; e += NT) {
+      const int i2 = e / N3, i3 = e - i2 * N3;
+      const cpx<T> v = s[i2 * S::PP + i3];
+      const T pa_ = __ldg(fa + e), pb_ = __ldg(fb + e);
+      const T pc_ = two ? __ldg(fc + e) : (T)0, pd_ = two ? __ldg(fd + e) : (T)0;
+      const T to_a = v.x * pb_ + (same_a ? v.y * pd_ : (T)0);
       if (use_acc) {
-        // W_row += v_ab phi_b + v_cd phi_d  (pk.x == pk.z == grow)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[e + k] += vab[k] * fb[k] + (two ? vcd[k] * fd[k] : (T)0);
+        acc[e] += to_a;  // pk.x == grow (and pk.z == grow when two)
       } else {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) t[k] = vab[k] * fb[k];
-        Vec4<T>::add(a.W + ga + e, t);
-        if (two) {
-#pragma unroll
-          for (int k = 0; k < 4; ++k) t[k] = vcd[k] * fd[k];
-          Vec4<T>::add(a.W + gc + e, t);
-        }
+        atomicAdd(wa + e, to_a);
+        if (two && !same_a) atomicAdd(wc + e, v.y * pd_);
       }
-      if (pk.y != pk.x) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) t[k] = vab[k] * fa[k];
-        Vec4<T>::add(a.W + gb + e, t);
-      }
-      if (two && pk.w != pk.z) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) t[k] = vcd[k] * fc[k];
-        Vec4<T>::add(a.W + gd + e, t);
-      }
+      if (pk.y != pk.x) atomicAdd(wb + e, v.x * pa_);
+      if (two && pk.w != pk.z) atomicAdd(wd + e, v.y * pc_);
     }
   }
   if (use_acc) {
     __syncthreads();
     T *wr = a.W + (long long)grow * a.N + off;
-    for (int e4 = tid; e4 < S::NPTS / 4; e4 += NT) {
-      const int e = 4 * e4;
-      T t[4] = {acc[e], acc[e + 1], acc[e + 2], acc[e + 3]};
-      Vec4<T>::add(wr + e, t);
-    }
+    for (int e = tid; e < S::NPTS; e += NT) atomicAdd(wr + e, acc[e]);
   }
 }
 
