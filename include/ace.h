@@ -88,8 +88,8 @@ ace_status ace_build_batched(int k, const ace_desc *desc, const void *const *phi
 
 /* Apply the ACE operator (section II): out = -xi (dV xi^T psi) = V_X^ACE psi, dense (no screen).
  *   psi, out: [m][N1][N2][N3] of `dtype`, host or device (both on the same side), m >= 1.
- * Stream-ordered on `cuda_stream`; returns after the work is enqueued (device buffers) or after
- * the result has been copied back (host buffers). */
+ * Runs on `cuda_stream` and returns after the result is complete (it reads back a device error
+ * flag).  Errors: ACE_ERR_ARG, ACE_ERR_CUDA, ACE_ERR_OOM, ACE_ERR_TIMEOUT. */
 ace_status ace_apply(const ace_op *op, const void *psi, ace_dtype dtype, int m, void *out,
                      void *cuda_stream);
 

@@ -225,6 +225,7 @@ struct ace_op {
   double *O = nullptr, *O_sym = nullptr, *M_raw = nullptr, *M = nullptr, *L = nullptr, *Linv = nullptr;
   double *energy_d = nullptr;
   int *status_d = nullptr, *count_d = nullptr;
+  int *tc_err = nullptr;  // set by a tensor-core kernel whose bounded wait gave up
   int2 *pairs = nullptr;
   int4 *packs = nullptr;
   long npairs = 0;
@@ -502,6 +503,37 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   return ACE_OK;
 }
 
+bool use_tc() { return env_int("ACE_NO_TC", 0) == 0; }
+
+// G = scale * X Y^T (FP64 result)
+template <typename T>
+cudaError_t dense_gram(const T *X, int nx, const T *Y, int ny, long long K, double scale, double *G, int *err,
+                       std::vector<void *> &temps, cudaStream_t st, long *launches) {
+  if constexpr (sizeof(T) == 4) {
+    if (use_tc() && ace::tc_shapes_ok(K)) {
+      void *ws = nullptr;
+      cudaError_t e = cudaMallocAsync(&ws, ace::tc_gram_workspace_bytes(nx, ny, K), st);
+      if (e != cudaSuccess) return e;
+      temps.push_back(ws);
+      *launches += 2;
+      return ace::launch_tc_gram(X, nx, Y, ny, K, scale, G, static_cast<float *>(ws), err, st);
+    }
+  }
+  *launches += 1;
+  return ace::launch_gram<T>(X, nx, Y, ny, K, scale, false, false, G, st);
+}
+
+// Z = A Y, A (m x n) in T
+template <typename T>
+cudaError_t dense_left_mul(const T *A, int m, int n, const T *Y, long long K, T *Z, int *err, cudaStream_t st,
+                           long *launches) {
+  *launches += 1;
+  if constexpr (sizeof(T) == 4) {
+    if (use_tc() && ace::tc_shapes_ok(K)) return ace::launch_tc_left_mul(A, m, n, Y, K, Z, err, st);
+  }
+  return ace::launch_left_mul<T>(A, m, n, Y, K, Z, st);
+}
+
 template <typename T>
 ace_status build_impl(ace_op *op, const void *phi_in, ace_dtype dtype) {
   const ace_desc &d = op->desc;
@@ -542,6 +574,8 @@ ace_status build_impl(ace_op *op, const void *phi_in, ace_dtype dtype) {
   ACE_CUDA(op_alloc(op, &op->packs, sizeof(int4) * ((size_t)n * (n + 1) / 4 + 2)), "alloc packs");
   ACE_CUDA(op_alloc(op, &op->count_d, sizeof(int) * 4), "alloc count");
   ACE_CUDA(op_alloc(op, &op->status_d, sizeof(int) * 4), "alloc status");
+  op->tc_err = op->status_d + 1;
+  ACE_CUDA(cudaMemsetAsync(op->status_d, 0, sizeof(int) * 4, st), "zero status");
   ACE_CUDA(op_alloc(op, &op->energy_d, sizeof(double) * 2), "alloc energy");
   if (d.rho_cut > 0.0) {
     ACE_CUDA(ace::launch_gram<T>(phi, n, phi, n, N, op->dV, true, true, op->O, st), "screen");
@@ -581,9 +615,9 @@ ace_status build_impl(ace_op *op, const void *phi_in, ace_dtype dtype) {
   ACE_CUDA(op_alloc(op, &op->M, sizeof(double) * n * n), "alloc M");
   ACE_CUDA(op_alloc(op, &op->L, sizeof(double) * n * n), "alloc L");
   ACE_CUDA(op_alloc(op, &op->Linv, sizeof(double) * n * n), "alloc Linv");
-  ACE_CUDA(ace::launch_gram<T>(phi, n, static_cast<const T *>(op->W), n, N, -op->dV, false, false, op->M_raw, st),
+  ACE_CUDA(dense_gram<T>(phi, n, static_cast<const T *>(op->W), n, N, -op->dV, op->M_raw, op->tc_err, temps, st,
+                         &op->launches),
            "M");
-  ++op->launches;
   ACE_CUDA(cudaEventRecord(op->ev[3], st), "event record");
 
   // ---- -M = L L^T, L^-1, E_x = (f/2) tr M ----
@@ -611,17 +645,19 @@ ace_status build_impl(ace_op *op, const void *phi_in, ace_dtype dtype) {
     ++op->launches;
     Linv_T = static_cast<const T *>(tmp);
   }
-  ACE_CUDA(ace::launch_left_mul<T>(Linv_T, n, n, static_cast<const T *>(op->W), N, static_cast<T *>(op->xi), st),
+  ACE_CUDA(dense_left_mul<T>(Linv_T, n, n, static_cast<const T *>(op->W), N, static_cast<T *>(op->xi), op->tc_err,
+                             st, &op->launches),
            "xi");
-  ++op->launches;
   ACE_CUDA(cudaEventRecord(op->ev[5], st), "event record");
 
-  int status = 0;
+  int status = 0, flags[2] = {0, 0};
   double energy = 0.0;
-  ACE_CUDA(cudaMemcpyAsync(&status, op->status_d, sizeof(int), cudaMemcpyDeviceToHost, st), "status readback");
+  ACE_CUDA(cudaMemcpyAsync(flags, op->status_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, st), "status readback");
   ACE_CUDA(cudaMemcpyAsync(&energy, op->energy_d, sizeof(double), cudaMemcpyDeviceToHost, st), "energy readback");
   ACE_CUDA(cudaStreamSynchronize(st), "build");
+  status = flags[0];
   op->status = status;
+  if (flags[1]) return fail(ACE_ERR_TIMEOUT, "a tensor-core kernel gave up waiting for its MMAs");
   op->energy = energy;
   for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&op->stage_ms[i], op->ev[i], op->ev[i + 1]);
   cudaEventElapsedTime(&op->stage_ms[5], op->ev[0], op->ev[5]);
@@ -654,7 +690,12 @@ ace_status apply_impl(const ace_op *op, const void *psi_in, ace_dtype dtype, int
   ACE_CUDA(cudaMallocAsync(&tmp, sizeof(double) * n * m, st), "alloc C");
   temps.push_back(tmp);
   double *C = static_cast<double *>(tmp);
-  ACE_CUDA(ace::launch_gram<T>(static_cast<const T *>(op->xi), n, psi, m, N, op->dV, false, false, C, st), "xi^T psi");
+  ACE_CUDA(cudaMallocAsync(&tmp, sizeof(int), st), "alloc flag");
+  temps.push_back(tmp);
+  int *err_d = static_cast<int *>(tmp);
+  ACE_CUDA(cudaMemsetAsync(err_d, 0, sizeof(int), st), "zero flag");
+  long nl = 0;
+  ACE_CUDA(dense_gram<T>(static_cast<const T *>(op->xi), n, psi, m, N, op->dV, C, err_d, temps, st, &nl), "xi^T psi");
   ACE_CUDA(cudaMallocAsync(&tmp, sizeof(T) * n * m, st), "alloc A");
   temps.push_back(tmp);
   T *A = static_cast<T *>(tmp);
@@ -669,7 +710,7 @@ ace_status apply_impl(const ace_op *op, const void *psi_in, ace_dtype dtype, int
     temps.push_back(tmp);
     res = static_cast<T *>(tmp);
   }
-  ACE_CUDA(ace::launch_left_mul<T>(A, m, n, static_cast<const T *>(op->xi), N, res, st), "xi C");
+  ACE_CUDA(dense_left_mul<T>(A, m, n, static_cast<const T *>(op->xi), N, res, err_d, st, &nl), "xi C");
   void *final_dev = res;
   const size_t out_bytes = (size_t)m * N * (dtype == ACE_F64 ? 8 : 4);
   if (!same) {
@@ -686,10 +727,11 @@ ace_status apply_impl(const ace_op *op, const void *psi_in, ace_dtype dtype, int
       ACE_CUDA((ace::launch_convert<T, float>(res, static_cast<float *>(conv), (long long)m * N, 1.0, st)), "conv");
     final_dev = conv;
   }
-  if (host_out) {
-    ACE_CUDA(cudaMemcpyAsync(out, final_dev, out_bytes, cudaMemcpyDeviceToHost, st), "device-to-host copy");
-    ACE_CUDA(cudaStreamSynchronize(st), "apply");
-  }
+  if (host_out) ACE_CUDA(cudaMemcpyAsync(out, final_dev, out_bytes, cudaMemcpyDeviceToHost, st), "device-to-host copy");
+  int err_h = 0;
+  ACE_CUDA(cudaMemcpyAsync(&err_h, err_d, sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
+  ACE_CUDA(cudaStreamSynchronize(st), "apply");
+  if (err_h) return fail(ACE_ERR_TIMEOUT, "a tensor-core kernel gave up waiting for its MMAs");
   return ACE_OK;
 }
 

@@ -89,6 +89,15 @@ cudaError_t launch_screen_compact(const double *O, int n, double rho_cut, int2 *
 template <typename T>
 cudaError_t launch_transpose_scale(const double *C, int n, int m, double scale, T *A, cudaStream_t st);
 
+// Tensor-core (tcgen05) BF16x3 contractions for FP32 operands.  *err is set to 1 when a bounded
+// wait inside the kernel gave up.  K must be a multiple of 128 (tc_shapes_ok).
+bool tc_shapes_ok(long long K);
+size_t tc_gram_workspace_bytes(int nx, int ny, long long K);
+cudaError_t launch_tc_gram(const float *X, int nx, const float *Y, int ny, long long K, double scale, double *G,
+                           float *partial_ws, int *err, cudaStream_t st);
+cudaError_t launch_tc_left_mul(const float *A, int m, int n, const float *Y, long long K, float *Z, int *err,
+                               cudaStream_t st);
+
 // Sets the message returned by ace_last_error() on this thread.
 void set_last_error(const char *msg);
 

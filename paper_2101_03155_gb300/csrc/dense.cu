@@ -235,25 +235,27 @@ __global__ void __launch_bounds__(CH_NT) cholesky_kernel(const double *__restric
     if (tid == 0) *status = bad;
     return;
   }
-  // factorisation, lower triangle of A
+  // factorisation, lower triangle of A; warp w and lane t cover the trailing block in a 32 x 32 pattern
+  const int warp = tid >> 5, lane = tid & 31;
+  __shared__ double piv[2];  // sqrt and reciprocal of the pivot, computed once per step
   for (int j = 0; j < n; ++j) {
     const double d = A[j * n + j];
     if (!(d > 0.0) || !isfinite(d)) {
       if (tid == 0) *status = 1000000 + j;
       return;  // every thread read the same d
     }
-    const double r = sqrt(d);
-    const double rinv = 1.0 / r;
+    if (tid == 0) {
+      piv[0] = sqrt(d);
+      piv[1] = 1.0 / piv[0];
+    }
+    __syncthreads();
+    const double r = piv[0], rinv = piv[1];
     for (int i = j + 1 + tid; i < n; i += CH_NT) A[i * n + j] *= rinv;
     __syncthreads();
     if (tid == 0) A[j * n + j] = r;
-    const int m = n - j - 1;
-    for (int e = tid; e < m * m; e += CH_NT) {
-      const int ii = e / m, kk = e - ii * m;
-      if (kk <= ii) {
-        const int i = j + 1 + ii, k = j + 1 + kk;
-        A[i * n + k] -= A[i * n + j] * A[k * n + j];
-      }
+    for (int i = j + 1 + warp; i < n; i += CH_NT / 32) {
+      const double lij = A[i * n + j];
+      for (int k = j + 1 + lane; k <= i; k += 32) A[i * n + k] -= lij * A[k * n + j];
     }
     __syncthreads();
   }
@@ -262,18 +264,25 @@ __global__ void __launch_bounds__(CH_NT) cholesky_kernel(const double *__restric
     L[e] = (j <= i) ? A[e] : 0.0;
   }
   __syncthreads();
-  // in-place inverse of the lower triangle: for j = n-1 .. 0,
-  //   A[j][j] = 1 / L[j][j];  A[j+1:, j] = -A[j][j] * (Linv_trailing * L[j+1:, j])
-  for (int j = n - 1; j >= 0; --j) {
-    const double ajj = 1.0 / A[j * n + j];
-    for (int i = j + 1 + tid; i < n; i += CH_NT) {
-      double s = 0.0;
-      for (int k = j + 1; k <= i; ++k) s += A[i * n + k] * A[k * n + j];
-      tmp[i] = -ajj * s;
-    }
+  // in-place inverse of the lower triangle by forward substitution on L X = I with rank-1
+  // updates (no reductions: GB300 retires few FP64 operations per clock).  Entry (i, c), c < i,
+  // holds L[i][c] until step c reads it and X[i][c] afterwards.  Step k:
+  //   X[k][c] /= L[k][k] (c < k), X[k][k] = 1 / L[k][k];  X[i][c] -= L[i][k] X[k][c] (i > k, c <= k)
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) piv[0] = 1.0 / A[k * n + k];
+    for (int i = k + 1 + tid; i < n; i += CH_NT) tmp[i] = A[i * n + k];
     __syncthreads();
-    for (int i = j + 1 + tid; i < n; i += CH_NT) A[i * n + j] = tmp[i];
-    if (tid == 0) A[j * n + j] = ajj;
+    const double rk = piv[0];
+    for (int c = tid; c < k; c += CH_NT) A[k * n + c] *= rk;
+    if (tid == 0) A[k * n + k] = rk;
+    __syncthreads();
+    for (int i = k + 1 + warp; i < n; i += CH_NT / 32) {
+      const double lik = tmp[i];
+      for (int c = lane; c <= k; c += 32) {
+        const double xkc = A[k * n + c];
+        A[i * n + c] = (c < k ? A[i * n + c] : 0.0) - lik * xkc;
+      }
+    }
     __syncthreads();
   }
   for (int e = tid; e < n * n; e += CH_NT) {

@@ -1,0 +1,457 @@
+// gemm_tc.cu -- the dense contractions of the mixed form on the 5th-generation tensor cores
+// (tcgen05, sm_103a) as BF16x3 split products:
+//   a = a_hi + a_lo, a_hi = bf16(a), a_lo = bf16(a - a_hi);  a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi
+// accumulated in FP32 in tensor memory (TMEM).
+//
+//   tc_gram:     G = scale * X Y^T  (M = -dV Phi^T W of App. A; C = dV xi^T psi of the ACE
+//                application).  Each CTA sums one chunk of grid points (256 by default) in FP32 in
+//                TMEM and writes a 128 x 128 partial; a second kernel adds the chunks in FP64 in a
+//                fixed order.  Longer FP32 chunks lose accuracy in the tensor-core accumulator.
+//   tc_left_mul: Z = A Y with A small (xi = L^-1 W, i.e. xi = W L^-T of App. A; out = -C^T xi).
+//
+// Operands are staged through registers (FP32 -> bf16 hi/lo) into shared memory in the K-major,
+// no-swizzle canonical layout: 8 x 8 "core matrices" of 128 contiguous bytes, K-adjacent core
+// matrices LBO = 128 B apart, row-group-adjacent ones SBO = 512 B apart (a 32-wide K step).  One
+// thread issues the MMAs (M = 128, N = 128, K = 16 each) and commits them to an mbarrier; every
+// wait on an mbarrier is bounded and reports a timeout through *err instead of hanging.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+
+#include "ace_internal.h"
+
+namespace ace {
+namespace tc {
+
+constexpr int NT = 128;        // four warps: warp w reads TMEM lanes 32w .. 32w + 31
+constexpr int BM = 128;        // UMMA M
+constexpr int BN = 128;        // UMMA N
+constexpr int BK = 32;         // K per pipeline stage (two K = 16 MMAs)
+constexpr uint32_t LBO = 128;  // bytes between K-adjacent core matrices
+constexpr uint32_t SBO = 512;  // bytes between row-adjacent core-matrix groups (BK / 8 * 128)
+constexpr uint32_t TILE_BYTES = BM * BK * 2;  // one bf16 operand tile (8 KB)
+constexpr uint32_t kWaitLimit = 1u << 22;     // try_wait polls before a wait is declared stuck
+constexpr int kGramChunkDefault = 256;        // grid points summed in FP32 (in TMEM) before the FP64 sum
+
+// instruction descriptor of tcgen05.mma kind::f16: D = F32 (bits 4-5), A = B = BF16 (bits 7-9,
+// 10-12), both K-major (bits 15, 16 clear), N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// shared-memory matrix descriptor: start >> 4 (bits 0-13), LBO >> 4 (16-29), SBO >> 4 (32-45),
+// descriptor version 1 (bits 46-47), base offset 0, no swizzle (bits 61-63 = 0)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((LBO >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((SBO >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// bounded wait for the phase with the given parity; false if it never completed
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Two-stage commit tracking: commits on barrier s complete its phases in order.
+struct Pipe {
+  uint32_t phase[2];
+  int pending[2];
+  __device__ __forceinline__ void init() {
+    phase[0] = phase[1] = 0u;
+    pending[0] = pending[1] = 0;
+  }
+  // wait for the outstanding commit of stage s (if any); false on timeout
+  __device__ __forceinline__ bool drain(uint64_t *mbar, int s) {
+    if (!pending[s]) return true;
+    const bool ok = mbar_wait(smem_u32(&mbar[s]), phase[s]);
+    phase[s] ^= 1u;
+    pending[s] = 0;
+    return ok;
+  }
+};
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// byte offset of element (row, k) of a 128 x 32 K-major tile in the canonical layout
+__device__ __forceinline__ uint32_t tile_off(int row, int k) {
+  return (uint32_t)(row >> 3) * SBO + (uint32_t)(k >> 3) * LBO + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+
+__device__ __forceinline__ void split4(const float4 v, uint2 &hi, uint2 &lo) {
+  const float x[4] = {v.x, v.y, v.z, v.w};
+  uint16_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat16 bh = __float2bfloat16_rn(x[i]);
+    const __nv_bfloat16 bl = __float2bfloat16_rn(x[i] - __bfloat162float(bh));
+    h[i] = __bfloat16_as_ushort(bh);
+    l[i] = __bfloat16_as_ushort(bl);
+  }
+  hi = make_uint2((uint32_t)h[0] | ((uint32_t)h[1] << 16), (uint32_t)h[2] | ((uint32_t)h[3] << 16));
+  lo = make_uint2((uint32_t)l[0] | ((uint32_t)l[1] << 16), (uint32_t)l[2] | ((uint32_t)l[3] << 16));
+}
+
+__device__ __forceinline__ void split1(float x, uint16_t &hi, uint16_t &lo) {
+  const __nv_bfloat16 bh = __float2bfloat16_rn(x);
+  hi = __bfloat16_as_ushort(bh);
+  lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(bh)));
+}
+
+// Rows [r0, r0 + 128) x K-columns [k0, k0 + 32) of a row-major matrix (leading dimension ld, K
+// contiguous) into hi/lo tiles; rows >= nrows are zero.
+__device__ __forceinline__ void stage_kmajor(const float *__restrict__ M, long long ld, int r0, int nrows, long long k0,
+                                             unsigned char *hi, unsigned char *lo) {
+#pragma unroll
+  for (int q = 0; q < (BM * BK / 4) / NT; ++q) {
+    const int f = threadIdx.x + NT * q;
+    const int row = f >> 3, kq = (f & 7) * 4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r0 + row < nrows) v = __ldg(reinterpret_cast<const float4 *>(M + (long long)(r0 + row) * ld + k0 + kq));
+    uint2 h, l;
+    split4(v, h, l);
+    const uint32_t off = tile_off(row, kq);
+    *reinterpret_cast<uint2 *>(hi + off) = h;
+    *reinterpret_cast<uint2 *>(lo + off) = l;
+  }
+}
+
+// K-rows [l0, l0 + 32) x columns [c0, c0 + 128) of a row-major matrix Y (ld = K columns, the
+// output columns contiguous), transposed into a K-major 128 x 32 tile (tile row = column c).
+__device__ __forceinline__ void stage_transposed(const float *__restrict__ Y, long long ld, int l0, int nl,
+                                                 long long c0, unsigned char *hi, unsigned char *lo) {
+#pragma unroll
+  for (int q = 0; q < (BM * BK / 4) / NT; ++q) {
+    const int f = threadIdx.x + NT * q;
+    const int l = f >> 5, cq = (f & 31) * 4;  // 32 float4 per K-row
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (l0 + l < nl) v = __ldg(reinterpret_cast<const float4 *>(Y + (long long)(l0 + l) * ld + c0 + cq));
+    const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      uint16_t h, lo16;
+      split1(x[i], h, lo16);
+      const uint32_t off = tile_off(cq + i, l);
+      *reinterpret_cast<uint16_t *>(hi + off) = h;
+      *reinterpret_cast<uint16_t *>(lo + off) = lo16;
+    }
+  }
+}
+
+struct SmemLayout {
+  // two pipeline stages x {A_hi, A_lo, B_hi, B_lo}
+  static constexpr uint32_t kStage = 4 * TILE_BYTES;
+  static constexpr uint32_t kBytes = 2 * kStage + 2048;  // + barriers / TMEM address, + alignment slack
+};
+
+// ----------------------------------------------------------------------------------------
+// Gram: partial[chunk][i][j] = sum_{r in chunk} X[i][r] Y[j][r], 128 x 128 tile per CTA.
+// ----------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) tc_gram_kernel(const float *__restrict__ X, int nx, const float *__restrict__ Y,
+                                                     int ny, long long K, int chunk, int tiles_x,
+                                                     float *__restrict__ partial, int *__restrict__ err) {
+  extern __shared__ unsigned char dyn[];
+  unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(dyn) + 1023) & ~uintptr_t(1023));
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(base + 2 * SmemLayout::kStage);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int ti = blockIdx.x % tiles_x, tj = blockIdx.x / tiles_x;
+  const int i0 = ti * BM, j0 = tj * BN;
+  const long long kb = (long long)blockIdx.y * chunk;
+  const long long ke = min(K, kb + chunk);
+  const int nsteps = (int)((ke - kb) / BK);
+
+  if (warp == 0) tmem_alloc(tmem_slot, 128);
+  if (tid == 0) {
+    mbar_init(smem_u32(&mbar[0]));
+    mbar_init(smem_u32(&mbar[1]));
+    mbar_init_fence();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  Pipe pipe;
+  pipe.init();
+  bool ok = true;
+  for (int it = 0; it < nsteps; ++it) {
+    const int s = it & 1;
+    unsigned char *st = base + s * SmemLayout::kStage;
+    ok = pipe.drain(mbar, s);  // the MMAs that last read this stage are done
+    if (__syncthreads_or(!ok)) {
+      ok = false;
+      break;
+    }
+    const long long k0 = kb + (long long)it * BK;
+    stage_kmajor(X, K, i0, nx, k0, st, st + TILE_BYTES);
+    stage_kmajor(Y, K, j0, ny, k0, st + 2 * TILE_BYTES, st + 3 * TILE_BYTES);
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a_hi = smem_u32(st), a_lo = a_hi + TILE_BYTES, b_hi = a_hi + 2 * TILE_BYTES,
+                     b_lo = a_hi + 3 * TILE_BYTES;
+#pragma unroll
+      for (int ks = 0; ks < BK / 16; ++ks) {
+        const uint32_t o = ks * 2 * LBO;
+        mma(tmem, sdesc(a_hi + o), sdesc(b_hi + o), (it > 0 || ks > 0) ? 1u : 0u);
+        mma(tmem, sdesc(a_hi + o), sdesc(b_lo + o), 1u);
+        mma(tmem, sdesc(a_lo + o), sdesc(b_hi + o), 1u);
+      }
+      commit(smem_u32(&mbar[s]));
+    }
+    pipe.pending[s] = 1;
+  }
+  // every commit waited for (also after a timeout, so that no MMA is in flight at dealloc)
+  const bool d0 = pipe.drain(mbar, 0), d1 = pipe.drain(mbar, 1);
+  ok = !__syncthreads_or(!(ok && d0 && d1));
+  tc_fence_after();
+  if (ok) {
+    const int i = i0 + 32 * warp + (tid & 31);
+    float *dst = partial + ((long long)blockIdx.y * nx + i) * ny;
+#pragma unroll 1
+    for (int cb = 0; cb < BN / 32; ++cb) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + 32 * cb, v);
+      if (i < nx) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int j = j0 + 32 * cb + c;
+          if (j < ny) dst[j] = nsteps > 0 ? v[c] : 0.f;
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+// G[i][j] = scale * sum_c partial[c][i][j] in FP64, chunks in order
+__global__ void gram_reduce_kernel(const float *__restrict__ partial, int nchunks, int nx, int ny, double scale,
+                                   double *__restrict__ G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nx * ny) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunks; ++c) s += (double)partial[(long long)c * nx * ny + e];
+  G[e] = scale * s;
+}
+
+// ----------------------------------------------------------------------------------------
+// Left multiply: Z[i][c] = sum_l A[i][l] Y[l][c] for rows [i0, i0 + 128) of A (m x n) and
+// column tiles of 128, persistent over the column tiles.
+// ----------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) tc_left_mul_kernel(const float *__restrict__ A, int m, int n,
+                                                         const float *__restrict__ Y, long long K, float *__restrict__ Z,
+                                                         int *__restrict__ err) {
+  extern __shared__ unsigned char dyn[];
+  unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(dyn) + 1023) & ~uintptr_t(1023));
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(base + 2 * SmemLayout::kStage);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int i0 = blockIdx.y * BM;
+  const long long ntiles = K / BN;
+  const int nsteps = (n + BK - 1) / BK;
+
+  if (warp == 0) tmem_alloc(tmem_slot, 128);
+  if (tid == 0) {
+    mbar_init(smem_u32(&mbar[0]));
+    mbar_init(smem_u32(&mbar[1]));
+    mbar_init_fence();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  Pipe pipe;
+  pipe.init();
+  bool ok = true;
+  for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    const long long c0 = t * BN;
+    for (int it = 0; it < nsteps; ++it) {
+      const int s = it & 1;
+      unsigned char *st = base + s * SmemLayout::kStage;
+      ok = pipe.drain(mbar, s);
+      if (__syncthreads_or(!ok)) {
+        ok = false;
+        break;
+      }
+      const int l0 = it * BK;
+      // A rows i0.., K-columns l0..l0+31 (A is m x n, n contiguous; columns >= n are zero)
+#pragma unroll
+      for (int q = 0; q < (BM * BK) / NT; ++q) {
+        const int f = tid + NT * q;
+        const int row = f >> 5, l = f & 31;
+        const float v = (i0 + row < m && l0 + l < n) ? __ldg(A + (long long)(i0 + row) * n + l0 + l) : 0.f;
+        uint16_t h, lo16;
+        split1(v, h, lo16);
+        const uint32_t off = tile_off(row, l);
+        *reinterpret_cast<uint16_t *>(st + off) = h;
+        *reinterpret_cast<uint16_t *>(st + TILE_BYTES + off) = lo16;
+      }
+      stage_transposed(Y, K, l0, n, c0, st + 2 * TILE_BYTES, st + 3 * TILE_BYTES);
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t a_hi = smem_u32(st), a_lo = a_hi + TILE_BYTES, b_hi = a_hi + 2 * TILE_BYTES,
+                       b_lo = a_hi + 3 * TILE_BYTES;
+#pragma unroll
+        for (int ks = 0; ks < BK / 16; ++ks) {
+          const uint32_t o = ks * 2 * LBO;
+          mma(tmem, sdesc(a_hi + o), sdesc(b_hi + o), (it > 0 || ks > 0) ? 1u : 0u);
+          mma(tmem, sdesc(a_hi + o), sdesc(b_lo + o), 1u);
+          mma(tmem, sdesc(a_lo + o), sdesc(b_hi + o), 1u);
+        }
+        commit(smem_u32(&mbar[s]));
+      }
+      pipe.pending[s] = 1;
+    }
+    if (!ok) break;
+    // wait for every MMA of this tile, then read D (lane = row i, columns = c)
+    const bool d0 = pipe.drain(mbar, 0), d1 = pipe.drain(mbar, 1);
+    ok = !__syncthreads_or(!(d0 && d1));
+    if (!ok) break;
+    tc_fence_after();
+    const int i = i0 + 32 * warp + (tid & 31);
+#pragma unroll 1
+    for (int cb = 0; cb < BN / 32; ++cb) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + 32 * cb, v);
+      if (i < m) {
+        float4 *dst = reinterpret_cast<float4 *>(Z + (long long)i * K + c0 + 32 * cb);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) dst[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+      }
+    }
+    tc_fence_before();
+    __syncthreads();  // D is read before the next tile's first MMA overwrites it
+  }
+  if (!ok) {
+    pipe.drain(mbar, 0);  // bounded: leave no MMA in flight before TMEM is released
+    pipe.drain(mbar, 1);
+    if (tid == 0) atomicExch(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+}  // namespace tc
+
+bool tc_shapes_ok(long long K) { return K % tc::BN == 0 && K % tc::BK == 0; }
+
+// FP32 accumulation length of the tensor-core Gram (a multiple of 32; ACE_TC_CHUNK overrides)
+static int tc_chunk() {
+  static int c = [] {
+    const char *v = std::getenv("ACE_TC_CHUNK");
+    int x = (v && *v) ? std::atoi(v) : tc::kGramChunkDefault;
+    if (x < tc::BK) x = tc::BK;
+    return (x / tc::BK) * tc::BK;
+  }();
+  return c;
+}
+
+cudaError_t launch_tc_gram(const float *X, int nx, const float *Y, int ny, long long K, double scale, double *G,
+                           float *partial_ws, int *err, cudaStream_t st) {
+  const int tx = (nx + tc::BM - 1) / tc::BM, ty = (ny + tc::BN - 1) / tc::BN;
+  const int chunk = tc_chunk();
+  const long long chunks = (K + chunk - 1) / chunk;
+  if (K % tc::BK != 0 || chunks > 65535) return cudaErrorInvalidValue;
+  const int smem = (int)tc::SmemLayout::kBytes;
+  cudaError_t e = cudaFuncSetAttribute(tc::tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  tc::tc_gram_kernel<<<dim3(tx * ty, (unsigned)chunks), tc::NT, smem, st>>>(X, nx, Y, ny, K, chunk, tx, partial_ws,
+                                                                             err);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int n = nx * ny;
+  tc::gram_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(partial_ws, (int)chunks, nx, ny, scale, G);
+  return cudaGetLastError();
+}
+
+size_t tc_gram_workspace_bytes(int nx, int ny, long long K) {
+  const long long chunks = (K + tc_chunk() - 1) / tc_chunk();
+  return sizeof(float) * (size_t)chunks * nx * ny;
+}
+
+cudaError_t launch_tc_left_mul(const float *A, int m, int n, const float *Y, long long K, float *Z, int *err,
+                               cudaStream_t st) {
+  if (K % tc::BN != 0) return cudaErrorInvalidValue;
+  const int smem = (int)tc::SmemLayout::kBytes;
+  cudaError_t e = cudaFuncSetAttribute(tc::tc_left_mul_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long tiles = K / tc::BN;
+  const int rows = (m + tc::BM - 1) / tc::BM;
+  const long long want = (long long)sms * 3 / rows;
+  const unsigned gx = (unsigned)std::max(1LL, std::min(tiles, want));
+  tc::tc_left_mul_kernel<<<dim3(gx, rows), tc::NT, smem, st>>>(A, m, n, Y, K, Z, err);
+  return cudaGetLastError();
+}
+
+}  // namespace ace

@@ -221,3 +221,38 @@ def test_argument_errors():
     with pytest.raises(ace.AceError) as e:
         ace.ace_build(ace.make_desc((16, 16, 16), lat, 0), x[:0])
     assert e.value.status == ace.ace.ACE_ERR_ARG
+
+
+def test_mixed_apply_few_vectors(cfg1):
+    """Tensor-core BF16x3 contractions with padded shapes: 16 orbitals, 7 vectors."""
+    import torch
+
+    w, ref = cfg1
+    g = gpu_build(w.phi, w.lattice, ace.ACE_MIXED)
+    psi = np.random.default_rng(12).standard_normal((7,) + w.grid)
+    out = torch.empty((7,) + w.grid, dtype=torch.float32, device="cuda")
+    ace.ace_apply(g["op"], torch.from_numpy(psi.astype(np.float32)).cuda(), out)
+    kref = oracle.ace_apply(ref["xi"], psi, w.dV)
+    assert np.linalg.norm(out.cpu().numpy() - kref) <= MIXED_KPHI_RTOL * np.linalg.norm(kref)
+
+
+def test_mixed_dense_steps_beyond_one_tile():
+    """160 orbitals (two 128-row tiles): M, L and xi of the mixed build against FP64 contractions
+    of the build's own W (the pair chain is covered by the other tests)."""
+    import scipy.linalg as sla
+
+    rng = np.random.default_rng(77)
+    w = water_like(40, 20.07, (32, 32, 32), rng, rho_cut=1e-3, dmin=4.0)
+    g = gpu_build(w.phi, w.lattice, ace.ACE_MIXED, rho_cut=w.rho_cut)
+    assert g["status"] == 0
+    n = w.norb
+    phi32 = w.phi.astype(np.float32).astype(np.float64).reshape(n, -1)
+    W = g["W"].astype(np.float64)
+    M_ref = -w.dV * phi32 @ W.T
+    assert np.abs(g["M_raw"] - M_ref).max() <= 2e-5 * np.abs(M_ref).max()
+    Ms = 0.5 * (M_ref + M_ref.T)
+    assert abs(g["E_x"] - 0.5 * w.spin_factor * np.trace(Ms)) <= MIXED_EX_TOL_PER_ORB * n
+    L = np.linalg.cholesky(-g["M"])
+    assert np.abs(g["L"] - L).max() <= 1e-12 * np.abs(L).max()
+    xi_ref = sla.solve_triangular(L, W, lower=True)
+    assert rel_max(g["xi"], xi_ref) <= 1e-4
