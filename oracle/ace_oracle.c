@@ -33,6 +33,8 @@
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
+#else
+static int omp_in_parallel(void) { return 1; }
 #endif
 
 typedef double complex cplx;
@@ -119,38 +121,36 @@ static void plan_free(fft3_plan *pl) {
   for (int a = 0; a < 3; ++a) free(pl->tw[a]);
 }
 
-/* In-place unnormalised 3D DFT of z[i1][i2][i3] along each axis in turn.
- * work must hold 3 * maxn complex values. */
+/* In-place unnormalised 3D DFT of z[i1][i2][i3] along each axis in turn.  Lines are independent;
+ * when called outside a parallel region they are spread over threads (each line is computed the
+ * same way whatever the thread count, so results do not depend on it). */
+#define ORACLE_MAXN 1024
+static void fft_line(const fft3_plan *pl, int axis, cplx *base, long stride, int sign) {
+  cplx line[ORACLE_MAXN], out[ORACLE_MAXN], tmp[ORACLE_MAXN];
+  const int n = pl->n[axis];
+  for (int k = 0; k < n; ++k) line[k] = base[(long)k * stride];
+  dft_rec(line, 1, out, n, sign, pl->tw[axis], 1, tmp);
+  for (int k = 0; k < n; ++k) base[(long)k * stride] = out[k];
+}
+
 static void fft3(const fft3_plan *pl, cplx *z, int sign, cplx *work) {
   const int n1 = pl->n[0], n2 = pl->n[1], n3 = pl->n[2];
-  cplx *line = work, *out = work + pl->maxn, *tmp = work + 2 * pl->maxn;
+  (void)work;
+  const int par = !omp_in_parallel();
   /* axis 3 (contiguous) */
-  for (long a = 0; a < (long)n1 * n2; ++a) {
-    cplx *base = z + a * n3;
-    dft_rec(base, 1, out, n3, sign, pl->tw[2], 1, tmp);
-    memcpy(base, out, (size_t)n3 * sizeof(cplx));
-  }
+#pragma omp parallel for schedule(static) if (par)
+  for (long a = 0; a < (long)n1 * n2; ++a) fft_line(pl, 2, z + a * n3, 1, sign);
   /* axis 2 */
-  for (int i1 = 0; i1 < n1; ++i1)
-    for (int i3 = 0; i3 < n3; ++i3) {
-      cplx *base = z + (long)i1 * n2 * n3 + i3;
-      for (int i2 = 0; i2 < n2; ++i2) line[i2] = base[(long)i2 * n3];
-      dft_rec(line, 1, out, n2, sign, pl->tw[1], 1, tmp);
-      for (int i2 = 0; i2 < n2; ++i2) base[(long)i2 * n3] = out[i2];
-    }
+#pragma omp parallel for schedule(static) if (par)
+  for (long a = 0; a < (long)n1 * n3; ++a) fft_line(pl, 1, z + (a / n3) * n2 * n3 + (a % n3), n3, sign);
   /* axis 1 */
-  for (long a = 0; a < (long)n2 * n3; ++a) {
-    cplx *base = z + a;
-    for (int i1 = 0; i1 < n1; ++i1) line[i1] = base[(long)i1 * n2 * n3];
-    dft_rec(line, 1, out, n1, sign, pl->tw[0], 1, tmp);
-    for (int i1 = 0; i1 < n1; ++i1) base[(long)i1 * n2 * n3] = out[i1];
-  }
-  (void)line;
+#pragma omp parallel for schedule(static) if (par)
+  for (long a = 0; a < (long)n2 * n3; ++a) fft_line(pl, 0, z + a, (long)n2 * n3, sign);
 }
 
 /* Exported for the naive-DFT check: z is interleaved (re, im) of shape [n1][n2][n3]. */
 int oracle_fft3d(double *z, int n1, int n2, int n3, int sign) {
-  if (n1 < 1 || n2 < 1 || n3 < 1) return 1;
+  if (n1 < 1 || n2 < 1 || n3 < 1 || n1 > ORACLE_MAXN || n2 > ORACLE_MAXN || n3 > ORACLE_MAXN) return 1;
   fft3_plan pl;
   plan_init(&pl, n1, n2, n3);
   cplx *work = (cplx *)malloc(3 * (size_t)pl.maxn * sizeof(cplx));
@@ -231,16 +231,21 @@ int oracle_coulomb_kernel(const double *lattice, int n1, int n2, int n3, double 
  * ---------------------------------------------------------------------------------------- */
 static void pair_potential(const fft3_plan *pl, const double *K, const double *pi_, const double *pj,
                            long npts, cplx *z, cplx *work, double *v) {
+  const int par = !omp_in_parallel();
+#pragma omp parallel for schedule(static) if (par)
   for (long r = 0; r < npts; ++r) z[r] = pi_[r] * pj[r];
   fft3(pl, z, -1, work);
   const double invN = 1.0 / (double)npts;
+#pragma omp parallel for schedule(static) if (par)
   for (long r = 0; r < npts; ++r) z[r] *= K[r] * invN;
   fft3(pl, z, +1, work);
+#pragma omp parallel for schedule(static) if (par)
   for (long r = 0; r < npts; ++r) v[r] = creal(z[r]);
 }
 
 int oracle_pair_potential(const double *phi_i, const double *phi_j, int n1, int n2, int n3,
                           const double *lattice, double *v) {
+  if (n1 > ORACLE_MAXN || n2 > ORACLE_MAXN || n3 > ORACLE_MAXN) return 1;
   const long npts = (long)n1 * n2 * n3;
   fft3_plan pl;
   plan_init(&pl, n1, n2, n3);
@@ -285,13 +290,16 @@ int oracle_screen(const double *phi, int norb, long npts, double dV, double rho_
  * ---------------------------------------------------------------------------------------- */
 int oracle_exchange_w(const double *phi, int norb, int n1, int n2, int n3, const double *lattice,
                       const unsigned char *mask, const int *rows, int nrows, double *W) {
+  if (n1 > ORACLE_MAXN || n2 > ORACLE_MAXN || n3 > ORACLE_MAXN) return 2;
   const long npts = (long)n1 * n2 * n3;
   fft3_plan pl;
   plan_init(&pl, n1, n2, n3);
   double *K = (double *)malloc((size_t)npts * sizeof(double));
   oracle_coulomb_kernel(lattice, n1, n2, n3, K);
   int err = 0;
-#pragma omp parallel
+  /* many rows: one row per thread; few rows: rows in sequence, parallel inside each transform */
+  const int outer = nrows >= oracle_max_threads();
+#pragma omp parallel if (outer)
   {
     cplx *z = (cplx *)malloc((size_t)npts * sizeof(cplx));
     cplx *work = (cplx *)malloc(3 * (size_t)pl.maxn * sizeof(cplx));
@@ -309,6 +317,7 @@ int oracle_exchange_w(const double *phi, int norb, int n1, int n2, int n3, const
           if (mask && !mask[(long)i * norb + j]) continue;
           const double *pj = phi + (long)j * npts;
           pair_potential(&pl, K, phi + (long)i * npts, pj, npts, z, work, v);
+#pragma omp parallel for schedule(static) if (!omp_in_parallel())
           for (long r = 0; r < npts; ++r) Wi[r] += v[r] * pj[r];
         }
       }

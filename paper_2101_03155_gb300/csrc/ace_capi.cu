@@ -236,6 +236,12 @@ struct ace_op {
   long launches = 0;          // kernels of this library launched by the build
   std::vector<void *> owned;  // stream-ordered allocations freed by ace_destroy
   std::vector<int2> pairs_h;  // host copy of the kept pairs
+  std::vector<void *> temps;  // build workspaces released in stream order at the end of the build
+  const void *phi_work = nullptr;
+  const DeviceTables *tab = nullptr;
+  void *readback = nullptr;   // pinned host area for the asynchronous readbacks of a build
+  size_t readback_bytes = 0;
+  int lane = 0;               // stream lane of a batched build (selects its side streams)
 };
 
 namespace {
@@ -317,12 +323,39 @@ ace_status stage_input(ace_op *op, const void *src, ace_dtype dt, long long coun
   return ACE_OK;
 }
 
+// Small pinned host buffers for the asynchronous readbacks of builds, reused across builds.
+std::mutex g_pin_mu;
+std::vector<std::pair<size_t, void *>> g_pinned;
+
+cudaError_t pinned_get(size_t bytes, void **out) {
+  {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    for (size_t i = 0; i < g_pinned.size(); ++i)
+      if (g_pinned[i].first >= bytes) {
+        *out = g_pinned[i].second;
+        g_pinned.erase(g_pinned.begin() + i);
+        return cudaSuccess;
+      }
+  }
+  return cudaHostAlloc(out, bytes < 4096 ? 4096 : bytes, cudaHostAllocDefault);
+}
+
+void pinned_put(void *p, size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  if (g_pinned.size() < 64) {
+    g_pinned.emplace_back(bytes < 4096 ? 4096 : bytes, p);
+  } else {
+    cudaFreeHost(p);
+  }
+}
+
 // Per-device side streams of the pair chain (created once, non-blocking, kept until exit).
 std::mutex g_side_mu;
-cudaStream_t g_side[64][4] = {};
+constexpr int kLanes = 4;           // concurrent builds of one batched call
+cudaStream_t g_side[64][5 * kLanes] = {};  // per lane: 4 chain side streams + the lane stream
 
 cudaError_t get_side_stream(int dev, int k, cudaStream_t *out) {
-  if (dev < 0 || dev >= 64 || k < 0 || k >= 4) return cudaErrorInvalidValue;
+  if (dev < 0 || dev >= 64 || k < 0 || k >= 5 * kLanes) return cudaErrorInvalidValue;
   std::lock_guard<std::mutex> lk(g_side_mu);
   if (!g_side[dev][k]) {
     cudaError_t e = cudaStreamCreateWithFlags(&g_side[dev][k], cudaStreamNonBlocking);
@@ -451,7 +484,7 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
     ACE_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "event");
     ACE_CUDA(cudaEventRecord(fork, st), "event");
     for (int k = 0; k < nstreams; ++k) {
-      ACE_CUDA(get_side_stream(op->dev, k, &side[k]), "side stream");
+      ACE_CUDA(get_side_stream(op->dev, 4 * op->lane + k, &side[k]), "side stream");
       ACE_CUDA(cudaStreamWaitEvent(side[k], fork, 0), "wait");
     }
   }
@@ -534,44 +567,29 @@ cudaError_t dense_left_mul(const T *A, int m, int n, const T *Y, long long K, T 
   return ace::launch_left_mul<T>(A, m, n, Y, K, Z, st);
 }
 
+// Phase 1 of a build: inputs, tables, screen and compaction; the pair count and list are copied
+// to pinned host memory asynchronously (read after the stream reaches them).
 template <typename T>
-ace_status build_impl(ace_op *op, const void *phi_in, ace_dtype dtype) {
+ace_status build_begin(ace_op *op, const void *phi_in, ace_dtype dtype) {
   const ace_desc &d = op->desc;
   const int n = op->n;
   const long long N = op->N;
   cudaStream_t st = op->stream;
-  std::vector<void *> temps;
-  struct TempGuard {
-    std::vector<void *> *v;
-    cudaStream_t s;
-    ~TempGuard() {
-      for (void *p : *v) cudaFreeAsync(p, s);
-    }
-  } guard{&temps, st};
-
   for (int i = 0; i < 6; ++i) ACE_CUDA(cudaEventCreate(&op->ev[i]), "event create");
   ACE_CUDA(cudaEventRecord(op->ev[0], st), "event record");
-
   const T *phi = nullptr;
-  ace_status s = stage_input<T>(op, phi_in, dtype, (long long)n * N, &phi, &temps);
+  ace_status s = stage_input<T>(op, phi_in, dtype, (long long)n * N, &phi, &op->temps);
   if (s != ACE_OK) return s;
-
-  // tables (cached per device, grid, lattice and precision)
-  const DeviceTables *tab = nullptr;
-  {
-    cudaError_t e = get_tables<T>(op->dev, d, st, &tab);
-    if (e != cudaSuccess) return cuda_fail(e, "kernel and twiddle tables");
-  }
-  const T *Kd = static_cast<const T *>(tab->K);
-  const cpx<T> *twd[3] = {static_cast<const cpx<T> *>(tab->tw[0]), static_cast<const cpx<T> *>(tab->tw[1]),
-                          static_cast<const cpx<T> *>(tab->tw[2])};
-  void *tmp = nullptr;
+  op->phi_work = phi;
+  cudaError_t e = get_tables<T>(op->dev, d, st, &op->tab);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel and twiddle tables");
 
   // ---- screen (section II): O_ij = dV sum |phi_i phi_j|, pair list ----
+  const size_t maxpairs = (size_t)n * (n + 1) / 2;
   ACE_CUDA(op_alloc(op, &op->O, sizeof(double) * n * n), "alloc O");
   ACE_CUDA(op_alloc(op, &op->O_sym, sizeof(double) * n * n), "alloc O_sym");
-  ACE_CUDA(op_alloc(op, &op->pairs, sizeof(int2) * ((size_t)n * (n + 1) / 2 + 2)), "alloc pairs");
-  ACE_CUDA(op_alloc(op, &op->packs, sizeof(int4) * ((size_t)n * (n + 1) / 4 + 2)), "alloc packs");
+  ACE_CUDA(op_alloc(op, &op->pairs, sizeof(int2) * (maxpairs + 2)), "alloc pairs");
+  ACE_CUDA(op_alloc(op, &op->packs, sizeof(int4) * (maxpairs / 2 + 2)), "alloc packs");
   ACE_CUDA(op_alloc(op, &op->count_d, sizeof(int) * 4), "alloc count");
   ACE_CUDA(op_alloc(op, &op->status_d, sizeof(int) * 4), "alloc status");
   op->tc_err = op->status_d + 1;
@@ -586,16 +604,35 @@ ace_status build_impl(ace_op *op, const void *phi_in, ace_dtype dtype) {
   ACE_CUDA(ace::launch_screen_compact(op->O, n, d.rho_cut, op->pairs, op->packs, op->count_d, op->O_sym, st),
            "compact");
   ++op->launches;
-  int count = 0;
-  op->pairs_h.resize((size_t)n * (n + 1) / 2);
-  ACE_CUDA(cudaMemcpyAsync(&count, op->count_d, sizeof(int), cudaMemcpyDeviceToHost, st), "count readback");
-  ACE_CUDA(cudaMemcpyAsync(op->pairs_h.data(), op->pairs, sizeof(int2) * op->pairs_h.size(), cudaMemcpyDeviceToHost,
-                           st),
+  // pinned readback area: [count, flags0, flags1, pad] [energy] [pairs]
+  const size_t rb_bytes = 32 + sizeof(int2) * maxpairs;
+  ACE_CUDA(pinned_get(rb_bytes, &op->readback), "pinned readback");
+  op->readback_bytes = rb_bytes;
+  ACE_CUDA(cudaMemcpyAsync(op->readback, op->count_d, sizeof(int), cudaMemcpyDeviceToHost, st), "count readback");
+  ACE_CUDA(cudaMemcpyAsync(static_cast<char *>(op->readback) + 32, op->pairs, sizeof(int2) * maxpairs,
+                           cudaMemcpyDeviceToHost, st),
            "pair readback");
-  ACE_CUDA(cudaStreamSynchronize(st), "count readback");
-  op->npairs = count;
-  op->pairs_h.resize(count);
   ACE_CUDA(cudaEventRecord(op->ev[1], st), "event record");
+  return ACE_OK;
+}
+
+// Phase 2: with the pair list on the host, the pair chain, M, Cholesky and xi; status and E_x are
+// copied back asynchronously.  Call after op->ev[1] has completed.
+template <typename T>
+ace_status build_finish(ace_op *op) {
+  const ace_desc &d = op->desc;
+  const int n = op->n;
+  const long long N = op->N;
+  cudaStream_t st = op->stream;
+  const T *phi = static_cast<const T *>(op->phi_work);
+  const DeviceTables *tab = op->tab;
+  const int count = *static_cast<const int *>(op->readback);
+  op->npairs = count;
+  const int2 *ph = reinterpret_cast<const int2 *>(static_cast<const char *>(op->readback) + 32);
+  op->pairs_h.assign(ph, ph + count);
+  std::vector<void *> &temps = op->temps;
+  void *tmp = nullptr;
+  ace_status s = ACE_OK;
 
   // ---- pair chain (Eq. vx, Eq. e:vij): W_i = sum_j v_ij phi_j ----
   ACE_CUDA(op_alloc(op, &op->W, op->esz * (size_t)n * N), "alloc W");
@@ -605,7 +642,9 @@ ace_status build_impl(ace_op *op, const void *phi_in, ace_dtype dtype) {
   if (count > 0 && plane) {
     s = run_chain_plane<T>(op, phi, tab, pops, count, temps);
   } else if (count > 0) {
-    s = run_chain_pencil<T>(op, phi, Kd, twd, count, temps);
+    const cpx<T> *twd[3] = {static_cast<const cpx<T> *>(tab->tw[0]), static_cast<const cpx<T> *>(tab->tw[1]),
+                            static_cast<const cpx<T> *>(tab->tw[2])};
+    s = run_chain_pencil<T>(op, phi, static_cast<const T *>(tab->K), twd, count, temps);
   }
   if (s != ACE_OK) return s;
   ACE_CUDA(cudaEventRecord(op->ev[2], st), "event record");
@@ -649,21 +688,31 @@ ace_status build_impl(ace_op *op, const void *phi_in, ace_dtype dtype) {
                              st, &op->launches),
            "xi");
   ACE_CUDA(cudaEventRecord(op->ev[5], st), "event record");
+  char *rb = static_cast<char *>(op->readback);
+  ACE_CUDA(cudaMemcpyAsync(rb + 4, op->status_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, st), "status readback");
+  ACE_CUDA(cudaMemcpyAsync(rb + 16, op->energy_d, sizeof(double), cudaMemcpyDeviceToHost, st), "energy readback");
+  // workspaces of the build are released in stream order after their last use
+  for (void *p : temps) cudaFreeAsync(p, st);
+  temps.clear();
+  op->phi_work = nullptr;
+  return ACE_OK;
+}
 
-  int status = 0, flags[2] = {0, 0};
-  double energy = 0.0;
-  ACE_CUDA(cudaMemcpyAsync(flags, op->status_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, st), "status readback");
-  ACE_CUDA(cudaMemcpyAsync(&energy, op->energy_d, sizeof(double), cudaMemcpyDeviceToHost, st), "energy readback");
-  ACE_CUDA(cudaStreamSynchronize(st), "build");
-  status = flags[0];
-  op->status = status;
-  if (flags[1]) return fail(ACE_ERR_TIMEOUT, "a tensor-core kernel gave up waiting for its MMAs");
-  op->energy = energy;
+// Phase 3: after the stream has completed the build.
+ace_status build_collect(ace_op *op) {
+  const char *rb = static_cast<const char *>(op->readback);
+  int flags[2];
+  std::memcpy(flags, rb + 4, sizeof flags);
+  std::memcpy(&op->energy, rb + 16, sizeof(double));
+  op->status = flags[0];
   for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&op->stage_ms[i], op->ev[i], op->ev[i + 1]);
   cudaEventElapsedTime(&op->stage_ms[5], op->ev[0], op->ev[5]);
-  if (status >= 2000000) return fail(ACE_ERR_NONFINITE, "M has a non-finite entry");
-  if (status >= 1000000)
-    return fail(ACE_ERR_NOT_POSDEF, "-M is not positive definite: Cholesky pivot %d", status - 1000000);
+  pinned_put(op->readback, op->readback_bytes);
+  op->readback = nullptr;
+  if (flags[1]) return fail(ACE_ERR_TIMEOUT, "a tensor-core kernel gave up waiting for its MMAs");
+  if (op->status >= 2000000) return fail(ACE_ERR_NONFINITE, "M has a non-finite entry");
+  if (op->status >= 1000000)
+    return fail(ACE_ERR_NOT_POSDEF, "-M is not positive definite: Cholesky pivot %d", op->status - 1000000);
   return ACE_OK;
 }
 
@@ -764,16 +813,17 @@ int ace_grid_supported(int n_axis, ace_precision prec) {
   return ace::pass_length_supported(n_axis) ? 1 : 0;
 }
 
-ace_status ace_build(const ace_desc *desc, const void *phi, ace_dtype dtype, void *cuda_stream, ace_op **out) {
-  if (!out) return fail(ACE_ERR_ARG, "out is NULL");
-  *out = nullptr;
-  ace_status s = check_desc(desc);
-  if (s != ACE_OK) return s;
-  if (!phi) return fail(ACE_ERR_ARG, "phi is NULL");
-  if (dtype != ACE_F32 && dtype != ACE_F64) return fail(ACE_ERR_ARG, "unknown dtype %d", (int)dtype);
+}  // extern "C"
+
+namespace {
+
+ace_op *new_op(const ace_desc *desc, cudaStream_t st, ace_status *status) {
   ace_op *op = new (std::nothrow) ace_op();
-  if (!op) return fail(ACE_ERR_OOM, "host allocation failed");
-  op->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (!op) {
+    *status = fail(ACE_ERR_OOM, "host allocation failed");
+    return nullptr;
+  }
+  op->stream = st;
   op->desc = *desc;
   op->n = desc->norb;
   op->N = (long long)desc->n[0] * desc->n[1] * desc->n[2];
@@ -787,10 +837,43 @@ ace_status ace_build(const ace_desc *desc, const void *phi, ace_dtype dtype, voi
   if (e == cudaSuccess) e = prepare_pool(op->dev);
   if (e != cudaSuccess) {
     delete op;
-    return cuda_fail(e, "device setup");
+    *status = cuda_fail(e, "device setup");
+    return nullptr;
   }
-  s = op->fp64 ? build_impl<double>(op, phi, dtype) : build_impl<float>(op, phi, dtype);
-  if (s == ACE_OK || s == ACE_ERR_NOT_POSDEF || s == ACE_ERR_NONFINITE) {
+  *status = ACE_OK;
+  return op;
+}
+
+ace_status begin_any(ace_op *op, const void *phi, ace_dtype dt) {
+  return op->fp64 ? build_begin<double>(op, phi, dt) : build_begin<float>(op, phi, dt);
+}
+ace_status finish_any(ace_op *op) { return op->fp64 ? build_finish<double>(op) : build_finish<float>(op); }
+
+bool keeps_handle(ace_status s) { return s == ACE_OK || s == ACE_ERR_NOT_POSDEF || s == ACE_ERR_NONFINITE; }
+
+}  // namespace
+
+extern "C" {
+
+ace_status ace_build(const ace_desc *desc, const void *phi, ace_dtype dtype, void *cuda_stream, ace_op **out) {
+  if (!out) return fail(ACE_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  ace_status s = check_desc(desc);
+  if (s != ACE_OK) return s;
+  if (!phi) return fail(ACE_ERR_ARG, "phi is NULL");
+  if (dtype != ACE_F32 && dtype != ACE_F64) return fail(ACE_ERR_ARG, "unknown dtype %d", (int)dtype);
+  ace_op *op = new_op(desc, static_cast<cudaStream_t>(cuda_stream), &s);
+  if (!op) return s;
+  s = begin_any(op, phi, dtype);
+  if (s == ACE_OK) {
+    cudaError_t e = cudaEventSynchronize(op->ev[1]);
+    s = e == cudaSuccess ? finish_any(op) : cuda_fail(e, "pair list readback");
+  }
+  if (s == ACE_OK) {
+    cudaError_t e = cudaStreamSynchronize(op->stream);
+    s = e == cudaSuccess ? build_collect(op) : cuda_fail(e, "build");
+  }
+  if (keeps_handle(s)) {
     *out = op;
     return s;
   }
@@ -799,21 +882,70 @@ ace_status ace_build(const ace_desc *desc, const void *phi, ace_dtype dtype, voi
   return s;
 }
 
+// Builds are spread over up to four stream lanes forked from `cuda_stream`: all screens first,
+// one wait for the pair lists, then every build's chain and dense steps on its lane, then one
+// join back into `cuda_stream`.
 ace_status ace_build_batched(int k, const ace_desc *desc, const void *const *phi, ace_dtype dtype, void *cuda_stream,
                              ace_op **out) {
   if (k < 0 || (k > 0 && (!desc || !phi || !out))) return fail(ACE_ERR_ARG, "bad batched arguments");
+  if (dtype != ACE_F32 && dtype != ACE_F64) return fail(ACE_ERR_ARG, "unknown dtype %d", (int)dtype);
   for (int i = 0; i < k; ++i) out[i] = nullptr;
   for (int i = 0; i < k; ++i) {
-    ace_status s = ace_build(&desc[i], phi[i], dtype, cuda_stream, &out[i]);
-    if (s != ACE_OK) {
-      std::string msg = g_last_error;
-      for (int j = 0; j <= i; ++j) {
-        if (out[j]) ace_destroy(out[j]);
-        out[j] = nullptr;
-      }
-      return fail(s, "build %d of %d: %s", i, k, msg.c_str());
-    }
+    ace_status s = check_desc(&desc[i]);
+    if (s != ACE_OK) return fail(s, "build %d of %d: %s", i, k, g_last_error.c_str());
+    if (!phi[i]) return fail(ACE_ERR_ARG, "build %d of %d: phi is NULL", i, k);
   }
+  if (k == 0) return ACE_OK;
+  cudaStream_t user = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0;
+  ACE_CUDA(cudaGetDevice(&dev), "device");
+  const int lanes = std::min(kLanes, std::max(1, std::min(k, env_int("ACE_BATCH_LANES", kLanes))));
+  cudaStream_t lane_st[kLanes];
+  cudaEvent_t fork = nullptr;
+  ACE_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "event");
+  ACE_CUDA(cudaEventRecord(fork, user), "event");
+  for (int l = 0; l < lanes; ++l) {
+    ACE_CUDA(get_side_stream(dev, 4 * kLanes + l, &lane_st[l]), "lane stream");
+    ACE_CUDA(cudaStreamWaitEvent(lane_st[l], fork, 0), "fork");
+  }
+  ace_status s = ACE_OK;
+  int failed = -1;
+  for (int i = 0; i < k && s == ACE_OK; ++i) {
+    ace_op *op = new_op(&desc[i], lane_st[i % lanes], &s);
+    if (!op) {
+      failed = i;
+      break;
+    }
+    op->lane = i % lanes;
+    out[i] = op;
+    s = begin_any(op, phi[i], dtype);
+    if (s != ACE_OK) failed = i;
+  }
+  for (int i = 0; i < k && s == ACE_OK; ++i) {
+    cudaError_t e = cudaEventSynchronize(out[i]->ev[1]);
+    s = e == cudaSuccess ? finish_any(out[i]) : cuda_fail(e, "pair list readback");
+    if (s != ACE_OK) failed = i;
+  }
+  for (int l = 0; l < lanes; ++l) {
+    cudaEventRecord(fork, lane_st[l]);
+    cudaStreamWaitEvent(user, fork, 0);
+  }
+  for (int i = 0; i < k; ++i)
+    if (out[i]) cudaStreamSynchronize(out[i]->stream);
+  cudaEventDestroy(fork);
+  for (int i = 0; i < k && s == ACE_OK; ++i) {
+    s = build_collect(out[i]);
+    if (s != ACE_OK) failed = i;
+  }
+  if (s != ACE_OK) {
+    std::string msg = g_last_error;
+    for (int j = 0; j < k; ++j) {
+      if (out[j]) ace_destroy(out[j]);
+      out[j] = nullptr;
+    }
+    return fail(s, "build %d of %d: %s", failed, k, msg.c_str());
+  }
+  // the handles keep their lane stream for ace_destroy; later calls take a stream argument
   return ACE_OK;
 }
 
@@ -883,7 +1015,13 @@ ace_status ace_stage_times(const ace_op *op, float ms[6]) {
 
 void ace_destroy(ace_op *op) {
   if (!op) return;
+  for (void *p : op->temps) cudaFreeAsync(p, op->stream);
+  op->temps.clear();
   op_free_all(op);
+  if (op->readback) {
+    cudaStreamSynchronize(op->stream);  // an unfinished build may still copy into it
+    pinned_put(op->readback, op->readback_bytes);
+  }
   for (int i = 0; i < 6; ++i)
     if (op->ev[i]) cudaEventDestroy(op->ev[i]);
   delete op;

@@ -1,0 +1,76 @@
+"""Parity at the full configuration sizes, on outputs the oracle can compute one by one:
+sampled rows of W (Eq. vx for one orbital, on the GPU's pair list), the matching columns of M,
+and E_x against the stored oracle value of the 32-water-like build."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2101_03155_gb300 as ace
+from gpu_helpers import FP64_EX_TOL, MIXED_EX_TOL_PER_ORB, MIXED_W_RTOL, gpu_build, rel_max
+from workloads.generators import config2, config3, config5
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_values.json")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2101_03155_gb300 import build
+
+    build.build()
+    ace.ace.load()
+    oracle.build()
+
+
+def _check_sampled_rows(w, g, rows, w_rtol):
+    n = w.norb
+    W_gpu = g["W"].reshape((n,) + w.grid).astype(np.float64)
+    W_ref = oracle.exchange_w(w.phi, w.lattice, mask=g["mask"], rows=rows)
+    for k, i in enumerate(rows):
+        assert rel_max(W_gpu[i], W_ref[k]) <= w_rtol, f"W row {i}"
+        # column i of M_raw = -dV Phi^T W_i
+        Mcol = -w.dV * w.phi.reshape(n, -1) @ W_ref[k].reshape(-1)
+        assert np.abs(g["M_raw"][:, i] - Mcol).max() <= 2e-5 * np.abs(Mcol).max()
+
+
+@pytest.mark.parametrize("prec", [ace.ACE_MIXED, ace.ACE_FP64])
+def test_water32_full_size(prec):
+    w = config2()
+    g = gpu_build(w.phi, w.lattice, prec, rho_cut=w.rho_cut)
+    assert g["status"] == 0
+    gold = json.load(open(GOLDEN))["water32_128orb_96c_rhocut1e-3"]
+    O_ref, mask_ref = oracle.screen(w.phi, w.lattice, w.rho_cut)
+    band = np.abs(O_ref - w.rho_cut) < 1e-6 * w.rho_cut
+    assert np.array_equal(g["mask"] | band, mask_ref | band)
+    if prec == ace.ACE_FP64:
+        assert np.array_equal(g["mask"], mask_ref)
+        assert abs(g["E_x"] - gold["E_x"]) <= FP64_EX_TOL
+        _check_sampled_rows(w, g, [5, 77], 1e-10)
+    else:
+        assert abs(g["E_x"] - gold["E_x"]) <= MIXED_EX_TOL_PER_ORB * w.norb
+        _check_sampled_rows(w, g, [5, 77], MIXED_W_RTOL)
+
+
+def test_water64_full_size_mixed():
+    w = config3()
+    g = gpu_build(w.phi, w.lattice, ace.ACE_MIXED, rho_cut=w.rho_cut)
+    assert g["status"] == 0
+    assert 0 < len(g["pairs"]) < w.norb * (w.norb + 1) // 2
+    _check_sampled_rows(w, g, [3, 200], MIXED_W_RTOL)
+    # App. A on the GPU operator: dV xi^T Phi = L^T up to screening asymmetry and BF16x3 rounding
+    assert np.all(np.diag(g["L"]) > 0)
+
+
+def test_enzyme_snapshot_full_size_mixed():
+    w = config5(nsnap=1)[0]
+    g = gpu_build(w.phi, w.lattice, ace.ACE_MIXED, rho_cut=w.rho_cut)
+    assert g["status"] == 0
+    _check_sampled_rows(w, g, [0, 111], MIXED_W_RTOL)
