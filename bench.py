@@ -109,6 +109,23 @@ def _dist():
     return world, rank, local
 
 
+def combine_ranks(local_ms: float, steps: int, units_per_step: float, device: str = "cpu"):
+    """Whole-job figure of a weak-scaling run: every rank did `steps` steps of `units_per_step`
+    units; the job time is the slowest rank's.  Returns (max ms over ranks, units per second over
+    all ranks).  Without an initialised process group this is the single-rank value."""
+    import torch
+    import torch.distributed as dist
+
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    ms = float(local_ms)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        ms = float(t.item())
+    return ms, world * steps * units_per_step / (ms / 1e3)
+
+
 # ------------------------------------------------------------------------------------------
 # CPU oracle on a bounded sample (baseline leg and reference arm)
 # ------------------------------------------------------------------------------------------
@@ -167,6 +184,93 @@ def _workload():
     from workloads.generators import config2
 
     return config2()
+
+
+WORKLOADS = {
+    "water32": "water32_128orb_96c_rhocut1e-3",
+    "water64": "water64_256orb_128c_rhocut1e-3",
+    "enzyme8": "enzyme_112orb_160x144x128_8snap_rhocut1e-3",
+    "batched24": "batched24_uneven_rhocut1e-3",
+}
+
+
+def _batch_inputs(name):
+    """List of Workload objects of a multi-build workload (one step builds all of them)."""
+    from workloads.generators import batched_set, config3, config5, water_like
+
+    if name == "water64":
+        return [config3()]
+    if name == "enzyme8":
+        return config5(nsnap=8)
+    if name == "batched24":
+        rng = np.random.default_rng(1004)
+        out = []
+        for n, N, cell, seed in batched_set(rng):
+            out.append(water_like(n // 4, cell, (N, N, N), np.random.default_rng(seed), rho_cut=1e-3,
+                                  name=f"water{n // 4}_{n}orb_{N}c"))
+        return out
+    raise ValueError(name)
+
+
+def run_multi(args):
+    """Secondary workloads: one step is one ace_build_batched call over all builds of the workload."""
+    import torch
+
+    import paper_2101_03155_gb300 as ace
+    from paper_2101_03155_gb300 import build as cuda_build
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    cuda_build.build()
+    ace.ace.load()
+    ws = _batch_inputs(args.workload)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for prec, dt, steps in ((ace.ACE_MIXED, torch.float32, args.steps), (ace.ACE_FP64, torch.float64,
+                                                                         max(1, args.fp64_steps))):
+        descs = [ace.make_desc(w.grid, w.lattice, w.norb, rho_cut=w.rho_cut, spin_factor=w.spin_factor, prec=prec)
+                 for w in ws]
+        phis = [torch.from_numpy(w.phi).to(device="cuda", dtype=dt) for w in ws]
+        for _ in range(args.warmup if prec == ace.ACE_MIXED else 1):
+            for op in ace.ace_build_batched(descs, phis, stream):
+                op.close()
+        rec = {"launches": 0, "pairs": 0, "E": []}
+        torch.cuda.synchronize()
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(steps):
+            ops = ace.ace_build_batched(descs, phis, stream)
+            for op in ops:
+                rec["E"].append(ace.exchange_energy(op))
+                rec["launches"] += ace.ace.ace_kernel_launches(op)
+                rec["pairs"] += ace.ace_pair_count(op)
+                op.close()
+        end.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = start.elapsed_time(end)
+        res[prec] = {"builds_per_s": len(ws) * steps / (ms / 1e3), "ms_per_step": ms / steps, "rec": rec, "clk": clk}
+        del phis
+    mixed, f64 = res[ace.ACE_MIXED], res[ace.ACE_FP64]
+    line = {
+        "metric": METRIC, "value": mixed["builds_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mixed["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "builds_per_step": len(ws),
+                   "norb": [w.norb for w in ws], "grid": [list(w.grid) for w in ws],
+                   "pairs_per_step": mixed["rec"]["pairs"] // args.steps, "precision": "mixed",
+                   "l2": "inputs larger than L2"},
+        "fp64_form": {"value": f64["builds_per_s"], "unit": UNIT, "ms_per_step": f64["ms_per_step"],
+                      "speedup_mixed_over_fp64": mixed["builds_per_s"] / f64["builds_per_s"]},
+        "gpu_launches": mixed["rec"]["launches"],
+        "clocks": mixed["clk"],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -270,15 +374,8 @@ def run_ours(args):
     clocks.start()
     ms = _timed_builds(ace, desc, phi32, stream, args.steps, collect)
     clk = clocks.stop()
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        torch.distributed.barrier()
-        ms = float(t.item())
+    ms, value = combine_ranks(ms, args.steps, 1.0, "cuda")
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
 
     # end to end: host (pinned) orbitals through the same C ABI call; copies inside the timed region
     host32 = torch.from_numpy(w.phi.astype(np.float32)).pin_memory()
@@ -360,9 +457,13 @@ def main():
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="water32", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.impl == "reference":
+        args.ref_step_s = min(args.ref_step_s, max(2.0, 150.0 / max(1, args.steps + args.warmup)))
         return run_reference(args)
+    if args.workload != "water32":
+        return run_multi(args)
     return run_ours(args)
 
 
