@@ -423,8 +423,8 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   const long long N = op->N;
   cudaStream_t st = op->stream;
   const int G = std::max(1, env_int("ACE_GROUP", 1));
-  const int B = std::max(G, env_int("ACE_PLANE_BATCH", 4));
-  const int nstreams = std::min(4, std::max(1, env_int("ACE_STREAMS", 2)));
+  const int B = std::max(G, env_int("ACE_PLANE_BATCH", 2));
+  const int nstreams = std::min(4, std::max(1, env_int("ACE_STREAMS", 4)));
   const bool acc = pops.acc_fits && G > 1;
   // packs: two pairs of one row (i, j1), (i, j2); leftover single pairs of different rows are
   // packed together at the end as mixed packs
@@ -488,6 +488,22 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
       ACE_CUDA(cudaStreamWaitEvent(side[k], fork, 0), "wait");
     }
   }
+  // ask L2 to keep each stream's FFT scratch resident between the three passes (a per-context
+  // set-aside of the L2 for persisting lines; ACE_L2_PERSIST_MB=0 turns it off)
+  const int persist_mb = env_int("ACE_L2_PERSIST_MB", 60);
+  if (persist_mb > 0 && nstreams > 1) {
+    size_t limit = (size_t)persist_mb << 20;
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, limit);
+    for (int k = 0; k < nstreams; ++k) {
+      cudaStreamAttrValue v{};
+      v.accessPolicyWindow.base_ptr = scratch_all + (size_t)k * B * N;
+      v.accessPolicyWindow.num_bytes = std::min<size_t>(limit / (size_t)nstreams, sizeof(cpx<T>) * (size_t)B * (size_t)N);
+      v.accessPolicyWindow.hitRatio = 1.0f;
+      v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+      v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+      cudaStreamSetAttribute(side[k], cudaStreamAttributeAccessPolicyWindow, &v);
+    }
+  }
 
   ace::PlaneArgs<T> pa;
   pa.phi = phi;
@@ -522,12 +538,17 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
     pa.group0 = b.x;
     ca.pack0 = p0;
     ACE_CUDA(pops.fwd(pa, p1 - p0, side[k]), "plane forward");
-    ACE_CUDA(ace::launch_pair_pass<T>(ace::PASS_CONV1, ca, p1 - p0, side[k]), "pencil pass");
+    ACE_CUDA(ace::launch_conv_pass<T>(ca, p1 - p0, side[k]), "pencil pass");
     ACE_CUDA(pops.inv(pa, b.y - b.x, acc, side[k]), "plane inverse");
     op->launches += 3;
   }
   if (nstreams > 1) {
     for (int k = 0; k < nstreams; ++k) {
+      if (persist_mb > 0) {
+        cudaStreamAttrValue v{};
+        v.accessPolicyWindow.num_bytes = 0;  // window off again
+        cudaStreamSetAttribute(side[k], cudaStreamAttributeAccessPolicyWindow, &v);
+      }
       ACE_CUDA(cudaEventRecord(fork, side[k]), "event");
       ACE_CUDA(cudaStreamWaitEvent(st, fork, 0), "join");
     }

@@ -68,6 +68,10 @@ bool plane_ops_f64(int n2, int n3, PlaneOps<double> *out);
 template <typename T>
 cudaError_t launch_pair_pass(int mode, const PairPassArgs<T> &a, int npacks, cudaStream_t st);
 
+// Axis-1 pass of the plane chain (32-column tiles, direct global stage-1 loads and stores).
+template <typename T>
+cudaError_t launch_conv_pass(const PairPassArgs<T> &a, int npacks, cudaStream_t st);
+
 bool pass_length_supported(int L);
 // Two-stage factorisation L = r1 * r2 of a compiled axis length (output index k sits at
 // position (k % r1) * r2 + k / r1 after a forward transform).

@@ -20,6 +20,8 @@
 #include "ace_internal.h"
 #include "fft.cuh"
 
+#define ACE_PASS_LENGTHS(X) X(8) X(12) X(16) X(20) X(24) X(32) X(48) X(64) X(72) X(96) X(108) X(128) X(144) X(160)
+
 namespace ace {
 
 template <int L>
@@ -221,6 +223,105 @@ __global__ void __launch_bounds__(PassShape<L>::NT) pair_pass_kernel(PairPassArg
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Axis-1 pass of the plane chain: for 32 neighbouring (p2, p3) columns of one pack, forward
+// transform along i1, multiply by the Coulomb table, inverse transform.  Stage 1 reads its
+// elements straight from the scratch and the last inverse stage writes straight back (lanes
+// over the 32 columns: coalesced); only the two exchanges in between go through shared memory.
+// ---------------------------------------------------------------------------------------
+template <int L>
+struct ConvShape {
+  static constexpr int R1 = Factor<L>::R1, R2 = Factor<L>::R2;
+  static constexpr int TILE = 32;
+  static constexpr int LP = L + 1;
+  static constexpr int NT = 128;
+};
+
+template <typename T, int L>
+__global__ void __launch_bounds__(ConvShape<L>::NT) conv_pencil_kernel(PairPassArgs<T> a) {
+  using S = ConvShape<L>;
+  constexpr int R1 = S::R1, R2 = S::R2, TILE = S::TILE, LP = S::LP, NT = S::NT;
+  __shared__ cpx<T> s[TILE * LP];
+  __shared__ cpx<T> tw[L];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < L; e += NT) tw[e] = a.tw[e];
+  const long long cols = (long long)a.n2 * a.n3;
+  const long long c0 = (long long)blockIdx.x * TILE;
+  const int Ns = (int)cols;  // stride between consecutive i1 (fits: N < 2^31)
+  cpx<T> *z = a.scratch + (long long)blockIdx.y * a.N + c0;
+  const T *kc = a.kernel + c0;
+  const int t = tid & (TILE - 1);
+  const bool valid = c0 + t < cols;
+  __syncthreads();
+  // stage 1 (forward): tasks (t, n2), n2 = warp + 4 q
+#pragma unroll
+  for (int q = 0; q < (TILE * R2 + NT - 1) / NT; ++q) {
+    const int n2 = (tid >> 5) + (NT / TILE) * q;
+    if (n2 < R2 && valid) {
+      cpx<T> x[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) x[n1] = z[(n1 * R2 + n2) * Ns + t];
+      Dft<R1, -1, T>::run(x);
+      cpx<T> *line = s + t * LP + n2;
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) line[k1 * R2] = k1 ? cmul(x[k1], tw[n2 * k1]) : x[0];
+    }
+  }
+  __syncthreads();
+  // stage 2 (forward), kernel multiply, inverse stage A: tasks (t, k1)
+#pragma unroll
+  for (int q = 0; q < (TILE * R1 + NT - 1) / NT; ++q) {
+    const int k1 = (tid >> 5) + (NT / TILE) * q;
+    if (k1 < R1 && valid) {
+      cpx<T> *blk = s + t * LP + k1 * R2;
+      cpx<T> x[R2];
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) x[n2] = blk[n2];
+      Dft<R2, -1, T>::run(x);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) x[k2] = cscale(x[k2], __ldg(kc + (k1 + R1 * k2) * Ns + t));
+      Dft<R2, +1, T>::run(x);
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) blk[n2] = (n2 && k1) ? cmul(x[n2], conjc(tw[n2 * k1])) : x[n2];
+    }
+  }
+  __syncthreads();
+  // inverse stage B: tasks (t, n2); natural order i1 = n1 R2 + n2 straight to the scratch
+#pragma unroll
+  for (int q = 0; q < (TILE * R2 + NT - 1) / NT; ++q) {
+    const int n2 = (tid >> 5) + (NT / TILE) * q;
+    if (n2 < R2 && valid) {
+      const cpx<T> *line = s + t * LP + n2;
+      cpx<T> x[R1];
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) x[k1] = line[k1 * R2];
+      Dft<R1, +1, T>::run(x);
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) z[(n1 * R2 + n2) * Ns + t] = x[n1];
+    }
+  }
+}
+
+template <typename T, int L>
+cudaError_t launch_conv_L(const PairPassArgs<T> &a, int npacks, cudaStream_t st) {
+  using S = ConvShape<L>;
+  const long long cols = (long long)a.n2 * a.n3;
+  dim3 grid((unsigned)((cols + S::TILE - 1) / S::TILE), npacks);
+  conv_pencil_kernel<T, L><<<grid, S::NT, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_conv_impl(const PairPassArgs<T> &a, int npacks, cudaStream_t st) {
+  switch (a.n1) {
+#define ACE_CASE(L_) \
+  case L_: return launch_conv_L<T, L_>(a, npacks, st);
+    ACE_PASS_LENGTHS(ACE_CASE)
+#undef ACE_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename T, int L>
 cudaError_t launch_pass_L(int mode, const PairPassArgs<T> &a, int npacks, cudaStream_t st) {
   using S = PassShape<L>;
@@ -244,7 +345,6 @@ cudaError_t launch_pass_L(int mode, const PairPassArgs<T> &a, int npacks, cudaSt
   return cudaGetLastError();
 }
 
-#define ACE_PASS_LENGTHS(X) X(8) X(12) X(16) X(20) X(24) X(32) X(48) X(64) X(72) X(96) X(108) X(128) X(144) X(160)
 
 template <typename T>
 cudaError_t launch_pair_pass_impl(int mode, const PairPassArgs<T> &a, int npacks, cudaStream_t st) {

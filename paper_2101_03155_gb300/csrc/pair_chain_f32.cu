@@ -6,6 +6,10 @@ template <>
 cudaError_t launch_pair_pass<float>(int mode, const PairPassArgs<float> &a, int npacks, cudaStream_t st) {
   return launch_pair_pass_impl<float>(mode, a, npacks, st);
 }
+template <>
+cudaError_t launch_conv_pass<float>(const PairPassArgs<float> &a, int npacks, cudaStream_t st) {
+  return launch_conv_impl<float>(a, npacks, st);
+}
 
 bool axis_factors(int L, int *r1, int *r2) {
   switch (L) {

@@ -6,4 +6,8 @@ template <>
 cudaError_t launch_pair_pass<double>(int mode, const PairPassArgs<double> &a, int npacks, cudaStream_t st) {
   return launch_pair_pass_impl<double>(mode, a, npacks, st);
 }
+template <>
+cudaError_t launch_conv_pass<double>(const PairPassArgs<double> &a, int npacks, cudaStream_t st) {
+  return launch_conv_impl<double>(a, npacks, st);
+}
 }  // namespace ace
