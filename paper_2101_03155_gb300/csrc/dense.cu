@@ -107,9 +107,125 @@ __global__ void __launch_bounds__(GR_NT) gram_kernel(const T *__restrict__ X, in
     }
 }
 
+// FP32 operands: 128 x 64 output tile, 256 threads with 8 x 4 outputs each, k-tiles of 16 staged
+// in shared memory (double-buffered, next tile prefetched into registers), FP32 partial sums of 32
+// points added into a Kahan-compensated FP32 accumulator, FP64 atomics across 4096-point chunks.
+constexpr int G2_BM = 128, G2_BN = 64, G2_BK = 16, G2_NT = 256, G2_CHUNK = 4096;
+
+template <bool ABS>
+__global__ void __launch_bounds__(G2_NT, 1) gram_f32_kernel(const float *__restrict__ X, int nx,
+                                                            const float *__restrict__ Y, int ny, long long K,
+                                                            double scale, bool upper_only, int tiles_i,
+                                                            double *__restrict__ G) {
+  __shared__ __align__(16) float xs[2][G2_BK][G2_BM + 4];
+  __shared__ __align__(16) float ys[2][G2_BK][G2_BN + 4];
+  const int ti = blockIdx.x % tiles_i, tj = blockIdx.x / tiles_i;
+  const int i0 = ti * G2_BM, j0 = tj * G2_BN;
+  if (upper_only && j0 + G2_BN - 1 < i0) return;  // tile entirely below the diagonal
+  const long long kb = (long long)blockIdx.y * G2_CHUNK;
+  const long long ke = min(K, kb + G2_CHUNK);
+  const int ntiles = (int)((ke - kb + G2_BK - 1) / G2_BK);
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  float acc[8][4], comp[8][4], part[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = comp[a][b] = part[a][b] = 0.f;
+
+  float4 rx[2], ry;
+  auto load = [&](int t) {
+    const long long k0 = kb + (long long)t * G2_BK;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int f = tid + G2_NT * q, row = f >> 2, kq = (f & 3) * 4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i0 + row < nx && k0 + kq < ke) v = __ldg(reinterpret_cast<const float4 *>(X + (long long)(i0 + row) * K + k0 + kq));
+      rx[q] = v;
+    }
+    {
+      const int row = tid >> 2, kq = (tid & 3) * 4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j0 + row < ny && k0 + kq < ke) v = __ldg(reinterpret_cast<const float4 *>(Y + (long long)(j0 + row) * K + k0 + kq));
+      ry = v;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int f = tid + G2_NT * q, row = f >> 2, kq = (f & 3) * 4;
+      const float v[4] = {rx[q].x, rx[q].y, rx[q].z, rx[q].w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) xs[buf][kq + c][row] = ABS ? fabsf(v[c]) : v[c];
+    }
+    const int row = tid >> 2, kq = (tid & 3) * 4;
+    const float v[4] = {ry.x, ry.y, ry.z, ry.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) ys[buf][kq + c][row] = ABS ? fabsf(v[c]) : v[c];
+  };
+  if (ntiles > 0) {
+    load(0);
+    store(0);
+  }
+  __syncthreads();
+  for (int t = 0; t < ntiles; ++t) {
+    const int buf = t & 1;
+    if (t + 1 < ntiles) load(t + 1);
+#pragma unroll
+    for (int k = 0; k < G2_BK; ++k) {
+      const float4 a0 = *reinterpret_cast<const float4 *>(&xs[buf][k][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4 *>(&xs[buf][k][64 + ty * 4]);
+      const float4 b = *reinterpret_cast<const float4 *>(&ys[buf][k][tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) part[r][c] = fmaf(av[r], bv[c], part[r][c]);
+    }
+    if ((t & 1) || t + 1 == ntiles) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float y = part[r][c] - comp[r][c];
+          const float s = acc[r][c] + y;
+          comp[r][c] = (s - acc[r][c]) - y;
+          acc[r][c] = s;
+          part[r][c] = 0.f;
+        }
+    }
+    if (t + 1 < ntiles) store(buf ^ 1);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + tx * 4 + c;
+      if (i < nx && j < ny && !(upper_only && j < i)) atomicAdd(G + (long long)i * ny + j, scale * (double)acc[r][c]);
+    }
+  }
+}
+
 template <typename T>
 cudaError_t launch_gram(const T *X, int nx, const T *Y, int ny, long long K, double scale, bool abs_values,
                         bool upper_only, double *G, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (K % 4 == 0) {
+      const int tiles_i = (nx + G2_BM - 1) / G2_BM, tiles_j = (ny + G2_BN - 1) / G2_BN;
+      const long long chunks = (K + G2_CHUNK - 1) / G2_CHUNK;
+      if (chunks > 65535) return cudaErrorInvalidValue;
+      cudaError_t e = cudaMemsetAsync(G, 0, sizeof(double) * (size_t)nx * ny, st);
+      if (e != cudaSuccess) return e;
+      dim3 grid(tiles_i * tiles_j, (unsigned)chunks);
+      if (abs_values)
+        gram_f32_kernel<true><<<grid, G2_NT, 0, st>>>(X, nx, Y, ny, K, scale, upper_only, tiles_i, G);
+      else
+        gram_f32_kernel<false><<<grid, G2_NT, 0, st>>>(X, nx, Y, ny, K, scale, upper_only, tiles_i, G);
+      return cudaGetLastError();
+    }
+  }
   const int nbx = (nx + GR_BM - 1) / GR_BM, nby = (ny + GR_BM - 1) / GR_BM;
   const int tiles = upper_only ? nbx * (nbx + 1) / 2 : nbx * nby;
   const long long chunks = (K + GR_CHUNK - 1) / GR_CHUNK;

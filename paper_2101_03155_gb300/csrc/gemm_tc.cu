@@ -289,13 +289,25 @@ __global__ void __launch_bounds__(NT) tc_gram_kernel(const float *__restrict__ X
   if (warp == 0) tmem_dealloc(tmem, 128);
 }
 
-// G[i][j] = scale * sum_c partial[c][i][j] in FP64, chunks in order
-__global__ void gram_reduce_kernel(const float *__restrict__ partial, int nchunks, int nx, int ny, double scale,
-                                   double *__restrict__ G) {
+// Chunk partials summed in FP64 in two fixed-order levels: block (e-range, group g) adds chunks
+// g*per .. g*per + per - 1 for 256 consecutive entries into part2[g][e]; then G = scale * sum_g.
+constexpr int kReduceGroups = 64;
+__global__ void gram_reduce_kernel(const float *__restrict__ partial, int nchunks, int ne,
+                                   double *__restrict__ part2) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nx * ny) return;
+  if (e >= ne) return;
+  const int per = (nchunks + kReduceGroups - 1) / kReduceGroups;
+  const int c0 = blockIdx.y * per, c1 = min(nchunks, c0 + per);
   double s = 0.0;
-  for (int c = 0; c < nchunks; ++c) s += (double)partial[(long long)c * nx * ny + e];
+#pragma unroll 8
+  for (int c = c0; c < c1; ++c) s += (double)__ldg(partial + (long long)c * ne + e);
+  part2[(long long)blockIdx.y * ne + e] = s;
+}
+__global__ void gram_reduce2_kernel(const double *__restrict__ part2, int ne, double scale, double *__restrict__ G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  double s = 0.0;
+  for (int g = 0; g < kReduceGroups; ++g) s += part2[(long long)g * ne + e];
   G[e] = scale * s;
 }
 
@@ -428,13 +440,19 @@ cudaError_t launch_tc_gram(const float *X, int nx, const float *Y, int ny, long 
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int n = nx * ny;
-  tc::gram_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(partial_ws, (int)chunks, nx, ny, scale, G);
+  const size_t part2_off = ((sizeof(float) * (size_t)chunks * n + 255) / 256) * 256;  // aligned, after the partials
+  double *part2 = reinterpret_cast<double *>(reinterpret_cast<char *>(partial_ws) + part2_off);
+  tc::gram_reduce_kernel<<<dim3((n + 255) / 256, tc::kReduceGroups), 256, 0, st>>>(partial_ws, (int)chunks, n,
+                                                                                   part2);
+  tc::gram_reduce2_kernel<<<(n + 255) / 256, 256, 0, st>>>(part2, n, scale, G);
   return cudaGetLastError();
 }
 
 size_t tc_gram_workspace_bytes(int nx, int ny, long long K) {
   const long long chunks = (K + tc_chunk() - 1) / tc_chunk();
-  return sizeof(float) * (size_t)chunks * nx * ny;
+  // FP32 chunk partials, then (256-byte aligned) the FP64 group sums of the reduction
+  const size_t part2_off = ((sizeof(float) * (size_t)chunks * nx * ny + 255) / 256) * 256;
+  return part2_off + sizeof(double) * tc::kReduceGroups * (size_t)nx * ny;
 }
 
 cudaError_t launch_tc_left_mul(const float *A, int m, int n, const float *Y, long long K, float *Z, int *err,
