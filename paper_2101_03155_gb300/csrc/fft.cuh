@@ -35,6 +35,36 @@ template <typename T>
 __device__ __forceinline__ cpx<T> cscale(cpx<T> a, T s) {
   return {a.x * s, a.y * s};
 }
+#ifndef ACE_NO_F32X2
+// FP32 complex adds, subtracts and real scalings as packed f32x2 instructions (sm_100 family):
+// one instruction per complex operation, each lane rounded to nearest like the scalar forms.
+__device__ __forceinline__ unsigned long long f2_pack(cpx<float> a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ cpx<float> f2_unpack(unsigned long long v) {
+  cpx<float> r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ cpx<float> operator+(cpx<float> a, cpx<float> b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+  return f2_unpack(r);
+}
+__device__ __forceinline__ cpx<float> operator-(cpx<float> a, cpx<float> b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+  return f2_unpack(r);
+}
+__device__ __forceinline__ cpx<float> cscale(cpx<float> a, float s) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(cpx<float>{s, s})));
+  return f2_unpack(r);
+}
+#endif
+
 // multiply by D*i (D = -1: -i, D = +1: +i)
 template <int D, typename T>
 __device__ __forceinline__ cpx<T> rot(cpx<T> a) {

@@ -17,6 +17,17 @@
 #include "ace_internal.h"
 #include "fft.cuh"
 
+// unroll depth of the global-load loops (forward copy-in, inverse epilogue): loads of several
+// iterations are issued before the first one is used
+#ifndef ACE_FWD_UNROLL
+#define ACE_FWD_UNROLL 4
+#endif
+#ifndef ACE_INV_UNROLL
+#define ACE_INV_UNROLL 2
+#endif
+#define ACE_PRAGMA(x) _Pragma(#x)
+#define ACE_UNROLL(n) ACE_PRAGMA(unroll n)
+
 namespace ace {
 
 template <int N2, int N3>
@@ -148,7 +159,7 @@ __global__ void __launch_bounds__(NT) plane_fwd_kernel(PlaneArgs<T> a) {
   const bool two = pk.z >= 0;
   const T *pc = a.phi + (long long)(two ? pk.z : 0) * a.N + off;
   const T *pd = a.phi + (long long)(two ? pk.w : 0) * a.N + off;
-#pragma unroll 4
+  ACE_UNROLL(ACE_FWD_UNROLL)
   for (int e = tid; e < S::NPTS; e += NT) {
     const int i2 = e / N3, i3 = e - i2 * N3;
     const T re = __ldg(pa + e) * __ldg(pb + e);
@@ -241,7 +252,7 @@ __global__ void __launch_bounds__(NT) plane_inv_kernel(PlaneArgs<T> a) {
     T *wb = a.W + (long long)pk.y * a.N + off;
     T *wc = a.W + (long long)(two ? pk.z : 0) * a.N + off;
     T *wd = a.W + (long long)(two ? pk.w : 0) * a.N + off;
-#pragma unroll 2
+    ACE_UNROLL(ACE_INV_UNROLL)
     for (int e = tid; e < S::NPTS; e += NT) {
       const int i2 = e / N3, i3 = e - i2 * N3;
       const cpx<T> v = s[i2 * S::PP + i3];
