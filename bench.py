@@ -31,6 +31,10 @@ WORKLOAD = "water32_128orb_96c_rhocut1e-3"
 METRIC = "ACE builds/s (128 orb, 96^3), mixed vs FP64 GPU form; E_x err <=1e-6 Ha/orb"
 UNIT = "builds/s"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_values.json")
+# DRAM bytes (read + write) of the pair chain per build of the water32 workload, from one ncu capture
+# of the current chain kernels with caches not flushed (profiles/pair_chain_plane_water32_96c.md);
+# set to None whenever those kernels change.
+CHAIN_DRAM_BYTES_PER_BUILD = 27.8e9
 
 
 def _peaks():
@@ -417,9 +421,9 @@ def run_ours(args):
                       "steps": args.fp64_steps, "ex_err_ha_per_orb": ex_err64,
                       "speedup_mixed_over_fp64": value / world / fp64_value},
         "stage_ms": stage_mean,
-        "roofline": {"kernel": "pair chain (5 pencil passes per pack batch)", "bound": "hbm",
-                     "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                     "frac": achieved / peaks.get("hbm_gbs"), "traffic": None,
+        "roofline": {"kernel": "pair chain (plane fwd, axis-1 pencil, plane inv+accumulate per pack batch)",
+                     "bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                     "frac": achieved / peaks.get("hbm_gbs"), "traffic": CHAIN_DRAM_BYTES_PER_BUILD,
                      "peak_kind": peak_kind,
                      "algorithmic_bytes": f"24 B x N x npairs = {alg_bytes:.4g} B per build"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n * N, "d2h_bytes_per_step": 16,
