@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(GR_NT) gram_kernel(const T *__restrict__ X, in
 constexpr int G2_BM = 128, G2_BN = 64, G2_BK = 16, G2_NT = 256, G2_CHUNK = 4096;
 
 template <bool ABS>
-__global__ void __launch_bounds__(G2_NT, 1) gram_f32_kernel(const float *__restrict__ X, int nx,
+__global__ void __launch_bounds__(G2_NT, 2) gram_f32_kernel(const float *__restrict__ X, int nx,
                                                             const float *__restrict__ Y, int ny, long long K,
                                                             double scale, bool upper_only, int tiles_i,
                                                             double *__restrict__ G) {

@@ -138,64 +138,72 @@ __device__ __forceinline__ uint32_t tile_off(int row, int k) {
   return (uint32_t)(row >> 3) * SBO + (uint32_t)(k >> 3) * LBO + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 7) * 2u;
 }
 
-__device__ __forceinline__ void split4(const float4 v, uint2 &hi, uint2 &lo) {
-  const float x[4] = {v.x, v.y, v.z, v.w};
-  uint16_t h[4], l[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const __nv_bfloat16 bh = __float2bfloat16_rn(x[i]);
-    const __nv_bfloat16 bl = __float2bfloat16_rn(x[i] - __bfloat162float(bh));
-    h[i] = __bfloat16_as_ushort(bh);
-    l[i] = __bfloat16_as_ushort(bl);
-  }
-  hi = make_uint2((uint32_t)h[0] | ((uint32_t)h[1] << 16), (uint32_t)h[2] | ((uint32_t)h[3] << 16));
-  lo = make_uint2((uint32_t)l[0] | ((uint32_t)l[1] << 16), (uint32_t)l[2] | ((uint32_t)l[3] << 16));
-}
-
 __device__ __forceinline__ void split1(float x, uint16_t &hi, uint16_t &lo) {
   const __nv_bfloat16 bh = __float2bfloat16_rn(x);
   hi = __bfloat16_as_ushort(bh);
   lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(bh)));
 }
 
-// Rows [r0, r0 + 128) x K-columns [k0, k0 + 32) of a row-major matrix (leading dimension ld, K
-// contiguous) into hi/lo tiles; rows >= nrows are zero.
-__device__ __forceinline__ void stage_kmajor(const float *__restrict__ M, long long ld, int r0, int nrows, long long k0,
-                                             unsigned char *hi, unsigned char *lo) {
+// 16-byte core-matrix row: 8 bf16 (hi) and 8 bf16 (lo) of 8 consecutive K-values of one row
+__device__ __forceinline__ void split8(const float (&x)[8], uint4 &hi, uint4 &lo) {
+  uint32_t h[4], l[4];
 #pragma unroll
-  for (int q = 0; q < (BM * BK / 4) / NT; ++q) {
-    const int f = threadIdx.x + NT * q;
-    const int row = f >> 3, kq = (f & 7) * 4;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (r0 + row < nrows) v = __ldg(reinterpret_cast<const float4 *>(M + (long long)(r0 + row) * ld + k0 + kq));
-    uint2 h, l;
-    split4(v, h, l);
-    const uint32_t off = tile_off(row, kq);
-    *reinterpret_cast<uint2 *>(hi + off) = h;
-    *reinterpret_cast<uint2 *>(lo + off) = l;
+  for (int i = 0; i < 4; ++i) {
+    uint16_t h0, l0, h1, l1;
+    split1(x[2 * i], h0, l0);
+    split1(x[2 * i + 1], h1, l1);
+    h[i] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+    l[i] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// One operand row (32 K-values) per thread, held in registers between load and store.
+struct Row32 {
+  float v[32];
+};
+
+// row r of a row-major matrix (ld = K), K-values [k0, k0 + 32); zero past nrows
+__device__ __forceinline__ void load_row(const float *__restrict__ M, long long ld, int r, int nrows, long long k0,
+                                         Row32 &out) {
+  if (r < nrows) {
+    const float4 *src = reinterpret_cast<const float4 *>(M + (long long)r * ld + k0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 t = __ldg(src + q);
+      out.v[4 * q] = t.x;
+      out.v[4 * q + 1] = t.y;
+      out.v[4 * q + 2] = t.z;
+      out.v[4 * q + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 32; ++q) out.v[q] = 0.f;
   }
 }
 
-// K-rows [l0, l0 + 32) x columns [c0, c0 + 128) of a row-major matrix Y (ld = K columns, the
-// output columns contiguous), transposed into a K-major 128 x 32 tile (tile row = column c).
-__device__ __forceinline__ void stage_transposed(const float *__restrict__ Y, long long ld, int l0, int nl,
-                                                 long long c0, unsigned char *hi, unsigned char *lo) {
+// the thread's row of a 128 x 32 tile: four 16-byte stores into each of the hi and lo tiles
+// (lanes are consecutive rows, so each quarter-warp writes 128 contiguous bytes)
+__device__ __forceinline__ void store_row(const Row32 &r, int row, unsigned char *hi, unsigned char *lo) {
 #pragma unroll
-  for (int q = 0; q < (BM * BK / 4) / NT; ++q) {
-    const int f = threadIdx.x + NT * q;
-    const int l = f >> 5, cq = (f & 31) * 4;  // 32 float4 per K-row
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (l0 + l < nl) v = __ldg(reinterpret_cast<const float4 *>(Y + (long long)(l0 + l) * ld + c0 + cq));
-    const float x[4] = {v.x, v.y, v.z, v.w};
+  for (int q = 0; q < 4; ++q) {
+    float x[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      uint16_t h, lo16;
-      split1(x[i], h, lo16);
-      const uint32_t off = tile_off(cq + i, l);
-      *reinterpret_cast<uint16_t *>(hi + off) = h;
-      *reinterpret_cast<uint16_t *>(lo + off) = lo16;
-    }
+    for (int i = 0; i < 8; ++i) x[i] = r.v[8 * q + i];
+    uint4 h, l;
+    split8(x, h, l);
+    const uint32_t off = tile_off(row, 8 * q);
+    *reinterpret_cast<uint4 *>(hi + off) = h;
+    *reinterpret_cast<uint4 *>(lo + off) = l;
   }
+}
+
+// column c of Y (row-major n x K), K-rows [l0, l0 + 32): 32 scalar loads, coalesced across lanes
+__device__ __forceinline__ void load_col(const float *__restrict__ Y, long long ld, int l0, int nl, long long c,
+                                         Row32 &out) {
+#pragma unroll
+  for (int j = 0; j < 32; ++j) out.v[j] = (l0 + j < nl) ? __ldg(Y + (long long)(l0 + j) * ld + c) : 0.f;
 }
 
 struct SmemLayout {
@@ -234,17 +242,27 @@ __global__ void __launch_bounds__(NT) tc_gram_kernel(const float *__restrict__ X
   Pipe pipe;
   pipe.init();
   bool ok = true;
+  Row32 nx_a, nx_b;  // prefetched rows of the next K-step
+  if (nsteps > 0) {
+    load_row(X, K, i0 + tid, nx, kb, nx_a);
+    load_row(Y, K, j0 + tid, ny, kb, nx_b);
+  }
   for (int it = 0; it < nsteps; ++it) {
     const int s = it & 1;
     unsigned char *st = base + s * SmemLayout::kStage;
+    const Row32 cur_a = nx_a, cur_b = nx_b;
+    if (it + 1 < nsteps) {
+      const long long k1 = kb + (long long)(it + 1) * BK;
+      load_row(X, K, i0 + tid, nx, k1, nx_a);
+      load_row(Y, K, j0 + tid, ny, k1, nx_b);
+    }
     ok = pipe.drain(mbar, s);  // the MMAs that last read this stage are done
     if (__syncthreads_or(!ok)) {
       ok = false;
       break;
     }
-    const long long k0 = kb + (long long)it * BK;
-    stage_kmajor(X, K, i0, nx, k0, st, st + TILE_BYTES);
-    stage_kmajor(Y, K, j0, ny, k0, st + 2 * TILE_BYTES, st + 3 * TILE_BYTES);
+    store_row(cur_a, tid, st, st + TILE_BYTES);
+    store_row(cur_b, tid, st + 2 * TILE_BYTES, st + 3 * TILE_BYTES);
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -273,11 +291,20 @@ __global__ void __launch_bounds__(NT) tc_gram_kernel(const float *__restrict__ X
     for (int cb = 0; cb < BN / 32; ++cb) {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + 32 * cb, v);
-      if (i < nx) {
+      if (nsteps == 0) {
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const int j = j0 + 32 * cb + c;
-          if (j < ny) dst[j] = nsteps > 0 ? v[c] : 0.f;
+        for (int c = 0; c < 32; ++c) v[c] = 0.f;
+      }
+      const int jb = j0 + 32 * cb;
+      if (i < nx) {
+        if ((ny & 3) == 0 && jb + 32 <= ny) {
+          float4 *d4 = reinterpret_cast<float4 *>(dst + jb);  // 128 contiguous bytes of row i
+#pragma unroll
+          for (int c = 0; c < 8; ++c) d4[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 32; ++c)
+            if (jb + c < ny) dst[jb + c] = v[c];
         }
       }
     }
@@ -313,19 +340,23 @@ __global__ void gram_reduce2_kernel(const double *__restrict__ part2, int ne, do
 
 // ----------------------------------------------------------------------------------------
 // Left multiply: Z[i][c] = sum_l A[i][l] Y[l][c] for rows [i0, i0 + 128) of A (m x n) and
-// column tiles of 128, persistent over the column tiles.
+// column tiles of 128, persistent over the column tiles.  The A rows are split into bf16 hi/lo
+// once per CTA and stay in shared memory (n/32 K-steps of 2 x 8 KB); each K-step of Y is staged
+// one column per thread (32 coalesced scalar loads, prefetched one step ahead).
 // ----------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(NT) tc_left_mul_kernel(const float *__restrict__ A, int m, int n,
                                                          const float *__restrict__ Y, long long K, float *__restrict__ Z,
                                                          int *__restrict__ err) {
   extern __shared__ unsigned char dyn[];
   unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(dyn) + 1023) & ~uintptr_t(1023));
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(base + 2 * SmemLayout::kStage);
+  const int nsteps = (n + BK - 1) / BK;
+  unsigned char *a_tiles = base;                            // nsteps x {hi, lo}
+  unsigned char *b_stage = base + (size_t)nsteps * 2 * TILE_BYTES;  // 2 stages x {hi, lo}
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(b_stage + 2 * 2 * TILE_BYTES);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int i0 = blockIdx.y * BM;
   const long long ntiles = K / BN;
-  const int nsteps = (n + BK - 1) / BK;
 
   if (warp == 0) tmem_alloc(tmem_slot, 128);
   if (tid == 0) {
@@ -333,6 +364,20 @@ __global__ void __launch_bounds__(NT) tc_left_mul_kernel(const float *__restrict
     mbar_init(smem_u32(&mbar[1]));
     mbar_init_fence();
   }
+  // resident A: row i0 + tid, all K-steps
+  for (int it = 0; it < nsteps; ++it) {
+    Row32 r;
+    if (i0 + tid < m) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) r.v[j] = (it * BK + j < n) ? __ldg(A + (long long)(i0 + tid) * n + it * BK + j) : 0.f;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) r.v[j] = 0.f;
+    }
+    unsigned char *t = a_tiles + (size_t)it * 2 * TILE_BYTES;
+    store_row(r, tid, t, t + TILE_BYTES);
+  }
+  fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -340,36 +385,33 @@ __global__ void __launch_bounds__(NT) tc_left_mul_kernel(const float *__restrict
   Pipe pipe;
   pipe.init();
   bool ok = true;
-  for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+  Row32 nxt;
+  long long t0 = blockIdx.x;
+  if (t0 < ntiles) load_col(Y, K, 0, n, t0 * BN + tid, nxt);
+  for (long long t = t0; t < ntiles && ok; t += gridDim.x) {
     const long long c0 = t * BN;
     for (int it = 0; it < nsteps; ++it) {
       const int s = it & 1;
-      unsigned char *st = base + s * SmemLayout::kStage;
+      unsigned char *st = b_stage + s * 2 * TILE_BYTES;
+      const Row32 cur = nxt;
+      // prefetch the next K-step of this tile, or the first K-step of the next tile
+      if (it + 1 < nsteps) {
+        load_col(Y, K, (it + 1) * BK, n, c0 + tid, nxt);
+      } else if (t + gridDim.x < ntiles) {
+        load_col(Y, K, 0, n, (t + gridDim.x) * BN + tid, nxt);
+      }
       ok = pipe.drain(mbar, s);
       if (__syncthreads_or(!ok)) {
         ok = false;
         break;
       }
-      const int l0 = it * BK;
-      // A rows i0.., K-columns l0..l0+31 (A is m x n, n contiguous; columns >= n are zero)
-#pragma unroll
-      for (int q = 0; q < (BM * BK) / NT; ++q) {
-        const int f = tid + NT * q;
-        const int row = f >> 5, l = f & 31;
-        const float v = (i0 + row < m && l0 + l < n) ? __ldg(A + (long long)(i0 + row) * n + l0 + l) : 0.f;
-        uint16_t h, lo16;
-        split1(v, h, lo16);
-        const uint32_t off = tile_off(row, l);
-        *reinterpret_cast<uint16_t *>(st + off) = h;
-        *reinterpret_cast<uint16_t *>(st + TILE_BYTES + off) = lo16;
-      }
-      stage_transposed(Y, K, l0, n, c0, st + 2 * TILE_BYTES, st + 3 * TILE_BYTES);
+      store_row(cur, tid, st, st + TILE_BYTES);
       fence_async_smem();
       __syncthreads();
       if (tid == 0) {
         tc_fence_after();
-        const uint32_t a_hi = smem_u32(st), a_lo = a_hi + TILE_BYTES, b_hi = a_hi + 2 * TILE_BYTES,
-                       b_lo = a_hi + 3 * TILE_BYTES;
+        const uint32_t a_hi = smem_u32(a_tiles + (size_t)it * 2 * TILE_BYTES), a_lo = a_hi + TILE_BYTES;
+        const uint32_t b_hi = smem_u32(st), b_lo = b_hi + TILE_BYTES;
 #pragma unroll
         for (int ks = 0; ks < BK / 16; ++ks) {
           const uint32_t o = ks * 2 * LBO;
@@ -458,7 +500,9 @@ size_t tc_gram_workspace_bytes(int nx, int ny, long long K) {
 cudaError_t launch_tc_left_mul(const float *A, int m, int n, const float *Y, long long K, float *Z, int *err,
                                cudaStream_t st) {
   if (K % tc::BN != 0) return cudaErrorInvalidValue;
-  const int smem = (int)tc::SmemLayout::kBytes;
+  const int nsteps = (n + tc::BK - 1) / tc::BK;
+  const int smem = (int)(((size_t)nsteps * 2 + 4) * tc::TILE_BYTES + 2048);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(tc::tc_left_mul_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 152;
@@ -466,7 +510,8 @@ cudaError_t launch_tc_left_mul(const float *A, int m, int n, const float *Y, lon
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long tiles = K / tc::BN;
   const int rows = (m + tc::BM - 1) / tc::BM;
-  const long long want = (long long)sms * 3 / rows;
+  const int per_sm = smem <= 110 * 1024 ? 2 : 1;
+  const long long want = (long long)sms * per_sm / rows;
   const unsigned gx = (unsigned)std::max(1LL, std::min(tiles, want));
   tc::tc_left_mul_kernel<<<dim3(gx, rows), tc::NT, smem, st>>>(A, m, n, Y, K, Z, err);
   return cudaGetLastError();
