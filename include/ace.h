@@ -127,6 +127,17 @@ ace_status ace_stage_times(const ace_op *op, float ms[6]);
 /* Number of this library's CUDA kernels that the build of `op` launched. */
 ace_status ace_kernel_launches(const ace_op *op, long *launches);
 
+/* Autotuner of the pair chain; the paper has no counterpart (it is a property of this GPU code).
+ * Screens `phi` as ace_build does, then times the pair chain on a sample of up to 96 of its packs
+ * for each candidate setting: packs per batch {1,2,3,4,6}, side streams {2,4}, L2 set-aside for the
+ * scratch {0, 60 MB}.  The fastest setting is kept for this grid and precision and used by later
+ * builds in the process; with the environment variable ACE_TUNE_FILE set, the table is also read from
+ * and written to that file.  params (optional, 4 ints) receives {group, batch, streams, l2_mb}.
+ * Environment variables ACE_PLANE_BATCH, ACE_STREAMS, ACE_L2_PERSIST_MB, ACE_GROUP override the table.
+ * Grids without a plane-pass plan keep the defaults.  Synchronous.  Errors as ace_build. */
+ace_status ace_autotune(const ace_desc *desc, const void *phi, ace_dtype dtype, void *cuda_stream,
+                        int *params);
+
 /* 1 if an axis length has a compiled FFT plan for precision `prec`, else 0. */
 int ace_grid_supported(int n_axis, ace_precision prec);
 

@@ -45,7 +45,7 @@ ACE_GET_OVERLAP = 6
 EXPORTED = [
     "ace_build", "ace_build_batched", "ace_apply", "exchange_energy", "ace_get", "ace_pair_count",
     "ace_get_size", "ace_stage_times", "ace_kernel_launches", "ace_grid_supported", "ace_destroy",
-    "ace_last_error", "ace_exchange_w_noalloc",
+    "ace_last_error", "ace_exchange_w_noalloc", "ace_autotune",
 ]
 
 
@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH):
         lib.ace_pair_count.argtypes = [vp, ctypes.POINTER(c_long)]
         lib.ace_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         lib.ace_kernel_launches.argtypes = [vp, ctypes.POINTER(c_long)]
+        lib.ace_autotune.argtypes = [ctypes.POINTER(AceDesc), vp, c_int, vp, ctypes.POINTER(c_int)]
         lib.ace_exchange_w_noalloc.argtypes = [ctypes.POINTER(AceDesc), vp, c_int, ctypes.POINTER(c_int), c_long,
                                                vp, vp]
         lib.ace_grid_supported.argtypes = [c_int, c_int]
@@ -117,7 +118,8 @@ def load(path: str = LIB_PATH):
         lib.ace_destroy.restype = None
         lib.ace_last_error.restype = ctypes.c_char_p
         for name in ("ace_build", "ace_build_batched", "ace_apply", "exchange_energy", "ace_get", "ace_get_size",
-                     "ace_pair_count", "ace_stage_times", "ace_kernel_launches", "ace_exchange_w_noalloc"):
+                     "ace_pair_count", "ace_stage_times", "ace_kernel_launches", "ace_exchange_w_noalloc",
+                     "ace_autotune"):
             getattr(lib, name).restype = c_int
         _lib = lib
         return lib
@@ -270,6 +272,16 @@ def ace_stage_times(op: AceOp):
     ms = (ctypes.c_float * 6)()
     _check(load().ace_stage_times(op.handle, ms))
     return {k: float(v) for k, v in zip(("screen", "pair_chain", "M", "cholesky", "xi", "total"), ms)}
+
+
+def ace_autotune(desc: AceDesc, phi, stream=None) -> dict:
+    """ace_autotune: pick the pair-chain batch / stream / L2 settings for this grid and precision."""
+    ptr, code, numel = _array_info(phi)
+    if numel != desc.norb * desc.n[0] * desc.n[1] * desc.n[2]:
+        raise ValueError("phi does not match the descriptor")
+    out = (ctypes.c_int * 4)()
+    _check(load().ace_autotune(ctypes.byref(desc), ptr, code, _stream_handle(stream), out))
+    return {"group": out[0], "batch": out[1], "streams": out[2], "l2_mb": out[3]}
 
 
 def ace_kernel_launches(op: AceOp) -> int:

@@ -376,6 +376,76 @@ bool find_plane_ops<double>(int n2, int n3, ace::PlaneOps<double> *out) {
   return ace::plane_ops_f64(n2, n3, out);
 }
 
+// Run-time parameters of the plane chain: packs per CTA group (G), packs per batch (B), side
+// streams, and the L2 set-aside for the scratch window (MB).  Defaults, or values found by
+// ace_autotune for the grid and precision; ACE_* environment variables override both.
+struct ChainParams {
+  int G = 1, B = 2, streams = 4, persist_mb = 60;
+};
+
+struct TuneKey {
+  int n1, n2, n3, fp64;
+  bool operator==(const TuneKey &o) const {
+    return n1 == o.n1 && n2 == o.n2 && n3 == o.n3 && fp64 == o.fp64;
+  }
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, ChainParams>> g_tuned;
+bool g_tune_file_read = false;
+
+void tune_file_load_locked() {
+  if (g_tune_file_read) return;
+  g_tune_file_read = true;
+  const char *path = std::getenv("ACE_TUNE_FILE");
+  if (!path || !*path) return;
+  FILE *f = std::fopen(path, "r");
+  if (!f) return;
+  TuneKey k;
+  ChainParams c;
+  while (std::fscanf(f, "%d %d %d %d %d %d %d %d", &k.n1, &k.n2, &k.n3, &k.fp64, &c.G, &c.B, &c.streams,
+                     &c.persist_mb) == 8)
+    g_tuned.emplace_back(k, c);
+  std::fclose(f);
+}
+
+void tune_store(const TuneKey &k, const ChainParams &c) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_file_load_locked();
+  bool found = false;
+  for (auto &e : g_tuned)
+    if (e.first == k) {
+      e.second = c;
+      found = true;
+    }
+  if (!found) g_tuned.emplace_back(k, c);
+  const char *path = std::getenv("ACE_TUNE_FILE");
+  if (path && *path) {
+    FILE *f = std::fopen(path, "w");
+    if (f) {
+      for (const auto &e : g_tuned)
+        std::fprintf(f, "%d %d %d %d %d %d %d %d\n", e.first.n1, e.first.n2, e.first.n3, e.first.fp64, e.second.G,
+                     e.second.B, e.second.streams, e.second.persist_mb);
+      std::fclose(f);
+    }
+  }
+}
+
+ChainParams chain_params(const ace_desc &d, bool fp64) {
+  ChainParams c;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_file_load_locked();
+    const TuneKey k{d.n[0], d.n[1], d.n[2], fp64 ? 1 : 0};
+    for (const auto &e : g_tuned)
+      if (e.first == k) c = e.second;
+  }
+  c.G = std::max(1, env_int("ACE_GROUP", c.G));
+  c.B = std::max(c.G, env_int("ACE_PLANE_BATCH", c.B));
+  c.streams = std::min(4, std::max(1, env_int("ACE_STREAMS", c.streams)));
+  c.persist_mb = std::max(0, env_int("ACE_L2_PERSIST_MB", c.persist_mb));
+  return c;
+}
+
 // Five pencil passes per batch of packs (any compiled grid).
 template <typename T>
 ace_status run_chain_pencil(ace_op *op, const T *phi, const T *Kd, const cpx<T> *const *twd, int count,
@@ -418,13 +488,13 @@ ace_status run_chain_pencil(ace_op *op, const T *phi, const T *Kd, const cpx<T> 
 // Plane, pencil, plane per batch; packs grouped by their shared first orbital.
 template <typename T>
 ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, const ace::PlaneOps<T> &pops,
-                           int count, std::vector<void *> &temps) {
+                           int count, std::vector<void *> &temps, const ChainParams &cp, int max_packs = -1) {
   const ace_desc &d = op->desc;
   const long long N = op->N;
   cudaStream_t st = op->stream;
-  const int G = std::max(1, env_int("ACE_GROUP", 1));
-  const int B = std::max(G, env_int("ACE_PLANE_BATCH", 2));
-  const int nstreams = std::min(4, std::max(1, env_int("ACE_STREAMS", 4)));
+  const int G = cp.G;
+  const int B = std::max(G, cp.B);
+  const int nstreams = std::min(4, std::max(1, cp.streams));
   const bool acc = pops.acc_fits && G > 1;
   // packs: two pairs of one row (i, j1), (i, j2); leftover single pairs of different rows are
   // packed together at the end as mixed packs
@@ -490,7 +560,7 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   }
   // ask L2 to keep each stream's FFT scratch resident between the three passes (a per-context
   // set-aside of the L2 for persisting lines; ACE_L2_PERSIST_MB=0 turns it off)
-  const int persist_mb = env_int("ACE_L2_PERSIST_MB", 60);
+  const int persist_mb = cp.persist_mb;
   if (persist_mb > 0 && nstreams > 1) {
     size_t limit = (size_t)persist_mb << 20;
     cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, limit);
@@ -528,6 +598,7 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   ca.n3 = d.n[2];
   for (size_t bi = 0; bi < batches.size(); ++bi) {
     const int2 b = batches[bi];
+    if (max_packs >= 0 && groups[b.x].x >= max_packs) break;  // autotuning sample
     const int k = (int)(bi % nstreams);
     const int p0 = groups[b.x].x;
     const int p1 = groups[b.y - 1].x + groups[b.y - 1].y;
@@ -661,7 +732,7 @@ ace_status build_finish(ace_op *op) {
   ace::PlaneOps<T> pops{};
   const bool plane = find_plane_ops<T>(d.n[1], d.n[2], &pops) && env_int("ACE_FORCE_PENCIL", 0) == 0;
   if (count > 0 && plane) {
-    s = run_chain_plane<T>(op, phi, tab, pops, count, temps);
+    s = run_chain_plane<T>(op, phi, tab, pops, count, temps, chain_params(d, op->fp64));
   } else if (count > 0) {
     const cpx<T> *twd[3] = {static_cast<const cpx<T> *>(tab->tw[0]), static_cast<const cpx<T> *>(tab->tw[1]),
                             static_cast<const cpx<T> *>(tab->tw[2])};
@@ -1031,6 +1102,81 @@ ace_status ace_kernel_launches(const ace_op *op, long *launches) {
 ace_status ace_stage_times(const ace_op *op, float ms[6]) {
   if (!op || !ms) return fail(ACE_ERR_ARG, "NULL argument");
   for (int i = 0; i < 6; ++i) ms[i] = op->stage_ms[i];
+  return ACE_OK;
+}
+
+ace_status ace_autotune(const ace_desc *desc, const void *phi, ace_dtype dtype, void *cuda_stream, int *params) {
+  ace_status s = check_desc(desc);
+  if (s != ACE_OK) return s;
+  if (!phi) return fail(ACE_ERR_ARG, "phi is NULL");
+  if (dtype != ACE_F32 && dtype != ACE_F64) return fail(ACE_ERR_ARG, "unknown dtype %d", (int)dtype);
+  ace_op *op = new_op(desc, static_cast<cudaStream_t>(cuda_stream), &s);
+  if (!op) return s;
+  struct Guard {
+    ace_op *op;
+    ~Guard() {
+      cudaStreamSynchronize(op->stream);
+      ace_destroy(op);
+    }
+  } guard{op};
+  s = begin_any(op, phi, dtype);
+  if (s != ACE_OK) return s;
+  ACE_CUDA(cudaEventSynchronize(op->ev[1]), "pair list readback");
+  const int count = *static_cast<const int *>(op->readback);
+  op->npairs = count;
+  const int2 *ph = reinterpret_cast<const int2 *>(static_cast<const char *>(op->readback) + 32);
+  op->pairs_h.assign(ph, ph + count);
+  ChainParams best = chain_params(*desc, op->fp64);
+  auto run = [&](auto tag) -> ace_status {
+    using T = decltype(tag);
+    ace::PlaneOps<T> pops{};
+    if (count == 0 || !find_plane_ops<T>(desc->n[1], desc->n[2], &pops)) return ACE_OK;  // nothing to tune
+    ACE_CUDA(op_alloc(op, &op->W, op->esz * (size_t)op->n * op->N), "alloc W");
+    const T *phi_w = static_cast<const T *>(op->phi_work);
+    const int sample = std::min((count + 1) / 2, 96);
+    cudaEvent_t e0, e1;
+    ACE_CUDA(cudaEventCreate(&e0), "event");
+    ACE_CUDA(cudaEventCreate(&e1), "event");
+    float best_ms = 1e30f;
+    const int Bs[5] = {1, 2, 3, 4, 6}, Ss[2] = {2, 4}, Ps[2] = {0, 60};
+    for (int bi = 0; bi < 5; ++bi)
+      for (int si = 0; si < 2; ++si)
+        for (int pi = 0; pi < 2; ++pi) {
+          ChainParams c;
+          c.G = 1;
+          c.B = Bs[bi];
+          c.streams = Ss[si];
+          c.persist_mb = Ps[pi];
+          float t[2];
+          for (int rep = 0; rep < 2; ++rep) {
+            std::vector<void *> tmp;
+            ACE_CUDA(cudaEventRecord(e0, op->stream), "event");
+            ace_status r = run_chain_plane<T>(op, phi_w, op->tab, pops, count, tmp, c, sample);
+            ACE_CUDA(cudaEventRecord(e1, op->stream), "event");
+            for (void *q : tmp) cudaFreeAsync(q, op->stream);
+            if (r != ACE_OK) return r;
+            ACE_CUDA(cudaEventSynchronize(e1), "tuning run");
+            cudaEventElapsedTime(&t[rep], e0, e1);
+          }
+          const float ms = std::min(t[0], t[1]);
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+          }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    tune_store(TuneKey{desc->n[0], desc->n[1], desc->n[2], op->fp64 ? 1 : 0}, best);
+    return ACE_OK;
+  };
+  s = op->fp64 ? run(double{}) : run(float{});
+  if (s != ACE_OK) return s;
+  if (params) {
+    params[0] = best.G;
+    params[1] = best.B;
+    params[2] = best.streams;
+    params[3] = best.persist_mb;
+  }
   return ACE_OK;
 }
 
