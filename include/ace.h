@@ -61,7 +61,7 @@ typedef enum { ACE_F32 = 0, ACE_F64 = 1 } ace_dtype;
 typedef struct {
   int n[3];              /* N1, N2, N3 (each must satisfy ace_grid_supported)                  */
   double lattice[3][3];  /* rows a1, a2, a3 in bohr; det != 0                                    */
-  int norb;              /* n, 1 <= n <= 256                                                     */
+  int norb;              /* n, 1 <= n <= 1024                                                    */
   double rho_cut;        /* keep (i,j) iff dV sum_r |phi_i phi_j| >= rho_cut; <= 0 keeps all     */
   double spin_factor;    /* f in E_x = (f/2) tr M: 2 closed shell, 1 one spin channel            */
   ace_precision prec;
