@@ -129,11 +129,13 @@ ace_status ace_kernel_launches(const ace_op *op, long *launches);
 
 /* Autotuner of the pair chain; the paper has no counterpart (it is a property of this GPU code).
  * Screens `phi` as ace_build does, then times the pair chain on a sample of up to 96 of its packs
- * for each candidate setting: packs per batch {1,2,3,4,6}, side streams {2,4}, L2 set-aside for the
- * scratch {0, 60 MB}.  The fastest setting is kept for this grid and precision and used by later
- * builds in the process; with the environment variable ACE_TUNE_FILE set, the table is also read from
- * and written to that file.  params (optional, 4 ints) receives {group, batch, streams, l2_mb}.
- * Environment variables ACE_PLANE_BATCH, ACE_STREAMS, ACE_L2_PERSIST_MB, ACE_GROUP override the table.
+ * for each candidate setting: packs per batch {1,2,3,4,6}, side streams {2,4,8}, L2 set-aside for the
+ * scratch {0, 60 MB}, rows per block of the pack order {1,2,4,8}.  The fastest setting is kept for
+ * this grid and precision and used by later builds in the process; with the environment variable
+ * ACE_TUNE_FILE set, the table is also read from and written to that file (one line per grid:
+ * n1 n2 n3 fp64 group batch streams l2_mb row_block).  params (optional, 5 ints) receives
+ * {group, batch, streams, l2_mb, row_block}.  Environment variables ACE_PLANE_BATCH, ACE_STREAMS,
+ * ACE_L2_PERSIST_MB, ACE_GROUP, ACE_ROW_BLOCK override the table.
  * Grids without a plane-pass plan keep the defaults.  Synchronous.  Errors as ace_build. */
 ace_status ace_autotune(const ace_desc *desc, const void *phi, ace_dtype dtype, void *cuda_stream,
                         int *params);

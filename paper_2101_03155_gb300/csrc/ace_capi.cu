@@ -352,10 +352,11 @@ void pinned_put(void *p, size_t bytes) {
 // Per-device side streams of the pair chain (created once, non-blocking, kept until exit).
 std::mutex g_side_mu;
 constexpr int kLanes = 4;           // concurrent builds of one batched call
-cudaStream_t g_side[64][5 * kLanes] = {};  // per lane: 4 chain side streams + the lane stream
+constexpr int kSide = 8;            // pair-chain side streams per lane
+cudaStream_t g_side[64][(kSide + 1) * kLanes] = {};  // per lane: kSide chain side streams; then the lane streams
 
 cudaError_t get_side_stream(int dev, int k, cudaStream_t *out) {
-  if (dev < 0 || dev >= 64 || k < 0 || k >= 5 * kLanes) return cudaErrorInvalidValue;
+  if (dev < 0 || dev >= 64 || k < 0 || k >= (kSide + 1) * kLanes) return cudaErrorInvalidValue;
   std::lock_guard<std::mutex> lk(g_side_mu);
   if (!g_side[dev][k]) {
     cudaError_t e = cudaStreamCreateWithFlags(&g_side[dev][k], cudaStreamNonBlocking);
@@ -381,6 +382,7 @@ bool find_plane_ops<double>(int n2, int n3, ace::PlaneOps<double> *out) {
 // ace_autotune for the grid and precision; ACE_* environment variables override both.
 struct ChainParams {
   int G = 1, B = 2, streams = 4, persist_mb = 60;
+  int RB = 4;  // rows per block of the pack order
 };
 
 struct TuneKey {
@@ -402,8 +404,8 @@ void tune_file_load_locked() {
   if (!f) return;
   TuneKey k;
   ChainParams c;
-  while (std::fscanf(f, "%d %d %d %d %d %d %d %d", &k.n1, &k.n2, &k.n3, &k.fp64, &c.G, &c.B, &c.streams,
-                     &c.persist_mb) == 8)
+  while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d", &k.n1, &k.n2, &k.n3, &k.fp64, &c.G, &c.B, &c.streams,
+                     &c.persist_mb, &c.RB) == 9)
     g_tuned.emplace_back(k, c);
   std::fclose(f);
 }
@@ -423,8 +425,8 @@ void tune_store(const TuneKey &k, const ChainParams &c) {
     FILE *f = std::fopen(path, "w");
     if (f) {
       for (const auto &e : g_tuned)
-        std::fprintf(f, "%d %d %d %d %d %d %d %d\n", e.first.n1, e.first.n2, e.first.n3, e.first.fp64, e.second.G,
-                     e.second.B, e.second.streams, e.second.persist_mb);
+        std::fprintf(f, "%d %d %d %d %d %d %d %d %d\n", e.first.n1, e.first.n2, e.first.n3, e.first.fp64, e.second.G,
+                     e.second.B, e.second.streams, e.second.persist_mb, e.second.RB);
       std::fclose(f);
     }
   }
@@ -441,8 +443,9 @@ ChainParams chain_params(const ace_desc &d, bool fp64) {
   }
   c.G = std::max(1, env_int("ACE_GROUP", c.G));
   c.B = std::max(c.G, env_int("ACE_PLANE_BATCH", c.B));
-  c.streams = std::min(4, std::max(1, env_int("ACE_STREAMS", c.streams)));
+  c.streams = std::min(kSide, std::max(1, env_int("ACE_STREAMS", c.streams)));
   c.persist_mb = std::max(0, env_int("ACE_L2_PERSIST_MB", c.persist_mb));
+  c.RB = std::max(1, env_int("ACE_ROW_BLOCK", c.RB));
   return c;
 }
 
@@ -494,32 +497,70 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   cudaStream_t st = op->stream;
   const int G = cp.G;
   const int B = std::max(G, cp.B);
-  const int nstreams = std::min(4, std::max(1, cp.streams));
+  const int nstreams = std::min(kSide, std::max(1, cp.streams));
   const bool acc = pops.acc_fits && G > 1;
-  // packs: two pairs of one row (i, j1), (i, j2); leftover single pairs of different rows are
-  // packed together at the end as mixed packs
+  // packs: two pairs that share an orbital s, written (s, i1, s, i2), so that both plane passes
+  // read three planes and the W_s terms of the pack go out with one atomic.  The sorted pair list
+  // is taken in blocks of RB consecutive rows; inside a block, pairs with the same partner j are
+  // packed together first (phi_j and W_j are then reused while they are in L2, and the block's own
+  // rows stay in L2 for the whole block), then the block's remaining pairs by common row (RB = 1
+  // gives the row packs (i, j1), (i, j2) only).  Single pairs left over are packed together at the
+  // end as mixed packs.
+  const int RB = std::max(1, cp.RB);
   std::vector<int4> packs;
   std::vector<int4> groups;
   std::vector<int2> left;
-  const std::vector<int2> &pr = op->pairs_h;
-  size_t r0 = 0;
-  while (r0 < pr.size()) {
-    size_t r1 = r0;
-    while (r1 < pr.size() && pr[r1].x == pr[r0].x) ++r1;
-    const int row = pr[r0].x;
-    size_t k = r0;
-    const int gfirst = (int)packs.size();
-    for (; k + 1 < r1; k += 2) packs.push_back(make_int4(row, pr[k].y, row, pr[k + 1].y));
-    if (k < r1) left.push_back(pr[k]);
-    for (int g0 = gfirst; g0 < (int)packs.size(); g0 += G)
-      groups.push_back(make_int4(g0, std::min(G, (int)packs.size() - g0), acc ? row : -1, 0));
-    r0 = r1;
+  {
+    const std::vector<int2> &pr = op->pairs_h;
+    std::vector<int2> bp, rest;
+    size_t r0 = 0;
+    while (r0 < pr.size()) {
+      const int blk = pr[r0].x / RB;
+      size_t r1 = r0;
+      while (r1 < pr.size() && pr[r1].x / RB == blk) ++r1;
+      bp.assign(pr.begin() + r0, pr.begin() + r1);
+      rest.clear();
+      if (RB > 1) {
+        std::stable_sort(bp.begin(), bp.end(), [](int2 u, int2 v) { return u.y < v.y; });
+        for (size_t k = 0; k < bp.size();) {
+          size_t k1 = k;
+          while (k1 < bp.size() && bp[k1].y == bp[k].y) ++k1;
+          const int j = bp[k].y;
+          size_t m = k;
+          for (; m + 1 < k1; m += 2) packs.push_back(make_int4(j, bp[m].x, j, bp[m + 1].x));
+          if (m < k1) rest.push_back(bp[m]);
+          k = k1;
+        }
+        std::sort(rest.begin(), rest.end(), [](int2 u, int2 v) { return u.x < v.x || (u.x == v.x && u.y < v.y); });
+      } else {
+        rest.swap(bp);
+      }
+      for (size_t k = 0; k < rest.size();) {
+        size_t k1 = k;
+        while (k1 < rest.size() && rest[k1].x == rest[k].x) ++k1;
+        const int row = rest[k].x;
+        size_t m = k;
+        for (; m + 1 < k1; m += 2) packs.push_back(make_int4(row, rest[m].y, row, rest[m + 1].y));
+        if (m < k1) left.push_back(rest[m]);
+        k = k1;
+      }
+      r0 = r1;
+    }
   }
+  const int nshared = (int)packs.size();
   for (size_t k = 0; k < left.size(); k += 2) {
     const int2 p = left[k];
     const int2 q = (k + 1 < left.size()) ? left[k + 1] : make_int2(-1, -1);
-    groups.push_back(make_int4((int)packs.size(), 1, -1, 0));
     packs.push_back(make_int4(p.x, p.y, q.x, q.y));
+  }
+  // groups: runs of at most G consecutive packs with the same shared orbital (accumulated in
+  // shared memory by the inverse pass when acc); mixed packs are groups of their own
+  for (int k = 0; k < (int)packs.size();) {
+    int k1 = k + 1;
+    if (k < nshared)
+      while (k1 < nshared && k1 - k < G && packs[k1].x == packs[k].x) ++k1;
+    groups.push_back(make_int4(k, k1 - k, (acc && k < nshared) ? packs[k].x : -1, 0));
+    k = k1;
   }
   // batches of whole groups holding at most B packs
   std::vector<int2> batches;  // (first group, end group)
@@ -548,13 +589,14 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   cpx<T> *scratch_all = static_cast<cpx<T> *>(tmp);
   // consecutive batches alternate between side streams (own scratch each) so that one batch's
   // kernels fill the tail of the previous one; W is only touched by atomic adds
-  cudaStream_t side[4] = {st, st, st, st};
+  cudaStream_t side[kSide];
+  for (int k = 0; k < kSide; ++k) side[k] = st;
   cudaEvent_t fork = nullptr;
   if (nstreams > 1) {
     ACE_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "event");
     ACE_CUDA(cudaEventRecord(fork, st), "event");
     for (int k = 0; k < nstreams; ++k) {
-      ACE_CUDA(get_side_stream(op->dev, 4 * op->lane + k, &side[k]), "side stream");
+      ACE_CUDA(get_side_stream(op->dev, kSide * op->lane + k, &side[k]), "side stream");
       ACE_CUDA(cudaStreamWaitEvent(side[k], fork, 0), "wait");
     }
   }
@@ -997,7 +1039,7 @@ ace_status ace_build_batched(int k, const ace_desc *desc, const void *const *phi
   ACE_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "event");
   ACE_CUDA(cudaEventRecord(fork, user), "event");
   for (int l = 0; l < lanes; ++l) {
-    ACE_CUDA(get_side_stream(dev, 4 * kLanes + l, &lane_st[l]), "lane stream");
+    ACE_CUDA(get_side_stream(dev, kSide * kLanes + l, &lane_st[l]), "lane stream");
     ACE_CUDA(cudaStreamWaitEvent(lane_st[l], fork, 0), "fork");
   }
   ace_status s = ACE_OK;
@@ -1138,15 +1180,17 @@ ace_status ace_autotune(const ace_desc *desc, const void *phi, ace_dtype dtype, 
     ACE_CUDA(cudaEventCreate(&e0), "event");
     ACE_CUDA(cudaEventCreate(&e1), "event");
     float best_ms = 1e30f;
-    const int Bs[5] = {1, 2, 3, 4, 6}, Ss[2] = {2, 4}, Ps[2] = {0, 60};
+    const int Bs[5] = {1, 2, 3, 4, 6}, Ss[3] = {2, 4, 8}, Ps[2] = {0, 60}, Rs[4] = {1, 2, 4, 8};
+    for (int ri = 0; ri < 4; ++ri)
     for (int bi = 0; bi < 5; ++bi)
-      for (int si = 0; si < 2; ++si)
+      for (int si = 0; si < 3; ++si)
         for (int pi = 0; pi < 2; ++pi) {
           ChainParams c;
           c.G = 1;
           c.B = Bs[bi];
           c.streams = Ss[si];
           c.persist_mb = Ps[pi];
+          c.RB = Rs[ri];
           float t[2];
           for (int rep = 0; rep < 2; ++rep) {
             std::vector<void *> tmp;
@@ -1176,6 +1220,7 @@ ace_status ace_autotune(const ace_desc *desc, const void *phi, ace_dtype dtype, 
     params[1] = best.B;
     params[2] = best.streams;
     params[3] = best.persist_mb;
+    params[4] = best.RB;
   }
   return ACE_OK;
 }

@@ -23,12 +23,27 @@
 #define ACE_FWD_UNROLL 4
 #endif
 #ifndef ACE_INV_UNROLL
-#define ACE_INV_UNROLL 2
+#define ACE_INV_UNROLL 4
 #endif
 #define ACE_PRAGMA(x) _Pragma(#x)
 #define ACE_UNROLL(n) ACE_PRAGMA(unroll n)
 
 namespace ace {
+
+// FP32 plane kernels: CTAs per SM that shared memory allows (at most ACE_PLANE_MAXB), used as the
+// register budget so that registers do not lower that residency.  FP64 kernels keep the
+// compiler's choice (one or two CTAs fit by shared memory there).
+#ifndef ACE_PLANE_MAXB
+#define ACE_PLANE_MAXB 3
+#endif
+template <typename T, int N2, int N3, bool ACC>
+constexpr int plane_min_blocks() {
+  constexpr long long bytes =
+      (long long)sizeof(cpx<T>) * (N2 * (N3 + 1) + N2 + N3) + (ACC ? (long long)sizeof(T) * N2 * N3 : 0);
+  constexpr long long fit = (227LL * 1024) / bytes;
+  if (sizeof(T) != 4) return 1;
+  return fit < 1 ? 1 : (fit > ACE_PLANE_MAXB ? ACE_PLANE_MAXB : (int)fit);
+}
 
 template <int N2, int N3>
 struct PlaneShape {
@@ -39,6 +54,22 @@ struct PlaneShape {
   static_assert(N3 % 4 == 0, "rows are processed in groups of four points");
 };
 
+// Per-thread walk over the tasks (l, m), l < NL, m < NM, of one stage (l fastest).  When NT is a
+// multiple of NL a thread keeps one l and steps m by NT / NL, so the split of the task index is done
+// once per thread instead of once per task.
+template <int NL, int NM, int NT, typename F>
+__device__ __forceinline__ void for_tasks(F &&f) {
+  if constexpr (NT % NL == 0) {
+    constexpr int STEP = NT / NL;
+    const int l = threadIdx.x % NL;
+#pragma unroll 1
+    for (int m = threadIdx.x / NL; m < NM; m += STEP) f(l, m);
+  } else {
+#pragma unroll 1
+    for (int task = threadIdx.x; task < NL * NM; task += NT) f(task % NL, task / NL);
+  }
+}
+
 template <typename T, int NT>
 struct PlaneStages {
   // stage 1 over NL lines of length L (element p of line l at s[l*LS + p*PS]):
@@ -46,8 +77,7 @@ struct PlaneStages {
   template <int L, int NL, int LS, int PS, int D, bool TW>
   static __device__ __forceinline__ void stage1(cpx<T> *s, const cpx<T> *tw) {
     constexpr int R1 = Factor<L>::R1, R2 = Factor<L>::R2;
-    for (int task = threadIdx.x; task < NL * R2; task += NT) {
-      const int l = task % NL, n2 = task / NL;
+    for_tasks<NL, R2, NT>([&](int l, int n2) {
       cpx<T> *line = s + l * LS + n2 * PS;
       cpx<T> x[R1];
 #pragma unroll
@@ -62,14 +92,13 @@ struct PlaneStages {
         }
         line[k1 * R2 * PS] = v;
       }
-    }
+    });
   }
   // stage 2: tasks (l, k1): DFT_R2 of the contiguous block k1 R2 + n2; output k2 at k1 R2 + k2
   template <int L, int NL, int LS, int PS, int D>
   static __device__ __forceinline__ void stage2(cpx<T> *s) {
     constexpr int R1 = Factor<L>::R1, R2 = Factor<L>::R2;
-    for (int task = threadIdx.x; task < NL * R1; task += NT) {
-      const int l = task % NL, k1 = task / NL;
+    for_tasks<NL, R1, NT>([&](int l, int k1) {
       cpx<T> *blk = s + l * LS + k1 * R2 * PS;
       cpx<T> x[R2];
 #pragma unroll
@@ -77,15 +106,15 @@ struct PlaneStages {
       Dft<R2, D, T>::run(x);
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) blk[k2 * PS] = x[k2];
-    }
+    });
   }
   // inverse stage A (permuted input): tasks (l, k1): inverse DFT_R2 over k2 of the block
-  // k1 R2 + k2, conjugate twiddle w_L^{+n2 k1}; result n2 at k1 R2 + n2
+  // k1 R2 + k2, conjugate twiddle w_L^{+n2 k1}; result n2 at k1 R2 + n2.  The k1 = 0 twiddles are
+  // the table's exact 1 + 0i, so every n2 > 0 term is multiplied without a branch on k1.
   template <int L, int NL, int LS, int PS>
   static __device__ __forceinline__ void inv_stageA(cpx<T> *s, const cpx<T> *tw) {
     constexpr int R1 = Factor<L>::R1, R2 = Factor<L>::R2;
-    for (int task = threadIdx.x; task < NL * R1; task += NT) {
-      const int l = task % NL, k1 = task / NL;
+    for_tasks<NL, R1, NT>([&](int l, int k1) {
       cpx<T> *blk = s + l * LS + k1 * R2 * PS;
       cpx<T> x[R2];
 #pragma unroll
@@ -94,15 +123,35 @@ struct PlaneStages {
 #pragma unroll
       for (int n2 = 0; n2 < R2; ++n2) {
         cpx<T> v = x[n2];
-        if (n2 > 0 && k1 > 0) {
+        if (n2 > 0) {
           const cpx<T> w = tw[n2 * k1];
           v = cmul(v, cpx<T>{w.x, -w.y});
         }
         blk[n2 * PS] = v;
       }
-    }
+    });
   }
 };
+
+// Walk over the points e = tid + it NT of an N2 x N3 plane: f(it, e, si) with si = i2 PP + i3 the
+// padded shared-memory index.  When NT is a multiple of N3 the row of a thread's point advances by
+// NT / N3 per step, so si needs no division.
+template <int N2, int N3, int NT, int UNROLL, typename F>
+__device__ __forceinline__ void for_points(F &&f) {
+  constexpr int NPTS = N2 * N3, PP = N3 + 1;
+  const int tid = threadIdx.x;
+  if constexpr (NT % N3 == 0 && NPTS % NT == 0) {
+    const int si0 = tid + tid / N3;
+#pragma unroll UNROLL
+    for (int it = 0; it < NPTS / NT; ++it) f(tid + it * NT, si0 + it * (NT + NT / N3));
+  } else {
+#pragma unroll UNROLL
+    for (int e = tid; e < NPTS; e += NT) {
+      const int i2 = e / N3;
+      f(e, e + i2 * (PP - N3));
+    }
+  }
+}
 
 template <typename T>
 struct Vec4;
@@ -139,7 +188,7 @@ struct Vec4<double> {
 // Forward plane pass: one CTA per (plane i1, pack).
 // ---------------------------------------------------------------------------------------
 template <typename T, int N2, int N3, int NT>
-__global__ void __launch_bounds__(NT) plane_fwd_kernel(PlaneArgs<T> a) {
+__global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, false>())) plane_fwd_kernel(PlaneArgs<T> a) {
   using S = PlaneShape<N2, N3>;
   using F = PlaneStages<T, NT>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -156,15 +205,23 @@ __global__ void __launch_bounds__(NT) plane_fwd_kernel(PlaneArgs<T> a) {
   const long long off = (long long)i1 * S::NPTS;
   const T *pa = a.phi + (long long)pk.x * a.N + off;
   const T *pb = a.phi + (long long)pk.y * a.N + off;
-  const bool two = pk.z >= 0;
-  const T *pc = a.phi + (long long)(two ? pk.z : 0) * a.N + off;
-  const T *pd = a.phi + (long long)(two ? pk.w : 0) * a.N + off;
-  ACE_UNROLL(ACE_FWD_UNROLL)
-  for (int e = tid; e < S::NPTS; e += NT) {
-    const int i2 = e / N3, i3 = e - i2 * N3;
-    const T re = __ldg(pa + e) * __ldg(pb + e);
-    const T im = two ? __ldg(pc + e) * __ldg(pd + e) : (T)0;
-    s[i2 * S::PP + i3] = cpx<T>{re, im};
+  if (pk.z == pk.x) {
+    // row pack (a, b), (a, d): z = phi_a (phi_b + i phi_d), three planes read
+    const T *pd = a.phi + (long long)pk.w * a.N + off;
+    for_points<N2, N3, NT, ACE_FWD_UNROLL>([&](int e, int si) {
+      const T fa = __ldg(pa + e);
+      s[si] = cpx<T>{fa * __ldg(pb + e), fa * __ldg(pd + e)};
+    });
+  } else if (pk.z >= 0) {
+    const T *pc = a.phi + (long long)pk.z * a.N + off;
+    const T *pd = a.phi + (long long)pk.w * a.N + off;
+    for_points<N2, N3, NT, ACE_FWD_UNROLL>([&](int e, int si) {
+      s[si] = cpx<T>{__ldg(pa + e) * __ldg(pb + e), __ldg(pc + e) * __ldg(pd + e)};
+    });
+  } else {
+    for_points<N2, N3, NT, ACE_FWD_UNROLL>([&](int e, int si) {
+      s[si] = cpx<T>{__ldg(pa + e) * __ldg(pb + e), (T)0};
+    });
   }
   __syncthreads();
   // axis 3 (rows): natural -> permuted
@@ -176,15 +233,14 @@ __global__ void __launch_bounds__(NT) plane_fwd_kernel(PlaneArgs<T> a) {
   F::template stage1<N2, N3, 1, S::PP, -1, true>(s, tw2);
   __syncthreads();
   cpx<T> *dst = a.scratch + (long long)(pidx - a.batch0) * a.N + off;
-  for (int task = tid; task < N3 * S::R1c; task += NT) {
-    const int p3 = task % N3, k1 = task / N3;
+  for_tasks<N3, S::R1c, NT>([&](int p3, int k1) {
     cpx<T> x[S::R2c];
 #pragma unroll
     for (int n2 = 0; n2 < S::R2c; ++n2) x[n2] = s[(k1 * S::R2c + n2) * S::PP + p3];
     Dft<S::R2c, -1, T>::run(x);
 #pragma unroll
     for (int k2 = 0; k2 < S::R2c; ++k2) dst[(k1 * S::R2c + k2) * N3 + p3] = x[k2];
-  }
+  });
 }
 
 // ---------------------------------------------------------------------------------------
@@ -193,7 +249,7 @@ __global__ void __launch_bounds__(NT) plane_fwd_kernel(PlaneArgs<T> a) {
 // first orbital grow (accumulated in shared memory), grow < 0 a single mixed pack.
 // ---------------------------------------------------------------------------------------
 template <typename T, int N2, int N3, int NT, bool ACC>
-__global__ void __launch_bounds__(NT) plane_inv_kernel(PlaneArgs<T> a) {
+__global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, ACC>())) plane_inv_kernel(PlaneArgs<T> a) {
   using S = PlaneShape<N2, N3>;
   using F = PlaneStages<T, NT>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -211,15 +267,14 @@ __global__ void __launch_bounds__(NT) plane_inv_kernel(PlaneArgs<T> a) {
   if (use_acc)
     for (int e = tid; e < S::NPTS; e += NT) acc[e] = (T)0;
   const long long off = (long long)i1 * S::NPTS;
-
   for (int q = 0; q < grp.y; ++q) {
     const int pidx = grp.x + q;
     const int4 pk = a.packs[pidx];
     const cpx<T> *src = a.scratch + (long long)(pidx - a.batch0) * a.N + off;
     __syncthreads();  // previous pack's epilogue has finished reading s
-    // axis 2 inverse, stage A straight from the scratch plane (permuted rows p2 = k1 R2c + k2)
-    for (int task = tid; task < N3 * S::R1c; task += NT) {
-      const int p3 = task % N3, k1 = task / N3;
+    // axis 2 inverse, stage A straight from the scratch plane (permuted rows p2 = k1 R2c + k2);
+    // the k1 = 0 twiddles are the table's exact 1 + 0i
+    for_tasks<N3, S::R1c, NT>([&](int p3, int k1) {
       cpx<T> x[S::R2c];
 #pragma unroll
       for (int k2 = 0; k2 < S::R2c; ++k2) x[k2] = src[(k1 * S::R2c + k2) * N3 + p3];
@@ -227,19 +282,17 @@ __global__ void __launch_bounds__(NT) plane_inv_kernel(PlaneArgs<T> a) {
 #pragma unroll
       for (int n2 = 0; n2 < S::R2c; ++n2) {
         cpx<T> v = x[n2];
-        if (n2 > 0 && k1 > 0) {
+        if (n2 > 0) {
           const cpx<T> w = tw2[n2 * k1];
           v = cmul(v, cpx<T>{w.x, -w.y});
         }
         s[(k1 * S::R2c + n2) * S::PP + p3] = v;
       }
-    }
+    });
     __syncthreads();
     F::template stage1<N2, N3, 1, S::PP, +1, false>(s, tw2);  // inverse stage B: natural rows
     __syncthreads();
     F::template inv_stageA<N3, N2, S::PP, 1>(s, tw3);
-    __syncthreads();
-    F::template stage1<N3, N2, S::PP, 1, +1, false>(s, tw3);  // natural columns
     __syncthreads();
     // epilogue: v = v_ab + i v_cd at natural points, one point per lane
     const bool two = pk.z >= 0;
@@ -252,21 +305,35 @@ __global__ void __launch_bounds__(NT) plane_inv_kernel(PlaneArgs<T> a) {
     T *wb = a.W + (long long)pk.y * a.N + off;
     T *wc = a.W + (long long)(two ? pk.z : 0) * a.N + off;
     T *wd = a.W + (long long)(two ? pk.w : 0) * a.N + off;
-    ACE_UNROLL(ACE_INV_UNROLL)
-    for (int e = tid; e < S::NPTS; e += NT) {
-      const int i2 = e / N3, i3 = e - i2 * N3;
-      const cpx<T> v = s[i2 * S::PP + i3];
-      const T pa_ = __ldg(fa + e), pb_ = __ldg(fb + e);
-      const T pc_ = two ? __ldg(fc + e) : (T)0, pd_ = two ? __ldg(fd + e) : (T)0;
-      const T to_a = v.x * pb_ + (same_a ? v.y * pd_ : (T)0);
-      if (use_acc) {
-        acc[e] += to_a;  // pk.x == grow (and pk.z == grow when two)
-      } else {
-        atomicAdd(wa + e, to_a);
-        if (two && !same_a) atomicAdd(wc + e, v.y * pd_);
-      }
-      if (pk.y != pk.x) atomicAdd(wb + e, v.x * pa_);
-      if (two && pk.w != pk.z) atomicAdd(wd + e, v.y * pc_);
+    F::template stage1<N3, N2, S::PP, 1, +1, false>(s, tw3);  // natural columns
+    __syncthreads();
+    auto last = [&](auto &&epi) {
+      for_points<N2, N3, NT, ACE_INV_UNROLL>([&](int e, int si) { epi(e, s[si]); });
+    };
+    if (!use_acc && same_a && pk.y != pk.x && pk.w != pk.x) {
+      // row pack (a, b), (a, d) with b, d != a: W_a += v_ab phi_b + v_ad phi_d, W_b += v_ab phi_a,
+      // W_d += v_ad phi_a  (v = v_ab + i v_ad)
+      last([&](int e, cpx<T> v) {
+        const T pa_ = __ldg(fa + e), pb_ = __ldg(fb + e), pd_ = __ldg(fd + e);
+        atomicAdd(wa + e, v.x * pb_ + v.y * pd_);
+        atomicAdd(wb + e, v.x * pa_);
+        atomicAdd(wd + e, v.y * pa_);
+      });
+    } else {
+      // any pack: v = v_ab + i v_cd
+      last([&](int e, cpx<T> v) {
+        const T pa_ = __ldg(fa + e), pb_ = __ldg(fb + e);
+        const T pc_ = two ? __ldg(fc + e) : (T)0, pd_ = two ? __ldg(fd + e) : (T)0;
+        const T to_a = v.x * pb_ + (same_a ? v.y * pd_ : (T)0);
+        if (use_acc) {
+          acc[e] += to_a;  // pk.x == grow (and pk.z == grow when two)
+        } else {
+          atomicAdd(wa + e, to_a);
+          if (two && !same_a) atomicAdd(wc + e, v.y * pd_);
+        }
+        if (pk.y != pk.x) atomicAdd(wb + e, v.x * pa_);
+        if (two && pk.w != pk.z) atomicAdd(wd + e, v.y * pc_);
+      });
     }
   }
   if (use_acc) {

@@ -34,10 +34,11 @@ def test_autotune_picks_valid_settings_and_builds_agree(tmp_path):
         p = abi.ace_autotune(d, phi, stream)
     finally:
         del os.environ["ACE_TUNE_FILE"]
-    assert p["group"] >= 1 and p["batch"] in (1, 2, 3, 4, 6) and p["streams"] in (2, 4) and p["l2_mb"] in (0, 60)
+    assert p["group"] >= 1 and p["batch"] in (1, 2, 3, 4, 6) and p["streams"] in (2, 4, 8) and p["l2_mb"] in (0, 60)
+    assert p["row_block"] in (1, 2, 4, 8)
     fields = tune_file.read_text().split()
-    assert fields[:4] == ["48", "48", "48", "0"] and [int(x) for x in fields[4:8]] == [
-        p["group"], p["batch"], p["streams"], p["l2_mb"]]
+    assert fields[:4] == ["48", "48", "48", "0"] and [int(x) for x in fields[4:9]] == [
+        p["group"], p["batch"], p["streams"], p["l2_mb"], p["row_block"]]
     after = ace.ace_build(d, phi, stream)
     assert abs(ace.exchange_energy(after) - e0) <= MIXED_EX_TOL_PER_ORB * w.norb
     after.close()
