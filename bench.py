@@ -34,7 +34,7 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_values.json")
 # DRAM bytes (read + write) of the pair chain per build of the water32 workload, from one ncu capture
 # of the current chain kernels with caches not flushed (profiles/pair_chain_plane_water32_96c.md);
 # set to None whenever those kernels change.
-CHAIN_DRAM_BYTES_PER_BUILD = None
+CHAIN_DRAM_BYTES_PER_BUILD = 14.9e9
 
 
 def _peaks():
@@ -368,7 +368,8 @@ def run_ours(args):
         rec["launches"] += ace.ace.ace_kernel_launches(op)
         rec["npairs"] = ace.ace_pair_count(op)
 
-    tuned = ace.ace.ace_autotune(desc, phi32, stream)  # pair-chain batch / stream / L2 settings for this grid
+    # pair-chain batch / stream / L2 / pack-order settings for this grid (library defaults when skipped)
+    tuned = None if args.no_autotune else ace.ace.ace_autotune(desc, phi32, stream)
     for _ in range(args.warmup):
         op = ace.ace_build(desc, phi32, stream)
         op.close()
@@ -462,6 +463,7 @@ def main():
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default chain settings")
     ap.add_argument("--workload", default="water32", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.impl == "reference":
