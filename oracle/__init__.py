@@ -80,13 +80,17 @@ def _declare(lib):
     lib.oracle_set_threads.argtypes = [ctypes.c_int]
     lib.oracle_max_threads.restype = ctypes.c_int
     lib.oracle_fft3d.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
-    lib.oracle_coulomb_kernel.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
-    lib.oracle_pair_potential.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
-    lib.oracle_pair_energy.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
+    _i, _d = ctypes.c_int, ctypes.c_double
+    lib.oracle_inscribed_radius.argtypes = [_dp]
+    lib.oracle_inscribed_radius.restype = _d
+    lib.oracle_coulomb_kernel.argtypes = [_dp, _i, _i, _i, _i, _d, _dp]
+    lib.oracle_pair_potential.argtypes = [_dp, _dp, _i, _i, _i, _dp, _i, _d, _dp]
+    lib.oracle_pair_energy.argtypes = [_dp, _dp, _i, _i, _i, _dp, _i, _d]
     lib.oracle_pair_energy.restype = ctypes.c_double
     lib.oracle_screen.argtypes = [_dp, ctypes.c_int, ctypes.c_long, ctypes.c_double, ctypes.c_double, _dp, _up]
     lib.oracle_exchange_w.argtypes = [
-        _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _up, _ip, ctypes.c_int, _dp,
+        _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double, _up, _ip,
+        ctypes.c_int, _dp,
     ]
     lib.oracle_ace_from_w.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_long, ctypes.c_double, _dp, _dp, _dp, _dp]
     lib.oracle_ace_apply.argtypes = [_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_long, ctypes.c_double, _dp]
@@ -119,28 +123,37 @@ def fft3d(z: np.ndarray, sign: int = -1) -> np.ndarray:
     return z
 
 
-def coulomb_kernel(lattice, grid) -> np.ndarray:
-    """4 pi / |G_m|^2 on the FFT box (G = 0 -> 0, Nyquist-averaged), shape grid."""
+PERIODIC, TRUNCATED = 0, 1  # Coulomb kernel kinds: 4 pi/|G|^2 (G = 0 dropped); 1/r cut off at r_cut
+
+
+def inscribed_radius(lattice) -> float:
+    """Radius of the largest sphere inside the cell (the default cut-off of the truncated kernel)."""
+    return float(_load().oracle_inscribed_radius(_ptr(_f64(lattice).reshape(3, 3))))
+
+
+def coulomb_kernel(lattice, grid, kind: int = PERIODIC, r_cut: float = 0.0) -> np.ndarray:
+    """Kernel on the FFT box, Nyquist-averaged, shape grid: PERIODIC 4 pi/|G_m|^2 with G = 0 -> 0;
+    TRUNCATED 4 pi (1 - cos(|G| r_cut))/|G|^2 with G = 0 -> 2 pi r_cut^2 (r_cut <= 0: inscribed radius)."""
     lat = _f64(lattice).reshape(3, 3)
     K = np.empty(tuple(grid), dtype=np.float64)
-    _load().oracle_coulomb_kernel(_ptr(lat), *[int(g) for g in grid], _ptr(K))
+    _load().oracle_coulomb_kernel(_ptr(lat), *[int(g) for g in grid], int(kind), float(r_cut), _ptr(K))
     return K
 
 
-def pair_potential(phi_i, phi_j, lattice) -> np.ndarray:
+def pair_potential(phi_i, phi_j, lattice, kind: int = PERIODIC, r_cut: float = 0.0) -> np.ndarray:
     """v_ij(r) of Eq. (e:vij) on the grid."""
     a, b = _f64(phi_i), _f64(phi_j)
     lat = _f64(lattice).reshape(3, 3)
     v = np.empty_like(a)
-    _load().oracle_pair_potential(_ptr(a), _ptr(b), *a.shape, _ptr(lat), _ptr(v))
+    _load().oracle_pair_potential(_ptr(a), _ptr(b), *a.shape, _ptr(lat), int(kind), float(r_cut), _ptr(v))
     return v
 
 
-def pair_energy(phi_i, phi_j, lattice) -> float:
+def pair_energy(phi_i, phi_j, lattice, kind: int = PERIODIC, r_cut: float = 0.0) -> float:
     """(ij|ij) = dV sum_r phi_i phi_j v_ij."""
     a, b = _f64(phi_i), _f64(phi_j)
     lat = _f64(lattice).reshape(3, 3)
-    return float(_load().oracle_pair_energy(_ptr(a), _ptr(b), *a.shape, _ptr(lat)))
+    return float(_load().oracle_pair_energy(_ptr(a), _ptr(b), *a.shape, _ptr(lat), int(kind), float(r_cut)))
 
 
 def screen(phi, lattice, rho_cut: float):
@@ -155,7 +168,7 @@ def screen(phi, lattice, rho_cut: float):
     return O, mask.astype(bool)
 
 
-def exchange_w(phi, lattice, mask=None, rows=None) -> np.ndarray:
+def exchange_w(phi, lattice, mask=None, rows=None, kind: int = PERIODIC, r_cut: float = 0.0) -> np.ndarray:
     """W_i = sum_j v_ij phi_j (Eq. vx with W = -V_X phi) for the requested rows."""
     phi = _f64(phi)
     n = phi.shape[0]
@@ -166,7 +179,7 @@ def exchange_w(phi, lattice, mask=None, rows=None) -> np.ndarray:
     W = np.empty((nrows,) + tuple(grid))
     m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
     rc = _load().oracle_exchange_w(
-        _ptr(phi), n, *grid, _ptr(lat),
+        _ptr(phi), n, *grid, _ptr(lat), int(kind), float(r_cut),
         None if m is None else _ptr(m, _up),
         None if rows_arr is None else _ptr(rows_arr, _ip),
         nrows, _ptr(W),
@@ -208,7 +221,8 @@ def exchange_energy(M, spin_factor: float) -> float:
     return float(_load().oracle_exchange_energy(_ptr(M), M.shape[0], float(spin_factor)))
 
 
-def ace_build(phi, lattice, rho_cut: float = 0.0, spin_factor: float = 2.0, mask=None, want_xi=True):
+def ace_build(phi, lattice, rho_cut: float = 0.0, spin_factor: float = 2.0, mask=None, want_xi=True,
+              kind: int = PERIODIC, r_cut: float = 0.0):
     """Whole build: optional screen (rho_cut > 0 and no explicit mask), W, M, L, xi, E_x."""
     phi = _f64(phi)
     lat = _f64(lattice).reshape(3, 3)
@@ -217,7 +231,7 @@ def ace_build(phi, lattice, rho_cut: float = 0.0, spin_factor: float = 2.0, mask
     O = None
     if mask is None and rho_cut > 0:
         O, mask = screen(phi, lat, rho_cut)
-    W = exchange_w(phi, lat, mask=mask)
+    W = exchange_w(phi, lat, mask=mask, kind=kind, r_cut=r_cut)
     res = ace_from_w(phi, W, dV, want_xi=want_xi)
     res.update(W=W, mask=mask, O=O, dV=dV)
     res["E_x"] = exchange_energy(res["M"], spin_factor)

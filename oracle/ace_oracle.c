@@ -21,6 +21,12 @@
  *     v(r) = sum_m 4 pi/|G_m|^2 rho~(m) exp(+i G_m.x_r); G_m = sum_k m_k b_k, b = 2 pi A^-T,
  *     m_k wrapped to [-N_k/2, N_k/2); full FFT box; G = 0 dropped; at a Nyquist index the
  *     kernel is the mean of 4 pi/|G|^2 over the +-N_k/2 choices (keeps it even, v real).
+ *   - isolated cell (the QM box of section III's enzyme application, for which the paper names no
+ *     Poisson solver): the interaction 1/r cut off at r = rc, i.e. the kernel
+ *     4 pi (1 - cos(|G| rc))/|G|^2 with the G = 0 term 2 pi rc^2 kept; rc defaults to the radius
+ *     of the largest sphere inside the cell.  For a density of diameter D with D <= rc and
+ *     D + rc <= the distance to its nearest periodic image this is the open-boundary Coulomb
+ *     interaction exactly (pinned against closed-form Gaussian self-energies).
  *   - energy: E_x = (f/2) tr M.
  *   - diagonal pairs contribute once; the mask is symmetric; M is symmetrised before Cholesky.
  *
@@ -188,10 +194,33 @@ static double cell_volume(const double A[9]) {
   return fabs(det);
 }
 
-int oracle_coulomb_kernel(const double *lattice, int n1, int n2, int n3, double *K) {
+/* Radius of the largest sphere inside the cell: half the smallest distance between lattice
+ * planes, pi / |b_k| minimised over k. */
+double oracle_inscribed_radius(const double *lattice) {
+  double B[9];
+  reciprocal(lattice, B);
+  double r = HUGE_VAL;
+  for (int k = 0; k < 3; ++k) {
+    const double b = sqrt(B[k * 3] * B[k * 3] + B[k * 3 + 1] * B[k * 3 + 1] + B[k * 3 + 2] * B[k * 3 + 2]);
+    if (ORACLE_PI / b < r) r = ORACLE_PI / b;
+  }
+  return r;
+}
+
+/* Coulomb kernel at G of |G|^2 = g2:
+ *   kind 0 (periodic cell): 4 pi / |G|^2, and the G = 0 term is dropped;
+ *   kind 1 (isolated cell, the interaction 1/r cut off at r = rc): the Fourier transform of
+ *          theta(rc - r) / r, 4 pi (1 - cos(|G| rc)) / |G|^2, whose G -> 0 limit is 2 pi rc^2. */
+static double kernel_at(double g2, int kind, double rc) {
+  if (kind == 1) return g2 == 0.0 ? 2.0 * ORACLE_PI * rc * rc : 4.0 * ORACLE_PI * (1.0 - cos(sqrt(g2) * rc)) / g2;
+  return 4.0 * ORACLE_PI / g2;
+}
+
+int oracle_coulomb_kernel(const double *lattice, int n1, int n2, int n3, int kind, double rc, double *K) {
   const int n[3] = {n1, n2, n3};
   double B[9];
   reciprocal(lattice, B);
+  if (kind == 1 && rc <= 0.0) rc = oracle_inscribed_radius(lattice);
   for (int i1 = 0; i1 < n1; ++i1)
     for (int i2 = 0; i2 < n2; ++i2)
       for (int i3 = 0; i3 < n3; ++i3) {
@@ -203,7 +232,7 @@ int oracle_coulomb_kernel(const double *lattice, int n1, int n2, int n3, double 
         }
         const long lin = ((long)i1 * n2 + i2) * n3 + i3;
         if (m[0] == 0 && m[1] == 0 && m[2] == 0) {
-          K[lin] = 0.0;
+          K[lin] = kind == 1 ? kernel_at(0.0, kind, rc) : 0.0;
           continue;
         }
         double acc = 0.0;
@@ -218,7 +247,7 @@ int oracle_coulomb_kernel(const double *lattice, int n1, int n2, int n3, double 
           if (!ok) continue;
           double G[3];
           for (int c = 0; c < 3; ++c) G[c] = mm[0] * B[0 * 3 + c] + mm[1] * B[1 * 3 + c] + mm[2] * B[2 * 3 + c];
-          acc += 4.0 * ORACLE_PI / (G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
+          acc += kernel_at(G[0] * G[0] + G[1] * G[1] + G[2] * G[2], kind, rc);
           ++cnt;
         }
         K[lin] = acc / cnt;
@@ -244,7 +273,7 @@ static void pair_potential(const fft3_plan *pl, const double *K, const double *p
 }
 
 int oracle_pair_potential(const double *phi_i, const double *phi_j, int n1, int n2, int n3,
-                          const double *lattice, double *v) {
+                          const double *lattice, int kind, double rc, double *v) {
   if (n1 > ORACLE_MAXN || n2 > ORACLE_MAXN || n3 > ORACLE_MAXN) return 1;
   const long npts = (long)n1 * n2 * n3;
   fft3_plan pl;
@@ -252,7 +281,7 @@ int oracle_pair_potential(const double *phi_i, const double *phi_j, int n1, int 
   double *K = (double *)malloc((size_t)npts * sizeof(double));
   cplx *z = (cplx *)malloc((size_t)npts * sizeof(cplx));
   cplx *work = (cplx *)malloc(3 * (size_t)pl.maxn * sizeof(cplx));
-  oracle_coulomb_kernel(lattice, n1, n2, n3, K);
+  oracle_coulomb_kernel(lattice, n1, n2, n3, kind, rc, K);
   pair_potential(&pl, K, phi_i, phi_j, npts, z, work, v);
   free(work);
   free(z);
@@ -289,13 +318,13 @@ int oracle_screen(const double *phi, int norb, long npts, double dV, double rho_
  * mask (optional, norb x norb) restricts j; NULL means all pairs.
  * ---------------------------------------------------------------------------------------- */
 int oracle_exchange_w(const double *phi, int norb, int n1, int n2, int n3, const double *lattice,
-                      const unsigned char *mask, const int *rows, int nrows, double *W) {
+                      int kind, double rc, const unsigned char *mask, const int *rows, int nrows, double *W) {
   if (n1 > ORACLE_MAXN || n2 > ORACLE_MAXN || n3 > ORACLE_MAXN) return 2;
   const long npts = (long)n1 * n2 * n3;
   fft3_plan pl;
   plan_init(&pl, n1, n2, n3);
   double *K = (double *)malloc((size_t)npts * sizeof(double));
-  oracle_coulomb_kernel(lattice, n1, n2, n3, K);
+  oracle_coulomb_kernel(lattice, n1, n2, n3, kind, rc, K);
   int err = 0;
   /* many rows: one row per thread; few rows: rows in sequence, parallel inside each transform */
   const int outer = nrows >= oracle_max_threads();
@@ -333,10 +362,10 @@ int oracle_exchange_w(const double *phi, int norb, int n1, int n2, int n3, const
 
 /* (ij|ij) = dV sum_r rho_ij(r) v_ij(r) */
 double oracle_pair_energy(const double *phi_i, const double *phi_j, int n1, int n2, int n3,
-                          const double *lattice) {
+                          const double *lattice, int kind, double rc) {
   const long npts = (long)n1 * n2 * n3;
   double *v = (double *)malloc((size_t)npts * sizeof(double));
-  oracle_pair_potential(phi_i, phi_j, n1, n2, n3, lattice, v);
+  oracle_pair_potential(phi_i, phi_j, n1, n2, n3, lattice, kind, rc, v);
   double s = 0.0;
   for (long r = 0; r < npts; ++r) s += phi_i[r] * phi_j[r] * v[r];
   free(v);

@@ -238,12 +238,45 @@ struct DftCT {
   }
 };
 
-template <int D, typename T> struct Dft<6, D, T> : DftCT<2, 3, D, T> {};
+// Inverse of a modulo m (a, m coprime), by search: compile time only.
+constexpr int ct_inv_mod(int a, int m) {
+  for (int x = 1; x < m; ++x)
+    if ((a * x) % m == 1) return x;
+  return m == 1 ? 0 : -1;
+}
+
+// Composite R = P * Q with gcd(P, Q) = 1 by the prime-factor (Good-Thomas) mapping: input
+// n = (Q n1 + P n2) mod R, output k = (Q (Q^-1 mod P) k1 + P (P^-1 mod Q) k2) mod R.  The cross
+// terms of n k are multiples of R, so X is a plain P x Q two-dimensional DFT with no twiddles.
+template <int P, int Q, int D, typename T>
+struct DftPFA {
+  static constexpr int R = P * Q, A = ct_inv_mod(Q % P, P), B = ct_inv_mod(P % Q, Q);
+  static_assert(A >= 0 && B >= 0, "factors must be coprime");
+  static __device__ __forceinline__ void run(cpx<T> *x) {
+    cpx<T> y[R];
+    static_for<Q>([&](auto n2c) {
+      constexpr int n2 = decltype(n2c)::value;
+      cpx<T> t[P];
+      static_for<P>([&](auto n1c) { t[decltype(n1c)::value] = x[(Q * decltype(n1c)::value + P * n2) % R]; });
+      Dft<P, D, T>::run(t);
+      static_for<P>([&](auto k1c) { y[n2 * P + decltype(k1c)::value] = t[decltype(k1c)::value]; });
+    });
+    static_for<P>([&](auto k1c) {
+      constexpr int k1 = decltype(k1c)::value;
+      cpx<T> t[Q];
+      static_for<Q>([&](auto n2c) { t[decltype(n2c)::value] = y[decltype(n2c)::value * P + k1]; });
+      Dft<Q, D, T>::run(t);
+      static_for<Q>([&](auto k2c) { x[(Q * A * k1 + P * B * decltype(k2c)::value) % R] = t[decltype(k2c)::value]; });
+    });
+  }
+};
+
+template <int D, typename T> struct Dft<6, D, T> : DftPFA<2, 3, D, T> {};
 template <int D, typename T> struct Dft<8, D, T> : DftCT<2, 4, D, T> {};
 template <int D, typename T> struct Dft<9, D, T> : DftCT<3, 3, D, T> {};
-template <int D, typename T> struct Dft<10, D, T> : DftCT<2, 5, D, T> {};
-template <int D, typename T> struct Dft<12, D, T> : DftCT<3, 4, D, T> {};
-template <int D, typename T> struct Dft<15, D, T> : DftCT<3, 5, D, T> {};
+template <int D, typename T> struct Dft<10, D, T> : DftPFA<2, 5, D, T> {};
+template <int D, typename T> struct Dft<12, D, T> : DftPFA<3, 4, D, T> {};
+template <int D, typename T> struct Dft<15, D, T> : DftPFA<3, 5, D, T> {};
 template <int D, typename T> struct Dft<16, D, T> : DftCT<4, 4, D, T> {};
 
 // ---------------------------------------------------------------------------------------

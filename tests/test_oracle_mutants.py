@@ -23,10 +23,11 @@ MUTANTS = {
     "missing_1_over_N": ("z[r] *= K[r] * invN;", "z[r] *= K[r];"),
     "nyquist_sum_not_mean": ("K[lin] = acc / cnt;", "K[lin] = acc;"),
     "reciprocal_transposed": ("2.0 * ORACLE_PI * inv[c * 3 + k]", "2.0 * ORACLE_PI * inv[k * 3 + c]"),
-    "kernel_not_squared": (
-        "acc += 4.0 * ORACLE_PI / (G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);",
-        "acc += 4.0 * ORACLE_PI / sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);",
-    ),
+    "kernel_not_squared": ("return 4.0 * ORACLE_PI / g2;", "return 4.0 * ORACLE_PI / sqrt(g2);"),
+    "trunc_g0_dropped": ("g2 == 0.0 ? 2.0 * ORACLE_PI * rc * rc :", "g2 == 0.0 ? 0.0 :"),
+    "trunc_radius_doubled": ("(1.0 - cos(sqrt(g2) * rc))", "(1.0 - cos(sqrt(g2) * 2.0 * rc))"),
+    "trunc_cos_sign": ("(1.0 - cos(sqrt(g2) * rc))", "(1.0 + cos(sqrt(g2) * rc))"),
+    "inscribed_radius_2pi": ("if (ORACLE_PI / b < r) r = ORACLE_PI / b;", "if (ORACLE_PI / b < r) r = 2.0 * ORACLE_PI / b;"),
     "diagonal_pair_dropped": (
         "if (mask && !mask[(long)i * norb + j]) continue;",
         "if (j == i || (mask && !mask[(long)i * norb + j])) continue;",
@@ -56,7 +57,11 @@ def battery_inputs():
     E = cf.pair_energies(D, coeffs, TRICLINIC, grid)
     rng2 = np.random.default_rng(1)
     z = rng2.standard_normal((6, 10, 15)) + 1j * rng2.standard_normal((6, 10, 15))
-    return dict(grid=grid, phi=phi, E=E, z=z)
+    n = 48
+    x = np.arange(n) * 16.0 / n
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    iso_phi = (2 / np.pi) ** 0.75 * np.exp(-((X - 8.0) ** 2 + (Y - 8.0) ** 2 + (Z - 8.0) ** 2))
+    return dict(grid=grid, phi=phi, E=E, z=z, iso_phi=iso_phi, iso_ref=2 * np.sqrt(1 / np.pi))
 
 
 def _naive(z, sign):
@@ -104,6 +109,11 @@ def run_battery(orc, inp):
     _, mask = orc.screen(phi, TRICLINIC, big)
     if not np.array_equal(mask, np.eye(3, dtype=bool)):
         failed.append("screen_diagonal")
+    # isolated-cell kernel: closed-form self-energy of a Gaussian density (default cut-off)
+    g = inp["iso_phi"]
+    e = orc.pair_energy(g, g, np.eye(3) * 16.0, orc.TRUNCATED, 0.0)
+    if not abs(e - inp["iso_ref"]) <= 1e-9 * inp["iso_ref"]:
+        failed.append("truncated_self_energy")
     return failed
 
 

@@ -261,3 +261,73 @@ def test_not_posdef_reported(oracle_mod):
     W = oracle_mod.exchange_w(phi, lat)
     res = oracle_mod.ace_from_w(phi, W, 512.0 / 1000, want_xi=False)
     assert res["status"] == 4
+
+
+# ------------------------------------------------------------------------------------------
+# Isolated-cell kernel (the interaction 1/r cut off at r_cut): for a Gaussian density of
+# diameter D with D <= r_cut and D + r_cut <= the nearest periodic image, the truncated
+# interaction is the open-boundary Coulomb interaction, whose Gaussian values are closed forms:
+# a charge-Q density (gamma/pi)^{3/2} Q exp(-gamma r^2) has self-energy Q^2 sqrt(2 gamma / pi).
+# ------------------------------------------------------------------------------------------
+def _gaussian_orbital(grid, lattice, alpha, centre):
+    """(2 alpha / pi)^{3/4} exp(-alpha |r - centre|^2) sampled at the grid points (no images)."""
+    frac = np.stack(np.meshgrid(*[np.arange(n) / n for n in grid], indexing="ij"), -1)
+    r = frac @ np.asarray(lattice)
+    d2 = np.sum((r - np.asarray(centre)) ** 2, axis=-1)
+    return (2 * alpha / np.pi) ** 0.75 * np.exp(-alpha * d2)
+
+
+ISO_L = 16.0
+ISO_GRID = (48, 48, 48)
+
+
+def test_truncated_kernel_values(oracle_mod):
+    lat = np.diag([ISO_L, 12.0, 14.0])
+    grid = (8, 6, 10)
+    rc = 5.5
+    K = oracle_mod.coulomb_kernel(lat, grid, oracle_mod.TRUNCATED, rc)
+    assert K[0, 0, 0] == pytest.approx(2 * np.pi * rc * rc, rel=1e-15)
+    for m in [(1, 0, 0), (0, 2, 3), (3, 1, 4), (1, 2, 1)]:
+        G = 2 * np.pi * np.array(m) / np.diag(lat)
+        g = np.linalg.norm(G)
+        assert K[m] == pytest.approx(4 * np.pi * (1 - np.cos(g * rc)) / g**2, rel=1e-13)
+    assert oracle_mod.inscribed_radius(lat) == pytest.approx(6.0, rel=1e-15)
+    assert oracle_mod.inscribed_radius(TRICLINIC) < 3.5
+
+
+def test_truncated_self_energy_closed_form(oracle_mod):
+    lat = np.eye(3) * ISO_L
+    alpha = 1.0
+    phi = _gaussian_orbital(ISO_GRID, lat, alpha, [ISO_L / 2] * 3)
+    ref = 2 * np.sqrt(alpha / np.pi)  # gamma = 2 alpha, Q = 1
+    for rc in (0.0, 7.0, 8.0):  # 0: inscribed radius 8
+        e = oracle_mod.pair_energy(phi, phi, lat, oracle_mod.TRUNCATED, rc)
+        assert e == pytest.approx(ref, rel=1e-9), rc
+    # the periodic kernel (G = 0 dropped) is a different interaction
+    assert abs(oracle_mod.pair_energy(phi, phi, lat) - ref) > 1e-2
+
+
+def test_truncated_cross_pair_closed_form(oracle_mod):
+    lat = np.array([[ISO_L, 0.0, 0.0], [0.8, ISO_L, 0.0], [-0.5, 0.6, ISO_L]])
+    alpha = 1.2
+    c = np.array([ISO_L / 2, ISO_L / 2, ISO_L / 2]) @ np.eye(3)
+    d = np.array([0.9, -0.4, 0.7])
+    a = _gaussian_orbital(ISO_GRID, lat, alpha, c)
+    b = _gaussian_orbital(ISO_GRID, lat, alpha, c + d)
+    S = np.exp(-alpha * d @ d / 2)  # charge of phi_a phi_b, a Gaussian of exponent 2 alpha
+    ref = S * S * 2 * np.sqrt(alpha / np.pi)
+    assert oracle_mod.pair_energy(a, b, lat, oracle_mod.TRUNCATED, 7.5) == pytest.approx(ref, rel=1e-9)
+
+
+def test_truncated_exchange_energy_of_separated_orbitals(oracle_mod):
+    """Two far-apart Gaussian orbitals: E_x = -(f/2) sum of the two self-energies (the cross
+    pair density vanishes), through the whole oracle build."""
+    lat = np.eye(3) * ISO_L
+    alpha = 1.0  # resolved by the 1/3-bohr grid to ~1e-10; overlap exp(-alpha 49 / 2) ~ 2e-11
+    a = _gaussian_orbital(ISO_GRID, lat, alpha, [4.5, 8.0, 8.0])
+    b = _gaussian_orbital(ISO_GRID, lat, alpha, [11.5, 8.0, 8.0])
+    phi = np.stack([a, b])
+    r = oracle_mod.ace_build(phi, lat, 0.0, 2.0, kind=oracle_mod.TRUNCATED, r_cut=0.0)
+    assert r["status"] == 0
+    ref = -(2.0 / 2) * 2 * (2 * np.sqrt(alpha / np.pi))
+    assert r["E_x"] == pytest.approx(ref, rel=1e-9)
