@@ -6,6 +6,7 @@
  *
  *   pair screen (section II, display after Eq. unit): keep pair (i,j) iff int |phi_i phi_j| >= rho_cut
  *   pair potential (Eq. e:vij): v_ij = <phi_j | 1/r12 | phi_i>, by FFT with the 4 pi/|G|^2 kernel
+ *                              (or the isolated-cell kernel, see Conventions)
  *   exchange action (Eq. vx):  W_i = sum_j v_ij phi_j            (W = -V_X phi)
  *   Appendix A:                M = -dV Phi^T W, -M = L L^T, xi = W L^-T   (xi = -P of App. A)
  *   ACE application (section II): K psi = -xi (dV xi^T psi) = V_X^ACE psi
@@ -19,6 +20,12 @@
  *   - Fourier convention: rho~(m) = (1/N) sum_r rho(r) e^{-i G_m . x_r}; G_m = sum_k m_k b_k,
  *     b = 2 pi A^-T, m_k wrapped to [-N_k/2, N_k/2); full FFT box; G = 0 term dropped; at a Nyquist
  *     index the kernel is the mean of 4 pi/|G|^2 over the +-N_k/2 choices.
+ *   - isolated cell (ace_desc.coulomb = ACE_COULOMB_TRUNCATED; the QM box of the paper's enzyme
+ *     application in section III, for which the paper names no Poisson solver): the interaction is
+ *     1/r cut off at r = r_cut, i.e. the kernel 4 pi (1 - cos(|G| r_cut))/|G|^2 with its G = 0 limit
+ *     2 pi r_cut^2 kept (same Nyquist mean).  For a pair density of diameter D with D <= r_cut and
+ *     D + r_cut <= the distance to its nearest periodic image it is the open-boundary Coulomb
+ *     interaction exactly.
  *   - pointers named *_dev are CUDA device pointers; pointers that the comments say "host or
  *     device" may be either (host memory, pageable or pinned, is copied inside the call on the
  *     given stream).  `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
@@ -52,11 +59,16 @@ typedef enum {
 typedef enum {
   ACE_FP64 = 0,  /* plain form: every step in double precision                                 */
   ACE_MIXED = 1  /* mixed form: FP32 pair densities/FFTs/kernel multiply/accumulation,
-                    BF16x3 split products (FP32 accumulate within 4096-point chunks, FP64 across)
+                    BF16x3 split products (FP32 accumulate within 256-point chunks, FP64 across)
                     for Phi^T W, xi^T psi and xi C; M, Cholesky, L^-1 and E_x in FP64            */
 } ace_precision;
 
 typedef enum { ACE_F32 = 0, ACE_F64 = 1 } ace_dtype;
+
+typedef enum {
+  ACE_COULOMB_PERIODIC = 0,  /* 4 pi/|G|^2, G = 0 dropped (Eq. e:vij in reciprocal space)        */
+  ACE_COULOMB_TRUNCATED = 1  /* isolated cell: 1/r cut off at r_cut (see Conventions)           */
+} ace_coulomb;
 
 typedef struct {
   int n[3];              /* N1, N2, N3 (each must satisfy ace_grid_supported)                  */
@@ -65,6 +77,9 @@ typedef struct {
   double rho_cut;        /* keep (i,j) iff dV sum_r |phi_i phi_j| >= rho_cut; <= 0 keeps all     */
   double spin_factor;    /* f in E_x = (f/2) tr M: 2 closed shell, 1 one spin channel            */
   ace_precision prec;
+  ace_coulomb coulomb;   /* kernel of step a4; a zeroed field is the periodic kernel             */
+  double r_cut;          /* ACE_COULOMB_TRUNCATED: cut-off radius in bohr; <= 0 selects the
+                            radius of the largest sphere inside the cell, min_k pi/|b_k|         */
 } ace_desc;
 
 typedef struct ace_op ace_op; /* opaque: owns xi, W, M, L, L^-1, the pair list and workspaces  */
@@ -151,7 +166,7 @@ void ace_destroy(ace_op *op);
  * whose framework owns all device memory.
  *
  * Computes the pair-potential chain of Eq. (vx) for an explicit pair list:
- *   W_i = sum_{j : (i,j) or (j,i) listed} v_ij phi_j,  v_ij by FFT with the 4 pi/|G|^2 kernel,
+ *   W_i = sum_{j : (i,j) or (j,i) listed} v_ij phi_j,  v_ij by FFT with the kernel desc->coulomb selects,
  * the same arithmetic as the W step of ace_build (desc->rho_cut and desc->spin_factor are ignored).
  *   phi_dev:    device orbitals [norb][N1][N2][N3]; W_dev: device output of the same shape (zeroed
  *               by the call).  dtype must be the working type of desc->prec (ACE_F32 for ACE_MIXED,

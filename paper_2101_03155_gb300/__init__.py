@@ -6,6 +6,8 @@ binding with the same entry-point names, and ``build`` compiles the library with
 
 from . import ace  # noqa: F401
 from .ace import (  # noqa: F401
+    ACE_COULOMB_PERIODIC,
+    ACE_COULOMB_TRUNCATED,
     ACE_FP64,
     ACE_MIXED,
     AceDesc,

@@ -33,6 +33,8 @@ ACE_FP64 = 0
 ACE_MIXED = 1
 ACE_F32 = 0
 ACE_F64 = 1
+ACE_COULOMB_PERIODIC = 0
+ACE_COULOMB_TRUNCATED = 1
 
 ACE_GET_XI = 0
 ACE_GET_W = 1
@@ -64,10 +66,14 @@ class AceDesc(ctypes.Structure):
         ("rho_cut", ctypes.c_double),
         ("spin_factor", ctypes.c_double),
         ("prec", ctypes.c_int),
+        ("coulomb", ctypes.c_int),
+        ("r_cut", ctypes.c_double),
     ]
 
 
-def make_desc(grid, lattice, norb, rho_cut=0.0, spin_factor=2.0, prec=ACE_MIXED) -> AceDesc:
+def make_desc(grid, lattice, norb, rho_cut=0.0, spin_factor=2.0, prec=ACE_MIXED, coulomb=0, r_cut=0.0) -> AceDesc:
+    """Descriptor of one build; coulomb = ACE_COULOMB_PERIODIC (4 pi/|G|^2) or ACE_COULOMB_TRUNCATED
+    (isolated cell, 1/r cut off at r_cut; r_cut <= 0 selects the inscribed-sphere radius)."""
     d = AceDesc()
     for k in range(3):
         d.n[k] = int(grid[k])
@@ -79,6 +85,8 @@ def make_desc(grid, lattice, norb, rho_cut=0.0, spin_factor=2.0, prec=ACE_MIXED)
     d.rho_cut = float(rho_cut)
     d.spin_factor = float(spin_factor)
     d.prec = int(prec)
+    d.coulomb = int(coulomb)
+    d.r_cut = float(r_cut)
     return d
 
 

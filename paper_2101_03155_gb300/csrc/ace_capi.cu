@@ -72,27 +72,42 @@ bool is_device_pointer(const void *p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// 4 pi / (N |G_m|^2) on the FFT box; G = 0 -> 0; mean over +-N_k/2 at Nyquist indices.
-void coulomb_table(const ace_desc &d, std::vector<double> &K) {
-  const int n1 = d.n[0], n2 = d.n[1], n3 = d.n[2];
+// Reciprocal basis b_k = 2 pi (row k of A^-T) of the lattice rows A.
+void reciprocal_basis(const ace_desc &d, double B[3][3]) {
   const double *A = &d.lattice[0][0];
   const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
                      A[2] * (A[3] * A[7] - A[4] * A[6]);
-  // b_k = 2 pi * (row k of A^-T) = 2 pi * (column k of A^-1); A^-1 = adj(A) / det
-  double adj[9];
-  adj[0] = A[4] * A[8] - A[5] * A[7];
-  adj[1] = A[2] * A[7] - A[1] * A[8];
-  adj[2] = A[1] * A[5] - A[2] * A[4];
-  adj[3] = A[5] * A[6] - A[3] * A[8];
-  adj[4] = A[0] * A[8] - A[2] * A[6];
-  adj[5] = A[2] * A[3] - A[0] * A[5];
-  adj[6] = A[3] * A[7] - A[4] * A[6];
-  adj[7] = A[1] * A[6] - A[0] * A[7];
-  adj[8] = A[0] * A[4] - A[1] * A[3];
-  const double twopi = 2.0 * ace::kPi;
-  double B[3][3];
+  // row k of A^-T = column k of A^-1; A^-1 = adj(A) / det
+  const double adj[9] = {A[4] * A[8] - A[5] * A[7], A[2] * A[7] - A[1] * A[8], A[1] * A[5] - A[2] * A[4],
+                         A[5] * A[6] - A[3] * A[8], A[0] * A[8] - A[2] * A[6], A[2] * A[3] - A[0] * A[5],
+                         A[3] * A[7] - A[4] * A[6], A[1] * A[6] - A[0] * A[7], A[0] * A[4] - A[1] * A[3]};
   for (int k = 0; k < 3; ++k)
-    for (int c = 0; c < 3; ++c) B[k][c] = twopi * adj[c * 3 + k] / det;
+    for (int c = 0; c < 3; ++c) B[k][c] = 2.0 * ace::kPi * adj[c * 3 + k] / det;
+}
+
+// Cut-off radius of the truncated kernel: r_cut, or when r_cut <= 0 the radius of the largest
+// sphere inside the cell (half the smallest distance between lattice planes, min_k pi / |b_k|).
+double cutoff_radius(const ace_desc &d) {
+  if (d.r_cut > 0.0) return d.r_cut;
+  double B[3][3];
+  reciprocal_basis(d, B);
+  double r = HUGE_VAL;
+  for (int k = 0; k < 3; ++k)
+    r = std::min(r, ace::kPi / std::sqrt(B[k][0] * B[k][0] + B[k][1] * B[k][1] + B[k][2] * B[k][2]));
+  return r;
+}
+
+// Kernel table on the FFT box, divided by N (the 1/N of the forward transform), mean over the
+// +-N_k/2 choices at Nyquist indices:
+//   ACE_COULOMB_PERIODIC  4 pi / |G|^2, G = 0 -> 0 (Eq. e:vij in reciprocal space);
+//   ACE_COULOMB_TRUNCATED 4 pi (1 - cos(|G| rc)) / |G|^2 (the interaction 1/r for r < rc), whose
+//                         G = 0 limit 2 pi rc^2 is kept.
+void coulomb_table(const ace_desc &d, std::vector<double> &K) {
+  const int n1 = d.n[0], n2 = d.n[1], n3 = d.n[2];
+  double B[3][3];
+  reciprocal_basis(d, B);
+  const bool trunc = d.coulomb == ACE_COULOMB_TRUNCATED;
+  const double rc = trunc ? cutoff_radius(d) : 0.0;
   // Gram matrix of the reciprocal basis: |G|^2 = sum_kl m_k m_l (b_k . b_l)
   double g[3][3];
   for (int k = 0; k < 3; ++k)
@@ -112,7 +127,10 @@ void coulomb_table(const ace_desc &d, std::vector<double> &K) {
           nyq[k] = (nn[k] % 2 == 0) && (2 * idx[k] == nn[k]);
         }
         const long long lin = ((long long)i1 * n2 + i2) * n3 + i3;
-        if (m[0] == 0 && m[1] == 0 && m[2] == 0) continue;
+        if (m[0] == 0 && m[1] == 0 && m[2] == 0) {
+          if (trunc) K[(size_t)lin] = fourpi_over_N * 0.5 * rc * rc;
+          continue;
+        }
         double acc = 0.0;
         int cnt = 0;
         for (int s = 0; s < 8; ++s) {
@@ -127,7 +145,7 @@ void coulomb_table(const ace_desc &d, std::vector<double> &K) {
           double q = 0.0;
           for (int k = 0; k < 3; ++k)
             for (int l = 0; l < 3; ++l) q += mm[k] * mm[l] * g[k][l];
-          acc += 1.0 / q;
+          acc += trunc ? (1.0 - std::cos(std::sqrt(q) * rc)) / q : 1.0 / q;
           ++cnt;
         }
         K[(size_t)lin] = fourpi_over_N * acc / cnt;
@@ -141,6 +159,8 @@ struct DeviceTables {
   int dev;
   int n[3];
   double lattice[9];
+  int coulomb;
+  double rc;
   size_t esz;
   void *K;
   void *Kperm;  // K[m1][k2(p2)][k3(p3)]: axes 2 and 3 in the plane passes' output positions
@@ -154,7 +174,8 @@ cudaError_t get_tables(int dev, const ace_desc &d, cudaStream_t st, const Device
   std::lock_guard<std::mutex> lk(g_tab_mu);
   for (const DeviceTables &t : g_tables) {
     if (t.dev == dev && t.esz == sizeof(T) && t.n[0] == d.n[0] && t.n[1] == d.n[1] && t.n[2] == d.n[2] &&
-        std::memcmp(t.lattice, &d.lattice[0][0], sizeof(t.lattice)) == 0) {
+        std::memcmp(t.lattice, &d.lattice[0][0], sizeof(t.lattice)) == 0 && t.coulomb == (int)d.coulomb &&
+        (d.coulomb != ACE_COULOMB_TRUNCATED || t.rc == cutoff_radius(d))) {
       *out = &t;
       return cudaSuccess;
     }
@@ -164,6 +185,8 @@ cudaError_t get_tables(int dev, const ace_desc &d, cudaStream_t st, const Device
   t.esz = sizeof(T);
   for (int k = 0; k < 3; ++k) t.n[k] = d.n[k];
   std::memcpy(t.lattice, &d.lattice[0][0], sizeof(t.lattice));
+  t.coulomb = (int)d.coulomb;
+  t.rc = d.coulomb == ACE_COULOMB_TRUNCATED ? cutoff_radius(d) : 0.0;
   std::vector<double> Kh;
   coulomb_table(d, Kh);
   std::vector<T> Kt(Kh.begin(), Kh.end());
@@ -277,6 +300,9 @@ ace_status check_desc(const ace_desc *d) {
   if (!(std::fabs(det) > 0.0)) return fail(ACE_ERR_ARG, "lattice is singular");
   if (d->prec != ACE_FP64 && d->prec != ACE_MIXED) return fail(ACE_ERR_ARG, "unknown precision %d", (int)d->prec);
   if (!std::isfinite(d->spin_factor) || !std::isfinite(d->rho_cut)) return fail(ACE_ERR_ARG, "non-finite scalar");
+  if (d->coulomb != ACE_COULOMB_PERIODIC && d->coulomb != ACE_COULOMB_TRUNCATED)
+    return fail(ACE_ERR_ARG, "unknown Coulomb kernel %d", (int)d->coulomb);
+  if (d->coulomb == ACE_COULOMB_TRUNCATED && !std::isfinite(d->r_cut)) return fail(ACE_ERR_ARG, "non-finite r_cut");
   return ACE_OK;
 }
 
@@ -796,7 +822,7 @@ ace_status build_finish(ace_op *op) {
   // ---- -M = L L^T, L^-1, E_x = (f/2) tr M ----
   double *chol_work = nullptr;
   if (n > 128) {
-    ACE_CUDA(cudaMallocAsync(&tmp, sizeof(double) * ((size_t)n * n + n), st), "alloc cholesky workspace");
+    ACE_CUDA(cudaMallocAsync(&tmp, sizeof(double) * ((size_t)n * n + 4 * n), st), "alloc cholesky workspace");
     temps.push_back(tmp);
     chol_work = static_cast<double *>(tmp);
   }

@@ -351,27 +351,50 @@ __global__ void __launch_bounds__(CH_NT) cholesky_kernel(const double *__restric
     if (tid == 0) *status = bad;
     return;
   }
-  // factorisation, lower triangle of A; warp w and lane t cover the trailing block in a 32 x 32 pattern
-  const int warp = tid >> 5, lane = tid & 31;
-  __shared__ double piv[2];  // sqrt and reciprocal of the pivot, computed once per step
+  // Right-looking factorisation of the lower triangle, two barriers per step:
+  //   (a) column j scaled by 1/L_jj (and copied to col[] for conflict-free reads), L_jj stored;
+  //   (b) trailing update A_ik -= L_ij L_kj over the triangle j < k <= i < n, flattened over all
+  //       threads; the thread that finishes A_{j+1,j+1} (element 0) takes its square root and
+  //       reciprocal for the next step, so no thread waits on a serial pivot computation.
+  // The pivot test reads A_jj after the barrier, so every thread takes the same branch.
+  double *col = tmp;                       // n: scaled column j
+  double *rinv = tmp + n;                  // n: 1 / L_jj
+  __shared__ double piv[2];                // sqrt and reciprocal of the next pivot
+  if (tid == 0) {
+    const double d0 = A[0];
+    piv[0] = sqrt(d0);
+    piv[1] = 1.0 / piv[0];
+  }
+  __syncthreads();
   for (int j = 0; j < n; ++j) {
     const double d = A[j * n + j];
     if (!(d > 0.0) || !isfinite(d)) {
       if (tid == 0) *status = 1000000 + j;
-      return;  // every thread read the same d
+      return;
     }
-    if (tid == 0) {
-      piv[0] = sqrt(d);
-      piv[1] = 1.0 / piv[0];
+    const double r = piv[0], ri = piv[1];
+    for (int i = j + 1 + tid; i < n; i += CH_NT) {
+      const double v = A[i * n + j] * ri;
+      A[i * n + j] = v;
+      col[i] = v;
     }
+    if (tid == 0) rinv[j] = ri;
     __syncthreads();
-    const double r = piv[0], rinv = piv[1];
-    for (int i = j + 1 + tid; i < n; i += CH_NT) A[i * n + j] *= rinv;
-    __syncthreads();
-    if (tid == 0) A[j * n + j] = r;
-    for (int i = j + 1 + warp; i < n; i += CH_NT / 32) {
-      const double lij = A[i * n + j];
-      for (int k = j + 1 + lane; k <= i; k += 32) A[i * n + k] -= lij * A[k * n + j];
+    if (tid == 0) A[j * n + j] = r;  // after the barrier: every thread has read the pivot d
+    const int m = n - 1 - j;  // trailing rows j+1 .. n-1
+    const int T = m * (m + 1) / 2;
+    for (int e = tid; e < T; e += CH_NT) {
+      // row q of the trailing triangle starts at q (q + 1) / 2
+      int q = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while (q * (q + 1) / 2 > e) --q;
+      while ((q + 1) * (q + 2) / 2 <= e) ++q;
+      const int i = j + 1 + q, k = j + 1 + (e - q * (q + 1) / 2);
+      const double v = A[i * n + k] - col[i] * col[k];
+      A[i * n + k] = v;
+      if (e == 0 && v > 0.0 && isfinite(v)) {  // i == k == j + 1: the next pivot
+        piv[0] = sqrt(v);
+        piv[1] = 1.0 / piv[0];
+      }
     }
     __syncthreads();
   }
@@ -379,38 +402,42 @@ __global__ void __launch_bounds__(CH_NT) cholesky_kernel(const double *__restric
     const int i = e / n, j = e % n;
     L[e] = (j <= i) ? A[e] : 0.0;
   }
+  // Inverse: L = U D with U = L D^-1 unit lower (U_ik = L_ik / L_kk) and D = diag(L), so
+  // L^-1 = D^-1 Y with Y = U^-1.  Y by right-looking forward substitution from Y = I:
+  //   step k: Y_ic -= U_ik Y_kc  for i > k, c <= k   (Y_kk = 1; Y_kc final after step k - 1).
+  // Y_ic (c < i) lives in the unused upper triangle at A[c][i]; column k of U is staged in a
+  // double buffer during the previous step, so one barrier per step suffices.
+  double *ucol = tmp + 2 * n;              // 2 n: columns k (even / odd) of U
+  for (int i = 1 + tid; i < n; i += CH_NT) ucol[i] = A[i * n] * rinv[0];
+  for (int e = tid; e < n * n; e += CH_NT) {
+    const int i = e / n, c = e % n;
+    if (c > i) A[e] = 0.0;                 // Y starts at the identity (unit diagonal implicit)
+  }
   __syncthreads();
-  // in-place inverse of the lower triangle by forward substitution on L X = I with rank-1
-  // updates (no reductions: GB300 retires few FP64 operations per clock).  Entry (i, c), c < i,
-  // holds L[i][c] until step c reads it and X[i][c] afterwards.  Step k:
-  //   X[k][c] /= L[k][k] (c < k), X[k][k] = 1 / L[k][k];  X[i][c] -= L[i][k] X[k][c] (i > k, c <= k)
   for (int k = 0; k < n; ++k) {
-    if (tid == 0) piv[0] = 1.0 / A[k * n + k];
-    for (int i = k + 1 + tid; i < n; i += CH_NT) tmp[i] = A[i * n + k];
-    __syncthreads();
-    const double rk = piv[0];
-    for (int c = tid; c < k; c += CH_NT) A[k * n + c] *= rk;
-    if (tid == 0) A[k * n + k] = rk;
-    __syncthreads();
-    for (int i = k + 1 + warp; i < n; i += CH_NT / 32) {
-      const double lik = tmp[i];
-      for (int c = lane; c <= k; c += 32) {
-        const double xkc = A[k * n + c];
-        A[i * n + c] = (c < k ? A[i * n + c] : 0.0) - lik * xkc;
-      }
+    const double *u = ucol + (k & 1) * n;
+    double *unext = ucol + ((k + 1) & 1) * n;
+    if (k + 1 < n)
+      for (int i = k + 2 + tid; i < n; i += CH_NT) unext[i] = A[i * n + k + 1] * rinv[k + 1];
+    // rectangle i in (k, n), c in [0, k]: lanes along i (contiguous in the upper triangle)
+    const int rows = n - 1 - k, cols = k + 1;
+    for (int e = tid; e < rows * cols; e += CH_NT) {
+      const int c = e / rows, i = k + 1 + (e - c * rows);
+      const double ykc = (c == k) ? 1.0 : A[c * n + k];
+      A[c * n + i] -= u[i] * ykc;
     }
     __syncthreads();
   }
   for (int e = tid; e < n * n; e += CH_NT) {
-    const int i = e / n, j = e % n;
-    Linv[e] = (j <= i) ? A[e] : 0.0;
+    const int i = e / n, c = e % n;
+    Linv[e] = (c < i) ? A[c * n + i] * rinv[i] : (c == i ? rinv[i] : 0.0);
   }
   if (tid == 0) *status = 0;
 }
 
 cudaError_t launch_cholesky(const double *M_raw, int n, double spin_factor, double *M, double *L, double *Linv,
                             double *energy, int *status, double *gwork, cudaStream_t st) {
-  const size_t smem = n <= CH_SMEM_MAX_N ? sizeof(double) * ((size_t)n * n + n) : 0;
+  const size_t smem = n <= CH_SMEM_MAX_N ? sizeof(double) * ((size_t)n * n + 4 * n) : 0;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -77,10 +77,13 @@ __global__ void noalloc_twiddle_kernel(cpx<T> *tw, int L) {
   }
 }
 
-// 4 pi / (N |G_m|^2) with |G|^2 = m^T g m (g = Gram matrix of the reciprocal basis), G = 0 -> 0,
-// averaged over the +-N_k/2 choices at Nyquist indices.
+// Kernel / N with |G|^2 = m^T g m (g = Gram matrix of the reciprocal basis), averaged over the
+// +-N_k/2 choices at Nyquist indices: periodic 4 pi / |G|^2 with G = 0 -> 0, or (trunc) the
+// isolated-cell kernel 4 pi (1 - cos(|G| rc)) / |G|^2 with its G = 0 limit 2 pi rc^2.
 struct RecipGram {
   double g[3][3];
+  int trunc;
+  double rc;
 };
 
 template <typename T>
@@ -100,7 +103,7 @@ __global__ void noalloc_kernel_table(T *K, int n1, int n2, int n3, RecipGram rg)
       nyq[k] = (nn[k] % 2 == 0) && (2 * idx[k] == nn[k]);
     }
     if (m[0] == 0 && m[1] == 0 && m[2] == 0) {
-      K[lin] = (T)0;
+      K[lin] = rg.trunc ? (T)(fourpi_over_N * 0.5 * rg.rc * rg.rc) : (T)0;
       continue;
     }
     double acc = 0.0;
@@ -117,7 +120,7 @@ __global__ void noalloc_kernel_table(T *K, int n1, int n2, int n3, RecipGram rg)
       double q = 0.0;
       for (int k = 0; k < 3; ++k)
         for (int l = 0; l < 3; ++l) q += mm[k] * mm[l] * rg.g[k][l];
-      acc += 1.0 / q;
+      acc += rg.trunc ? (1.0 - cos(sqrt(q) * rg.rc)) / q : 1.0 / q;
       ++cnt;
     }
     K[lin] = (T)(fourpi_over_N * acc / cnt);
@@ -166,6 +169,12 @@ ace_status run_noalloc(const ace_desc &d, const T *phi, const int *pairs, long n
   RecipGram rg;
   for (int k = 0; k < 3; ++k)
     for (int l = 0; l < 3; ++l) rg.g[k][l] = B[k][0] * B[l][0] + B[k][1] * B[l][1] + B[k][2] * B[l][2];
+  rg.trunc = d.coulomb == ACE_COULOMB_TRUNCATED;
+  rg.rc = d.r_cut;
+  if (rg.trunc && !(rg.rc > 0.0)) {  // radius of the largest sphere inside the cell
+    rg.rc = HUGE_VAL;
+    for (int k = 0; k < 3; ++k) rg.rc = std::min(rg.rc, ace::kPi / std::sqrt(rg.g[k][k]));
+  }
   for (int a = 0; a < 3; ++a) noalloc_twiddle_kernel<T><<<1, 256, 0, st>>>(tw_d[a], d.n[a]);
   noalloc_kernel_table<T><<<(unsigned)std::min<long long>((N + 255) / 256, 4096), 256, 0, st>>>(K_d, d.n[0], d.n[1],
                                                                                               d.n[2], rg);
@@ -236,6 +245,10 @@ ace_status ace_exchange_w_noalloc(const ace_desc *desc, const void *phi_dev, ace
   for (int k = 0; k < 3; ++k)
     if (!ace::pass_length_supported(desc->n[k]))
       return nf_fail(ACE_ERR_UNSUPPORTED_GRID, "grid axis %d length %d has no compiled FFT plan", k, desc->n[k]);
+  if (desc->coulomb != ACE_COULOMB_PERIODIC && desc->coulomb != ACE_COULOMB_TRUNCATED)
+    return nf_fail(ACE_ERR_ARG, "unknown Coulomb kernel %d", (int)desc->coulomb);
+  if (desc->coulomb == ACE_COULOMB_TRUNCATED && !std::isfinite(desc->r_cut))
+    return nf_fail(ACE_ERR_ARG, "non-finite r_cut");
   const bool fp64 = desc->prec == ACE_FP64;
   if ((fp64 && dtype != ACE_F64) || (!fp64 && dtype != ACE_F32))
     return nf_fail(ACE_ERR_ARG, "dtype must be the working type of the precision (F64 for ACE_FP64, F32 for ACE_MIXED)");

@@ -22,7 +22,8 @@ def mask_from_pairs(pairs, n):
     return m
 
 
-def gpu_build(phi, lattice, prec, rho_cut=0.0, spin_factor=2.0, dtype=None, host=False, stream=None):
+def gpu_build(phi, lattice, prec, rho_cut=0.0, spin_factor=2.0, dtype=None, host=False, stream=None, coulomb=0,
+              r_cut=0.0):
     import torch
 
     n = phi.shape[0]
@@ -31,7 +32,8 @@ def gpu_build(phi, lattice, prec, rho_cut=0.0, spin_factor=2.0, dtype=None, host
         dtype = np.float64 if prec == ace.ACE_FP64 else np.float32
     arr = np.ascontiguousarray(phi, dtype=dtype)
     src = arr if host else torch.from_numpy(arr).cuda()
-    d = ace.make_desc(grid, lattice, n, rho_cut=rho_cut, spin_factor=spin_factor, prec=prec)
+    d = ace.make_desc(grid, lattice, n, rho_cut=rho_cut, spin_factor=spin_factor, prec=prec, coulomb=coulomb,
+                      r_cut=r_cut)
     st, op = ace.ace_build(d, src, stream or torch.cuda.current_stream(), check=False)
     out = {"status": st, "op": op}
     if op is None:

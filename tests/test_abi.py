@@ -74,3 +74,29 @@ def test_product_path_does_not_import_oracle():
             "bad=[m for m in sys.modules if m == 'oracle' or m.startswith('oracle.')]; "
             "assert not bad, bad")
     subprocess.run([sys.executable, "-c", code], cwd=ROOT, check=True)
+
+
+def test_descriptor_layout_matches_header(tmp_path):
+    """The binding's ace_desc has the C layout: a C program compiled against include/ace.h prints
+    sizeof and every field offset, and the ctypes structure must agree."""
+    import shutil
+    import subprocess
+
+    from paper_2101_03155_gb300 import ace
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f[0] for f in ace.AceDesc._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "ace.h"\nint main(void) {\n'
+        '  printf("%zu\\n", sizeof(ace_desc));\n'
+        + "".join(f'  printf("%zu\\n", offsetof(ace_desc, {f}));\n' for f in fields)
+        + "  return 0;\n}\n"
+    )
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(ace.AceDesc)
+    assert out[1:] == [getattr(ace.AceDesc, f).offset for f in fields]

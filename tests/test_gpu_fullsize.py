@@ -30,10 +30,10 @@ def _lib():
     oracle.build()
 
 
-def _check_sampled_rows(w, g, rows, w_rtol):
+def _check_sampled_rows(w, g, rows, w_rtol, kind=oracle.PERIODIC):
     n = w.norb
     W_gpu = g["W"].reshape((n,) + w.grid).astype(np.float64)
-    W_ref = oracle.exchange_w(w.phi, w.lattice, mask=g["mask"], rows=rows)
+    W_ref = oracle.exchange_w(w.phi, w.lattice, mask=g["mask"], rows=rows, kind=kind)
     for k, i in enumerate(rows):
         assert rel_max(W_gpu[i], W_ref[k]) <= w_rtol, f"W row {i}"
         # column i of M_raw = -dV Phi^T W_i
@@ -74,3 +74,23 @@ def test_enzyme_snapshot_full_size_mixed():
     g = gpu_build(w.phi, w.lattice, ace.ACE_MIXED, rho_cut=w.rho_cut)
     assert g["status"] == 0
     _check_sampled_rows(w, g, [0, 111], MIXED_W_RTOL)
+
+
+@pytest.mark.parametrize("prec", [ace.ACE_MIXED, ace.ACE_FP64])
+def test_enzyme_snapshot_isolated_cell_full_size(prec):
+    """The enzyme-like cluster with the isolated-cell kernel (1/r cut off at the inscribed radius):
+    sampled rows of W and E_x against the stored oracle value of the same build."""
+    w = config5(nsnap=1)[0]
+    g = gpu_build(w.phi, w.lattice, prec, rho_cut=w.rho_cut, coulomb=ace.ACE_COULOMB_TRUNCATED)
+    assert g["status"] == 0
+    gold = json.load(open(GOLDEN))["enzyme_snap0_isolated"]
+    O_ref, mask_ref = oracle.screen(w.phi, w.lattice, w.rho_cut)
+    band = np.abs(O_ref - w.rho_cut) < 1e-6 * w.rho_cut
+    assert np.array_equal(g["mask"] | band, mask_ref | band)
+    if prec == ace.ACE_FP64:
+        assert np.array_equal(g["mask"], mask_ref)
+        assert abs(g["E_x"] - gold["E_x"]) <= FP64_EX_TOL
+        _check_sampled_rows(w, g, [0, 111], 1e-10, kind=oracle.TRUNCATED)
+    else:
+        assert abs(g["E_x"] - gold["E_x"]) <= MIXED_EX_TOL_PER_ORB * w.norb
+        _check_sampled_rows(w, g, [0, 111], MIXED_W_RTOL, kind=oracle.TRUNCATED)

@@ -256,3 +256,57 @@ def test_mixed_dense_steps_beyond_one_tile():
     assert np.abs(g["L"] - L).max() <= 1e-12 * np.abs(L).max()
     xi_ref = sla.solve_triangular(L, W, lower=True)
     assert rel_max(g["xi"], xi_ref) <= 1e-4
+
+
+@pytest.fixture(scope="module")
+def cluster_small():
+    """16 localized orbitals in a 3.5-bohr cluster at the centre of a mostly empty 16-bohr cell."""
+    from workloads.generators import enzyme_like
+
+    return enzyme_like(np.random.default_rng(1050), ncentres=16, cell=(16.0, 16.0, 16.0), grid=(48, 48, 48),
+                       radius=3.5, dmin=2.0, nsnap=1)[0]
+
+
+@pytest.mark.parametrize("prec", [ace.ACE_FP64, ace.ACE_MIXED])
+def test_truncated_kernel_build(cluster_small, prec):
+    """Isolated-cell kernel (1/r cut off at the inscribed radius): screen, W, M, L, xi and E_x
+    against the oracle with the same kernel."""
+    w = cluster_small
+    g = gpu_build(w.phi, w.lattice, prec, rho_cut=w.rho_cut, coulomb=ace.ACE_COULOMB_TRUNCATED)
+    assert g["status"] == 0
+    ref = oracle.ace_build(w.phi, w.lattice, mask=g["mask"], spin_factor=w.spin_factor, kind=oracle.TRUNCATED)
+    assert ref["status"] == 0
+    n = w.norb
+    if prec == ace.ACE_FP64:
+        assert abs(g["E_x"] - ref["E_x"]) <= FP64_EX_TOL
+        assert rel_max(g["W"].reshape(ref["W"].shape), ref["W"]) <= FP64_ARRAY_RTOL
+        assert rel_max(g["xi"].reshape(ref["xi"].shape), ref["xi"]) <= FP64_ARRAY_RTOL
+        assert rel_max(g["L"], ref["L"]) <= FP64_ARRAY_RTOL
+    else:
+        assert abs(g["E_x"] - ref["E_x"]) <= MIXED_EX_TOL_PER_ORB * n
+        assert rel_max(g["W"].reshape(ref["W"].shape), ref["W"]) <= MIXED_W_RTOL
+    # the periodic kernel is a different interaction on the same input
+    per = oracle.ace_build(w.phi, w.lattice, mask=g["mask"], spin_factor=w.spin_factor)
+    assert abs(per["E_x"] - ref["E_x"]) > 1e3 * FP64_EX_TOL
+
+
+def test_truncated_kernel_explicit_radius(cluster_small):
+    """An explicit cut-off radius reaches the kernel table (and the table cache keeps kernels apart)."""
+    w = cluster_small
+    for rc in (6.5, 7.25):
+        g = gpu_build(w.phi, w.lattice, ace.ACE_FP64, coulomb=ace.ACE_COULOMB_TRUNCATED, r_cut=rc)
+        ref = oracle.ace_build(w.phi, w.lattice, spin_factor=w.spin_factor, kind=oracle.TRUNCATED, r_cut=rc)
+        assert abs(g["E_x"] - ref["E_x"]) <= FP64_EX_TOL, rc
+
+
+def test_truncated_kernel_argument_errors():
+    import torch
+
+    lat = np.eye(3) * 8
+    x = torch.zeros((2, 16, 16, 16), device="cuda")
+    with pytest.raises(ace.AceError) as e:
+        ace.ace_build(ace.make_desc((16, 16, 16), lat, 2, coulomb=7), x)
+    assert e.value.status == ace.ace.ACE_ERR_ARG
+    with pytest.raises(ace.AceError) as e:
+        ace.ace_build(ace.make_desc((16, 16, 16), lat, 2, coulomb=ace.ACE_COULOMB_TRUNCATED, r_cut=float("nan")), x)
+    assert e.value.status == ace.ace.ACE_ERR_ARG

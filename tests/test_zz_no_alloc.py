@@ -69,3 +69,26 @@ def test_noalloc_refuses_grids_beyond_its_array():
         ace.ace.ace_exchange_w_noalloc(desc, tiny, np.array([[0, 0]], np.int32), tiny)
     assert e.value.status == ace.ace.ACE_ERR_ARG
     assert "fixed array" in str(e.value)
+
+
+@pytest.mark.parametrize("prec", [ace.ACE_FP64, ace.ACE_MIXED])
+def test_noalloc_truncated_kernel(prec):
+    """The isolated-cell kernel table built on the device matches ace_build's host-built table."""
+    import torch
+
+    from workloads.generators import enzyme_like
+
+    w = enzyme_like(np.random.default_rng(1050), ncentres=16, cell=(16.0, 16.0, 16.0), grid=(48, 48, 48),
+                    radius=3.5, dmin=2.0, nsnap=1)[0]
+    dtype = torch.float64 if prec == ace.ACE_FP64 else torch.float32
+    tol = FP64_ARRAY_RTOL if prec == ace.ACE_FP64 else MIXED_W_RTOL
+    for rc in (0.0, 6.5):
+        g = gpu_build(w.phi, w.lattice, prec, rho_cut=w.rho_cut, coulomb=ace.ACE_COULOMB_TRUNCATED, r_cut=rc)
+        assert g["status"] == 0
+        desc = ace.make_desc(w.grid, w.lattice, w.norb, prec=prec, coulomb=ace.ACE_COULOMB_TRUNCATED, r_cut=rc)
+        phi = torch.from_numpy(w.phi).to(device="cuda", dtype=dtype)
+        W = torch.full_like(phi, float("nan"))
+        ace.ace.ace_exchange_w_noalloc(desc, phi, g["pairs"], W, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert rel_max(W.cpu().numpy(), g["W"].reshape(w.phi.shape)) <= tol
+        g["op"].close()
