@@ -208,10 +208,170 @@ __global__ void __launch_bounds__(G2_NT, 2) gram_f32_kernel(const float *__restr
   }
 }
 
+// ----------------------------------------------------------------------------------------
+// Symmetric FP32 Gram (the screen, X = Y, upper triangle): 64 x 64 tiles enumerated over the
+// upper triangle of 64-row blocks only, 256 threads with 4 x 4 outputs each, k-step 16, chunks of
+// ACE_GS_CHUNK points per CTA.  Products run as packed f32x2 FMAs: the row operand is stored twice in
+// shared memory ((a, a) pairs) so that a pair of outputs (c, c + 1) takes one instruction.
+// Within a chunk, 32-point FP32 partials are added with Kahan compensation; chunks meet in FP64
+// atomics.
+// ----------------------------------------------------------------------------------------
+// points per CTA and CTAs per SM of the symmetric kernel (the register budget follows)
+#ifndef ACE_GS_CHUNK
+#define ACE_GS_CHUNK 2048
+#endif
+#ifndef ACE_GS_MINB
+#define ACE_GS_MINB 2
+#endif
+constexpr int GS_B = 64, GS_BK = 16, GS_NT = 256, GS_CHUNK = ACE_GS_CHUNK;
+
+__device__ __forceinline__ unsigned long long f2pk(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 f2up(unsigned long long v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+template <bool ABS>
+__global__ void __launch_bounds__(GS_NT, ACE_GS_MINB) gram_sym_f32_kernel(const float *__restrict__ X, int n, long long K,
+                                                             double scale, double *__restrict__ G) {
+  // (a, a) pairs of the row block and plain values of the column block, double-buffered
+  __shared__ __align__(16) float2 xs[2][GS_BK][GS_B + 2];
+  __shared__ __align__(16) float ys[2][GS_BK][GS_B + 4];
+  // tile t of the upper triangle of nb x nb blocks: row-major over bi <= bj
+  int bi = 0, t = blockIdx.x;
+  {
+    const int nb = (n + GS_B - 1) / GS_B;
+    while (t >= nb - bi) {
+      t -= nb - bi;
+      ++bi;
+    }
+  }
+  const int bj = bi + t;
+  const int i0 = bi * GS_B, j0 = bj * GS_B;
+  const long long kb = (long long)blockIdx.y * GS_CHUNK;
+  const long long ke = min(K, kb + GS_CHUNK);
+  const int ntiles = (int)((ke - kb + GS_BK - 1) / GS_BK);
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  unsigned long long acc[4][2], comp[4][2], part[4][2];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) acc[a][b] = comp[a][b] = part[a][b] = 0ull;
+
+  // each thread stages one float4 (4 consecutive points) of one row of each block; the global
+  // loads run two k-tiles ahead (register sets 0 and 1 alternate)
+  const int lrow = tid >> 2, lk = (tid & 3) * 4;
+  float4 rx[2], ry[2];
+  auto load = [&](int tt, float4 &vx, float4 &vy) {
+    const long long k0 = kb + (long long)tt * GS_BK + lk;
+    vx = make_float4(0.f, 0.f, 0.f, 0.f);
+    vy = vx;
+    if (tt < ntiles && k0 < ke) {
+      if (i0 + lrow < n) vx = __ldg(reinterpret_cast<const float4 *>(X + (long long)(i0 + lrow) * K + k0));
+      if (j0 + lrow < n) vy = __ldg(reinterpret_cast<const float4 *>(X + (long long)(j0 + lrow) * K + k0));
+    }
+  };
+  auto store = [&](int buf, const float4 &ux, const float4 &uy) {
+    const float vx[4] = {ux.x, ux.y, ux.z, ux.w}, vy[4] = {uy.x, uy.y, uy.z, uy.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float a = ABS ? fabsf(vx[c]) : vx[c];
+      xs[buf][lk + c][lrow] = make_float2(a, a);
+      ys[buf][lk + c][lrow] = ABS ? fabsf(vy[c]) : vy[c];
+    }
+  };
+  auto compute = [&](int buf, int tt) {
+#pragma unroll
+    for (int k = 0; k < GS_BK; ++k) {
+      const ulonglong2 a01 = *reinterpret_cast<const ulonglong2 *>(&xs[buf][k][ty * 4]);
+      const ulonglong2 a23 = *reinterpret_cast<const ulonglong2 *>(&xs[buf][k][ty * 4 + 2]);
+      const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&ys[buf][k][tx * 4]);
+      const unsigned long long av[4] = {a01.x, a01.y, a23.x, a23.y};
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        part[r][0] = f2fma(av[r], b.x, part[r][0]);
+        part[r][1] = f2fma(av[r], b.y, part[r][1]);
+      }
+    }
+    if ((tt & 1) || tt + 1 == ntiles) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const unsigned long long y = f2sub(part[r][c], comp[r][c]);
+          const unsigned long long sm = f2add(acc[r][c], y);
+          comp[r][c] = f2sub(f2sub(sm, acc[r][c]), y);
+          acc[r][c] = sm;
+          part[r][c] = 0ull;
+        }
+    }
+  };
+  load(0, rx[0], ry[0]);
+  store(0, rx[0], ry[0]);
+  load(1, rx[1], ry[1]);
+  __syncthreads();
+  // tile tt sits in shared buffer tt & 1; tile tt + 1 in register set (tt + 1) & 1
+  for (int tt = 0; tt < ntiles; tt += 2) {
+    load(tt + 2, rx[0], ry[0]);
+    compute(0, tt);
+    store(1, rx[1], ry[1]);
+    __syncthreads();
+    if (tt + 1 >= ntiles) break;
+    load(tt + 3, rx[1], ry[1]);
+    compute(1, tt + 1);
+    store(0, rx[0], ry[0]);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + ty * 4 + r;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float2 v = f2up(acc[r][c]);
+      const int j = j0 + tx * 4 + 2 * c;
+      if (i < n && j < n && j >= i) atomicAdd(G + (long long)i * n + j, scale * (double)v.x);
+      if (i < n && j + 1 < n && j + 1 >= i) atomicAdd(G + (long long)i * n + j + 1, scale * (double)v.y);
+    }
+  }
+}
+
 template <typename T>
 cudaError_t launch_gram(const T *X, int nx, const T *Y, int ny, long long K, double scale, bool abs_values,
                         bool upper_only, double *G, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
+    if (K % 4 == 0 && X == Y && nx == ny && upper_only) {
+      const int nb = (nx + GS_B - 1) / GS_B;
+      const long long chunks = (K + GS_CHUNK - 1) / GS_CHUNK;
+      if (chunks > 65535) return cudaErrorInvalidValue;
+      cudaError_t e = cudaMemsetAsync(G, 0, sizeof(double) * (size_t)nx * ny, st);
+      if (e != cudaSuccess) return e;
+      dim3 grid(nb * (nb + 1) / 2, (unsigned)chunks);
+      if (abs_values)
+        gram_sym_f32_kernel<true><<<grid, GS_NT, 0, st>>>(X, nx, K, scale, G);
+      else
+        gram_sym_f32_kernel<false><<<grid, GS_NT, 0, st>>>(X, nx, K, scale, G);
+      return cudaGetLastError();
+    }
     if (K % 4 == 0) {
       const int tiles_i = (nx + G2_BM - 1) / G2_BM, tiles_j = (ny + G2_BN - 1) / G2_BN;
       const long long chunks = (K + G2_CHUNK - 1) / G2_CHUNK;
