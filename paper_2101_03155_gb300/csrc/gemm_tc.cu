@@ -14,12 +14,15 @@
 // matrices LBO = 128 B apart, row-group-adjacent ones SBO = 512 B apart (a 32-wide K step).  One
 // thread issues the MMAs (M = 128, N = 128, K = 16 each) and commits them to an mbarrier; every
 // wait on an mbarrier is bounded and reports a timeout through *err instead of hanging.
+#include <cuda.h>  // CUtensorMap and its enums (types only; the encoder is reached through cudart)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
+#include <mutex>
 
 #include "ace_internal.h"
 
@@ -133,10 +136,45 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// first 1024-byte aligned address of the dynamic shared array, as an offset from it (so that the
+// compiler keeps the shared state space and emits LDS / STS rather than generic accesses)
+__device__ __forceinline__ unsigned char *align1024(unsigned char *dyn) {
+  return dyn + ((1024u - (smem_u32(dyn) & 1023u)) & 1023u);
+}
+
 // byte offset of element (row, k) of a 128 x 32 K-major tile in the canonical layout
 __device__ __forceinline__ uint32_t tile_off(int row, int k) {
   return (uint32_t)(row >> 3) * SBO + (uint32_t)(k >> 3) * LBO + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 7) * 2u;
 }
+
+// ---- TMA (cp.async.bulk.tensor) into shared memory, completion counted on an mbarrier ----
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+// box at (x, y) of a 2D tensor map (x innermost, a multiple of 4 FP32 = 16 bytes)
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+
+// box at (x, y) of a 2D tensor map from shared memory (bulk-group completion)
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// wait until at most N committed bulk groups still read their shared-memory source
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+// wait until every committed bulk group has completed its writes
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ void split1(float x, uint16_t &hi, uint16_t &lo) {
   const __nv_bfloat16 bh = __float2bfloat16_rn(x);
@@ -219,7 +257,7 @@ __global__ void __launch_bounds__(NT) tc_gram_kernel(const float *__restrict__ X
                                                      int ny, long long K, int chunk, int tiles_x,
                                                      float *__restrict__ partial, int *__restrict__ err) {
   extern __shared__ unsigned char dyn[];
-  unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(dyn) + 1023) & ~uintptr_t(1023));
+  unsigned char *base = align1024(dyn);
   uint64_t *mbar = reinterpret_cast<uint64_t *>(base + 2 * SmemLayout::kStage);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -348,7 +386,7 @@ __global__ void __launch_bounds__(NT) tc_left_mul_kernel(const float *__restrict
                                                          const float *__restrict__ Y, long long K, float *__restrict__ Z,
                                                          int *__restrict__ err) {
   extern __shared__ unsigned char dyn[];
-  unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(dyn) + 1023) & ~uintptr_t(1023));
+  unsigned char *base = align1024(dyn);
   const int nsteps = (n + BK - 1) / BK;
   unsigned char *a_tiles = base;                            // nsteps x {hi, lo}
   unsigned char *b_stage = base + (size_t)nsteps * 2 * TILE_BYTES;  // 2 stages x {hi, lo}
@@ -453,6 +491,193 @@ __global__ void __launch_bounds__(NT) tc_left_mul_kernel(const float *__restrict
   if (warp == 0) tmem_dealloc(tmem, 128);
 }
 
+// ----------------------------------------------------------------------------------------
+// Left multiply fed by TMA: Z[i][c] = sum_l A[i][l] Y[l][c] for rows [i0, i0 + 128) of A.
+//   - A rows: split into bf16 hi/lo once per CTA, resident in shared memory (n/32 K-steps).
+//   - Y: boxes of 32 rows x 128 columns (16 KB FP32) arrive by TMA in a ring of `ring` stages,
+//     issued `ring` items ahead by thread 0; an item is one (column tile, K-step).
+//   - Each thread splits column `tid` of a box into the K-major B tile (two B buffers, so that
+//     the split of item q overlaps the MMAs of item q - 1).
+//   - Two TMEM accumulators: tile j accumulates in accumulator j & 1 while the epilogue of
+//     tile j - 1 reads the other one.
+// Every wait is bounded; after a timeout the kernel waits (bounded) for its copies and MMAs in
+// flight, releases TMEM and reports through *err.
+// ----------------------------------------------------------------------------------------
+constexpr uint32_t kLmBox = BK * BN * 4;   // one Y box: 32 rows x 128 FP32 columns
+constexpr uint32_t kEpiBox = BM * 32 * 4;  // one Z box: 128 rows x 32 FP32 columns
+
+__global__ void __launch_bounds__(NT, 1) tc_left_mul_tma_kernel(const float *__restrict__ A, int m, int n,
+                                                                const __grid_constant__ CUtensorMap tmY,
+                                                                const __grid_constant__ CUtensorMap tmZ, long long K,
+                                                                int ring, int *__restrict__ err) {
+  extern __shared__ unsigned char dyn[];
+  unsigned char *base = align1024(dyn);
+  const int nsteps = (n + BK - 1) / BK;
+  unsigned char *a_tiles = base;                                    // nsteps x {hi, lo}
+  unsigned char *b_ops = a_tiles + (size_t)nsteps * 2 * TILE_BYTES;  // 2 buffers x {hi, lo}
+  unsigned char *epi = b_ops + 2 * 2 * TILE_BYTES;                  // 2 x 128 rows x 32 FP32 (swizzled)
+  unsigned char *boxes = epi + 2 * kEpiBox;                         // ring x kLmBox
+  uint64_t *full = reinterpret_cast<uint64_t *>(boxes + (size_t)ring * kLmBox);
+  uint64_t *mmad = full + ring;  // MMAs of the items that read B buffer b
+  uint64_t *accf = mmad + 2;     // every MMA of the tile in accumulator a
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accf + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int i0 = blockIdx.y * BM;
+  const long long ntiles = K / BN;
+  const long long mytiles = ntiles > (long long)blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const long long Q = mytiles * nsteps;
+
+  if (warp == 0) tmem_alloc(tmem_slot, 256);
+  if (tid == 0) {
+    for (int r = 0; r < ring; ++r) mbar_init(smem_u32(&full[r]));
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&mmad[b]));
+      mbar_init(smem_u32(&accf[b]));
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();
+  // items are numbered q = tile_slot * nsteps + kstep; the producer walks them with counters
+  int p_stage = 0, p_step = 0;
+  long long p_tile = blockIdx.x;
+  auto issue_next = [&]() {  // thread 0: the next item into stage p_stage
+    const uint32_t mb = smem_u32(&full[p_stage]);
+    mbar_expect_tx(mb, kLmBox);
+    tma_load_2d(smem_u32(boxes + (size_t)p_stage * kLmBox), &tmY, (int)(p_tile * BN), p_step * BK, mb);
+    if (++p_stage == ring) p_stage = 0;
+    if (++p_step == nsteps) {
+      p_step = 0;
+      p_tile += gridDim.x;
+    }
+  };
+  const int Qi = (int)Q;
+  int issued = Qi < ring ? Qi : ring;
+  if (tid == 0)
+    for (int k = 0; k < issued; ++k) issue_next();
+  // resident A: row i0 + tid, all K-steps (overlaps the first copies)
+  for (int it = 0; it < nsteps; ++it) {
+    Row32 r;
+    if (i0 + tid < m) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) r.v[j] = (it * BK + j < n) ? __ldg(A + (long long)(i0 + tid) * n + it * BK + j) : 0.f;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) r.v[j] = 0.f;
+    }
+    unsigned char *t = a_tiles + (size_t)it * 2 * TILE_BYTES;
+    store_row(r, tid, t, t + TILE_BYTES);
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  Pipe pipe;
+  pipe.init();
+  bool ok = true;
+  int q = 0;
+  auto epilogue = [&](int j) -> bool {
+    const int a = j & 1;
+    const bool w = mbar_wait(smem_u32(&accf[a]), (uint32_t)((j >> 1) & 1));
+    if (__syncthreads_or(!w)) return false;
+    tc_fence_after();
+    const long long c0 = (blockIdx.x + (long long)j * gridDim.x) * BN;
+    const int row = 32 * warp + (tid & 31);  // TMEM lane = row of the tile
+#pragma unroll 1
+    for (int cb = 0; cb < BN / 32; ++cb) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)a * BN + 32 * cb, v);
+      // staging buffer e is free once the store that last read it has read it
+      unsigned char *eb = epi + (size_t)(cb & 1) * kEpiBox;
+      if (tid == 0) bulk_wait_read<1>();
+      __syncthreads();
+      // row `row`: 128 bytes, 16-byte chunk q at position q ^ (row & 7) (the map's 128-byte swizzle)
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        *reinterpret_cast<float4 *>(eb + row * 128 + ((q ^ (row & 7)) << 4)) =
+            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tma_store_2d(&tmZ, (int)(c0 + 32 * cb), i0, smem_u32(eb));
+        bulk_commit();
+      }
+    }
+    tc_fence_before();
+    __syncthreads();  // accumulator a is read before tile j + 2 writes it
+    return true;
+  };
+  int stage = 0, st = 0, j = 0;
+  uint32_t fpar = 0;  // parity of the current pass over the ring
+  for (; q < Qi; ++q) {
+    const int b = q & 1;
+    const bool got = mbar_wait(smem_u32(&full[stage]), fpar);
+    const bool freed = pipe.drain(mmad, b);
+    if (__syncthreads_or(!(got && freed))) {
+      ok = false;
+      break;
+    }
+    {
+      Row32 r;
+      const float *box = reinterpret_cast<const float *>(boxes + (size_t)stage * kLmBox);
+#pragma unroll
+      for (int k = 0; k < BK; ++k) r.v[k] = box[k * BN + tid];
+      unsigned char *bt = b_ops + (size_t)b * 2 * TILE_BYTES;
+      store_row(r, tid, bt, bt + TILE_BYTES);
+    }
+    fence_async_smem();
+    __syncthreads();  // the box is consumed and the B tile written
+    if (tid == 0) {
+      if (issued < Qi) {
+        issue_next();
+        ++issued;
+      }
+      tc_fence_after();
+      const uint32_t acc = tmem + (uint32_t)(j & 1) * BN;
+      const uint32_t a_hi = smem_u32(a_tiles + (size_t)st * 2 * TILE_BYTES), a_lo = a_hi + TILE_BYTES;
+      const uint32_t b_hi = smem_u32(b_ops + (size_t)b * 2 * TILE_BYTES), b_lo = b_hi + TILE_BYTES;
+#pragma unroll
+      for (int ks = 0; ks < BK / 16; ++ks) {
+        const uint32_t o = ks * 2 * LBO;
+        mma(acc, sdesc(a_hi + o), sdesc(b_hi + o), (st > 0 || ks > 0) ? 1u : 0u);
+        mma(acc, sdesc(a_hi + o), sdesc(b_lo + o), 1u);
+        mma(acc, sdesc(a_lo + o), sdesc(b_hi + o), 1u);
+      }
+      commit(smem_u32(&mmad[b]));
+      if (st == nsteps - 1) commit(smem_u32(&accf[j & 1]));
+    } else if (issued < Qi) {
+      ++issued;  // every thread tracks what thread 0 has issued
+    }
+    pipe.pending[b] = 1;
+    const bool first = st == 0;
+    if (++stage == ring) {
+      stage = 0;
+      fpar ^= 1u;
+    }
+    if (first && j > 0 && !epilogue(j - 1)) {
+      ok = false;
+      ++q;  // item q was consumed
+      break;
+    }
+    if (++st == nsteps) {
+      st = 0;
+      ++j;
+    }
+  }
+  if (ok && Qi > 0) ok = epilogue((int)mytiles - 1);
+  if (!ok) {
+    // bounded waits for the copies still in flight (items q .. issued - 1) and the last MMAs
+    for (int r = q; r < issued; ++r) mbar_wait(smem_u32(&full[r % ring]), (uint32_t)((r / ring) & 1));
+    pipe.drain(mmad, 0);
+    pipe.drain(mmad, 1);
+    if (tid == 0) atomicExch(err, 1);
+  }
+  if (tid == 0) bulk_wait_all();  // the stores have left shared memory before the CTA exits
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
 }  // namespace tc
 
 bool tc_shapes_ok(long long K) { return K % tc::BN == 0 && K % tc::BK == 0; }
@@ -497,8 +722,70 @@ size_t tc_gram_workspace_bytes(int nx, int ny, long long K) {
   return part2_off + sizeof(double) * tc::kReduceGroups * (size_t)nx * ny;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// 2D map of a row-major FP32 matrix [rows][cols] with boxes of box_rows x box_cols; false when
+// the encoder is unavailable or refuses the layout (base 16-byte aligned, cols % 4 == 0)
+static bool make_map_f32(CUtensorMap *map, const float *ptr, long long rows, long long cols, int box_rows,
+                         int box_cols, bool swizzle128) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || (reinterpret_cast<uintptr_t>(ptr) & 15) || (cols & 3)) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static bool use_tma() {
+  static const bool on = [] {
+    const char *v = std::getenv("ACE_NO_TMA");
+    return !(v && *v && *v != '0');
+  }();
+  return on;
+}
+
 cudaError_t launch_tc_left_mul(const float *A, int m, int n, const float *Y, long long K, float *Z, int *err,
                                cudaStream_t st) {
+  if (K % tc::BN != 0) return cudaErrorInvalidValue;
+  if (use_tma()) {
+    const int nsteps = (n + tc::BK - 1) / tc::BK;
+    const size_t fixed = ((size_t)nsteps * 2 + 4) * tc::TILE_BYTES + 2 * tc::kEpiBox + 1024 + 256;
+    const size_t cap = 227 * 1024;
+    const int ring = fixed + 2 * tc::kLmBox <= cap ? (int)std::min<size_t>(8, (cap - fixed) / tc::kLmBox) : 0;
+    CUtensorMap map, zmap;
+    if (ring >= 2 && make_map_f32(&map, Y, n, K, tc::BK, tc::BN, false) &&
+        make_map_f32(&zmap, Z, m, K, tc::BM, 32, true)) {
+      const int smem = (int)(fixed + (size_t)ring * tc::kLmBox);
+      cudaError_t e =
+          cudaFuncSetAttribute(tc::tc_left_mul_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      int dev = 0, sms = 152;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      const long long tiles = K / tc::BN;
+      const int rows = (m + tc::BM - 1) / tc::BM;
+      const unsigned gx = (unsigned)std::max(1LL, std::min(tiles, (long long)std::max(1, sms / rows)));
+      tc::tc_left_mul_tma_kernel<<<dim3(gx, rows), tc::NT, smem, st>>>(A, m, n, map, zmap, K, ring, err);
+      return cudaGetLastError();
+    }
+  }
   if (K % tc::BN != 0) return cudaErrorInvalidValue;
   const int nsteps = (n + tc::BK - 1) / tc::BK;
   const int smem = (int)(((size_t)nsteps * 2 + 4) * tc::TILE_BYTES + 2048);
