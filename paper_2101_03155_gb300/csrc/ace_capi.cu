@@ -705,11 +705,10 @@ cudaError_t dense_gram(const T *X, int nx, const T *Y, int ny, long long K, doub
   if constexpr (sizeof(T) == 4) {
     if (use_tc() && ace::tc_shapes_ok(K)) {
       void *ws = nullptr;
-      cudaError_t e = cudaMallocAsync(&ws, ace::tc_gram_workspace_bytes(nx, ny, K), st);
+      cudaError_t e = cudaMallocAsync(&ws, ace::tc_gram_workspace_bytes(X, nx, Y, ny, K), st);
       if (e != cudaSuccess) return e;
       temps.push_back(ws);
-      *launches += 2;
-      return ace::launch_tc_gram(X, nx, Y, ny, K, scale, G, static_cast<float *>(ws), err, st);
+      return ace::launch_tc_gram(X, nx, Y, ny, K, scale, G, ws, err, st, launches);
     }
   }
   *launches += 1;

@@ -96,9 +96,10 @@ cudaError_t launch_transpose_scale(const double *C, int n, int m, double scale, 
 // Tensor-core (tcgen05) BF16x3 contractions for FP32 operands.  *err is set to 1 when a bounded
 // wait inside the kernel gave up.  K must be a multiple of 128 (tc_shapes_ok).
 bool tc_shapes_ok(long long K);
-size_t tc_gram_workspace_bytes(int nx, int ny, long long K);
+// workspace of launch_tc_gram for these operands (the path it takes depends on them)
+size_t tc_gram_workspace_bytes(const float *X, int nx, const float *Y, int ny, long long K);
 cudaError_t launch_tc_gram(const float *X, int nx, const float *Y, int ny, long long K, double scale, double *G,
-                           float *partial_ws, int *err, cudaStream_t st);
+                           void *ws, int *err, cudaStream_t st, long *launches);
 cudaError_t launch_tc_left_mul(const float *A, int m, int n, const float *Y, long long K, float *Z, int *err,
                                cudaStream_t st);
 

@@ -136,6 +136,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 consecutive FP32 columns of this thread's TMEM lane from registers (completion: tmem_st_wait)
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+      "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+      "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+      "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+      "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+      "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // first 1024-byte aligned address of the dynamic shared array, as an offset from it (so that the
 // compiler keeps the shared state space and emits LDS / STS rather than generic accesses)
 __device__ __forceinline__ unsigned char *align1024(unsigned char *dyn) {
@@ -678,6 +697,218 @@ __global__ void __launch_bounds__(NT, 1) tc_left_mul_tma_kernel(const float *__r
   if (warp == 0) tmem_dealloc(tmem, 256);
 }
 
+// ----------------------------------------------------------------------------------------
+// Gram fed by TMA: partial[s][i][j] = sum over the chunks of split s of sum_r X[i][r] Y[j][r] for
+// one 128 x 128 tile.
+//   - X and Y boxes of 128 rows x 32 points (16 KB FP32, 128-byte swizzled) arrive by TMA in a
+//     ring of `ring` stages; one item = one 32-point K-step of both operands.
+//   - Each thread splits row `tid` of both boxes into the K-major A and B tiles (two buffers).
+//   - Each chunk of `cs` K-steps accumulates in FP32 in one of two TMEM accumulators (a longer
+//     FP32 accumulation in the tensor core loses accuracy); while the next chunk runs, the
+//     finished one is added to a running sum kept in TMEM with Kahan compensation (sum and
+//     compensation in TMEM columns 256-383 and 384-511).
+//   - At the end the split's sum minus its compensation is written in FP64; a second kernel adds
+//     the splits in FP64 in a fixed order.
+// Every wait is bounded, as in the left multiply.
+// ----------------------------------------------------------------------------------------
+constexpr uint32_t kGBox = BM * BK * 4;  // 128 rows x 32 FP32
+
+__global__ void __launch_bounds__(NT, 1) tc_gram_tma_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                            const __grid_constant__ CUtensorMap tmY, int nx, int ny,
+                                                            long long K, int cs, int tiles_x, int ring,
+                                                            double *__restrict__ partial, int *__restrict__ err) {
+  extern __shared__ unsigned char dyn[];
+  unsigned char *base = align1024(dyn);
+  unsigned char *ops = base;                  // 2 buffers x {A_hi, A_lo, B_hi, B_lo}
+  unsigned char *boxes = ops + 2 * 4 * TILE_BYTES;  // ring x {X box, Y box}
+  uint64_t *full = reinterpret_cast<uint64_t *>(boxes + (size_t)ring * 2 * kGBox);
+  uint64_t *mmad = full + ring;
+  uint64_t *accf = mmad + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accf + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int ti = blockIdx.x % tiles_x, tj = blockIdx.x / tiles_x;
+  const int i0 = ti * BM, j0 = tj * BN;
+  // this split's K-steps: whole chunks [c_lo, c_hi) of cs steps (the last chunk may be short)
+  const long long KS = K / BK, C = (KS + cs - 1) / cs;
+  const long long c_lo = (long long)blockIdx.y * C / gridDim.y, c_hi = (long long)(blockIdx.y + 1) * C / gridDim.y;
+  const long long ks_lo = c_lo * cs, ks_hi = min(KS, c_hi * (long long)cs);
+  const int Q = (int)(ks_hi > ks_lo ? ks_hi - ks_lo : 0);
+
+  if (warp == 0) tmem_alloc(tmem_slot, 512);
+  if (tid == 0) {
+    for (int r = 0; r < ring; ++r) mbar_init(smem_u32(&full[r]));
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&mmad[b]));
+      mbar_init(smem_u32(&accf[b]));
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();
+  int p_stage = 0;
+  long long p_ks = ks_lo;
+  auto issue_next = [&]() {  // thread 0: K-step p_ks into stage p_stage
+    const uint32_t mb = smem_u32(&full[p_stage]);
+    unsigned char *bx = boxes + (size_t)p_stage * 2 * kGBox;
+    mbar_expect_tx(mb, 2 * kGBox);
+    tma_load_2d(smem_u32(bx), &tmX, (int)(p_ks * BK), i0, mb);
+    tma_load_2d(smem_u32(bx + kGBox), &tmY, (int)(p_ks * BK), j0, mb);
+    if (++p_stage == ring) p_stage = 0;
+    ++p_ks;
+  };
+  int issued = Q < ring ? Q : ring;
+  if (tid == 0)
+    for (int k = 0; k < issued; ++k) issue_next();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  {  // running sum and compensation start at zero
+    float z[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) z[c] = 0.f;
+#pragma unroll 1
+    for (int cb = 0; cb < 8; ++cb) tmem_st32(tmem + lane_off + 256 + 32 * cb, z);
+    tmem_st_wait();
+  }
+  Pipe pipe;
+  pipe.init();
+  bool ok = true;
+  // Kahan add of the finished chunk held in accumulator c & 1
+  auto fold = [&](int c) -> bool {
+    const int a = c & 1;
+    const bool w = mbar_wait(smem_u32(&accf[a]), (uint32_t)((c >> 1) & 1));
+    if (__syncthreads_or(!w)) return false;
+    tc_fence_after();
+#pragma unroll 1
+    for (int cb = 0; cb < BN / 32; ++cb) {
+      float x[32], sm[32], cp[32];
+      tmem_ld32(tmem + lane_off + (uint32_t)a * BN + 32 * cb, x);
+      tmem_ld32(tmem + lane_off + 256 + 32 * cb, sm);
+      tmem_ld32(tmem + lane_off + 384 + 32 * cb, cp);
+#pragma unroll
+      for (int e = 0; e < 32; ++e) {
+        const float y = x[e] - cp[e];
+        const float t = sm[e] + y;
+        cp[e] = (t - sm[e]) - y;
+        sm[e] = t;
+      }
+      tmem_st32(tmem + lane_off + 256 + 32 * cb, sm);
+      tmem_st32(tmem + lane_off + 384 + 32 * cb, cp);
+    }
+    tmem_st_wait();
+    tc_fence_before();
+    __syncthreads();  // accumulator a is folded before chunk c + 2 overwrites it
+    return true;
+  };
+  int q = 0, stage = 0, kin = 0, cl = 0;
+  uint32_t fpar = 0;
+  for (; q < Q; ++q) {
+    const int b = q & 1;
+    const bool got = mbar_wait(smem_u32(&full[stage]), fpar);
+    const bool freed = pipe.drain(mmad, b);
+    if (__syncthreads_or(!(got && freed))) {
+      ok = false;
+      break;
+    }
+    {
+      const unsigned char *bx = boxes + (size_t)stage * 2 * kGBox;
+      unsigned char *ob = ops + (size_t)b * 4 * TILE_BYTES;
+#pragma unroll
+      for (int op = 0; op < 2; ++op) {
+        // row tid of the box: 16-byte chunk k4 sits at position k4 ^ (tid & 7) (128-byte swizzle)
+        const unsigned char *rowp = bx + (size_t)op * kGBox + tid * 128;
+        Row32 r;
+#pragma unroll
+        for (int k4 = 0; k4 < 8; ++k4) {
+          const float4 t = *reinterpret_cast<const float4 *>(rowp + ((k4 ^ (tid & 7)) << 4));
+          r.v[4 * k4] = t.x;
+          r.v[4 * k4 + 1] = t.y;
+          r.v[4 * k4 + 2] = t.z;
+          r.v[4 * k4 + 3] = t.w;
+        }
+        store_row(r, tid, ob + (size_t)op * 2 * TILE_BYTES, ob + (size_t)op * 2 * TILE_BYTES + TILE_BYTES);
+      }
+    }
+    fence_async_smem();
+    __syncthreads();
+    const bool last_in_chunk = (kin == cs - 1) || (q == Q - 1);
+    if (tid == 0) {
+      if (issued < Q) {
+        issue_next();
+        ++issued;
+      }
+      tc_fence_after();
+      const uint32_t acc = tmem + (uint32_t)(cl & 1) * BN;
+      const uint32_t a_hi = smem_u32(ops + (size_t)b * 4 * TILE_BYTES), a_lo = a_hi + TILE_BYTES;
+      const uint32_t b_hi = a_hi + 2 * TILE_BYTES, b_lo = a_hi + 3 * TILE_BYTES;
+#pragma unroll
+      for (int ks = 0; ks < BK / 16; ++ks) {
+        const uint32_t o = ks * 2 * LBO;
+        mma(acc, sdesc(a_hi + o), sdesc(b_hi + o), (kin > 0 || ks > 0) ? 1u : 0u);
+        mma(acc, sdesc(a_hi + o), sdesc(b_lo + o), 1u);
+        mma(acc, sdesc(a_lo + o), sdesc(b_hi + o), 1u);
+      }
+      commit(smem_u32(&mmad[b]));
+      if (last_in_chunk) commit(smem_u32(&accf[cl & 1]));
+    } else if (issued < Q) {
+      ++issued;
+    }
+    pipe.pending[b] = 1;
+    if (++stage == ring) {
+      stage = 0;
+      fpar ^= 1u;
+    }
+    if (kin == 0 && cl > 0 && !fold(cl - 1)) {
+      ok = false;
+      ++q;
+      break;
+    }
+    if (last_in_chunk) {
+      kin = 0;
+      ++cl;
+    } else {
+      ++kin;
+    }
+  }
+  if (ok && Q > 0) ok = fold(cl - 1);
+  if (ok) {
+    tc_fence_after();
+    const int i = i0 + 32 * warp + (tid & 31);
+    double *dst = partial + ((long long)blockIdx.y * nx + i) * ny;
+#pragma unroll 1
+    for (int cb = 0; cb < BN / 32; ++cb) {
+      float sm[32], cp[32];
+      tmem_ld32(tmem + lane_off + 256 + 32 * cb, sm);
+      tmem_ld32(tmem + lane_off + 384 + 32 * cb, cp);
+      const int jb = j0 + 32 * cb;
+      if (i < nx) {
+#pragma unroll
+        for (int e = 0; e < 32; ++e)
+          if (jb + e < ny) dst[jb + e] = (double)sm[e] - (double)cp[e];
+      }
+    }
+  } else {
+    for (int r = q; r < issued; ++r) mbar_wait(smem_u32(&full[r % ring]), (uint32_t)((r / ring) & 1));
+    pipe.drain(mmad, 0);
+    pipe.drain(mmad, 1);
+    if (tid == 0) atomicExch(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// G = scale * sum over the splits of partial[s] (FP64, fixed order)
+__global__ void gram_splits_reduce_kernel(const double *__restrict__ partial, int splits, int ne, double scale,
+                                          double *__restrict__ G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  double s = 0.0;
+  for (int k = 0; k < splits; ++k) s += partial[(long long)k * ne + e];
+  G[e] = scale * s;
+}
+
 }  // namespace tc
 
 bool tc_shapes_ok(long long K) { return K % tc::BN == 0 && K % tc::BK == 0; }
@@ -691,35 +922,6 @@ static int tc_chunk() {
     return (x / tc::BK) * tc::BK;
   }();
   return c;
-}
-
-cudaError_t launch_tc_gram(const float *X, int nx, const float *Y, int ny, long long K, double scale, double *G,
-                           float *partial_ws, int *err, cudaStream_t st) {
-  const int tx = (nx + tc::BM - 1) / tc::BM, ty = (ny + tc::BN - 1) / tc::BN;
-  const int chunk = tc_chunk();
-  const long long chunks = (K + chunk - 1) / chunk;
-  if (K % tc::BK != 0 || chunks > 65535) return cudaErrorInvalidValue;
-  const int smem = (int)tc::SmemLayout::kBytes;
-  cudaError_t e = cudaFuncSetAttribute(tc::tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  tc::tc_gram_kernel<<<dim3(tx * ty, (unsigned)chunks), tc::NT, smem, st>>>(X, nx, Y, ny, K, chunk, tx, partial_ws,
-                                                                             err);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int n = nx * ny;
-  const size_t part2_off = ((sizeof(float) * (size_t)chunks * n + 255) / 256) * 256;  // aligned, after the partials
-  double *part2 = reinterpret_cast<double *>(reinterpret_cast<char *>(partial_ws) + part2_off);
-  tc::gram_reduce_kernel<<<dim3((n + 255) / 256, tc::kReduceGroups), 256, 0, st>>>(partial_ws, (int)chunks, n,
-                                                                                   part2);
-  tc::gram_reduce2_kernel<<<(n + 255) / 256, 256, 0, st>>>(part2, n, scale, G);
-  return cudaGetLastError();
-}
-
-size_t tc_gram_workspace_bytes(int nx, int ny, long long K) {
-  const long long chunks = (K + tc_chunk() - 1) / tc_chunk();
-  // FP32 chunk partials, then (256-byte aligned) the FP64 group sums of the reduction
-  const size_t part2_off = ((sizeof(float) * (size_t)chunks * nx * ny + 255) / 256) * 256;
-  return part2_off + sizeof(double) * tc::kReduceGroups * (size_t)nx * ny;
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda)
@@ -759,6 +961,88 @@ static bool use_tma() {
     return !(v && *v && *v != '0');
   }();
   return on;
+}
+
+// Chunk-partial Gram (each CTA one chunk, FP32 partials, two-level FP64 reduction): the path
+// for operands the TMA Gram cannot map.
+static cudaError_t launch_tc_gram_chunks(const float *X, int nx, const float *Y, int ny, long long K, double scale,
+                                        double *G, float *partial_ws, int *err, cudaStream_t st) {
+  const int tx = (nx + tc::BM - 1) / tc::BM, ty = (ny + tc::BN - 1) / tc::BN;
+  const int chunk = tc_chunk();
+  const long long chunks = (K + chunk - 1) / chunk;
+  if (K % tc::BK != 0 || chunks > 65535) return cudaErrorInvalidValue;
+  const int smem = (int)tc::SmemLayout::kBytes;
+  cudaError_t e = cudaFuncSetAttribute(tc::tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  tc::tc_gram_kernel<<<dim3(tx * ty, (unsigned)chunks), tc::NT, smem, st>>>(X, nx, Y, ny, K, chunk, tx, partial_ws,
+                                                                             err);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int n = nx * ny;
+  const size_t part2_off = ((sizeof(float) * (size_t)chunks * n + 255) / 256) * 256;  // aligned, after the partials
+  double *part2 = reinterpret_cast<double *>(reinterpret_cast<char *>(partial_ws) + part2_off);
+  tc::gram_reduce_kernel<<<dim3((n + 255) / 256, tc::kReduceGroups), 256, 0, st>>>(partial_ws, (int)chunks, n,
+                                                                                   part2);
+  tc::gram_reduce2_kernel<<<(n + 255) / 256, 256, 0, st>>>(part2, n, scale, G);
+  return cudaGetLastError();
+}
+
+static size_t gram_chunks_workspace_bytes(int nx, int ny, long long K) {
+  const long long chunks = (K + tc_chunk() - 1) / tc_chunk();
+  // FP32 chunk partials, then (256-byte aligned) the FP64 group sums of the reduction
+  const size_t part2_off = ((sizeof(float) * (size_t)chunks * nx * ny + 255) / 256) * 256;
+  return part2_off + sizeof(double) * tc::kReduceGroups * (size_t)nx * ny;
+}
+
+// TMA Gram plan: splits of the K range (whole chunks) and ring depth; false when TMA cannot be
+// used for these operands (disabled, encoder missing, misaligned base, K not a multiple of 32).
+struct GramPlan {
+  int splits, ring, tiles_x, tiles;
+};
+static bool gram_tma_plan(const float *X, int nx, const float *Y, int ny, long long K, GramPlan *p) {
+  if (!use_tma() || !tensor_map_encoder() || (reinterpret_cast<uintptr_t>(X) & 15) ||
+      (reinterpret_cast<uintptr_t>(Y) & 15) || K % tc::BK != 0 || K / tc::BK > (1LL << 30))
+    return false;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  p->tiles_x = (nx + tc::BM - 1) / tc::BM;
+  p->tiles = p->tiles_x * ((ny + tc::BN - 1) / tc::BN);
+  const int cs = tc_chunk() / tc::BK;
+  const long long chunks = (K / tc::BK + cs - 1) / cs;
+  p->splits = (int)std::max(1LL, std::min(chunks, (long long)std::max(1, sms / p->tiles)));
+  const size_t fixed = 8 * (size_t)tc::TILE_BYTES + 1024 + 256;
+  p->ring = (int)std::min<size_t>(6, (227 * 1024 - fixed) / (2 * tc::kGBox));
+  return p->ring >= 2;
+}
+
+size_t tc_gram_workspace_bytes(const float *X, int nx, const float *Y, int ny, long long K) {
+  GramPlan p;
+  if (gram_tma_plan(X, nx, Y, ny, K, &p)) return sizeof(double) * (size_t)p.splits * nx * ny;
+  return gram_chunks_workspace_bytes(nx, ny, K);
+}
+
+cudaError_t launch_tc_gram(const float *X, int nx, const float *Y, int ny, long long K, double scale, double *G,
+                           void *ws, int *err, cudaStream_t st, long *launches) {
+  GramPlan p;
+  CUtensorMap mx, my;
+  if (gram_tma_plan(X, nx, Y, ny, K, &p) && make_map_f32(&mx, X, nx, K, tc::BM, tc::BK, true) &&
+      make_map_f32(&my, Y, ny, K, tc::BN, tc::BK, true)) {
+    const int smem = (int)(8 * (size_t)tc::TILE_BYTES + (size_t)p.ring * 2 * tc::kGBox + 1024 + 256);
+    cudaError_t e = cudaFuncSetAttribute(tc::tc_gram_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    double *partial = static_cast<double *>(ws);
+    tc::tc_gram_tma_kernel<<<dim3(p.tiles, p.splits), tc::NT, smem, st>>>(mx, my, nx, ny, K, tc_chunk() / tc::BK,
+                                                                          p.tiles_x, p.ring, partial, err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int n = nx * ny;
+    tc::gram_splits_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(partial, p.splits, n, scale, G);
+    *launches += 2;
+    return cudaGetLastError();
+  }
+  *launches += 3;
+  return launch_tc_gram_chunks(X, nx, Y, ny, K, scale, G, static_cast<float *>(ws), err, st);
 }
 
 cudaError_t launch_tc_left_mul(const float *A, int m, int n, const float *Y, long long K, float *Z, int *err,
