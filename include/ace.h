@@ -28,7 +28,9 @@
  *     interaction exactly.
  *   - pointers named *_dev are CUDA device pointers; pointers that the comments say "host or
  *     device" may be either (host memory, pageable or pinned, is copied inside the call on the
- *     given stream).  `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+ *     given stream; device memory that does not start on a 16-byte boundary is likewise read
+ *     through, or written through, an aligned copy).  `cuda_stream` is a cudaStream_t (NULL =
+ *     legacy default stream).
  *   - every entry point returns an ace_status and never throws; on failure the message is
  *     available from ace_last_error() on the calling thread.
  *   - ownership: the caller owns every buffer it passes and must keep it valid and unchanged
@@ -169,7 +171,8 @@ void ace_destroy(ace_op *op);
  *   W_i = sum_{j : (i,j) or (j,i) listed} v_ij phi_j,  v_ij by FFT with the kernel desc->coulomb selects,
  * the same arithmetic as the W step of ace_build (desc->rho_cut and desc->spin_factor are ignored).
  *   phi_dev:    device orbitals [norb][N1][N2][N3]; W_dev: device output of the same shape (zeroed
- *               by the call).  dtype must be the working type of desc->prec (ACE_F32 for ACE_MIXED,
+ *               by the call); both 16-byte aligned (else ACE_ERR_ARG: this entry point makes no
+ *               copies).  dtype must be the working type of desc->prec (ACE_F32 for ACE_MIXED,
  *               ACE_F64 for ACE_FP64).
  *   pairs_host: host int32 [npairs][2] with 0 <= i <= j < norb (checked before any work is queued).
  * All workspace (FFT scratch, pack list, kernel table, twiddles) lives in one array of

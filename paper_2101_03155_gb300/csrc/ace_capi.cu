@@ -322,11 +322,15 @@ ace_status stage_input(ace_op *op, const void *src, ace_dtype dt, long long coun
   const bool same = (dt == ACE_F64) == (sizeof(T) == 8);
   const size_t in_bytes = (size_t)count * (dt == ACE_F64 ? 8 : 4);
   const void *d_in = src;
-  if (!dev) {
+  // host memory, and device memory off a 16-byte boundary when no conversion follows (the
+  // kernels read operands in 16-byte vectors and by TMA), go through an aligned device copy
+  const bool misaligned = (reinterpret_cast<uintptr_t>(src) & 15) != 0;
+  if (!dev || (same && misaligned)) {
     void *tmp = nullptr;
     ACE_CUDA(cudaMallocAsync(&tmp, in_bytes, op->stream), "staging allocation");
     temps->push_back(tmp);
-    ACE_CUDA(cudaMemcpyAsync(tmp, src, in_bytes, cudaMemcpyHostToDevice, op->stream), "host-to-device copy");
+    ACE_CUDA(cudaMemcpyAsync(tmp, src, in_bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, op->stream),
+             "staging copy");
     d_in = tmp;
   }
   if (same) {
@@ -911,7 +915,8 @@ ace_status apply_impl(const ace_op *op, const void *psi_in, ace_dtype dtype, int
   // out = -C^T xi  (m x N)
   const bool same = (dtype == ACE_F64) == (sizeof(T) == 8);
   T *res = nullptr;
-  if (same && !host_out) {
+  const bool out_aligned = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+  if (same && !host_out && out_aligned) {
     res = static_cast<T *>(out);
   } else {
     ACE_CUDA(cudaMallocAsync(&tmp, sizeof(T) * (size_t)m * N, st), "alloc out");
@@ -935,7 +940,10 @@ ace_status apply_impl(const ace_op *op, const void *psi_in, ace_dtype dtype, int
       ACE_CUDA((ace::launch_convert<T, float>(res, static_cast<float *>(conv), (long long)m * N, 1.0, st)), "conv");
     final_dev = conv;
   }
-  if (host_out) ACE_CUDA(cudaMemcpyAsync(out, final_dev, out_bytes, cudaMemcpyDeviceToHost, st), "device-to-host copy");
+  if (host_out)
+    ACE_CUDA(cudaMemcpyAsync(out, final_dev, out_bytes, cudaMemcpyDeviceToHost, st), "device-to-host copy");
+  else if (final_dev != out)
+    ACE_CUDA(cudaMemcpyAsync(out, final_dev, out_bytes, cudaMemcpyDeviceToDevice, st), "unaligned output copy");
   int err_h = 0;
   ACE_CUDA(cudaMemcpyAsync(&err_h, err_d, sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
   ACE_CUDA(cudaStreamSynchronize(st), "apply");

@@ -30,6 +30,7 @@ namespace ace {
 namespace tc {
 
 constexpr int NT = 128;        // four warps: warp w reads TMEM lanes 32w .. 32w + 31
+constexpr int NT2 = 256;       // TMA kernels: warps w and w + 4 share TMEM lanes 32w .. 32w + 31
 constexpr int BM = 128;        // UMMA M
 constexpr int BN = 128;        // UMMA N
 constexpr int BK = 32;         // K per pipeline stage (two K = 16 MMAs)
@@ -195,23 +196,19 @@ __device__ __forceinline__ void bulk_wait_read() {
 // wait until every committed bulk group has completed its writes
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
-__device__ __forceinline__ void split1(float x, uint16_t &hi, uint16_t &lo) {
-  const __nv_bfloat16 bh = __float2bfloat16_rn(x);
-  hi = __bfloat16_as_ushort(bh);
-  lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(bh)));
+// bf16 hi/lo of two values at once: hi = bf16_rn(x) for the pair (one packed conversion), the
+// residuals x - hi in FP32 (exact: hi carries the top bits of x), lo = bf16_rn(residual)
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x1), "f"(x0));  // x0 in the low half
+  const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xFFFF0000u);
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(x1 - h1), "f"(x0 - h0));
 }
 
 // 16-byte core-matrix row: 8 bf16 (hi) and 8 bf16 (lo) of 8 consecutive K-values of one row
 __device__ __forceinline__ void split8(const float (&x)[8], uint4 &hi, uint4 &lo) {
   uint32_t h[4], l[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    uint16_t h0, l0, h1, l1;
-    split1(x[2 * i], h0, l0);
-    split1(x[2 * i + 1], h1, l1);
-    h[i] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-    l[i] = (uint32_t)l0 | ((uint32_t)l1 << 16);
-  }
+  for (int i = 0; i < 4; ++i) split2(x[2 * i], x[2 * i + 1], h[i], l[i]);
   hi = make_uint4(h[0], h[1], h[2], h[3]);
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
@@ -253,6 +250,23 @@ __device__ __forceinline__ void store_row(const Row32 &r, int row, unsigned char
     const uint32_t off = tile_off(row, 8 * q);
     *reinterpret_cast<uint4 *>(hi + off) = h;
     *reinterpret_cast<uint4 *>(lo + off) = l;
+  }
+}
+
+// K-values [16 h, 16 h + 16) of the thread's row of a 128 x 32 tile (two 16-byte stores into each
+// of the hi and lo tiles)
+__device__ __forceinline__ void store_half_row(const float (&v)[16], int row, int h, unsigned char *hi,
+                                               unsigned char *lo) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    float x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = v[8 * q + i];
+    uint4 hv, lv;
+    split8(x, hv, lv);
+    const uint32_t off = tile_off(row, 16 * h + 8 * q);
+    *reinterpret_cast<uint4 *>(hi + off) = hv;
+    *reinterpret_cast<uint4 *>(lo + off) = lv;
   }
 }
 
@@ -525,7 +539,7 @@ __global__ void __launch_bounds__(NT) tc_left_mul_kernel(const float *__restrict
 constexpr uint32_t kLmBox = BK * BN * 4;   // one Y box: 32 rows x 128 FP32 columns
 constexpr uint32_t kEpiBox = BM * 32 * 4;  // one Z box: 128 rows x 32 FP32 columns
 
-__global__ void __launch_bounds__(NT, 1) tc_left_mul_tma_kernel(const float *__restrict__ A, int m, int n,
+__global__ void __launch_bounds__(NT2, 1) tc_left_mul_tma_kernel(const float *__restrict__ A, int m, int n,
                                                                 const __grid_constant__ CUtensorMap tmY,
                                                                 const __grid_constant__ CUtensorMap tmZ, long long K,
                                                                 int ring, int *__restrict__ err) {
@@ -541,6 +555,8 @@ __global__ void __launch_bounds__(NT, 1) tc_left_mul_tma_kernel(const float *__r
   uint64_t *accf = mmad + 2;     // every MMA of the tile in accumulator a
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accf + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int quarter = warp & 3, half = warp >> 2;  // TMEM lane quarter; K-half / column half
+  const int col = tid & 127;                       // row of the A tile / column of the Y box
   const int i0 = blockIdx.y * BM;
   const long long ntiles = K / BN;
   const long long mytiles = ntiles > (long long)blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
@@ -573,18 +589,16 @@ __global__ void __launch_bounds__(NT, 1) tc_left_mul_tma_kernel(const float *__r
   int issued = Qi < ring ? Qi : ring;
   if (tid == 0)
     for (int k = 0; k < issued; ++k) issue_next();
-  // resident A: row i0 + tid, all K-steps (overlaps the first copies)
+  // resident A: row i0 + col, K-values [16 half, 16 half + 16) of every K-step (overlaps the first copies)
   for (int it = 0; it < nsteps; ++it) {
-    Row32 r;
-    if (i0 + tid < m) {
+    float v[16];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) r.v[j] = (it * BK + j < n) ? __ldg(A + (long long)(i0 + tid) * n + it * BK + j) : 0.f;
-    } else {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) r.v[j] = 0.f;
+    for (int j = 0; j < 16; ++j) {
+      const int k = it * BK + 16 * half + j;
+      v[j] = (i0 + col < m && k < n) ? __ldg(A + (long long)(i0 + col) * n + k) : 0.f;
     }
     unsigned char *t = a_tiles + (size_t)it * 2 * TILE_BYTES;
-    store_row(r, tid, t, t + TILE_BYTES);
+    store_half_row(v, col, half, t, t + TILE_BYTES);
   }
   fence_async_smem();
   tc_fence_before();
@@ -601,14 +615,15 @@ __global__ void __launch_bounds__(NT, 1) tc_left_mul_tma_kernel(const float *__r
     if (__syncthreads_or(!w)) return false;
     tc_fence_after();
     const long long c0 = (blockIdx.x + (long long)j * gridDim.x) * BN;
-    const int row = 32 * warp + (tid & 31);  // TMEM lane = row of the tile
+    const int row = 32 * quarter + (tid & 31);  // TMEM lane = row of the tile
+    // two rounds: warps 0-3 stage column block r in buffer 0, warps 4-7 block r + 2 in buffer 1
 #pragma unroll 1
-    for (int cb = 0; cb < BN / 32; ++cb) {
+    for (int r = 0; r < 2; ++r) {
+      const int cb = r + 2 * half;
       float v[32];
-      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)a * BN + 32 * cb, v);
-      // staging buffer e is free once the store that last read it has read it
-      unsigned char *eb = epi + (size_t)(cb & 1) * kEpiBox;
-      if (tid == 0) bulk_wait_read<1>();
+      tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)a * BN + 32 * cb, v);
+      unsigned char *eb = epi + (size_t)half * kEpiBox;
+      if (tid == 0) bulk_wait_read<0>();  // both buffers have been read by the previous stores
       __syncthreads();
       // row `row`: 128 bytes, 16-byte chunk q at position q ^ (row & 7) (the map's 128-byte swizzle)
 #pragma unroll
@@ -618,7 +633,8 @@ __global__ void __launch_bounds__(NT, 1) tc_left_mul_tma_kernel(const float *__r
       fence_async_smem();
       __syncthreads();
       if (tid == 0) {
-        tma_store_2d(&tmZ, (int)(c0 + 32 * cb), i0, smem_u32(eb));
+        tma_store_2d(&tmZ, (int)(c0 + 32 * r), i0, smem_u32(epi));
+        tma_store_2d(&tmZ, (int)(c0 + 32 * (r + 2)), i0, smem_u32(epi + kEpiBox));
         bulk_commit();
       }
     }
@@ -637,12 +653,13 @@ __global__ void __launch_bounds__(NT, 1) tc_left_mul_tma_kernel(const float *__r
       break;
     }
     {
-      Row32 r;
+      // column `col` of the box, rows [16 half, 16 half + 16)
+      float v[16];
       const float *box = reinterpret_cast<const float *>(boxes + (size_t)stage * kLmBox);
 #pragma unroll
-      for (int k = 0; k < BK; ++k) r.v[k] = box[k * BN + tid];
+      for (int k = 0; k < 16; ++k) v[k] = box[(16 * half + k) * BN + col];
       unsigned char *bt = b_ops + (size_t)b * 2 * TILE_BYTES;
-      store_row(r, tid, bt, bt + TILE_BYTES);
+      store_half_row(v, col, half, bt, bt + TILE_BYTES);
     }
     fence_async_smem();
     __syncthreads();  // the box is consumed and the B tile written
@@ -713,7 +730,7 @@ __global__ void __launch_bounds__(NT, 1) tc_left_mul_tma_kernel(const float *__r
 // ----------------------------------------------------------------------------------------
 constexpr uint32_t kGBox = BM * BK * 4;  // 128 rows x 32 FP32
 
-__global__ void __launch_bounds__(NT, 1) tc_gram_tma_kernel(const __grid_constant__ CUtensorMap tmX,
+__global__ void __launch_bounds__(NT2, 1) tc_gram_tma_kernel(const __grid_constant__ CUtensorMap tmX,
                                                             const __grid_constant__ CUtensorMap tmY, int nx, int ny,
                                                             long long K, int cs, int tiles_x, int ring,
                                                             double *__restrict__ partial, int *__restrict__ err) {
@@ -726,6 +743,7 @@ __global__ void __launch_bounds__(NT, 1) tc_gram_tma_kernel(const __grid_constan
   uint64_t *accf = mmad + 2;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accf + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int quarter = warp & 3, half = warp >> 2;  // TMEM lane quarter; operand / column half
   const int ti = blockIdx.x % tiles_x, tj = blockIdx.x / tiles_x;
   const int i0 = ti * BM, j0 = tj * BN;
   // this split's K-steps: whole chunks [c_lo, c_hi) of cs steps (the last chunk may be short)
@@ -762,13 +780,16 @@ __global__ void __launch_bounds__(NT, 1) tc_gram_tma_kernel(const __grid_constan
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
-  {  // running sum and compensation start at zero
+  const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
+  {  // running sum and compensation start at zero (each warp group its column half)
     float z[32];
 #pragma unroll
     for (int c = 0; c < 32; ++c) z[c] = 0.f;
 #pragma unroll 1
-    for (int cb = 0; cb < 8; ++cb) tmem_st32(tmem + lane_off + 256 + 32 * cb, z);
+    for (int cb = 2 * half; cb < 2 * half + 2; ++cb) {
+      tmem_st32(tmem + lane_off + 256 + 32 * cb, z);
+      tmem_st32(tmem + lane_off + 384 + 32 * cb, z);
+    }
     tmem_st_wait();
   }
   Pipe pipe;
@@ -781,7 +802,7 @@ __global__ void __launch_bounds__(NT, 1) tc_gram_tma_kernel(const __grid_constan
     if (__syncthreads_or(!w)) return false;
     tc_fence_after();
 #pragma unroll 1
-    for (int cb = 0; cb < BN / 32; ++cb) {
+    for (int cb = 2 * half; cb < 2 * half + 2; ++cb) {
       float x[32], sm[32], cp[32];
       tmem_ld32(tmem + lane_off + (uint32_t)a * BN + 32 * cb, x);
       tmem_ld32(tmem + lane_off + 256 + 32 * cb, sm);
@@ -812,23 +833,21 @@ __global__ void __launch_bounds__(NT, 1) tc_gram_tma_kernel(const __grid_constan
       break;
     }
     {
-      const unsigned char *bx = boxes + (size_t)stage * 2 * kGBox;
-      unsigned char *ob = ops + (size_t)b * 4 * TILE_BYTES;
+      // warps 0-3 split X, warps 4-7 split Y: row `row` of the box, whose 16-byte chunk k4 sits
+      // at position k4 ^ (row & 7) (128-byte swizzle)
+      const int row = tid & 127;
+      const unsigned char *rowp = boxes + (size_t)stage * 2 * kGBox + (size_t)half * kGBox + row * 128;
+      unsigned char *ob = ops + (size_t)b * 4 * TILE_BYTES + (size_t)half * 2 * TILE_BYTES;
+      Row32 r;
 #pragma unroll
-      for (int op = 0; op < 2; ++op) {
-        // row tid of the box: 16-byte chunk k4 sits at position k4 ^ (tid & 7) (128-byte swizzle)
-        const unsigned char *rowp = bx + (size_t)op * kGBox + tid * 128;
-        Row32 r;
-#pragma unroll
-        for (int k4 = 0; k4 < 8; ++k4) {
-          const float4 t = *reinterpret_cast<const float4 *>(rowp + ((k4 ^ (tid & 7)) << 4));
-          r.v[4 * k4] = t.x;
-          r.v[4 * k4 + 1] = t.y;
-          r.v[4 * k4 + 2] = t.z;
-          r.v[4 * k4 + 3] = t.w;
-        }
-        store_row(r, tid, ob + (size_t)op * 2 * TILE_BYTES, ob + (size_t)op * 2 * TILE_BYTES + TILE_BYTES);
+      for (int k4 = 0; k4 < 8; ++k4) {
+        const float4 t = *reinterpret_cast<const float4 *>(rowp + ((k4 ^ (row & 7)) << 4));
+        r.v[4 * k4] = t.x;
+        r.v[4 * k4 + 1] = t.y;
+        r.v[4 * k4 + 2] = t.z;
+        r.v[4 * k4 + 3] = t.w;
       }
+      store_row(r, row, ob, ob + TILE_BYTES);
     }
     fence_async_smem();
     __syncthreads();
@@ -874,10 +893,10 @@ __global__ void __launch_bounds__(NT, 1) tc_gram_tma_kernel(const __grid_constan
   if (ok && Q > 0) ok = fold(cl - 1);
   if (ok) {
     tc_fence_after();
-    const int i = i0 + 32 * warp + (tid & 31);
+    const int i = i0 + 32 * quarter + (tid & 31);
     double *dst = partial + ((long long)blockIdx.y * nx + i) * ny;
 #pragma unroll 1
-    for (int cb = 0; cb < BN / 32; ++cb) {
+    for (int cb = 2 * half; cb < 2 * half + 2; ++cb) {
       float sm[32], cp[32];
       tmem_ld32(tmem + lane_off + 256 + 32 * cb, sm);
       tmem_ld32(tmem + lane_off + 384 + 32 * cb, cp);
@@ -1032,7 +1051,7 @@ cudaError_t launch_tc_gram(const float *X, int nx, const float *Y, int ny, long 
     cudaError_t e = cudaFuncSetAttribute(tc::tc_gram_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     double *partial = static_cast<double *>(ws);
-    tc::tc_gram_tma_kernel<<<dim3(p.tiles, p.splits), tc::NT, smem, st>>>(mx, my, nx, ny, K, tc_chunk() / tc::BK,
+    tc::tc_gram_tma_kernel<<<dim3(p.tiles, p.splits), tc::NT2, smem, st>>>(mx, my, nx, ny, K, tc_chunk() / tc::BK,
                                                                           p.tiles_x, p.ring, partial, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1066,7 +1085,7 @@ cudaError_t launch_tc_left_mul(const float *A, int m, int n, const float *Y, lon
       const long long tiles = K / tc::BN;
       const int rows = (m + tc::BM - 1) / tc::BM;
       const unsigned gx = (unsigned)std::max(1LL, std::min(tiles, (long long)std::max(1, sms / rows)));
-      tc::tc_left_mul_tma_kernel<<<dim3(gx, rows), tc::NT, smem, st>>>(A, m, n, map, zmap, K, ring, err);
+      tc::tc_left_mul_tma_kernel<<<dim3(gx, rows), tc::NT2, smem, st>>>(A, m, n, map, zmap, K, ring, err);
       return cudaGetLastError();
     }
   }

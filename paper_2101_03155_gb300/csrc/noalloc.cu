@@ -242,6 +242,8 @@ ace_status ace_exchange_w_noalloc(const ace_desc *desc, const void *phi_dev, ace
   if (!desc || !phi_dev || !W_dev || (npairs > 0 && !pairs_host) || npairs < 0)
     return nf_fail(ACE_ERR_ARG, "NULL argument or negative pair count");
   if (desc->norb < 1) return nf_fail(ACE_ERR_ARG, "norb = %d < 1", desc->norb);
+  if ((reinterpret_cast<uintptr_t>(phi_dev) | reinterpret_cast<uintptr_t>(W_dev)) & 15)
+    return nf_fail(ACE_ERR_ARG, "phi_dev and W_dev must be 16-byte aligned");
   for (int k = 0; k < 3; ++k)
     if (!ace::pass_length_supported(desc->n[k]))
       return nf_fail(ACE_ERR_UNSUPPORTED_GRID, "grid axis %d length %d has no compiled FFT plan", k, desc->n[k]);

@@ -1,0 +1,52 @@
+"""The register-staged tensor-core kernels (used when TMA cannot map an operand, or with
+ACE_NO_TMA=1) give the same mixed build and application as the TMA kernels, against the oracle.
+The switch is read once per process, so the fallback runs in a child process."""
+
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import MIXED_EX_TOL_PER_ORB, MIXED_KPHI_RTOL
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CHILD = r"""
+import json, sys
+import numpy as np, torch
+sys.path.insert(0, {root!r})
+import paper_2101_03155_gb300 as ace
+from workloads.generators import config1
+w = config1()
+d = ace.make_desc(w.grid, w.lattice, w.norb, prec=ace.ACE_MIXED)
+op = ace.ace_build(d, torch.from_numpy(w.phi.astype(np.float32)).cuda())
+psi = np.random.default_rng(21).standard_normal((3,) + w.grid).astype(np.float32)
+out = torch.empty((3,) + w.grid, dtype=torch.float32, device="cuda")
+ace.ace_apply(op, torch.from_numpy(psi).cuda(), out)
+np.save(sys.argv[1], out.cpu().numpy())
+print(json.dumps({{"E_x": ace.exchange_energy(op)}}))
+"""
+
+
+def test_fallback_kernels_match_oracle(tmp_path):
+    from workloads.generators import config1
+
+    w = config1()
+    ref = oracle.ace_build(w.phi, w.lattice, 0.0, w.spin_factor)
+    out_file = tmp_path / "kphi.npy"
+    env = dict(os.environ, ACE_NO_TMA="1")
+    r = subprocess.run([sys.executable, "-c", CHILD.format(root=ROOT), str(out_file)], env=env, capture_output=True,
+                       text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    assert abs(res["E_x"] - ref["E_x"]) <= MIXED_EX_TOL_PER_ORB * w.norb
+    psi = np.random.default_rng(21).standard_normal((3,) + w.grid).astype(np.float32)
+    kref = oracle.ace_apply(ref["xi"], psi.astype(np.float64), w.dV)
+    got = np.load(out_file)
+    assert np.linalg.norm(got - kref) <= MIXED_KPHI_RTOL * np.linalg.norm(kref)

@@ -236,6 +236,26 @@ def test_mixed_apply_few_vectors(cfg1):
     assert np.linalg.norm(out.cpu().numpy() - kref) <= MIXED_KPHI_RTOL * np.linalg.norm(kref)
 
 
+def test_mixed_apply_unaligned_buffers(cfg1):
+    """psi and out views 4 bytes past a 16-byte boundary are read and written through aligned
+    copies (the kernels load 16-byte vectors and TMA boxes); the result is unchanged."""
+    import torch
+
+    w, ref = cfg1
+    g = gpu_build(w.phi, w.lattice, ace.ACE_MIXED)
+    N = int(np.prod(w.grid))
+    psi = np.random.default_rng(13).standard_normal((5,) + w.grid)
+    big_in = torch.empty(5 * N + 1, dtype=torch.float32, device="cuda")
+    big_out = torch.empty(5 * N + 1, dtype=torch.float32, device="cuda")
+    psi_v, out_v = big_in[1:], big_out[1:]
+    assert psi_v.data_ptr() % 16 == 4 and out_v.data_ptr() % 16 == 4
+    psi_v.copy_(torch.from_numpy(psi.astype(np.float32).reshape(-1)).cuda())
+    ace.ace_apply(g["op"], psi_v, out_v)
+    kref = oracle.ace_apply(ref["xi"], psi, w.dV)
+    got = out_v.cpu().numpy().reshape(kref.shape)
+    assert np.linalg.norm(got - kref) <= MIXED_KPHI_RTOL * np.linalg.norm(kref)
+
+
 def test_mixed_dense_steps_beyond_one_tile():
     """160 orbitals (two 128-row tiles): M, L and xi of the mixed build against FP64 contractions
     of the build's own W (the pair chain is covered by the other tests)."""

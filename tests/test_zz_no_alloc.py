@@ -92,3 +92,16 @@ def test_noalloc_truncated_kernel(prec):
         torch.cuda.synchronize()
         assert rel_max(W.cpu().numpy(), g["W"].reshape(w.phi.shape)) <= tol
         g["op"].close()
+
+
+def test_noalloc_refuses_unaligned_buffers():
+    import torch
+
+    lat = np.eye(3) * 8.0
+    desc = ace.make_desc((16, 16, 16), lat, 1, prec=ace.ACE_MIXED)
+    big = torch.zeros(2 * 4096 + 1, dtype=torch.float32, device="cuda")
+    phi, W = big[1:4097], big[4097:]  # 4 bytes past a 16-byte boundary: refused before any access
+    with pytest.raises(ace.AceError) as e:
+        ace.ace.ace_exchange_w_noalloc(desc, phi, np.array([[0, 0]], np.int32), W)
+    assert e.value.status == ace.ace.ACE_ERR_ARG
+    assert "aligned" in str(e.value)
