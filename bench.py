@@ -440,6 +440,13 @@ def run_ours(args):
                      "frac": achieved / peaks.get("hbm_gbs"), "traffic": CHAIN_DRAM_BYTES_PER_BUILD,
                      "peak_kind": peak_kind,
                      "algorithmic_bytes": f"24 B x N x npairs = {alg_bytes:.4g} B per build"},
+        # the dense contractions on the tensor cores are HBM-bound as well (intensity n/4 flop/B):
+        # M reads Phi and W, xi reads W and writes xi (FP32, n x N each)
+        "dense_roofline": {
+            k: {"bound": "hbm", "achieved": 2 * 4 * n * N / (stage_mean[k] * 1e-3) / 1e9, "peak": peaks.get("hbm_gbs"),
+                "unit": "GB/s", "frac": 2 * 4 * n * N / (stage_mean[k] * 1e-3) / 1e9 / peaks.get("hbm_gbs"),
+                "algorithmic_bytes": f"2 x 4 B x n x N = {2 * 4 * n * N:.4g} B"}
+            for k in ("M", "xi")},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n * N, "d2h_bytes_per_step": 16,
                 "steps": e2e_steps},
         "gpu_launches": rec["launches"],
