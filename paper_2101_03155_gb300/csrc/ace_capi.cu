@@ -383,10 +383,11 @@ void pinned_put(void *p, size_t bytes) {
 std::mutex g_side_mu;
 constexpr int kLanes = 4;           // concurrent builds of one batched call
 constexpr int kSide = 8;            // pair-chain side streams per lane
-cudaStream_t g_side[64][(kSide + 1) * kLanes] = {};  // per lane: kSide chain side streams; then the lane streams
+// per lane: kSide chain side streams; then the lane streams; then one input-copy stream per lane
+cudaStream_t g_side[64][(kSide + 2) * kLanes] = {};
 
 cudaError_t get_side_stream(int dev, int k, cudaStream_t *out) {
-  if (dev < 0 || dev >= 64 || k < 0 || k >= (kSide + 1) * kLanes) return cudaErrorInvalidValue;
+  if (dev < 0 || dev >= 64 || k < 0 || k >= (kSide + 2) * kLanes) return cudaErrorInvalidValue;
   std::lock_guard<std::mutex> lk(g_side_mu);
   if (!g_side[dev][k]) {
     cudaError_t e = cudaStreamCreateWithFlags(&g_side[dev][k], cudaStreamNonBlocking);
@@ -740,9 +741,21 @@ ace_status build_begin(ace_op *op, const void *phi_in, ace_dtype dtype) {
   cudaStream_t st = op->stream;
   for (int i = 0; i < 6; ++i) ACE_CUDA(cudaEventCreate(&op->ev[i]), "event create");
   ACE_CUDA(cudaEventRecord(op->ev[0], st), "event record");
+  // FP32 host input of a screened build: copied in column chunks on a copy stream while the
+  // screen adds each chunk's contribution on the build stream (the transfer hides the screen)
+  const bool same = (dtype == ACE_F64) == (sizeof(T) == 8);
+  const bool pipelined = sizeof(T) == 4 && same && d.rho_cut > 0.0 && N % 4 == 0 && !is_device_pointer(phi_in) &&
+                         env_int("ACE_PIPELINED_INPUT", 1) != 0;
   const T *phi = nullptr;
-  ace_status s = stage_input<T>(op, phi_in, dtype, (long long)n * N, &phi, &op->temps);
-  if (s != ACE_OK) return s;
+  if (pipelined) {
+    void *tmp = nullptr;
+    ACE_CUDA(cudaMallocAsync(&tmp, sizeof(T) * (size_t)n * N, st), "staging allocation");
+    op->temps.push_back(tmp);
+    phi = static_cast<const T *>(tmp);
+  } else {
+    ace_status s = stage_input<T>(op, phi_in, dtype, (long long)n * N, &phi, &op->temps);
+    if (s != ACE_OK) return s;
+  }
   op->phi_work = phi;
   cudaError_t e = get_tables<T>(op->dev, d, st, &op->tab);
   if (e != cudaSuccess) return cuda_fail(e, "kernel and twiddle tables");
@@ -758,7 +771,30 @@ ace_status build_begin(ace_op *op, const void *phi_in, ace_dtype dtype) {
   op->tc_err = op->status_d + 1;
   ACE_CUDA(cudaMemsetAsync(op->status_d, 0, sizeof(int) * 4, st), "zero status");
   ACE_CUDA(op_alloc(op, &op->energy_d, sizeof(double) * 2), "alloc energy");
-  if (d.rho_cut > 0.0) {
+  if (pipelined) {
+    ACE_CUDA(cudaMemsetAsync(op->O, 0, sizeof(double) * n * n, st), "zero O");
+    cudaStream_t cs;
+    ACE_CUDA(get_side_stream(op->dev, (kSide + 1) * kLanes + op->lane, &cs), "copy stream");
+    cudaEvent_t ev;
+    ACE_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+    ACE_CUDA(cudaEventRecord(ev, st), "event");  // the staging buffer is allocated on st
+    ACE_CUDA(cudaStreamWaitEvent(cs, ev, 0), "wait");
+    cudaEventDestroy(ev);
+    const long long w = ((N + 7) / 8 + 2047) / 2048 * 2048;  // about 8 chunks, 2048-point aligned
+    for (long long c0 = 0; c0 < N; c0 += w) {
+      const long long wc = std::min(w, N - c0);
+      ACE_CUDA(cudaMemcpy2DAsync(const_cast<T *>(phi) + c0, sizeof(T) * N, static_cast<const T *>(phi_in) + c0,
+                                 sizeof(T) * N, sizeof(T) * wc, n, cudaMemcpyHostToDevice, cs),
+               "host-to-device copy");
+      ACE_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+      ACE_CUDA(cudaEventRecord(ev, cs), "event");
+      ACE_CUDA(cudaStreamWaitEvent(st, ev, 0), "wait");
+      cudaEventDestroy(ev);
+      ACE_CUDA(ace::launch_screen_cols(reinterpret_cast<const float *>(phi) + c0, n, N, wc, op->dV, op->O, st),
+               "screen");
+      ++op->launches;
+    }
+  } else if (d.rho_cut > 0.0) {
     ACE_CUDA(ace::launch_gram<T>(phi, n, phi, n, N, op->dV, true, true, op->O, st), "screen");
     ++op->launches;
   } else {

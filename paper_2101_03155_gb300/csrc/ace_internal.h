@@ -96,6 +96,9 @@ cudaError_t launch_transpose_scale(const double *C, int n, int m, double scale, 
 // Tensor-core (tcgen05) BF16x3 contractions for FP32 operands.  *err is set to 1 when a bounded
 // wait inside the kernel gave up.  K must be a multiple of 128 (tc_shapes_ok).
 bool tc_shapes_ok(long long K);
+// Screen contribution of columns [0, K) of X (row stride ld): G += scale |X||X|^T, upper triangle.
+cudaError_t launch_screen_cols(const float *X, int n, long long ld, long long K, double scale, double *G,
+                               cudaStream_t st);
 // workspace of launch_tc_gram for these operands (the path it takes depends on them)
 size_t tc_gram_workspace_bytes(const float *X, int nx, const float *Y, int ny, long long K);
 cudaError_t launch_tc_gram(const float *X, int nx, const float *Y, int ny, long long K, double scale, double *G,

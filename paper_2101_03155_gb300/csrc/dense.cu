@@ -10,6 +10,8 @@
 //   compact:   pair list of the screen (i <= j, sorted) and packs of two pairs.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "ace_internal.h"
 #include "fft.cuh"
 
@@ -252,8 +254,9 @@ __device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsign
 }
 
 template <bool ABS>
-__global__ void __launch_bounds__(GS_NT, ACE_GS_MINB) gram_sym_f32_kernel(const float *__restrict__ X, int n, long long K,
-                                                             double scale, double *__restrict__ G) {
+__global__ void __launch_bounds__(GS_NT, ACE_GS_MINB) gram_sym_f32_kernel(const float *__restrict__ X, int n, long long ld,
+                                                                        long long K, double scale,
+                                                                        double *__restrict__ G) {
   // (a, a) pairs of the row block and plain values of the column block, double-buffered
   __shared__ __align__(16) float2 xs[2][GS_BK][GS_B + 2];
   __shared__ __align__(16) float ys[2][GS_BK][GS_B + 4];
@@ -287,8 +290,8 @@ __global__ void __launch_bounds__(GS_NT, ACE_GS_MINB) gram_sym_f32_kernel(const 
     vx = make_float4(0.f, 0.f, 0.f, 0.f);
     vy = vx;
     if (tt < ntiles && k0 < ke) {
-      if (i0 + lrow < n) vx = __ldg(reinterpret_cast<const float4 *>(X + (long long)(i0 + lrow) * K + k0));
-      if (j0 + lrow < n) vy = __ldg(reinterpret_cast<const float4 *>(X + (long long)(j0 + lrow) * K + k0));
+      if (i0 + lrow < n) vx = __ldg(reinterpret_cast<const float4 *>(X + (long long)(i0 + lrow) * ld + k0));
+      if (j0 + lrow < n) vy = __ldg(reinterpret_cast<const float4 *>(X + (long long)(j0 + lrow) * ld + k0));
     }
   };
   auto store = [&](int buf, const float4 &ux, const float4 &uy) {
@@ -355,6 +358,18 @@ __global__ void __launch_bounds__(GS_NT, ACE_GS_MINB) gram_sym_f32_kernel(const 
   }
 }
 
+// Screen contribution of the columns [0, K) of X (rows of stride ld): G += scale * |X| |X|^T on the
+// upper triangle (G is not cleared; columns must start on a 16-byte boundary, K % 4 == 0).
+cudaError_t launch_screen_cols(const float *X, int n, long long ld, long long K, double scale, double *G,
+                               cudaStream_t st) {
+  if (K % 4 != 0 || ld % 4 != 0 || (reinterpret_cast<uintptr_t>(X) & 15)) return cudaErrorInvalidValue;
+  const int nb = (n + GS_B - 1) / GS_B;
+  const long long chunks = (K + GS_CHUNK - 1) / GS_CHUNK;
+  if (chunks > 65535) return cudaErrorInvalidValue;
+  gram_sym_f32_kernel<true><<<dim3(nb * (nb + 1) / 2, (unsigned)chunks), GS_NT, 0, st>>>(X, n, ld, K, scale, G);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_gram(const T *X, int nx, const T *Y, int ny, long long K, double scale, bool abs_values,
                         bool upper_only, double *G, cudaStream_t st) {
@@ -367,9 +382,9 @@ cudaError_t launch_gram(const T *X, int nx, const T *Y, int ny, long long K, dou
       if (e != cudaSuccess) return e;
       dim3 grid(nb * (nb + 1) / 2, (unsigned)chunks);
       if (abs_values)
-        gram_sym_f32_kernel<true><<<grid, GS_NT, 0, st>>>(X, nx, K, scale, G);
+        gram_sym_f32_kernel<true><<<grid, GS_NT, 0, st>>>(X, nx, K, K, scale, G);
       else
-        gram_sym_f32_kernel<false><<<grid, GS_NT, 0, st>>>(X, nx, K, scale, G);
+        gram_sym_f32_kernel<false><<<grid, GS_NT, 0, st>>>(X, nx, K, K, scale, G);
       return cudaGetLastError();
     }
     if (K % 4 == 0) {

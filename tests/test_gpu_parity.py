@@ -159,6 +159,21 @@ def test_screen_and_screened_build(water_small, prec):
         assert rel_max(g["W"].reshape(ref["W"].shape), ref["W"]) <= MIXED_W_RTOL
 
 
+def test_screened_build_from_host_memory(water_small):
+    """An FP32 host input of a screened build is copied in column chunks while the screen adds each
+    chunk: the screen, the pair list and the build match the build from device memory."""
+    w = water_small
+    dev = gpu_build(w.phi, w.lattice, ace.ACE_MIXED, rho_cut=w.rho_cut)
+    host = gpu_build(w.phi, w.lattice, ace.ACE_MIXED, rho_cut=w.rho_cut, host=True)
+    assert dev["status"] == 0 and host["status"] == 0
+    assert np.all(np.abs(host["O"] - dev["O"]) <= 1e-12 * np.abs(dev["O"]).max())
+    band = np.abs(dev["O"] - w.rho_cut) < 1e-6 * w.rho_cut
+    assert np.array_equal(host["mask"] | band, dev["mask"] | band)
+    assert abs(host["E_x"] - dev["E_x"]) <= 1e-3 * MIXED_EX_TOL_PER_ORB * w.norb
+    O_ref, _ = oracle.screen(w.phi, w.lattice, w.rho_cut)
+    assert np.all(np.abs(host["O"] - O_ref) <= 1e-6 * O_ref + 1e-14)
+
+
 def test_odd_pair_count_and_single_orbital():
     lat = np.diag([8.0, 8.0, 8.0])
     grid = (16, 16, 16)
