@@ -195,6 +195,7 @@ WORKLOADS = {
     "water64": "water64_256orb_128c_rhocut1e-3",
     "enzyme8": "enzyme_112orb_160x144x128_8snap_rhocut1e-3",
     "enzyme8_iso": "enzyme_112orb_160x144x128_8snap_rhocut1e-3_isolated_cell",
+    "enzyme8_reuse": "enzyme_112orb_160x144x128_8snap_rhocut1e-3_pairlist_reuse",
     "batched24": "batched24_uneven_rhocut1e-3",
 }
 
@@ -283,6 +284,99 @@ def run_multi(args):
                       "speedup_mixed_over_fp64": mixed["builds_per_s"] / f64["builds_per_s"]},
         "gpu_launches": mixed["rec"]["launches"],
         "clocks": mixed["clk"],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reuse(args):
+    """Reuse of a pair list across snapshots: one step screens snapshot 0 (ace_build) and builds
+    snapshots 1..7 on its pair list (ace_build_pairs); timed against a step that screens every
+    snapshot, and the pair-list drift (pairs of each snapshot's own screen that the reused list
+    lacks or adds) is reported."""
+    import torch
+
+    import paper_2101_03155_gb300 as ace
+    from paper_2101_03155_gb300 import ace as abi
+    from paper_2101_03155_gb300 import build as cuda_build
+    from workloads.generators import config5
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    cuda_build.build()
+    ace.ace.load()
+    ws = config5(nsnap=8)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for prec, dt, steps in ((ace.ACE_MIXED, torch.float32, args.steps), (ace.ACE_FP64, torch.float64,
+                                                                         max(1, args.fp64_steps))):
+        descs = [ace.make_desc(w.grid, w.lattice, w.norb, rho_cut=w.rho_cut, spin_factor=w.spin_factor, prec=prec)
+                 for w in ws]
+        phis = [torch.from_numpy(w.phi).to(device="cuda", dtype=dt) for w in ws]
+
+        def step_reuse(rec):
+            op0 = ace.ace_build(descs[0], phis[0], stream)
+            pairs = abi.get_numpy(op0, abi.ACE_GET_PAIRS)
+            rec["launches"] += ace.ace.ace_kernel_launches(op0)
+            op0.close()
+            for k in range(1, len(ws)):
+                op = ace.ace_build_pairs(descs[k], phis[k], pairs, stream)
+                rec["launches"] += ace.ace.ace_kernel_launches(op)
+                op.close()
+            return pairs
+
+        def step_screen(rec):
+            out = []
+            for k in range(len(ws)):
+                op = ace.ace_build(descs[k], phis[k], stream)
+                out.append(abi.get_numpy(op, abi.ACE_GET_PAIRS))
+                rec["launches"] += ace.ace.ace_kernel_launches(op)
+                op.close()
+            return out
+
+        timings = {}
+        for name, fn in (("reuse", step_reuse), ("screen_every_snapshot", step_screen)):
+            rec = {"launches": 0}
+            for _ in range(args.warmup if prec == ace.ACE_MIXED else 1):
+                fn(rec)
+            rec = {"launches": 0}
+            torch.cuda.synchronize()
+            clocks = ClockSampler(torch.cuda.current_device())
+            clocks.start()
+            start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            for _ in range(steps):
+                last = fn(rec)
+            end.record(stream)
+            torch.cuda.synchronize()
+            ms = start.elapsed_time(end)
+            timings[name] = {"builds_per_s": len(ws) * steps / (ms / 1e3), "ms_per_step": ms / steps,
+                             "launches": rec["launches"], "clk": clocks.stop(), "last": last}
+        res[prec] = timings
+        del phis
+    mixed = res[ace.ACE_MIXED]
+    reused = {tuple(p) for p in mixed["reuse"]["last"].tolist()}
+    drift = []
+    for k, own in enumerate(mixed["screen_every_snapshot"]["last"]):
+        own_set = {tuple(p) for p in own.tolist()}
+        drift.append({"snapshot": k, "own_pairs": len(own_set), "missing_from_reused": len(own_set - reused),
+                      "extra_in_reused": len(reused - own_set)})
+    line = {
+        "metric": METRIC, "value": mixed["reuse"]["builds_per_s"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mixed["reuse"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "builds_per_step": len(ws), "norb": ws[0].norb,
+                   "grid": list(ws[0].grid), "precision": "mixed",
+                   "step": "snapshot 0 screened, snapshots 1-7 built on its pair list (ace_build_pairs)",
+                   "l2": "inputs larger than L2"},
+        "screen_every_snapshot": {"value": mixed["screen_every_snapshot"]["builds_per_s"], "unit": UNIT},
+        "fp64_form": {"value": res[ace.ACE_FP64]["reuse"]["builds_per_s"], "unit": UNIT,
+                      "speedup_mixed_over_fp64": mixed["reuse"]["builds_per_s"]
+                      / res[ace.ACE_FP64]["reuse"]["builds_per_s"]},
+        "pair_list_drift": drift,
+        "gpu_launches": mixed["reuse"]["launches"],
+        "clocks": mixed["reuse"]["clk"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -488,6 +582,8 @@ def main():
     if args.impl == "reference":
         args.ref_step_s = min(args.ref_step_s, max(2.0, 150.0 / max(1, args.steps + args.warmup)))
         return run_reference(args)
+    if args.workload == "enzyme8_reuse":
+        return run_reuse(args)
     if args.workload != "water32":
         return run_multi(args)
     return run_ours(args)

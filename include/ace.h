@@ -97,6 +97,17 @@ typedef struct ace_op ace_op; /* opaque: owns xi, W, M, L, L^-1, the pair list a
 ace_status ace_build(const ace_desc *desc, const void *phi, ace_dtype dtype, void *cuda_stream,
                      ace_op **out);
 
+/* Build the ACE operator on a given pair list instead of the screen: the reuse step of a
+ * multiple-time-step run (section III: an outer step every n steps, many snapshots in between that
+ * move each centre by ~0.05 bohr), where the pair list of an earlier snapshot (ace_get(...,
+ * ACE_GET_PAIRS)) serves the next ones.  W, M, L, xi and E_x are those of Appendix A with Eq. (vx)
+ * summed over exactly the listed pairs (desc->rho_cut is not used; ACE_GET_OVERLAP returns zeros).
+ *   pairs_host: host int32 [npairs][2], 0 <= i, j < norb; (i, j) and (j, i) are the same pair, each
+ *               pair at most once (ACE_ERR_ARG otherwise); the diagonal pairs (i, i) are not added.
+ * Synchronous like ace_build; the same errors. */
+ace_status ace_build_pairs(const ace_desc *desc, const void *phi, ace_dtype dtype, const int *pairs_host,
+                           long npairs, void *cuda_stream, ace_op **out);
+
 /* k independent builds (replicas or snapshots) issued back to back on one stream.  desc, phi and
  * out are arrays of length k; each build is as in ace_build.  On the first failing build the
  * handles already created are destroyed, every out[i] is NULL, and its status is returned. */

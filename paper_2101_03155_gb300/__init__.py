@@ -16,6 +16,7 @@ from .ace import (  # noqa: F401
     ace_apply,
     ace_build,
     ace_build_batched,
+    ace_build_pairs,
     ace_destroy,
     ace_get,
     ace_grid_supported,

@@ -47,7 +47,7 @@ ACE_GET_OVERLAP = 6
 EXPORTED = [
     "ace_build", "ace_build_batched", "ace_apply", "exchange_energy", "ace_get", "ace_pair_count",
     "ace_get_size", "ace_stage_times", "ace_kernel_launches", "ace_grid_supported", "ace_destroy",
-    "ace_last_error", "ace_exchange_w_noalloc", "ace_autotune",
+    "ace_last_error", "ace_exchange_w_noalloc", "ace_autotune", "ace_build_pairs",
 ]
 
 
@@ -108,6 +108,7 @@ def load(path: str = LIB_PATH):
         lib = ctypes.CDLL(path)
         vp, c_int, c_long, c_size = ctypes.c_void_p, ctypes.c_int, ctypes.c_long, ctypes.c_size_t
         lib.ace_build.argtypes = [ctypes.POINTER(AceDesc), vp, c_int, vp, ctypes.POINTER(vp)]
+        lib.ace_build_pairs.argtypes = [ctypes.POINTER(AceDesc), vp, c_int, vp, ctypes.c_long, vp, ctypes.POINTER(vp)]
         lib.ace_build_batched.argtypes = [c_int, ctypes.POINTER(AceDesc), ctypes.POINTER(vp), c_int, vp,
                                           ctypes.POINTER(vp)]
         lib.ace_apply.argtypes = [vp, vp, c_int, c_int, vp, vp]
@@ -212,6 +213,21 @@ def ace_build(desc: AceDesc, phi, stream=None, check: bool = True) -> AceOp:
         raise ValueError(f"phi has {numel} elements, descriptor needs {expect}")
     h = ctypes.c_void_p()
     st = load().ace_build(ctypes.byref(desc), ptr, code, _stream_handle(stream), ctypes.byref(h))
+    op = AceOp(h.value, desc) if h.value else None
+    if check:
+        _check(st, op)
+    return op if check else (st, op)
+
+
+def ace_build_pairs(desc: AceDesc, phi, pairs, stream=None, check: bool = True) -> AceOp:
+    """ace_build_pairs: the build on a given pair list (int [npairs][2]) instead of the screen."""
+    ptr, code, numel = _array_info(phi)
+    if numel != desc.norb * desc.n[0] * desc.n[1] * desc.n[2]:
+        raise ValueError("phi does not match the descriptor")
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    h = ctypes.c_void_p()
+    st = load().ace_build_pairs(ctypes.byref(desc), ptr, code, pr.ctypes.data if len(pr) else None, len(pr),
+                                _stream_handle(stream), ctypes.byref(h))
     op = AceOp(h.value, desc) if h.value else None
     if check:
         _check(st, op)

@@ -259,6 +259,8 @@ struct ace_op {
   long launches = 0;          // kernels of this library launched by the build
   std::vector<void *> owned;  // stream-ordered allocations freed by ace_destroy
   std::vector<int2> pairs_h;  // host copy of the kept pairs
+  std::vector<int2> given;    // ace_build_pairs: the caller's pair list (sorted, unique); skips the screen
+  bool use_given = false;
   std::vector<void *> temps;  // build workspaces released in stream order at the end of the build
   const void *phi_work = nullptr;
   const DeviceTables *tab = nullptr;
@@ -744,7 +746,8 @@ ace_status build_begin(ace_op *op, const void *phi_in, ace_dtype dtype) {
   // FP32 host input of a screened build: copied in column chunks on a copy stream while the
   // screen adds each chunk's contribution on the build stream (the transfer hides the screen)
   const bool same = (dtype == ACE_F64) == (sizeof(T) == 8);
-  const bool pipelined = sizeof(T) == 4 && same && d.rho_cut > 0.0 && N % 4 == 0 && !is_device_pointer(phi_in) &&
+  const bool pipelined = sizeof(T) == 4 && same && d.rho_cut > 0.0 && !op->use_given && N % 4 == 0 &&
+                         !is_device_pointer(phi_in) &&
                          env_int("ACE_PIPELINED_INPUT", 1) != 0;
   const T *phi = nullptr;
   if (pipelined) {
@@ -771,6 +774,35 @@ ace_status build_begin(ace_op *op, const void *phi_in, ace_dtype dtype) {
   op->tc_err = op->status_d + 1;
   ACE_CUDA(cudaMemsetAsync(op->status_d, 0, sizeof(int) * 4, st), "zero status");
   ACE_CUDA(op_alloc(op, &op->energy_d, sizeof(double) * 2), "alloc energy");
+  if (op->use_given) {
+    // the caller's pair list: no screen (O stays zero); pairs and packs uploaded, count and pairs
+    // written straight into the host readback area
+    const size_t np = op->given.size();
+    std::vector<int4> pk((np + 1) / 2);
+    for (size_t p = 0; p < pk.size(); ++p) {
+      const int2 a = op->given[2 * p];
+      const int2 b = 2 * p + 1 < np ? op->given[2 * p + 1] : make_int2(-1, -1);
+      pk[p] = make_int4(a.x, a.y, b.x, b.y);
+    }
+    ACE_CUDA(cudaMemsetAsync(op->O, 0, sizeof(double) * n * n, st), "zero O");
+    ACE_CUDA(cudaMemsetAsync(op->O_sym, 0, sizeof(double) * n * n, st), "zero O");
+    const size_t rb_bytes = 32 + sizeof(int2) * maxpairs;
+    ACE_CUDA(pinned_get(rb_bytes, &op->readback), "pinned readback");
+    op->readback_bytes = rb_bytes;
+    *static_cast<int *>(op->readback) = (int)np;
+    int2 *rp = reinterpret_cast<int2 *>(static_cast<char *>(op->readback) + 32);
+    std::copy(op->given.begin(), op->given.end(), rp);
+    // uploads from the pinned area, so that they stay asynchronous (the area lives until destroy)
+    ACE_CUDA(cudaMemcpyAsync(op->pairs, rp, sizeof(int2) * np, cudaMemcpyHostToDevice, st), "pair upload");
+    ACE_CUDA(cudaMemcpyAsync(op->count_d, op->readback, sizeof(int), cudaMemcpyHostToDevice, st), "count upload");
+    if (!pk.empty()) {
+      ACE_CUDA(cudaMemcpyAsync(op->packs, pk.data(), sizeof(int4) * pk.size(), cudaMemcpyHostToDevice, st),
+               "pack upload");
+      ACE_CUDA(cudaStreamSynchronize(st), "pack upload");  // pk is a host temporary
+    }
+    ACE_CUDA(cudaEventRecord(op->ev[1], st), "event record");
+    return ACE_OK;
+  }
   if (pipelined) {
     ACE_CUDA(cudaMemsetAsync(op->O, 0, sizeof(double) * n * n, st), "zero O");
     cudaStream_t cs;
@@ -1071,6 +1103,50 @@ ace_status ace_build(const ace_desc *desc, const void *phi, ace_dtype dtype, voi
   if (s == ACE_OK) {
     cudaError_t e = cudaEventSynchronize(op->ev[1]);
     s = e == cudaSuccess ? finish_any(op) : cuda_fail(e, "pair list readback");
+  }
+  if (s == ACE_OK) {
+    cudaError_t e = cudaStreamSynchronize(op->stream);
+    s = e == cudaSuccess ? build_collect(op) : cuda_fail(e, "build");
+  }
+  if (keeps_handle(s)) {
+    *out = op;
+    return s;
+  }
+  cudaStreamSynchronize(op->stream);
+  ace_destroy(op);
+  return s;
+}
+
+ace_status ace_build_pairs(const ace_desc *desc, const void *phi, ace_dtype dtype, const int *pairs_host, long npairs,
+                           void *cuda_stream, ace_op **out) {
+  if (!out) return fail(ACE_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  ace_status s = check_desc(desc);
+  if (s != ACE_OK) return s;
+  if (!phi) return fail(ACE_ERR_ARG, "phi is NULL");
+  if (dtype != ACE_F32 && dtype != ACE_F64) return fail(ACE_ERR_ARG, "unknown dtype %d", (int)dtype);
+  if (npairs < 0 || (npairs > 0 && !pairs_host)) return fail(ACE_ERR_ARG, "bad pair list");
+  const long maxp = (long)desc->norb * (desc->norb + 1) / 2;
+  if (npairs > maxp) return fail(ACE_ERR_ARG, "%ld pairs for %d orbitals", npairs, desc->norb);
+  std::vector<int2> given((size_t)npairs);
+  for (long p = 0; p < npairs; ++p) {
+    int i = pairs_host[2 * p], j = pairs_host[2 * p + 1];
+    if (i > j) std::swap(i, j);
+    if (i < 0 || j >= desc->norb) return fail(ACE_ERR_ARG, "pair %ld = (%d, %d) outside [0, %d)", p, i, j, desc->norb);
+    given[(size_t)p] = make_int2(i, j);
+  }
+  std::sort(given.begin(), given.end(), [](int2 a, int2 b) { return a.x < b.x || (a.x == b.x && a.y < b.y); });
+  for (size_t p = 1; p < given.size(); ++p)
+    if (given[p].x == given[p - 1].x && given[p].y == given[p - 1].y)
+      return fail(ACE_ERR_ARG, "pair (%d, %d) listed twice", given[p].x, given[p].y);
+  ace_op *op = new_op(desc, static_cast<cudaStream_t>(cuda_stream), &s);
+  if (!op) return s;
+  op->given.swap(given);
+  op->use_given = true;
+  s = begin_any(op, phi, dtype);
+  if (s == ACE_OK) {
+    cudaError_t e = cudaEventSynchronize(op->ev[1]);
+    s = e == cudaSuccess ? finish_any(op) : cuda_fail(e, "pair upload");
   }
   if (s == ACE_OK) {
     cudaError_t e = cudaStreamSynchronize(op->stream);
