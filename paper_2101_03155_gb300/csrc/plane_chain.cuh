@@ -343,6 +343,20 @@ __global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, ACC>())) plan
   }
 }
 
+// The dynamic shared-memory limit of a kernel, set once per device (a driver call per launch
+// would cost about as much host time as the launch itself).
+template <typename Kern>
+inline cudaError_t smem_attr_once(Kern k, size_t bytes, unsigned long long &done_bits) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (__atomic_load_n(&done_bits, __ATOMIC_ACQUIRE) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) __atomic_fetch_or(&done_bits, bit, __ATOMIC_RELEASE);
+  return e;
+}
+
 template <typename T, int N2, int N3>
 struct PlaneLaunch {
   static constexpr int NT = 384;
@@ -354,8 +368,8 @@ struct PlaneLaunch {
 
   static cudaError_t fwd(const PlaneArgs<T> &a, int npacks, cudaStream_t st) {
     const size_t sm = fwd_smem();
-    cudaError_t e = cudaFuncSetAttribute(plane_fwd_kernel<T, N2, N3, NT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static unsigned long long done = 0;
+    cudaError_t e = smem_attr_once(plane_fwd_kernel<T, N2, N3, NT>, sm, done);
     if (e != cudaSuccess) return e;
     plane_fwd_kernel<T, N2, N3, NT><<<dim3(a.n1, npacks), NT, sm, st>>>(a);
     return cudaGetLastError();
@@ -364,13 +378,13 @@ struct PlaneLaunch {
     const size_t sm = inv_smem(acc);
     cudaError_t e;
     if (acc) {
-      e = cudaFuncSetAttribute(plane_inv_kernel<T, N2, N3, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)sm);
+      static unsigned long long done_acc = 0;
+      e = smem_attr_once(plane_inv_kernel<T, N2, N3, NT, true>, sm, done_acc);
       if (e != cudaSuccess) return e;
       plane_inv_kernel<T, N2, N3, NT, true><<<dim3(a.n1, ngroups), NT, sm, st>>>(a);
     } else {
-      e = cudaFuncSetAttribute(plane_inv_kernel<T, N2, N3, NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)sm);
+      static unsigned long long done = 0;
+      e = smem_attr_once(plane_inv_kernel<T, N2, N3, NT, false>, sm, done);
       if (e != cudaSuccess) return e;
       plane_inv_kernel<T, N2, N3, NT, false><<<dim3(a.n1, ngroups), NT, sm, st>>>(a);
     }
