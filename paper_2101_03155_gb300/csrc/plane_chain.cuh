@@ -357,9 +357,25 @@ inline cudaError_t smem_attr_once(Kern k, size_t bytes, unsigned long long &done
   return e;
 }
 
+// Threads of a plane CTA: as many warps as the register file allows for the CTAs that shared
+// memory fits on an SM (FP32: exactly 3 CTAs -> 448 threads at 40 registers, 2 -> 768, 1 -> 1024;
+// smaller planes, which fit more CTAs, keep 384); FP64 planes keep 384 (twice the registers per
+// complex value).  ACE_PLANE_NT overrides.
+template <typename T, int N2, int N3>
+constexpr int plane_threads() {
+#ifdef ACE_PLANE_NT
+  return ACE_PLANE_NT;
+#else
+  constexpr long long bytes = (long long)sizeof(cpx<T>) * (N2 * (N3 + 1) + N2 + N3);
+  constexpr long long fit = (227LL * 1024) / bytes;
+  if (sizeof(T) != 4) return 384;
+  return fit > 3 ? 384 : (fit == 3 ? 448 : (fit == 2 ? 768 : 1024));
+#endif
+}
+
 template <typename T, int N2, int N3>
 struct PlaneLaunch {
-  static constexpr int NT = 384;
+  static constexpr int NT = plane_threads<T, N2, N3>();
   static size_t fwd_smem() { return sizeof(cpx<T>) * (N2 * PlaneShape<N2, N3>::PP + N2 + N3); }
   static size_t inv_smem(bool acc) {
     return fwd_smem() + (acc ? sizeof(T) * (size_t)N2 * N3 : 0);
