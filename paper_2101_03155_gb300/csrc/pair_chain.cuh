@@ -234,7 +234,13 @@ struct ConvShape {
   static constexpr int R1 = Factor<L>::R1, R2 = Factor<L>::R2;
   static constexpr int TILE = 32;
   static constexpr int LP = L + 1;
-  static constexpr int NT = 128;
+  // threads: 128 up to 108 points (more CTAs per SM), 256 for the longer pencils (measured on
+  // 96, 128 and 160 points); ACE_CONV_NT overrides
+#ifdef ACE_CONV_NT
+  static constexpr int NT = ACE_CONV_NT;
+#else
+  static constexpr int NT = L > 108 ? 256 : 128;
+#endif
 };
 
 template <typename T, int L>
