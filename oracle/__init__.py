@@ -95,6 +95,7 @@ def _declare(lib):
     lib.oracle_ace_from_w.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_long, ctypes.c_double, _dp, _dp, _dp, _dp]
     lib.oracle_ace_apply.argtypes = [_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_long, ctypes.c_double, _dp]
     lib.oracle_exchange_energy.argtypes = [_dp, ctypes.c_int, ctypes.c_double]
+    lib.oracle_scdm_select.argtypes = [_dp, ctypes.c_int, ctypes.c_long, ctypes.c_int, _ip]
     lib.oracle_exchange_energy.restype = ctypes.c_double
 
 
@@ -236,3 +237,30 @@ def ace_build(phi, lattice, rho_cut: float = 0.0, spin_factor: float = 2.0, mask
     res.update(W=W, mask=mask, O=O, dV=dV)
     res["E_x"] = exchange_energy(res["M"], spin_factor)
     return res
+
+
+def scdm_select(psi, npiv=None) -> np.ndarray:
+    """Greedy column-pivoted QR selection on Psi^T: the grid indices of the SCDM columns."""
+    psi = _f64(psi)
+    n = psi.shape[0]
+    npts = int(np.prod(psi.shape[1:]))
+    k = n if npiv is None else int(npiv)
+    piv = np.empty(k, dtype=np.int32)
+    _load().oracle_scdm_select(_ptr(psi), n, npts, k, _ptr(piv, _ip))
+    return piv
+
+
+def scdm(psi, dV: float):
+    """SCDM localisation: columns C of the density matrix P = Psi Psi^T (rows of Psi at the selected
+    grid points, M = Psi(C)^T), orthonormalised symmetrically under dV:
+    Phi = Psi^T M (M^T M)^{-1/2} (as rows [n][grid]).  Returns (Phi, pivots)."""
+    psi = _f64(psi)
+    n = psi.shape[0]
+    flat = psi.reshape(n, -1)
+    piv = scdm_select(psi)
+    M = flat[:, piv]                      # M[i][j] = psi_i(c_j)
+    S = M.T @ M                           # = dV Phi~^T Phi~ for orthonormal Psi
+    w, V = np.linalg.eigh(S)
+    U = M @ (V * (1.0 / np.sqrt(w))) @ V.T
+    phi = (U.T @ flat).reshape(psi.shape)
+    return phi, piv

@@ -445,3 +445,51 @@ double oracle_exchange_energy(const double *M, int norb, double spin_factor) {
   for (int k = 0; k < norb; ++k) t += M[(long)k * norb + k];
   return 0.5 * spin_factor * t;
 }
+
+/* ------------------------------------------------------------------------------------------
+ * SCDM column selection (the localisation step before the path, section II: selected columns
+ * of the density matrix): the greedy choice of column-pivoted QR of Psi^T (norb x npts, whose
+ * column r is the vector psi(r) = (psi_1(r), ..., psi_n(r))).  Step k takes the column of largest
+ * residual norm d(r) = |psi(r)|^2 - sum_{j<k} (u_j . psi(r))^2 (the first such index on ties),
+ * then extends the orthonormal basis u_j of the chosen columns by Gram-Schmidt (applied twice).
+ * piv receives the npiv chosen grid indices in order.  Returns 0.
+ * ---------------------------------------------------------------------------------------- */
+int oracle_scdm_select(const double *psi, int norb, long npts, int npiv, int *piv) {
+  double *d = (double *)malloc((size_t)npts * sizeof(double));
+  double *U = (double *)malloc((size_t)npiv * norb * sizeof(double));
+#pragma omp parallel for schedule(static)
+  for (long r = 0; r < npts; ++r) {
+    double s = 0.0;
+    for (int i = 0; i < norb; ++i) s += psi[(long)i * npts + r] * psi[(long)i * npts + r];
+    d[r] = s;
+  }
+  for (int k = 0; k < npiv; ++k) {
+    long best = 0;
+    for (long r = 1; r < npts; ++r)
+      if (d[r] > d[best]) best = r;
+    piv[k] = (int)best;
+    double *u = U + (long)k * norb;
+    for (int i = 0; i < norb; ++i) u[i] = psi[(long)i * npts + best];
+    for (int pass = 0; pass < 2; ++pass)
+      for (int j = 0; j < k; ++j) {
+        const double *v = U + (long)j * norb;
+        double c = 0.0;
+        for (int i = 0; i < norb; ++i) c += v[i] * u[i];
+        for (int i = 0; i < norb; ++i) u[i] -= c * v[i];
+      }
+    double nrm = 0.0;
+    for (int i = 0; i < norb; ++i) nrm += u[i] * u[i];
+    nrm = sqrt(nrm);
+    for (int i = 0; i < norb; ++i) u[i] /= nrm;
+#pragma omp parallel for schedule(static)
+    for (long r = 0; r < npts; ++r) {
+      double p = 0.0;
+      for (int i = 0; i < norb; ++i) p += u[i] * psi[(long)i * npts + r];
+      d[r] -= p * p;
+    }
+    d[best] = -1.0; /* chosen columns leave the candidate set (their residual is zero) */
+  }
+  free(U);
+  free(d);
+  return 0;
+}

@@ -45,6 +45,9 @@ MUTANTS = {
     "screen_strict": ("(s >= rho_cut)", "(s > rho_cut)"),
     "screen_no_abs": ("s += fabs(a[r] * b[r]);", "s += a[r] * b[r];"),
     "screen_diag_not_kept": ("(i == j) || (rho_cut <= 0.0)", "(rho_cut <= 0.0)"),
+    "scdm_argmin": ("if (d[r] > d[best]) best = r;", "if (d[r] < d[best]) best = r;"),
+    "scdm_no_orthogonalisation": ("for (int pass = 0; pass < 2; ++pass)", "for (int pass = 0; pass < 0; ++pass)"),
+    "scdm_no_downdate": ("d[r] -= p * p;", "d[r] -= 0.0 * p;"),
 }
 
 
@@ -61,7 +64,12 @@ def battery_inputs():
     x = np.arange(n) * 16.0 / n
     X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
     iso_phi = (2 / np.pi) ** 0.75 * np.exp(-((X - 8.0) ** 2 + (Y - 8.0) ** 2 + (Z - 8.0) ** 2))
-    return dict(grid=grid, phi=phi, E=E, z=z, iso_phi=iso_phi, iso_ref=2 * np.sqrt(1 / np.pi))
+    import scipy.linalg
+
+    A = np.random.default_rng(8).standard_normal((10, 200))
+    P = list(scipy.linalg.qr(A, pivoting=True, mode="economic")[2][:10])
+    return dict(grid=grid, phi=phi, E=E, z=z, iso_phi=iso_phi, iso_ref=2 * np.sqrt(1 / np.pi), scdm_A=A,
+                scdm_P=P)
 
 
 def _naive(z, sign):
@@ -109,6 +117,9 @@ def run_battery(orc, inp):
     _, mask = orc.screen(phi, TRICLINIC, big)
     if not np.array_equal(mask, np.eye(3, dtype=bool)):
         failed.append("screen_diagonal")
+    # SCDM selection: the greedy column-pivoted QR of LAPACK on a random matrix
+    if list(orc.scdm_select(inp["scdm_A"])) != inp["scdm_P"]:
+        failed.append("scdm_pivots")
     # isolated-cell kernel: closed-form self-energy of a Gaussian density (default cut-off)
     g = inp["iso_phi"]
     e = orc.pair_energy(g, g, np.eye(3) * 16.0, orc.TRUNCATED, 0.0)

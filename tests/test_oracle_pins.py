@@ -331,3 +331,45 @@ def test_truncated_exchange_energy_of_separated_orbitals(oracle_mod):
     assert r["status"] == 0
     ref = -(2.0 / 2) * 2 * (2 * np.sqrt(alpha / np.pi))
     assert r["E_x"] == pytest.approx(ref, rel=1e-9)
+
+
+# ------------------------------------------------------------------------------------------
+# SCDM localisation (selected columns of the density matrix, the step before the path):
+# column-pivoted QR selection, then symmetric orthonormalisation of the selected columns.
+# ------------------------------------------------------------------------------------------
+def test_scdm_pivots_match_lapack_qrcp(oracle_mod):
+    import scipy.linalg
+
+    rng = np.random.default_rng(7)
+    for n, m in [(6, 40), (12, 300), (20, 500)]:
+        A = rng.standard_normal((n, m)) * rng.uniform(0.5, 2.0, size=m)
+        _, _, P = scipy.linalg.qr(A, pivoting=True, mode="economic")
+        assert list(oracle_mod.scdm_select(A)) == list(P[:n]), (n, m)
+
+
+def test_scdm_localises_rotated_gaussians(oracle_mod):
+    lat = np.diag([12.0, 12.0, 12.0])
+    grid = (24, 24, 24)
+    rng = np.random.default_rng(31)
+    phi_loc, _, _ = gaussian_orbitals(grid, lat, 8, 1, rng, alpha_range=(1.0, 2.0))
+    dV = np.prod(np.diag(lat)) / np.prod(grid)
+    Q = random_orthogonal(8, rng)
+    psi = np.tensordot(Q, phi_loc, axes=(1, 0))  # delocalised combinations, same span
+    phi, piv = oracle_mod.scdm(psi, dV)
+    flat_p, flat_s = phi.reshape(8, -1), psi.reshape(8, -1)
+    # orthonormal under dV, and the same occupied space (psi = (dV psi phi^T) phi)
+    assert np.abs(dV * flat_p @ flat_p.T - np.eye(8)).max() <= 1e-12
+    assert np.abs((dV * flat_s @ flat_p.T) @ flat_p - flat_s).max() <= 1e-11 * np.abs(flat_s).max()
+    assert len(set(piv.tolist())) == 8
+    # E_x is invariant under the orthogonal change of basis (Eq. unit)
+    e_psi = oracle_mod.ace_build(psi, lat, 0.0, 2.0, want_xi=False)["E_x"]
+    e_phi = oracle_mod.ace_build(phi, lat, 0.0, 2.0, want_xi=False)["E_x"]
+    assert e_phi == pytest.approx(e_psi, rel=1e-10)
+    # localisation: the pair overlaps of the SCDM orbitals are those of the localized set, far
+    # below those of the rotated set
+    O_phi, _ = oracle_mod.screen(phi, lat, 0.0)
+    O_psi, _ = oracle_mod.screen(psi, lat, 0.0)
+    O_loc, _ = oracle_mod.screen(phi_loc, lat, 0.0)
+    off = ~np.eye(8, dtype=bool)
+    assert O_phi[off].mean() < 0.5 * O_psi[off].mean()
+    assert O_phi[off].mean() < 2.0 * O_loc[off].mean()
