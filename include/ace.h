@@ -121,6 +121,30 @@ ace_status ace_build_batched(int k, const ace_desc *desc, const void *const *phi
 ace_status ace_apply(const ace_op *op, const void *psi, ace_dtype dtype, int m, void *out,
                      void *cuda_stream);
 
+/* SCDM localisation (section II, Eq. unit, with the selected columns of the density matrix that
+ * section II names; the paper gives no formulas for it, this is the method of Damle, Lin and Ying,
+ * J. Chem. Theory Comput. 11, 1463 (2015)): phi_k = sum_i psi_i U[i][k] with U orthogonal,
+ *   1. c_0..c_{n-1}: greedy column-pivoted QR of Psi^T (n x npts): step k takes the grid point of
+ *      largest residual norm |psi(r)|^2 - sum_{j<k} (u_j . psi(r))^2 (the smallest index on ties),
+ *      u_j the orthonormalised columns chosen before;
+ *   2. M[i][j] = psi_i(c_j) (columns of the density matrix Psi Psi^T at the chosen points);
+ *   3. U = M (M^T M)^{-1/2} (symmetric orthonormalisation, so phi is orthonormal under dV whenever
+ *      psi is).
+ *   psi:  canonical orbitals [norb][npts] (npts = N1 N2 N3 in any grid order), host or device.
+ *   phi:  output [norb][npts] of `dtype`, on the same side as psi (may not alias it).
+ *   piv_host: optional host int32 [norb] receiving c_0..c_{n-1}; u_host: optional host double
+ *         [norb][norb] receiving U; launches: optional, the number of this library's kernels run.
+ *   prec: ACE_FP64 every step in FP64.  ACE_MIXED: psi in FP32, residual norms in FP64 with the
+ *         projections u_k . psi(r) summed as FP32 products in 16-term FP32 partials; M, U and
+ *         (M^T M)^{-1/2} (coupled Newton-Schulz) in FP64; Phi = U^T Psi by BF16x3 tensor-core
+ *         products (FP32-level).  Near-equal residuals may then select another, equally valid,
+ *         point than FP64 arithmetic would.
+ * 1 <= norb <= 1024, norb <= npts < 2^31.  Synchronous.  Errors: ACE_ERR_ARG, ACE_ERR_CUDA,
+ * ACE_ERR_OOM, ACE_ERR_TIMEOUT, ACE_ERR_NOT_POSDEF (the chosen columns are linearly dependent:
+ * psi has rank < norb, and the Newton-Schulz iteration did not converge). */
+ace_status ace_scdm(int norb, long long npts, ace_precision prec, const void *psi, ace_dtype dtype, void *phi,
+                    int *piv_host, double *u_host, void *cuda_stream, long *launches);
+
 /* E_x = (f/2) tr M in Hartree (host scalar), computed in FP64 during the build. */
 ace_status exchange_energy(const ace_op *op, double *ex_hartree);
 

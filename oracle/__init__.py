@@ -254,13 +254,20 @@ def scdm(psi, dV: float):
     """SCDM localisation: columns C of the density matrix P = Psi Psi^T (rows of Psi at the selected
     grid points, M = Psi(C)^T), orthonormalised symmetrically under dV:
     Phi = Psi^T M (M^T M)^{-1/2} (as rows [n][grid]).  Returns (Phi, pivots)."""
+    piv = scdm_select(psi)
+    phi, _ = scdm_orthonormalise(psi, piv)
+    return phi, piv
+
+
+def scdm_orthonormalise(psi, piv):
+    """Second half of SCDM for given grid columns piv: U = M (M^T M)^{-1/2} with M[i][j] = psi_i(c_j),
+    and Phi = U^T Psi.  Returns (Phi, U)."""
     psi = _f64(psi)
     n = psi.shape[0]
     flat = psi.reshape(n, -1)
-    piv = scdm_select(psi)
-    M = flat[:, piv]                      # M[i][j] = psi_i(c_j)
+    M = flat[:, np.asarray(piv)]          # M[i][j] = psi_i(c_j)
     S = M.T @ M                           # = dV Phi~^T Phi~ for orthonormal Psi
     w, V = np.linalg.eigh(S)
     U = M @ (V * (1.0 / np.sqrt(w))) @ V.T
     phi = (U.T @ flat).reshape(psi.shape)
-    return phi, piv
+    return phi, U

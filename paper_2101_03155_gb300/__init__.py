@@ -22,6 +22,7 @@ from .ace import (  # noqa: F401
     ace_grid_supported,
     ace_last_error,
     ace_pair_count,
+    ace_scdm,
     ace_stage_times,
     exchange_energy,
     make_desc,

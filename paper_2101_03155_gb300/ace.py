@@ -47,7 +47,7 @@ ACE_GET_OVERLAP = 6
 EXPORTED = [
     "ace_build", "ace_build_batched", "ace_apply", "exchange_energy", "ace_get", "ace_pair_count",
     "ace_get_size", "ace_stage_times", "ace_kernel_launches", "ace_grid_supported", "ace_destroy",
-    "ace_last_error", "ace_exchange_w_noalloc", "ace_autotune", "ace_build_pairs",
+    "ace_last_error", "ace_exchange_w_noalloc", "ace_autotune", "ace_build_pairs", "ace_scdm",
 ]
 
 
@@ -121,6 +121,8 @@ def load(path: str = LIB_PATH):
         lib.ace_autotune.argtypes = [ctypes.POINTER(AceDesc), vp, c_int, vp, ctypes.POINTER(c_int)]
         lib.ace_exchange_w_noalloc.argtypes = [ctypes.POINTER(AceDesc), vp, c_int, ctypes.POINTER(c_int), c_long,
                                                vp, vp]
+        lib.ace_scdm.argtypes = [c_int, ctypes.c_longlong, c_int, vp, c_int, vp, ctypes.POINTER(c_int),
+                                 ctypes.POINTER(ctypes.c_double), vp, ctypes.POINTER(c_long)]
         lib.ace_grid_supported.argtypes = [c_int, c_int]
         lib.ace_grid_supported.restype = c_int
         lib.ace_destroy.argtypes = [vp]
@@ -128,7 +130,7 @@ def load(path: str = LIB_PATH):
         lib.ace_last_error.restype = ctypes.c_char_p
         for name in ("ace_build", "ace_build_batched", "ace_apply", "exchange_energy", "ace_get", "ace_get_size",
                      "ace_pair_count", "ace_stage_times", "ace_kernel_launches", "ace_exchange_w_noalloc",
-                     "ace_autotune"):
+                     "ace_autotune", "ace_build_pairs", "ace_scdm"):
             getattr(lib, name).restype = c_int
         _lib = lib
         return lib
@@ -262,6 +264,24 @@ def ace_apply(op: AceOp, psi, out, stream=None):
         raise ValueError("psi and out must have the same dtype and [m][N] shape")
     _check(load().ace_apply(op.handle, p_ptr, p_code, p_numel // N, o_ptr, _stream_handle(stream)))
     return out
+
+
+def ace_scdm(psi, phi, prec: int = ACE_MIXED, stream=None, check: bool = True):
+    """ace_scdm: SCDM-localised orbitals of psi [norb][...] written into phi (same shape and dtype,
+    same side).  Returns (status, pivots int32 [norb], U float64 [norb][norb], kernel launches)."""
+    p_ptr, p_code, p_numel = _array_info(psi)
+    o_ptr, o_code, o_numel = _array_info(phi)
+    n = int(psi.shape[0])
+    if p_code != o_code or p_numel != o_numel or p_numel % n:
+        raise ValueError("psi and phi must have the same dtype and shape")
+    piv = np.zeros(n, dtype=np.int32)
+    U = np.zeros((n, n), dtype=np.float64)
+    nl = ctypes.c_long()
+    st = load().ace_scdm(n, p_numel // n, prec, p_ptr, o_code, o_ptr, piv.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                         U.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream_handle(stream), ctypes.byref(nl))
+    if check:
+        _check(st)
+    return st, piv, U, nl.value
 
 
 def exchange_energy(op: AceOp) -> float:

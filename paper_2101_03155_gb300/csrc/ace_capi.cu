@@ -961,6 +961,55 @@ ace_status build_collect(ace_op *op) {
   return ACE_OK;
 }
 
+// Buffer that a result of `count` T elements for the caller's `out` (dtype `dtype`, host or device)
+// is computed into: `out` itself when it is 16-byte aligned device memory of type T, else a
+// temporary that deliver_result passes on.
+template <typename T>
+ace_status result_target(void *out, ace_dtype dtype, long long count, cudaStream_t st, std::vector<void *> &temps,
+                         T **res) {
+  const bool same = (dtype == ACE_F64) == (sizeof(T) == 8);
+  if (same && is_device_pointer(out) && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+    *res = static_cast<T *>(out);
+    return ACE_OK;
+  }
+  void *tmp = nullptr;
+  ACE_CUDA(cudaMallocAsync(&tmp, sizeof(T) * (size_t)count, st), "alloc out");
+  temps.push_back(tmp);
+  *res = static_cast<T *>(tmp);
+  return ACE_OK;
+}
+
+// Pass a result from result_target's buffer to `out`: conversion to `dtype`, copy to the host, or
+// copy to a misaligned device buffer, as needed (stream-ordered on st).
+template <typename T>
+ace_status deliver_result(T *res, void *out, ace_dtype dtype, long long count, cudaStream_t st,
+                          std::vector<void *> &temps) {
+  if (res == out) return ACE_OK;
+  const bool same = (dtype == ACE_F64) == (sizeof(T) == 8);
+  const bool host_out = !is_device_pointer(out);
+  void *final_dev = res;
+  const size_t out_bytes = (size_t)count * (dtype == ACE_F64 ? 8 : 4);
+  if (!same) {
+    void *conv = nullptr;
+    if (!host_out) {
+      conv = out;
+    } else {
+      ACE_CUDA(cudaMallocAsync(&conv, out_bytes, st), "alloc out conv");
+      temps.push_back(conv);
+    }
+    if (dtype == ACE_F64)
+      ACE_CUDA((ace::launch_convert<T, double>(res, static_cast<double *>(conv), count, 1.0, st)), "conv");
+    else
+      ACE_CUDA((ace::launch_convert<T, float>(res, static_cast<float *>(conv), count, 1.0, st)), "conv");
+    final_dev = conv;
+  }
+  if (host_out)
+    ACE_CUDA(cudaMemcpyAsync(out, final_dev, out_bytes, cudaMemcpyDeviceToHost, st), "device-to-host copy");
+  else if (final_dev != out)
+    ACE_CUDA(cudaMemcpyAsync(out, final_dev, out_bytes, cudaMemcpyDeviceToDevice, st), "unaligned output copy");
+  return ACE_OK;
+}
+
 template <typename T>
 ace_status apply_impl(const ace_op *op, const void *psi_in, ace_dtype dtype, int m, void *out, cudaStream_t st) {
   const int n = op->n;
@@ -975,7 +1024,6 @@ ace_status apply_impl(const ace_op *op, const void *psi_in, ace_dtype dtype, int
   } guard{&temps, st};
   ace_op tmpop;  // only for staging on `st`
   tmpop.stream = st;
-  const bool host_out = !is_device_pointer(out);
   const T *psi = nullptr;
   ace_status s = stage_input<T>(&tmpop, psi_in, dtype, (long long)m * N, &psi, &temps);
   if (s != ACE_OK) return s;
@@ -995,41 +1043,70 @@ ace_status apply_impl(const ace_op *op, const void *psi_in, ace_dtype dtype, int
   T *A = static_cast<T *>(tmp);
   ACE_CUDA(ace::launch_transpose_scale<T>(C, n, m, -1.0, A, st), "transpose");
   // out = -C^T xi  (m x N)
-  const bool same = (dtype == ACE_F64) == (sizeof(T) == 8);
   T *res = nullptr;
-  const bool out_aligned = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
-  if (same && !host_out && out_aligned) {
-    res = static_cast<T *>(out);
-  } else {
-    ACE_CUDA(cudaMallocAsync(&tmp, sizeof(T) * (size_t)m * N, st), "alloc out");
-    temps.push_back(tmp);
-    res = static_cast<T *>(tmp);
-  }
+  ace_status s2 = result_target<T>(out, dtype, (long long)m * N, st, temps, &res);
+  if (s2 != ACE_OK) return s2;
   ACE_CUDA(dense_left_mul<T>(A, m, n, static_cast<const T *>(op->xi), N, res, err_d, st, &nl), "xi C");
-  void *final_dev = res;
-  const size_t out_bytes = (size_t)m * N * (dtype == ACE_F64 ? 8 : 4);
-  if (!same) {
-    void *conv = nullptr;
-    if (!host_out) {
-      conv = out;
-    } else {
-      ACE_CUDA(cudaMallocAsync(&conv, out_bytes, st), "alloc out conv");
-      temps.push_back(conv);
-    }
-    if (dtype == ACE_F64)
-      ACE_CUDA((ace::launch_convert<T, double>(res, static_cast<double *>(conv), (long long)m * N, 1.0, st)), "conv");
-    else
-      ACE_CUDA((ace::launch_convert<T, float>(res, static_cast<float *>(conv), (long long)m * N, 1.0, st)), "conv");
-    final_dev = conv;
-  }
-  if (host_out)
-    ACE_CUDA(cudaMemcpyAsync(out, final_dev, out_bytes, cudaMemcpyDeviceToHost, st), "device-to-host copy");
-  else if (final_dev != out)
-    ACE_CUDA(cudaMemcpyAsync(out, final_dev, out_bytes, cudaMemcpyDeviceToDevice, st), "unaligned output copy");
+  s2 = deliver_result<T>(res, out, dtype, (long long)m * N, st, temps);
+  if (s2 != ACE_OK) return s2;
   int err_h = 0;
   ACE_CUDA(cudaMemcpyAsync(&err_h, err_d, sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
   ACE_CUDA(cudaStreamSynchronize(st), "apply");
   if (err_h) return fail(ACE_ERR_TIMEOUT, "a tensor-core kernel gave up waiting for its MMAs");
+  return ACE_OK;
+}
+
+// SCDM localisation of n orbitals of N points: pivots and Loewdin factor (scdm.cu), then
+// Phi = U^T Psi by the dense left multiply of the working type.
+template <typename T>
+ace_status scdm_impl(int n, long long N, const void *psi_in, ace_dtype dtype, void *phi_out, int *piv_host,
+                     double *u_host, cudaStream_t st, long *launches) {
+  std::vector<void *> temps;
+  struct TempGuard {
+    std::vector<void *> *v;
+    cudaStream_t s;
+    ~TempGuard() {
+      for (void *p : *v) cudaFreeAsync(p, s);
+    }
+  } guard{&temps, st};
+  ace_op tmpop;  // only for staging on `st`
+  tmpop.stream = st;
+  const T *psi = nullptr;
+  ace_status s = stage_input<T>(&tmpop, psi_in, dtype, (long long)n * N, &psi, &temps);
+  if (s != ACE_OK) return s;
+  *launches += tmpop.launches;
+  void *ws = nullptr;
+  ACE_CUDA(cudaMallocAsync(&ws, ace::scdm_workspace_bytes(n, N, sizeof(T)) + 256, st), "alloc SCDM workspace");
+  temps.push_back(ws);
+  int *err_d = reinterpret_cast<int *>(static_cast<char *>(ws) + ace::scdm_workspace_bytes(n, N, sizeof(T)));
+  ACE_CUDA(cudaMemsetAsync(err_d, 0, sizeof(int), st), "zero flag");
+  ace::ScdmResult r{};
+  ACE_CUDA(ace::launch_scdm<T>(psi, n, N, ws, st, launches, &r), "SCDM selection");
+  T *res = nullptr;
+  s = result_target<T>(phi_out, dtype, (long long)n * N, st, temps, &res);
+  if (s != ACE_OK) return s;
+  ACE_CUDA(dense_left_mul<T>(static_cast<const T *>(r.Ut), n, n, psi, N, res, err_d, st, launches), "U^T Psi");
+  s = deliver_result<T>(res, phi_out, dtype, (long long)n * N, st, temps);
+  if (s != ACE_OK) return s;
+  if ((dtype == ACE_F64) != (sizeof(T) == 8)) ++*launches;  // the conversion to the caller's dtype
+  const int nit = ace::scdm_max_iterations();
+  std::vector<double> dev(nit);
+  std::vector<int> piv(n);
+  int err_h = 0, dep_h = 0;
+  ACE_CUDA(cudaMemcpyAsync(&dep_h, r.dependent, sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
+  ACE_CUDA(cudaMemcpyAsync(dev.data(), r.dev, sizeof(double) * nit, cudaMemcpyDeviceToHost, st), "readback");
+  ACE_CUDA(cudaMemcpyAsync(piv.data(), r.piv, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "readback");
+  if (u_host) ACE_CUDA(cudaMemcpyAsync(u_host, r.U, sizeof(double) * n * n, cudaMemcpyDeviceToHost, st), "readback");
+  ACE_CUDA(cudaMemcpyAsync(&err_h, err_d, sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
+  ACE_CUDA(cudaStreamSynchronize(st), "SCDM");
+  if (err_h) return fail(ACE_ERR_TIMEOUT, "a tensor-core kernel gave up waiting for its MMAs");
+  if (piv_host) std::copy(piv.begin(), piv.end(), piv_host);
+  // the last Newton-Schulz iteration that ran decides convergence
+  double last = dev[0];
+  for (int it = 1; it < nit && dev[it] != 0.0; ++it) last = dev[it];
+  if (dep_h) return fail(ACE_ERR_NOT_POSDEF, "psi has rank < norb: a selected column lies in the span of the others");
+  if (!(last < 1e-8))
+    return fail(ACE_ERR_NOT_POSDEF, "the selected columns are linearly dependent (Newton-Schulz residual %.3g)", last);
   return ACE_OK;
 }
 
@@ -1249,6 +1326,22 @@ ace_status ace_apply(const ace_op *op, const void *psi, ace_dtype dtype, int m, 
   if (op->status != 0) return fail(ACE_ERR_NOT_POSDEF, "operator build did not complete (status %d)", op->status);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   return op->fp64 ? apply_impl<double>(op, psi, dtype, m, out, st) : apply_impl<float>(op, psi, dtype, m, out, st);
+}
+
+ace_status ace_scdm(int norb, long long npts, ace_precision prec, const void *psi, ace_dtype dtype, void *phi,
+                    int *piv_host, double *u_host, void *cuda_stream, long *launches) {
+  if (!psi || !phi) return fail(ACE_ERR_ARG, "NULL argument");
+  if (norb < 1 || norb > 1024) return fail(ACE_ERR_ARG, "norb = %d outside [1, 1024]", norb);
+  if (npts < norb || npts > 0x7fffffffLL) return fail(ACE_ERR_ARG, "npts = %lld outside [norb, 2^31 - 1]", npts);
+  if (prec != ACE_FP64 && prec != ACE_MIXED) return fail(ACE_ERR_ARG, "unknown precision %d", (int)prec);
+  if (dtype != ACE_F32 && dtype != ACE_F64) return fail(ACE_ERR_ARG, "unknown dtype %d", (int)dtype);
+  if (is_device_pointer(psi) != is_device_pointer(phi)) return fail(ACE_ERR_ARG, "psi and phi on different sides");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  long nl = 0;
+  const ace_status s = prec == ACE_FP64 ? scdm_impl<double>(norb, npts, psi, dtype, phi, piv_host, u_host, st, &nl)
+                                        : scdm_impl<float>(norb, npts, psi, dtype, phi, piv_host, u_host, st, &nl);
+  if (launches) *launches = nl;
+  return s;
 }
 
 ace_status exchange_energy(const ace_op *op, double *ex_hartree) {

@@ -110,6 +110,20 @@ cudaError_t launch_tc_gram(const float *X, int nx, const float *Y, int ny, long 
 cudaError_t launch_tc_left_mul(const float *A, int m, int n, const float *Y, long long K, float *Z, int *err,
                                cudaStream_t st);
 
+// SCDM localisation (scdm.cu).  launch_scdm selects the n grid columns and computes the Loewdin
+// factor; every output lives in the workspace `ws` (scdm_workspace_bytes, 256-byte aligned).
+struct ScdmResult {
+  int *piv;     // [n] selected grid indices, in selection order
+  double *U;    // [n][n] FP64, phi_k = sum_i psi_i U[i][k]
+  void *Ut;     // [n][n] U^T in the working type: the left factor of Phi = U^T Psi
+  double *dev;  // [scdm_max_iterations()] max |T - I| of each Newton-Schulz iteration, 0 once skipped
+  int *dependent;  // 1 if a chosen column lay in the span of the earlier ones (Psi of rank < n)
+};
+int scdm_max_iterations();
+size_t scdm_workspace_bytes(int n, long long N, size_t elem);
+template <typename T>
+cudaError_t launch_scdm(const T *psi, int n, long long N, void *ws, cudaStream_t st, long *launches, ScdmResult *res);
+
 // Sets the message returned by ace_last_error() on this thread.
 void set_last_error(const char *msg);
 

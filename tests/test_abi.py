@@ -64,6 +64,12 @@ def test_host_side_checks_without_gpu(lib):
     h = ctypes.c_void_p()
     assert lib.ace_build(None, None, 0, None, ctypes.byref(h)) == ace.ACE_ERR_ARG
     lib.ace_destroy(None)  # no-op
+    # SCDM: orbital count, point count (at least one per orbital) and precision are checked first
+    a = np.zeros((4, 3), np.float32)
+    for n, npts, prec in ((0, 3, ace.ACE_MIXED), (1025, 4096, ace.ACE_MIXED), (4, 3, ace.ACE_MIXED), (4, 8, 7)):
+        st = ace.load().ace_scdm(n, npts, prec, a.ctypes.data, ace.ACE_F32, a.ctypes.data, None, None, None, None)
+        assert st == ace.ACE_ERR_ARG, (n, npts, prec)
+    assert "norb" in ace.ace_last_error() or "precision" in ace.ace_last_error()
 
 
 def test_product_path_does_not_import_oracle():

@@ -123,6 +123,14 @@ def random_orthogonal(n: int, rng: np.random.Generator) -> np.ndarray:
     return Q * np.sign(np.diag(R))[None, :]
 
 
+def delocalised(phi: np.ndarray, seed: int) -> np.ndarray:
+    """Canonical-like (delocalised) orbitals with the span of phi: Q phi with Q a seeded Haar-random
+    orthogonal matrix, the input of a localisation step."""
+    n = phi.shape[0]
+    Q = random_orthogonal(n, np.random.default_rng(seed))
+    return np.tensordot(Q, phi, axes=(1, 0))
+
+
 def _random_rotation(rng: np.random.Generator) -> np.ndarray:
     Q = random_orthogonal(3, rng)
     if np.linalg.det(Q) < 0:
