@@ -135,7 +135,7 @@ ace_status ace_apply(const ace_op *op, const void *psi, ace_dtype dtype, int m, 
  *   piv_host: optional host int32 [norb] receiving c_0..c_{n-1}; u_host: optional host double
  *         [norb][norb] receiving U; launches: optional, the number of this library's kernels run.
  *   prec: ACE_FP64 every step in FP64.  ACE_MIXED: psi in FP32, residual norms in FP64 with the
- *         projections u_k . psi(r) summed as FP32 products in 16-term FP32 partials; M, U and
+ *         projections u_k . psi(r) summed as FP32 products in 8-term FP32 partials; M, U and
  *         (M^T M)^{-1/2} (coupled Newton-Schulz) in FP64; Phi = U^T Psi by BF16x3 tensor-core
  *         products (FP32-level).  Near-equal residuals may then select another, equally valid,
  *         point than FP64 arithmetic would.
