@@ -61,8 +61,9 @@ typedef enum {
 typedef enum {
   ACE_FP64 = 0,  /* plain form: every step in double precision                                 */
   ACE_MIXED = 1  /* mixed form: FP32 pair densities/FFTs/kernel multiply/accumulation,
-                    BF16x3 split products (FP32 accumulate within 256-point chunks, FP64 across)
-                    for Phi^T W, xi^T psi and xi C; M, Cholesky, L^-1 and E_x in FP64            */
+                    BF16x3 split products (FP32 accumulate within 256-point chunks, FP64
+                    across) for the screen |Phi| |Phi|^T, Phi^T W, xi^T psi and xi C; M,
+                    Cholesky, L^-1 and E_x in FP64                                               */
 } ace_precision;
 
 typedef enum { ACE_F32 = 0, ACE_F64 = 1 } ace_dtype;

@@ -734,14 +734,22 @@ cudaError_t dense_left_mul(const T *A, int m, int n, const T *Y, long long K, T 
 }
 
 // Screen contribution of the columns [c0, c0 + K) of phi into O (accumulating; O zeroed by the
-// caller): the TMA-fed FP32 kernel where it applies, else the register-staged kernels.
+// caller; only the upper triangle is used): the tensor-core Gram of |phi| where it applies (ws of
+// ace::tc_screen_workspace_bytes, non-null), else the TMA-fed FP32 kernel, else the
+// register-staged kernels.
 template <typename T>
 cudaError_t screen_cols(const T *phi, int n, long long ld, long long c0, long long K, double dV, double *O, int *err,
-                        cudaStream_t st) {
+                        void *ws, cudaStream_t st, long *launches) {
   if constexpr (sizeof(T) == 4) {
+    cudaError_t e = cudaSuccess;
+    if (ws && use_tc() && env_int("ACE_NO_TC_SCREEN", 0) == 0 &&
+        ace::launch_tc_screen(phi, n, ld, c0, K, dV, O, ws, err, st, launches, &e))
+      return e;
+    ++*launches;
     if (ace::launch_screen_tma(phi, n, ld, c0, K, dV, O, err, st)) return cudaGetLastError();
     return ace::launch_screen_cols(phi + c0, n, ld, K, dV, O, st);
   } else {
+    ++*launches;
     if (c0 != 0 || K != ld) return cudaErrorInvalidValue;
     return ace::launch_gram<T>(phi, n, phi, n, K, dV, true, true, O, st);  // clears O itself
   }
@@ -817,6 +825,12 @@ ace_status build_begin(ace_op *op, const void *phi_in, ace_dtype dtype) {
     ACE_CUDA(cudaEventRecord(op->ev[1], st), "event record");
     return ACE_OK;
   }
+  // workspace of the tensor-core screen (FP64 partial sums of its K-splits; sized for the whole N)
+  void *screen_ws = nullptr;
+  if constexpr (sizeof(T) == 4) {
+    const size_t wsb = d.rho_cut > 0.0 ? ace::tc_screen_workspace_bytes(phi, n, N - N % 32) : 0;
+    if (wsb) ACE_CUDA(op_alloc(op, &screen_ws, wsb), "alloc screen workspace");
+  }
   if (pipelined) {
     ACE_CUDA(cudaMemsetAsync(op->O, 0, sizeof(double) * n * n, st), "zero O");
     cudaStream_t cs;
@@ -836,13 +850,11 @@ ace_status build_begin(ace_op *op, const void *phi_in, ace_dtype dtype) {
       ACE_CUDA(cudaEventRecord(ev, cs), "event");
       ACE_CUDA(cudaStreamWaitEvent(st, ev, 0), "wait");
       cudaEventDestroy(ev);
-      ACE_CUDA(screen_cols<T>(phi, n, N, c0, wc, op->dV, op->O, op->tc_err, st), "screen");
-      ++op->launches;
+      ACE_CUDA(screen_cols<T>(phi, n, N, c0, wc, op->dV, op->O, op->tc_err, screen_ws, st, &op->launches), "screen");
     }
   } else if (d.rho_cut > 0.0) {
     ACE_CUDA(cudaMemsetAsync(op->O, 0, sizeof(double) * n * n, st), "zero O");
-    ACE_CUDA(screen_cols<T>(phi, n, N, 0, N, op->dV, op->O, op->tc_err, st), "screen");
-    ++op->launches;
+    ACE_CUDA(screen_cols<T>(phi, n, N, 0, N, op->dV, op->O, op->tc_err, screen_ws, st, &op->launches), "screen");
   } else {
     ACE_CUDA(cudaMemsetAsync(op->O, 0, sizeof(double) * n * n, st), "screen skip");
   }

@@ -109,6 +109,13 @@ cudaError_t launch_tc_gram(const float *X, int nx, const float *Y, int ny, long 
                            void *ws, int *err, cudaStream_t st, long *launches);
 cudaError_t launch_tc_left_mul(const float *A, int m, int n, const float *Y, long long K, float *Z, int *err,
                                cudaStream_t st);
+// Screen contribution of the columns [c0, c0 + K) of phi (n rows of ld points) on the tensor cores:
+// G += scale |X| |X|^T (the whole n x n matrix), BF16x3 products as in the Gram.  ws holds
+// tc_screen_workspace_bytes (0: the plan does not apply).  false: nothing launched (no TMA map for
+// these operands); true: launched, *e the launch status.
+size_t tc_screen_workspace_bytes(const float *X, int n, long long K);
+bool launch_tc_screen(const float *X, int n, long long ld, long long c0, long long K, double scale, double *G,
+                      void *ws, int *err, cudaStream_t st, long *launches, cudaError_t *e);
 
 // SCDM localisation (scdm.cu).  launch_scdm selects the n grid columns and computes the Loewdin
 // factor; every output lives in the workspace `ws` (scdm_workspace_bytes, 256-byte aligned).

@@ -731,9 +731,10 @@ __global__ void __launch_bounds__(NT2, 1) tc_left_mul_tma_kernel(const float *__
 // ----------------------------------------------------------------------------------------
 constexpr uint32_t kGBox = BM * BK * 4;  // 128 rows x 32 FP32
 
+template <bool ABS>
 __global__ void __launch_bounds__(NT2, 1) tc_gram_tma_kernel(const __grid_constant__ CUtensorMap tmX,
                                                             const __grid_constant__ CUtensorMap tmY, int nx, int ny,
-                                                            long long K, int cs, int tiles_x, int ring,
+                                                            long long c0, long long K, int cs, int tiles_x, int ring,
                                                             double *__restrict__ partial, int *__restrict__ err) {
   extern __shared__ unsigned char dyn[];
   unsigned char *base = align1024(dyn);
@@ -747,6 +748,9 @@ __global__ void __launch_bounds__(NT2, 1) tc_gram_tma_kernel(const __grid_consta
   const int quarter = warp & 3, half = warp >> 2;  // TMEM lane quarter; operand / column half
   const int ti = blockIdx.x % tiles_x, tj = blockIdx.x / tiles_x;
   const int i0 = ti * BM, j0 = tj * BN;
+  // X and Y are the same matrix (the screen) and this tile is on the diagonal: one box per K-step
+  // serves both operands
+  const bool diag = ABS && ti == tj;
   // this split's K-steps: whole chunks [c_lo, c_hi) of cs steps (the last chunk may be short)
   const long long KS = K / BK, C = (KS + cs - 1) / cs;
   const long long c_lo = (long long)blockIdx.y * C / gridDim.y, c_hi = (long long)(blockIdx.y + 1) * C / gridDim.y;
@@ -768,9 +772,9 @@ __global__ void __launch_bounds__(NT2, 1) tc_gram_tma_kernel(const __grid_consta
   auto issue_next = [&]() {  // thread 0: K-step p_ks into stage p_stage
     const uint32_t mb = smem_u32(&full[p_stage]);
     unsigned char *bx = boxes + (size_t)p_stage * 2 * kGBox;
-    mbar_expect_tx(mb, 2 * kGBox);
-    tma_load_2d(smem_u32(bx), &tmX, (int)(p_ks * BK), i0, mb);
-    tma_load_2d(smem_u32(bx + kGBox), &tmY, (int)(p_ks * BK), j0, mb);
+    mbar_expect_tx(mb, diag ? kGBox : 2 * kGBox);
+    tma_load_2d(smem_u32(bx), &tmX, (int)(c0 + p_ks * BK), i0, mb);
+    if (!diag) tma_load_2d(smem_u32(bx + kGBox), &tmY, (int)(c0 + p_ks * BK), j0, mb);
     if (++p_stage == ring) p_stage = 0;
     ++p_ks;
   };
@@ -837,16 +841,16 @@ __global__ void __launch_bounds__(NT2, 1) tc_gram_tma_kernel(const __grid_consta
       // warps 0-3 split X, warps 4-7 split Y: row `row` of the box, whose 16-byte chunk k4 sits
       // at position k4 ^ (row & 7) (128-byte swizzle)
       const int row = tid & 127;
-      const unsigned char *rowp = boxes + (size_t)stage * 2 * kGBox + (size_t)half * kGBox + row * 128;
+      const unsigned char *rowp = boxes + (size_t)stage * 2 * kGBox + (size_t)(diag ? 0 : half) * kGBox + row * 128;
       unsigned char *ob = ops + (size_t)b * 4 * TILE_BYTES + (size_t)half * 2 * TILE_BYTES;
       Row32 r;
 #pragma unroll
       for (int k4 = 0; k4 < 8; ++k4) {
         const float4 t = *reinterpret_cast<const float4 *>(rowp + ((k4 ^ (row & 7)) << 4));
-        r.v[4 * k4] = t.x;
-        r.v[4 * k4 + 1] = t.y;
-        r.v[4 * k4 + 2] = t.z;
-        r.v[4 * k4 + 3] = t.w;
+        r.v[4 * k4] = ABS ? fabsf(t.x) : t.x;
+        r.v[4 * k4 + 1] = ABS ? fabsf(t.y) : t.y;
+        r.v[4 * k4 + 2] = ABS ? fabsf(t.z) : t.z;
+        r.v[4 * k4 + 3] = ABS ? fabsf(t.w) : t.w;
       }
       store_row(r, row, ob, ob + TILE_BYTES);
     }
@@ -919,14 +923,15 @@ __global__ void __launch_bounds__(NT2, 1) tc_gram_tma_kernel(const __grid_consta
   if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
-// G = scale * sum over the splits of partial[s] (FP64, fixed order)
+// G = scale * sum over the splits of partial[s] (FP64, fixed order); with `accumulate` the sum is
+// added to G instead
 __global__ void gram_splits_reduce_kernel(const double *__restrict__ partial, int splits, int ne, double scale,
-                                          double *__restrict__ G) {
+                                          bool accumulate, double *__restrict__ G) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
   double s = 0.0;
   for (int k = 0; k < splits; ++k) s += partial[(long long)k * ne + e];
-  G[e] = scale * s;
+  G[e] = (accumulate ? G[e] : 0.0) + scale * s;
 }
 
 // ----------------------------------------------------------------------------------------
@@ -1108,11 +1113,12 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // 2D map of a row-major FP32 matrix [rows][cols] with boxes of box_rows x box_cols; false when
 // the encoder is unavailable or refuses the layout (base 16-byte aligned, cols % 4 == 0)
 static bool make_map_f32(CUtensorMap *map, const float *ptr, long long rows, long long cols, int box_rows,
-                         int box_cols, bool swizzle128) {
+                         int box_cols, bool swizzle128, long long ld = 0) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc || (reinterpret_cast<uintptr_t>(ptr) & 15) || (cols & 3)) return false;
+  if (ld == 0) ld = cols;  // row stride in elements
+  if (!enc || (reinterpret_cast<uintptr_t>(ptr) & 15) || (cols & 3) || (ld & 3) || ld < cols) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
   const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box, estr,
@@ -1187,27 +1193,48 @@ size_t tc_gram_workspace_bytes(const float *X, int nx, const float *Y, int ny, l
   return gram_chunks_workspace_bytes(nx, ny, K);
 }
 
-cudaError_t launch_tc_gram(const float *X, int nx, const float *Y, int ny, long long K, double scale, double *G,
-                           void *ws, int *err, cudaStream_t st, long *launches) {
+// The TMA Gram over the columns [c0, c0 + K) of X and Y (rows of ld elements): G = scale X Y^T,
+// or G += scale |X| |Y|^T with ABS; false (nothing launched) when the plan or the maps fail.
+template <bool ABS>
+static bool launch_gram_tma(const float *X, int nx, const float *Y, int ny, long long ld, long long c0, long long K,
+                            double scale, double *G, void *ws, int *err, cudaStream_t st, long *launches,
+                            cudaError_t *e) {
   GramPlan p;
   CUtensorMap mx, my;
-  if (gram_tma_plan(X, nx, Y, ny, K, &p) && make_map_f32(&mx, X, nx, K, tc::BM, tc::BK, true) &&
-      make_map_f32(&my, Y, ny, K, tc::BN, tc::BK, true)) {
-    const int smem = (int)(8 * (size_t)tc::TILE_BYTES + (size_t)p.ring * 2 * tc::kGBox + 1024 + 256);
-    cudaError_t e = cudaFuncSetAttribute(tc::tc_gram_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    double *partial = static_cast<double *>(ws);
-    tc::tc_gram_tma_kernel<<<dim3(p.tiles, p.splits), tc::NT2, smem, st>>>(mx, my, nx, ny, K, tc_chunk() / tc::BK,
-                                                                          p.tiles_x, p.ring, partial, err);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const int n = nx * ny;
-    tc::gram_splits_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(partial, p.splits, n, scale, G);
-    *launches += 2;
-    return cudaGetLastError();
-  }
+  if (c0 % 4 != 0 || !gram_tma_plan(X, nx, Y, ny, K, &p) || !make_map_f32(&mx, X, nx, ld, tc::BM, tc::BK, true) ||
+      !make_map_f32(&my, Y, ny, ld, tc::BN, tc::BK, true))
+    return false;
+  const int smem = (int)(8 * (size_t)tc::TILE_BYTES + (size_t)p.ring * 2 * tc::kGBox + 1024 + 256);
+  *e = cudaFuncSetAttribute(tc::tc_gram_tma_kernel<ABS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (*e != cudaSuccess) return true;
+  double *partial = static_cast<double *>(ws);
+  tc::tc_gram_tma_kernel<ABS><<<dim3(p.tiles, p.splits), tc::NT2, smem, st>>>(
+      mx, my, nx, ny, c0, K, tc_chunk() / tc::BK, p.tiles_x, p.ring, partial, err);
+  *e = cudaGetLastError();
+  if (*e != cudaSuccess) return true;
+  const int n = nx * ny;
+  tc::gram_splits_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(partial, p.splits, n, scale, ABS, G);
+  *launches += 2;
+  *e = cudaGetLastError();
+  return true;
+}
+
+cudaError_t launch_tc_gram(const float *X, int nx, const float *Y, int ny, long long K, double scale, double *G,
+                           void *ws, int *err, cudaStream_t st, long *launches) {
+  cudaError_t e = cudaSuccess;
+  if (launch_gram_tma<false>(X, nx, Y, ny, K, 0, K, scale, G, ws, err, st, launches, &e)) return e;
   *launches += 3;
   return launch_tc_gram_chunks(X, nx, Y, ny, K, scale, G, static_cast<float *>(ws), err, st);
+}
+
+size_t tc_screen_workspace_bytes(const float *X, int n, long long K) {
+  GramPlan p;
+  return gram_tma_plan(X, n, X, n, K, &p) ? sizeof(double) * (size_t)p.splits * n * n : 0;
+}
+
+bool launch_tc_screen(const float *X, int n, long long ld, long long c0, long long K, double scale, double *G,
+                      void *ws, int *err, cudaStream_t st, long *launches, cudaError_t *e) {
+  return launch_gram_tma<true>(X, n, X, n, ld, c0, K, scale, G, ws, err, st, launches, e);
 }
 
 // Screen contribution of the columns [c0, c0 + K) of phi (n rows of ld points) through TMA; false

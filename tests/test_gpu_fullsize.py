@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import paper_2101_03155_gb300 as ace
-from gpu_helpers import FP64_EX_TOL, MIXED_EX_TOL_PER_ORB, MIXED_W_RTOL, gpu_build, rel_max
+from gpu_helpers import FP64_EX_TOL, MIXED_EX_TOL_PER_ORB, MIXED_W_RTOL, gpu_build, rel_max, screen_band
 from workloads.generators import config2, config3, config5
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -48,7 +48,7 @@ def test_water32_full_size(prec):
     assert g["status"] == 0
     gold = json.load(open(GOLDEN))["water32_128orb_96c_rhocut1e-3"]
     O_ref, mask_ref = oracle.screen(w.phi, w.lattice, w.rho_cut)
-    band = np.abs(O_ref - w.rho_cut) < 1e-6 * w.rho_cut
+    band = screen_band(O_ref, w.rho_cut, prec)
     assert np.array_equal(g["mask"] | band, mask_ref | band)
     if prec == ace.ACE_FP64:
         assert np.array_equal(g["mask"], mask_ref)
@@ -85,7 +85,7 @@ def test_enzyme_snapshot_isolated_cell_full_size(prec):
     assert g["status"] == 0
     gold = json.load(open(GOLDEN))["enzyme_snap0_isolated"]
     O_ref, mask_ref = oracle.screen(w.phi, w.lattice, w.rho_cut)
-    band = np.abs(O_ref - w.rho_cut) < 1e-6 * w.rho_cut
+    band = screen_band(O_ref, w.rho_cut, prec)
     assert np.array_equal(g["mask"] | band, mask_ref | band)
     if prec == ace.ACE_FP64:
         assert np.array_equal(g["mask"], mask_ref)

@@ -5,8 +5,8 @@ import pytest
 
 import oracle
 import paper_2101_03155_gb300 as ace
-from gpu_helpers import (FP64_ARRAY_RTOL, FP64_EX_TOL, MIXED_EX_TOL_PER_ORB, MIXED_KPHI_RTOL, MIXED_W_RTOL,
-                         gpu_build, rel_max)
+from gpu_helpers import (FP64_ARRAY_RTOL, FP64_EX_TOL, MIXED_EX_TOL_PER_ORB, MIXED_KPHI_RTOL, MIXED_SCREEN_RTOL,
+                         MIXED_W_RTOL, gpu_build, rel_max, screen_band)
 from workloads.generators import config1, gaussian_orbitals, loewdin, periodic_gaussian, water_like
 
 pytestmark = pytest.mark.gpu
@@ -140,10 +140,10 @@ def test_screen_and_screened_build(water_small, prec):
     w = water_small
     O_ref, mask_ref = oracle.screen(w.phi, w.lattice, w.rho_cut)
     g = gpu_build(w.phi, w.lattice, prec, rho_cut=w.rho_cut)
-    # screen values: FP64 accumulation of FP32 (mixed) or FP64 (plain) products
-    tol = 1e-12 if prec == ace.ACE_FP64 else 1e-6
+    # screen values: FP64 products (plain) or BF16x3 tensor-core products (mixed)
+    tol = 1e-12 if prec == ace.ACE_FP64 else MIXED_SCREEN_RTOL
     assert np.all(np.abs(g["O"] - O_ref) <= tol * O_ref + 1e-14)
-    band = np.abs(O_ref - w.rho_cut) < 1e-6 * w.rho_cut
+    band = screen_band(O_ref, w.rho_cut, prec)
     assert np.array_equal(g["mask"] | band, mask_ref | band)
     assert not g["mask"].all()  # the screen drops pairs here
     pairs = g["pairs"]
@@ -166,13 +166,13 @@ def test_screened_build_from_host_memory(water_small):
     dev = gpu_build(w.phi, w.lattice, ace.ACE_MIXED, rho_cut=w.rho_cut)
     host = gpu_build(w.phi, w.lattice, ace.ACE_MIXED, rho_cut=w.rho_cut, host=True)
     assert dev["status"] == 0 and host["status"] == 0
-    # the chunked screen sums the same FP32 products over other column splits
-    assert np.all(np.abs(host["O"] - dev["O"]) <= 1e-6 * np.abs(dev["O"]) + 1e-14)
-    band = np.abs(dev["O"] - w.rho_cut) < 1e-6 * w.rho_cut
+    # the chunked screen sums the same products over other column splits
+    assert np.all(np.abs(host["O"] - dev["O"]) <= MIXED_SCREEN_RTOL * np.abs(dev["O"]) + 1e-14)
+    band = screen_band(dev["O"], w.rho_cut, ace.ACE_MIXED)
     assert np.array_equal(host["mask"] | band, dev["mask"] | band)
     assert abs(host["E_x"] - dev["E_x"]) <= 0.1 * MIXED_EX_TOL_PER_ORB * w.norb  # FP32 atomics: order varies run to run
     O_ref, _ = oracle.screen(w.phi, w.lattice, w.rho_cut)
-    assert np.all(np.abs(host["O"] - O_ref) <= 1e-6 * O_ref + 1e-14)
+    assert np.all(np.abs(host["O"] - O_ref) <= MIXED_SCREEN_RTOL * O_ref + 1e-14)
 
 
 def test_odd_pair_count_and_single_orbital():
