@@ -733,6 +733,10 @@ cudaError_t dense_left_mul(const T *A, int m, int n, const T *Y, long long K, T 
   return ace::launch_left_mul<T>(A, m, n, Y, K, Z, st);
 }
 
+// Relative distance from rho_cut within which screen values are recomputed (twice the BF16x3
+// tensor-core bound of 3 * 2^-16 per product).
+constexpr double kScreenRefineBand = 1e-4;
+
 // Screen contribution of the columns [c0, c0 + K) of phi into O (accumulating; O zeroed by the
 // caller; only the upper triangle is used): the tensor-core Gram of |phi| where it applies (ws of
 // ace::tc_screen_workspace_bytes, non-null), else the TMA-fed FP32 kernel, else the
@@ -857,6 +861,13 @@ ace_status build_begin(ace_op *op, const void *phi_in, ace_dtype dtype) {
     ACE_CUDA(screen_cols<T>(phi, n, N, 0, N, op->dV, op->O, op->tc_err, screen_ws, st, &op->launches), "screen");
   } else {
     ACE_CUDA(cudaMemsetAsync(op->O, 0, sizeof(double) * n * n, st), "screen skip");
+  }
+  if constexpr (sizeof(T) == 4) {
+    // pair decisions within the tensor-core products' error of rho_cut are taken on recomputed values
+    if (d.rho_cut > 0.0) {
+      ACE_CUDA(ace::launch_screen_refine(phi, n, N, op->dV, d.rho_cut, kScreenRefineBand, op->O, st), "refine");
+      ++op->launches;
+    }
   }
   ACE_CUDA(ace::launch_screen_compact(op->O, n, d.rho_cut, op->pairs, op->packs, op->count_d, op->O_sym, st),
            "compact");

@@ -99,6 +99,10 @@ bool tc_shapes_ok(long long K);
 // Screen contribution of columns [0, K) of X (row stride ld): G += scale |X||X|^T, upper triangle.
 cudaError_t launch_screen_cols(const float *X, int n, long long ld, long long K, double scale, double *G,
                                cudaStream_t st);
+// Recompute the screen values within band * rho_cut of rho_cut from phi (n rows of N points) with
+// FP32 products and compensated sums (upper triangle, off-diagonal).
+cudaError_t launch_screen_refine(const float *phi, int n, long long N, double dV, double rho_cut, double band,
+                                 double *O, cudaStream_t st);
 // Screen contribution of the columns [c0, c0 + K) of phi (n rows of ld points) by the TMA-fed
 // kernel; false (nothing launched) when TMA cannot be used for these operands.
 bool launch_screen_tma(const float *X, int n, long long ld, long long c0, long long K, double scale, double *G,

@@ -10,6 +10,8 @@
 //   compact:   pair list of the screen (i <= j, sorted) and packs of two pairs.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cstdint>
 
 #include "ace_internal.h"
@@ -342,6 +344,54 @@ cudaError_t launch_screen_cols(const float *X, int n, long long ld, long long K,
   const long long chunks = (K + GS_CHUNK - 1) / GS_CHUNK;
   if (chunks > 65535) return cudaErrorInvalidValue;
   gram_sym_f32_kernel<true><<<dim3(nb * (nb + 1) / 2, (unsigned)chunks), GS_NT, 0, st>>>(X, n, ld, K, scale, G);
+  return cudaGetLastError();
+}
+
+// Screen values within band * rho_cut of the threshold, recomputed from phi so that the pair
+// decision does not rest on the tensor-core products (BF16x3: up to 3 * 2^-16 relative error per
+// product): O_ij = dV sum_r |phi_i(r) phi_j(r)| with FP32 products summed per thread with Kahan
+// compensation in FP32, then across the block's threads in FP64 in a fixed order.  Off-diagonal
+// upper-triangle entries only (the diagonal is always kept).  One block per candidate pair.
+constexpr int RF_NT = 256;
+__global__ void __launch_bounds__(RF_NT) screen_refine_kernel(const float *__restrict__ phi, int n, long long N,
+                                                              double dV, double rho_cut, double band,
+                                                              double *__restrict__ O) {
+  __shared__ double red[RF_NT / 32];
+  const long long ne = (long long)n * n;
+  for (long long e = blockIdx.x; e < ne; e += gridDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    if (i >= j) continue;
+    const double o = O[e];  // the same value for every thread: the branch is uniform
+    if (!(fabs(o - rho_cut) <= band * rho_cut)) continue;
+    const float *a = phi + (long long)i * N, *b = phi + (long long)j * N;
+    float sum = 0.f, comp = 0.f;
+    for (long long r = threadIdx.x; r < N; r += RF_NT) {
+      const float y = fabsf(a[r] * b[r]) - comp;
+      const float t = sum + y;
+      comp = (t - sum) - y;
+      sum = t;
+    }
+    double v = (double)sum - (double)comp;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < RF_NT / 32; ++w) t += red[w];
+      O[e] = dV * t;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_screen_refine(const float *phi, int n, long long N, double dV, double rho_cut, double band,
+                                 double *O, cudaStream_t st) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long ne = (long long)n * n;
+  const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(ne, 2LL * sms));
+  screen_refine_kernel<<<grid, RF_NT, 0, st>>>(phi, n, N, dV, rho_cut, band, O);
   return cudaGetLastError();
 }
 

@@ -14,15 +14,16 @@ MIXED_EX_TOL_PER_ORB = 1e-6
 MIXED_KPHI_RTOL = 1e-5
 MIXED_W_RTOL = 2e-5
 # mixed-form screen values O_ij = dV sum |phi_i||phi_j| (tensor-core BF16x3 products): each product
-# carries at most 3 * 2^-16 = 4.6e-5 relative error (hi*hi + hi*lo + lo*hi of bf16 halves); the same
-# bound is the band around rho_cut inside which the pair decision may differ from the oracle's
+# carries at most 3 * 2^-16 = 4.6e-5 relative error (hi*hi + hi*lo + lo*hi of bf16 halves).  Values
+# within 1e-4 of rho_cut are recomputed with FP32 products and compensated sums before the decision,
+# so decisions may differ from the oracle's only inside the band of 1e-6 rho_cut around rho_cut.
 MIXED_SCREEN_RTOL = 5e-5
+SCREEN_BAND_RTOL = 1e-6
 
 
-def screen_band(O_ref, rho_cut, prec):
-    """Pairs whose oracle screen value lies within the screen's error bound of rho_cut."""
-    rtol = 1e-12 if prec == ace.ACE_FP64 else MIXED_SCREEN_RTOL
-    return np.abs(O_ref - rho_cut) < max(rtol, 1e-6) * rho_cut
+def screen_band(O_ref, rho_cut, prec=None):
+    """Pairs whose oracle screen value lies within 1e-6 rho_cut of rho_cut (either decision holds)."""
+    return np.abs(O_ref - rho_cut) < SCREEN_BAND_RTOL * rho_cut
 
 
 def mask_from_pairs(pairs, n):

@@ -159,6 +159,27 @@ def test_screen_and_screened_build(water_small, prec):
         assert rel_max(g["W"].reshape(ref["W"].shape), ref["W"]) <= MIXED_W_RTOL
 
 
+@pytest.mark.parametrize("side", [+1, -1])
+def test_screen_decision_next_to_the_threshold(water_small, side):
+    """A threshold 3e-6 (relative) above or below a pair's oracle value: outside the 1e-6 band, so
+    the decision must be the oracle's although the tensor-core products alone could not take it;
+    the value of that pair comes back recomputed (FP32 products, compensated sums)."""
+    w = water_small
+    O_ref, _ = oracle.screen(w.phi, w.lattice, w.rho_cut)
+    iu = np.triu_indices(w.norb, 1)
+    k = int(np.argmin(np.abs(np.log(O_ref[iu] / 1e-3))))
+    i, j = int(iu[0][k]), int(iu[1][k])
+    rho = O_ref[i, j] * (1.0 + side * 3e-6)
+    g = gpu_build(w.phi, w.lattice, ace.ACE_MIXED, rho_cut=rho)
+    assert g["status"] == 0
+    assert g["mask"][i, j] == (O_ref[i, j] >= rho)
+    assert abs(g["O"][i, j] - O_ref[i, j]) <= 1e-6 * O_ref[i, j]
+    mask_ref = O_ref >= rho
+    np.fill_diagonal(mask_ref, True)
+    band = screen_band(O_ref, rho)
+    assert np.array_equal(g["mask"] | band, mask_ref | band)
+
+
 def test_screened_build_from_host_memory(water_small):
     """An FP32 host input of a screened build is copied in column chunks while the screen adds each
     chunk: the screen, the pair list and the build match the build from device memory."""
