@@ -8,11 +8,13 @@
 //              the ACE application out = -C^T xi (section II).
 //   cholesky:  M = (M_raw + M_raw^T)/2; -M = L L^T; L^-1; E_x = (f/2) tr M, all FP64 (App. A).
 //   compact:   pair list of the screen (i <= j, sorted) and packs of two pairs.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
 #include <cstdint>
+#include <cstdlib>
 
 #include "ace_internal.h"
 #include "f32x2.cuh"
@@ -635,8 +637,246 @@ __global__ void __launch_bounds__(CH_NT) cholesky_kernel(const double *__restric
   if (tid == 0) *status = 0;
 }
 
+// ----------------------------------------------------------------------------------------
+// The same factorisation on a cluster of CHC_C CTAs, for n <= CHC_MAX_N.  This GPU retires about
+// two FP64 FMA per clock per SM, so the one-CTA kernel above is bound by one SM's FP64 pipe; here
+// the trailing updates and the inverse are spread over CHC_C SMs.
+//   - Every CTA holds the whole symmetrised -M in shared memory (row stride lda = n | 1, odd, so
+//     that a column walk does not hit one bank).
+//   - Columns are dealt in panels of CHC_B, panel p owned by CTA p % CHC_C.  The owner factors its
+//     panel (right-looking inside the panel), a cluster barrier publishes it, every other CTA copies
+//     it from the owner's shared memory (distributed shared memory), and every CTA applies the
+//     panel's rank-CHC_B update to the columns it owns.  One cluster barrier per panel.
+//   - Afterwards every CTA holds all of L and computes its own columns of L^-1 by forward
+//     substitution (column-oriented, two CTA barriers per row).
+//   - A non-positive or non-finite pivot is announced to every CTA's flag before the barrier, so all
+//     CTAs leave the panel loop together; the outputs then carry the same status codes as above.
+// All waits are hardware barriers (CTA and cluster); no CTA reads another's shared memory after the
+// cluster barrier that follows the last panel.
+// ----------------------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+constexpr int CHC_NT = 256;
+constexpr int CHC_C = 8;
+constexpr int CHC_B = 8;
+constexpr int CHC_MAX_N = 128;
+constexpr int CHC_OWN = 16;  // columns a CTA owns at most: 128 / (8 x 8) panels of 8
+static_assert(CHC_MAX_N <= CHC_C * CHC_B * (CHC_OWN / CHC_B), "own columns per CTA");
+
+__global__ void __cluster_dims__(CHC_C, 1, 1) __launch_bounds__(CHC_NT)
+    cholesky_cluster_kernel(const double *__restrict__ M_raw, int n, double spin_factor, double *__restrict__ M,
+                            double *__restrict__ L, double *__restrict__ Linv, double *__restrict__ energy,
+                            int *__restrict__ status) {
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ double dyn[];
+  __shared__ int bad;   // non-finite input: set before the panel loop, the same in every CTA
+  __shared__ int pf;    // pivot failure met by this CTA while it factors its panel
+  __shared__ int fail;  // pivot failure of the panel's owner, written into every CTA before the
+                        // cluster barrier and read only after it
+  __shared__ int own[CHC_OWN];  // the columns this CTA owns, ascending (-1: none)
+  __shared__ double red[CHC_NT / 32];
+  __shared__ double piv[2];     // sqrt and reciprocal of the next pivot
+  __shared__ double col[CHC_MAX_N];
+  const int rank = (int)cluster.block_rank(), tid = threadIdx.x;
+  const int lda = n | 1;
+  double *A = dyn;                          // n x lda
+  double *X = dyn + (size_t)n * lda;        // n x CHC_OWN: own columns of L^-1
+  double *rinv = X + (size_t)n * CHC_OWN;   // n: 1 / L_kk
+  const int P = (n + CHC_B - 1) / CHC_B;
+  if (tid == 0) {
+    bad = 0;
+    pf = 0;
+    fail = 0;
+    int m = 0;
+    for (int p = rank; p < P; p += CHC_C)
+      for (int c = p * CHC_B; c < min(n, (p + 1) * CHC_B); ++c) own[m++] = c;
+    for (; m < CHC_OWN; ++m) own[m] = -1;
+  }
+  // -M symmetrised: a coalesced copy (eight loads in flight per thread), then each pair (i < j)
+  // averaged by one thread
+  for (int base = tid; base < n * n; base += 8 * CHC_NT) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + u * CHC_NT;
+      v[u] = e < n * n ? M_raw[e] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + u * CHC_NT;
+      if (e < n * n) A[(e / n) * lda + e % n] = v[u];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += CHC_NT) {
+    const int i = e / n, j = e % n;
+    if (i < j) {
+      const double v = 0.5 * (A[i * lda + j] + A[j * lda + i]);
+      A[i * lda + j] = -v;
+      A[j * lda + i] = -v;
+      if (!isfinite(v)) bad = 2000000;  // every CTA sees the same input
+    } else if (i == j) {
+      A[i * lda + i] = -A[i * lda + i];
+      if (!isfinite(A[i * lda + i])) bad = 2000000;
+    }
+  }
+  __syncthreads();
+  if (rank == 0) {
+    for (int e = tid; e < n * n; e += CHC_NT) M[e] = -A[(e / n) * lda + e % n];
+    double part = 0.0;
+    for (int k = tid; k < n; k += CHC_NT) part -= A[k * lda + k];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((tid & 31) == 0) red[tid >> 5] = part;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < CHC_NT / 32; ++w) t += red[w];
+      *energy = 0.5 * spin_factor * t;
+    }
+  }
+  cluster.sync();  // every CTA has started and cleared its flags before any shared-memory access across CTAs
+  const int lane16 = tid & 15, row16 = tid >> 4;  // (own column, row) lanes of the column-parallel loops
+  for (int p = 0; p < P; ++p) {
+    if (bad) break;  // set before the loop: every CTA leaves at the same point
+    const int c0 = p * CHC_B, c1 = min(n, c0 + CHC_B), w = c1 - c0, owner = p % CHC_C;
+    if (rank == owner) {
+      // right-looking inside the panel, two barriers per column; the thread that finishes the next
+      // diagonal element takes its reciprocal square root
+      if (tid == 0) {
+        const double d = A[c0 * lda + c0];
+        if (!(d > 0.0) || !isfinite(d)) pf = 1000000 + c0;
+        piv[1] = rsqrt(d);
+        piv[0] = d * piv[1];
+      }
+      __syncthreads();
+      for (int j = c0; j < c1 && !pf; ++j) {
+        const double ri = piv[1];
+        for (int i = j + 1 + tid; i < n; i += CHC_NT) {
+          const double l = A[i * lda + j] * ri;
+          A[i * lda + j] = l;
+          col[i] = l;
+        }
+        if (tid == 0) A[j * lda + j] = piv[0];
+        __syncthreads();
+        for (int i = j + 1 + tid; i < n; i += CHC_NT) {
+          const double li = col[i];
+          for (int k = j + 1; k < c1 && k <= i; ++k) {
+            const double v = A[i * lda + k] - li * col[k];
+            A[i * lda + k] = v;
+            if (i == k && k == j + 1) {  // the next pivot
+              if (!(v > 0.0) || !isfinite(v)) pf = 1000000 + k;
+              piv[1] = rsqrt(v);
+              piv[0] = v * piv[1];
+            }
+          }
+        }
+        __syncthreads();
+      }
+      if (pf && tid < CHC_C) *cluster.map_shared_rank(&fail, tid) = pf;
+    }
+    cluster.sync();  // panel p is final in its owner's shared memory (or the failure is announced)
+    if (fail) break;  // the same in every CTA after the barrier
+    if (rank != owner) {  // rows c0.. of the panel's columns from the owner, four loads in flight
+      const double *src = cluster.map_shared_rank(A, owner);
+      const int ne = (n - c0) * w;
+      for (int base = tid; base < ne; base += 4 * CHC_NT) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = base + u * CHC_NT;
+          v[u] = e < ne ? src[(c0 + e / w) * lda + c0 + e % w] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = base + u * CHC_NT;
+          if (e < ne) A[(c0 + e / w) * lda + c0 + e % w] = v[u];
+        }
+      }
+      __syncthreads();
+    }
+    // rank-w update of this CTA's columns k >= c1, rows i >= k: A_ik -= sum_j L_ij L_kj
+    {
+      const int k = own[lane16];
+      if (k >= c1)
+        for (int i = k + row16; i < n; i += CHC_NT / 16) {
+          double acc = 0.0;
+          for (int j = c0; j < c1; ++j) acc += A[i * lda + j] * A[k * lda + j];
+          A[i * lda + k] -= acc;
+        }
+    }
+    __syncthreads();
+  }
+  cluster.sync();  // no CTA reads another's shared memory past this point
+  if (bad || fail) {
+    if (rank == 0 && tid == 0) *status = bad ? bad : fail;
+    return;
+  }
+  // own columns of L^-1 by forward substitution, one barrier per row: at step k the rows i > k take
+  // X_ik -= L_ik X_kk.. and row k + 1, then final, is scaled by 1 / L_(k+1)(k+1)
+  for (int k = tid; k < n; k += CHC_NT) rinv[k] = 1.0 / A[k * lda + k];
+  for (int e = tid; e < n * CHC_OWN; e += CHC_NT) X[e] = 0.0;
+  __syncthreads();
+  if (tid < CHC_OWN && own[tid] >= 0) X[own[tid] * CHC_OWN + tid] = rinv[own[tid]];  // X_cc = 1 / L_cc
+  __syncthreads();
+  {
+    const int c = own[lane16];
+    for (int k = 0; k + 1 < n; ++k) {
+      if (c >= 0 && c <= k) {
+        const double xk = X[k * CHC_OWN + lane16];
+        for (int i = k + 1 + row16; i < n; i += CHC_NT / 16) {
+          double v = X[i * CHC_OWN + lane16] - A[i * lda + k] * xk;
+          if (i == k + 1) v *= rinv[i];
+          X[i * CHC_OWN + lane16] = v;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int e = tid; e < n * CHC_OWN; e += CHC_NT) {
+    const int i = e / CHC_OWN, cc = e % CHC_OWN, c = own[cc];
+    if (c < 0) continue;
+    L[(long long)i * n + c] = (i >= c) ? A[i * lda + c] : 0.0;
+    Linv[(long long)i * n + c] = (i >= c) ? X[i * CHC_OWN + cc] : 0.0;
+  }
+  if (rank == 0 && tid == 0) *status = 0;
+}
+
+static bool use_cluster_cholesky(int n) {
+  static const bool off = [] {
+    const char *v = std::getenv("ACE_CHOLESKY_ONE_CTA");
+    return v && *v && *v != '0';
+  }();
+  return !off && n <= CHC_MAX_N;
+}
+
 cudaError_t launch_cholesky(const double *M_raw, int n, double spin_factor, double *M, double *L, double *Linv,
                             double *energy, int *status, double *gwork, cudaStream_t st) {
+  if (use_cluster_cholesky(n)) {
+    // once per device: the shared-memory limit for the largest n, and whether such a cluster fits
+    static int ready[64] = {};  // 0 unknown, 1 usable, -1 not
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && ready[dev] == 0) {
+      const size_t smax = sizeof(double) * ((size_t)CHC_MAX_N * (CHC_MAX_N | 1) + (size_t)CHC_MAX_N * (CHC_OWN + 1));
+      cudaError_t e = cudaFuncSetAttribute(cholesky_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smax);
+      int clusters = 0;
+      if (e == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(CHC_C);
+        cfg.blockDim = dim3(CHC_NT);
+        cfg.dynamicSmemBytes = smax;
+        cfg.stream = st;
+        e = cudaOccupancyMaxActiveClusters(&clusters, cholesky_cluster_kernel, &cfg);
+      }
+      cudaGetLastError();
+      ready[dev] = (e == cudaSuccess && clusters > 0) ? 1 : -1;
+    }
+    if (dev >= 0 && dev < 64 && ready[dev] == 1) {
+      const size_t smem = sizeof(double) * ((size_t)n * (n | 1) + (size_t)n * (CHC_OWN + 1));
+      cholesky_cluster_kernel<<<CHC_C, CHC_NT, smem, st>>>(M_raw, n, spin_factor, M, L, Linv, energy, status);
+      return cudaGetLastError();
+    }
+  }
   const size_t smem = n <= CH_SMEM_MAX_N ? sizeof(double) * ((size_t)n * n + 4 * n) : 0;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -50,3 +50,40 @@ def test_fallback_kernels_match_oracle(tmp_path):
     kref = oracle.ace_apply(ref["xi"], psi.astype(np.float64), w.dV)
     got = np.load(out_file)
     assert np.linalg.norm(got - kref) <= MIXED_KPHI_RTOL * np.linalg.norm(kref)
+
+
+CHILD_CHOL = r"""
+import sys
+import numpy as np, torch
+sys.path.insert(0, {root!r})
+sys.path.insert(0, {tests!r})
+import paper_2101_03155_gb300 as ace
+from gpu_helpers import gpu_build
+from workloads.generators import water_like
+w = water_like(8, 11.74, (48, 48, 48), np.random.default_rng(1010), rho_cut=1e-3, dmin=4.0)
+g = gpu_build(w.phi, w.lattice, ace.ACE_FP64, rho_cut=w.rho_cut)
+np.savez(sys.argv[1], L=g["L"], M=g["M"], E=np.array(g["E_x"]))
+"""
+
+
+def test_one_cta_cholesky_matches_cluster_cholesky(tmp_path):
+    """The cluster Cholesky (default for n <= 128) and the one-CTA kernel (ACE_CHOLESKY_ONE_CTA=1)
+    factor the same M to FP64 rounding, and both L L^T = -M."""
+    outs = {}
+    for name, flag in (("cluster", "0"), ("one_cta", "1")):
+        f = tmp_path / f"{name}.npz"
+        env = dict(os.environ, ACE_CHOLESKY_ONE_CTA=flag)
+        r = subprocess.run([sys.executable, "-c", CHILD_CHOL.format(root=ROOT, tests=os.path.join(ROOT, "tests")),
+                            str(f)], env=env, capture_output=True, text=True, timeout=600, cwd=ROOT)
+        assert r.returncode == 0, r.stderr[-2000:]
+        outs[name] = np.load(f)
+    # the FP64 pair chain accumulates W with atomics, so M itself differs at the rounding level
+    # between the two runs: each factor is checked against LAPACK's factor of its own M
+    a, b = outs["cluster"], outs["one_cta"]
+    assert np.abs(a["M"] - b["M"]).max() <= 1e-13 * np.abs(b["M"]).max()
+    assert abs(float(a["E"]) - float(b["E"])) <= 1e-12 * abs(float(b["E"]))
+    for o in (a, b):
+        L = o["L"]
+        L_ref = np.linalg.cholesky(-o["M"])
+        assert np.abs(L - L_ref).max() <= 1e-12 * np.abs(L_ref).max()
+        assert np.all(np.triu(L, 1) == 0.0)
