@@ -35,6 +35,12 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_values.json")
 # of the current chain kernels with caches not flushed (profiles/pair_chain_plane_water32_96c.md);
 # set to None whenever those kernels change.
 CHAIN_DRAM_BYTES_PER_BUILD = 14.9e9
+# DRAM bytes (read + write) per launch of the dense tensor-core kernels of the same workload, one ncu
+# capture with caches not flushed (profiles/dense_tc_water32_96c.md); None once those kernels change
+DENSE_DRAM_BYTES = {"screen": 482.8e6, "M": 929.8e6, "xi": 897.9e6}
+# DRAM bytes per SCDM localisation of the 128-orbital 96^3 set: 128 selection passes at 436.1 MB
+# (ncu, profiles/scdm_water32_96c.md) + the left multiply Phi = U^T Psi (897.9 MB) + the transpose
+SCDM_DRAM_BYTES = 128 * 436.1e6 + 897.9e6 + 906e6
 
 
 def _peaks():
@@ -453,7 +459,7 @@ def run_scdm(args):
                       "same_pivots_as_mixed": bool(np.array_equal(res[ace.ACE_FP64]["piv"], mixed["piv"]))},
         "roofline": {"kernel": "whole ace_scdm call (n selection passes over Psi dominate)", "bound": "hbm",
                      "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                     "frac": achieved / peaks.get("hbm_gbs"), "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / peaks.get("hbm_gbs"), "traffic": SCDM_DRAM_BYTES, "peak_kind": peak_kind,
                      "algorithmic_bytes": f"n (4 n N + 16 N) + 8 n N = {alg:.4g} B per localisation"},
         "e2e": res["e2e"],
         "gpu_launches": mixed["launches"],
@@ -651,12 +657,13 @@ def run_ours(args):
                      "peak_kind": peak_kind,
                      "algorithmic_bytes": f"24 B x N x npairs = {alg_bytes:.4g} B per build"},
         # the dense contractions on the tensor cores are HBM-bound as well (intensity n/4 flop/B):
-        # M reads Phi and W, xi reads W and writes xi (FP32, n x N each)
+        # M reads Phi and W, xi reads W and writes xi (FP32, n x N each); the screen reads Phi once
         "dense_roofline": {
-            k: {"bound": "hbm", "achieved": 2 * 4 * n * N / (stage_mean[k] * 1e-3) / 1e9, "peak": peaks.get("hbm_gbs"),
-                "unit": "GB/s", "frac": 2 * 4 * n * N / (stage_mean[k] * 1e-3) / 1e9 / peaks.get("hbm_gbs"),
-                "algorithmic_bytes": f"2 x 4 B x n x N = {2 * 4 * n * N:.4g} B"}
-            for k in ("M", "xi")},
+            k: {"bound": "hbm", "achieved": nb * 4 * n * N / (stage_mean[k] * 1e-3) / 1e9, "peak": peaks.get("hbm_gbs"),
+                "unit": "GB/s", "frac": nb * 4 * n * N / (stage_mean[k] * 1e-3) / 1e9 / peaks.get("hbm_gbs"),
+                "traffic": DENSE_DRAM_BYTES.get(k),
+                "algorithmic_bytes": f"{nb} x 4 B x n x N = {nb * 4 * n * N:.4g} B"}
+            for k, nb in (("screen", 1), ("M", 2), ("xi", 2))},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n * N, "d2h_bytes_per_step": 16,
                 "steps": e2e_steps},
         "batched": {"value": batched_value, "unit": UNIT, "builds_per_call": batch_k, "calls": b_steps,
