@@ -900,9 +900,16 @@ __global__ void __launch_bounds__(CP_NT) compact_kernel(const double *__restrict
   __shared__ int running;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) running = 0;
-  for (int e = tid; e < n * n; e += CP_NT) {
-    const int i = e / n, j = e % n;
-    O_sym[e] = (i <= j) ? O[e] : O[(long long)j * n + i];
+  for (int base = tid; base < n * n; base += 4 * CP_NT) {  // four loads in flight per thread
+    double v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = base + u * CP_NT, i = e / n, j = e % n;
+      v[u] = e < n * n ? ((i <= j) ? O[e] : O[(long long)j * n + i]) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (base + u * CP_NT < n * n) O_sym[base + u * CP_NT] = v[u];
   }
   __syncthreads();
   const long long total = (long long)n * (n + 1) / 2;
@@ -911,10 +918,12 @@ __global__ void __launch_bounds__(CP_NT) compact_kernel(const double *__restrict
     int keep = 0, i = 0, j = 0;
     if (e < total) {
       // row-major enumeration of the upper triangle: row i holds n - i entries
-      // row i starts at s(i) = i (2n - i + 1) / 2; take the largest i with s(i) <= e
-      const double b = 2.0 * n + 1.0;
-      i = (int)((b - sqrt(b * b - 8.0 * (double)e)) * 0.5);
+      // row i starts at s(i) = i (2n - i + 1) / 2; take the largest i with s(i) <= e (an FP32
+      // estimate, made exact by the integer corrections below; FP64 is slow on this GPU)
+      const float b = 2.0f * (float)n + 1.0f;
+      i = (int)((b - sqrtf(fmaxf(b * b - 8.0f * (float)e, 0.0f))) * 0.5f);
       if (i < 0) i = 0;
+      if (i > n - 1) i = n - 1;
       while (i > 0 && (long long)i * (2 * n - i + 1) / 2 > e) --i;
       while ((long long)(i + 1) * (2 * n - i) / 2 <= e) ++i;
       j = i + (int)(e - (long long)i * (2 * n - i + 1) / 2);

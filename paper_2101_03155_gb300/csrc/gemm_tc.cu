@@ -930,6 +930,7 @@ __global__ void gram_splits_reduce_kernel(const double *__restrict__ partial, in
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
   double s = 0.0;
+#pragma unroll 8
   for (int k = 0; k < splits; ++k) s += partial[(long long)k * ne + e];
   G[e] = (accumulate ? G[e] : 0.0) + scale * s;
 }
@@ -1213,7 +1214,8 @@ static bool launch_gram_tma(const float *X, int nx, const float *Y, int ny, long
   *e = cudaGetLastError();
   if (*e != cudaSuccess) return true;
   const int n = nx * ny;
-  tc::gram_splits_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(partial, p.splits, n, scale, ABS, G);
+  // 64-thread blocks spread the FP64 adds (splits x n elements) over most SMs
+  tc::gram_splits_reduce_kernel<<<(n + 63) / 64, 64, 0, st>>>(partial, p.splits, n, scale, ABS, G);
   *launches += 2;
   *e = cudaGetLastError();
   return true;
