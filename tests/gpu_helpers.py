@@ -5,9 +5,12 @@ import numpy as np
 import paper_2101_03155_gb300 as ace
 from paper_2101_03155_gb300 import ace as abi
 
-# Tolerances (derivation in DESIGN.md, "Tolerances"):
-#   plain FP64 form: |dE_x| <= 1e-10 Ha; W, xi within 1e-10 of their max magnitude.
-#   mixed form:      |dE_x| <= 1e-6 Ha per orbital; ||K phi - K_oracle phi|| / ||K_oracle phi|| <= 1e-5.
+# Tolerances:
+#   plain FP64 form: |dE_x| <= 1e-10 Ha; W, xi within 1e-10 of their max magnitude (about 10 ulp of
+#                    FFT rounding growth over log2 N ~ 20 stages, with a wide margin).
+#   mixed form:      |dE_x| <= 1e-6 Ha per orbital; ||K phi - K_oracle phi|| / ||K_oracle phi|| <= 1e-5;
+#                    W within 2e-5 of its max magnitude (FP32 FFT rounding ~ 20 * 2^-24 * sqrt(N) plus
+#                    FP32 accumulation of up to ~40 pair contributions per row).
 FP64_EX_TOL = 1e-10
 FP64_ARRAY_RTOL = 1e-10
 MIXED_EX_TOL_PER_ORB = 1e-6
