@@ -373,3 +373,28 @@ def test_scdm_localises_rotated_gaussians(oracle_mod):
     off = ~np.eye(8, dtype=bool)
     assert O_phi[off].mean() < 0.5 * O_psi[off].mean()
     assert O_phi[off].mean() < 2.0 * O_loc[off].mean()
+
+
+def test_scdm_disjoint_orbitals_are_returned_unchanged(oracle_mod):
+    """Orbitals on disjoint sets of grid points: the residual norm at a point is |psi_i(r)|^2 of
+    the one orbital living there until that orbital's column is chosen, so the pivots are each
+    orbital's largest point (in decreasing order of those maxima); M is diagonal, U = diag(sign),
+    and the localized set is the input up to sign."""
+    rng = np.random.default_rng(17)
+    n, npts = 5, 400
+    owner = rng.permutation(np.arange(npts) % n)  # every point belongs to one orbital
+    psi = np.zeros((n, npts))
+    for i in range(n):
+        pts = np.flatnonzero(owner == i)
+        psi[i, pts] = rng.standard_normal(pts.size)
+        psi[i] /= np.linalg.norm(psi[i])
+    phi, piv = oracle_mod.scdm(psi, 1.0)
+    peaks = [int(np.argmax(np.abs(psi[i]))) for i in range(n)]
+    order = np.argsort([-np.abs(psi[i, peaks[i]]) for i in range(n)], kind="stable")
+    assert list(piv) == [peaks[i] for i in order]
+    _, U = oracle_mod.scdm_orthonormalise(psi, piv)
+    for col, i in enumerate(order):
+        s = np.sign(psi[i, peaks[i]])
+        assert abs(U[i, col] - s) <= 1e-14
+        assert np.abs(np.delete(U[:, col], i)).max() <= 1e-14
+        assert np.abs(phi[col] - s * psi[i]).max() <= 1e-14
