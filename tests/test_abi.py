@@ -106,3 +106,13 @@ def test_descriptor_layout_matches_header(tmp_path):
     out = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert out[0] == ctypes.sizeof(ace.AceDesc)
     assert out[1:] == [getattr(ace.AceDesc, f).offset for f in fields]
+
+
+def test_scdm_binding_checks_shapes_before_the_library():
+    """The Python binding of ace_scdm refuses mismatched input and output arrays itself."""
+    from paper_2101_03155_gb300 import ace
+
+    a = np.zeros((4, 64), np.float32)
+    for out in (np.zeros((4, 64), np.float64), np.zeros((4, 65), np.float32)):
+        with pytest.raises(ValueError):
+            ace.ace_scdm(a, out)
