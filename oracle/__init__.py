@@ -94,6 +94,9 @@ def _declare(lib):
     ]
     lib.oracle_ace_from_w.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_long, ctypes.c_double, _dp, _dp, _dp, _dp]
     lib.oracle_ace_apply.argtypes = [_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_long, ctypes.c_double, _dp]
+    _lp = ctypes.POINTER(ctypes.c_long)
+    lib.oracle_ace_apply_at.argtypes = [_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_long, ctypes.c_double, _lp,
+                                        ctypes.c_int, _dp, _dp]
     lib.oracle_exchange_energy.argtypes = [_dp, ctypes.c_int, ctypes.c_double]
     lib.oracle_scdm_select.argtypes = [_dp, ctypes.c_int, ctypes.c_long, ctypes.c_int, _ip]
     lib.oracle_exchange_energy.restype = ctypes.c_double
@@ -271,3 +274,19 @@ def scdm_orthonormalise(psi, piv):
     U = M @ (V * (1.0 / np.sqrt(w))) @ V.T
     phi = (U.T @ flat).reshape(psi.shape)
     return phi, U
+
+
+def ace_apply_at(xi, psi, dV: float, idx):
+    """K psi = -xi (dV xi^T psi) at the flat grid indices idx only.  Returns (C, out) with
+    C = dV xi^T psi (norb x m) and out (m x len(idx))."""
+    xi, psi = _f64(xi), _f64(psi)
+    n, m = xi.shape[0], psi.shape[0]
+    npts = int(np.prod(xi.shape[1:]))
+    ix = np.ascontiguousarray(idx, dtype=np.int64)
+    if ix.size and (ix.min() < 0 or ix.max() >= npts):
+        raise IndexError("grid index out of range")
+    C = np.empty((n, m))
+    out = np.empty((m, len(ix)))
+    _load().oracle_ace_apply_at(_ptr(xi), n, _ptr(psi), m, npts, float(dV), ix.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                                len(ix), _ptr(C), _ptr(out))
+    return C, out

@@ -417,10 +417,8 @@ int oracle_ace_from_w(const double *phi, const double *W, int norb, long npts, d
   return 0;
 }
 
-/* K psi = -xi (dV xi^T psi) (section II, ACE application).  xi [norb][npts], psi/out [m][npts]. */
-int oracle_ace_apply(const double *xi, int norb, const double *psi, int m, long npts, double dV,
-                     double *out) {
-  double *C = (double *)malloc((size_t)norb * m * sizeof(double));
+/* C = dV xi^T psi (norb x m), the projection that the ACE application multiplies back by -xi */
+static void ace_coefficients(const double *xi, int norb, const double *psi, int m, long npts, double dV, double *C) {
 #pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < norb; ++k)
     for (int c = 0; c < m; ++c) {
@@ -428,6 +426,13 @@ int oracle_ace_apply(const double *xi, int norb, const double *psi, int m, long 
       for (long r = 0; r < npts; ++r) s += xi[(long)k * npts + r] * psi[(long)c * npts + r];
       C[(long)k * m + c] = dV * s;
     }
+}
+
+/* K psi = -xi (dV xi^T psi) (section II, ACE application).  xi [norb][npts], psi/out [m][npts]. */
+int oracle_ace_apply(const double *xi, int norb, const double *psi, int m, long npts, double dV,
+                     double *out) {
+  double *C = (double *)malloc((size_t)norb * m * sizeof(double));
+  ace_coefficients(xi, norb, psi, m, npts, dV, C);
 #pragma omp parallel for schedule(static)
   for (int c = 0; c < m; ++c)
     for (long r = 0; r < npts; ++r) {
@@ -436,6 +441,21 @@ int oracle_ace_apply(const double *xi, int norb, const double *psi, int m, long 
       out[(long)c * npts + r] = -s;
     }
   free(C);
+  return 0;
+}
+
+/* The same application evaluated at nidx chosen grid points only: C = dV xi^T psi over the whole
+ * grid (norb x m, returned), then out[c][q] = -sum_k xi_k(idx[q]) C[k][c] (m x nidx). */
+int oracle_ace_apply_at(const double *xi, int norb, const double *psi, int m, long npts, double dV,
+                        const long *idx, int nidx, double *C, double *out) {
+  ace_coefficients(xi, norb, psi, m, npts, dV, C);
+#pragma omp parallel for schedule(static)
+  for (int c = 0; c < m; ++c)
+    for (int q = 0; q < nidx; ++q) {
+      double s = 0.0;
+      for (int k = 0; k < norb; ++k) s += xi[(long)k * npts + idx[q]] * C[(long)k * m + c];
+      out[(long)c * nidx + q] = -s;
+    }
   return 0;
 }
 

@@ -191,6 +191,28 @@ def test_apply_matches_library(oracle_mod, cfg1_build):
     assert np.abs(got.reshape(5, -1) - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+def test_apply_at_points_matches_library(oracle_mod, cfg1_build):
+    """The application evaluated at chosen points only (the form the stored full-size values use):
+    C = dV xi^T psi and -xi C at those points, from library matrix products; on the orbitals
+    themselves it gives -W_k at the points (App. A, K phi_k = V_X phi_k)."""
+    from workloads.generators import probe_vectors, sample_points
+
+    w, r = cfg1_build
+    X = r["xi"].reshape(w.norb, -1)
+    idx = sample_points(w.npts, 300, 11)
+    assert len(np.unique(idx)) == 300 and idx.min() >= 0 and idx.max() < w.npts
+    psi = probe_vectors(w.phi, w.dV, 3)
+    assert np.allclose(w.dV * np.sum(psi.reshape(2, -1) ** 2, axis=1), 1.0, rtol=1e-14)
+    C, out = oracle_mod.ace_apply_at(r["xi"], psi, w.dV, idx)
+    C_ref = w.dV * X @ psi.reshape(2, -1).T
+    assert np.abs(C - C_ref).max() <= 1e-13 * np.abs(C_ref).max()
+    ref = -(X[:, idx].T @ C_ref).T
+    assert np.abs(out - ref).max() <= 1e-13 * np.abs(ref).max()
+    _, kphi = oracle_mod.ace_apply_at(r["xi"], w.phi, w.dV, idx)
+    Wm = r["W"].reshape(w.norb, -1)[:, idx]
+    assert np.abs(kphi + Wm).max() <= 1e-12 * np.abs(Wm).max()
+
+
 def test_unitary_invariance(oracle_mod):
     """Eq. unit: a unitary mix of the occupied orbitals leaves E_x and the operator unchanged."""
     rng = np.random.default_rng(21)

@@ -349,6 +349,43 @@ def config3(seed: int = 1003, grid=(128, 128, 128), rho_cut=1e-3) -> Workload:
     return water_like(64, WATER_CELL_64, grid, rng, rho_cut=rho_cut, name="water64_256orb_128c")
 
 
+def config4(seed: int = 1004, builds=None):
+    """The 24 uneven builds of the batched configuration (or the ones listed in ``builds``): n from
+    {64, ..., 256}, N^3 from {72^3, ..., 128^3}, cells scaled to water density, rho_cut 1e-3."""
+    specs = batched_set(np.random.default_rng(seed))
+    out = []
+    for b in (range(len(specs)) if builds is None else builds):
+        n, N, cell, s = specs[b]
+        out.append(water_like(n // 4, cell, (N, N, N), np.random.default_rng(s), rho_cut=1e-3,
+                              name=f"water{n // 4}_{n}orb_{N}c"))
+    return out
+
+
 def config5(seed: int = 1005, nsnap: int = 8):
     rng = np.random.default_rng(seed)
     return enzyme_like(rng, nsnap=nsnap)
+
+
+# ----------------------------------------------------------------------------------------
+# Seeded probes for comparing whole-grid outputs at full size
+# ----------------------------------------------------------------------------------------
+
+
+def sample_points(npts: int, k: int, seed: int) -> np.ndarray:
+    """k distinct flat grid indices drawn uniformly (seeded), sorted."""
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(npts, size=min(k, npts), replace=False)).astype(np.int64)
+
+
+def probe_vectors(phi: np.ndarray, dV: float, seed: int) -> np.ndarray:
+    """Two seeded test vectors for the ACE application, shape (2,) + grid, each with dV sum psi^2 = 1:
+    psi_0 a random combination of the orbitals (inside their span), psi_1 white noise on the grid."""
+    rng = np.random.default_rng(seed)
+    n = phi.shape[0]
+    c = rng.standard_normal(n)
+    a = np.tensordot(c, phi, axes=(0, 0))
+    b = rng.standard_normal(phi.shape[1:])
+    out = np.stack([a, b])
+    for v in out:
+        v /= np.sqrt(dV * float((v * v).sum()))
+    return out
