@@ -734,21 +734,34 @@ cudaError_t dense_left_mul(const T *A, int m, int n, const T *Y, long long K, T 
 }
 
 // Relative distance from rho_cut within which screen values are recomputed (twice the BF16x3
-// tensor-core bound of 3 * 2^-16 per product).
+// tensor-core bound of 3 * 2^-16 per product, the opt-in tensor-core screen).
 constexpr double kScreenRefineBand = 1e-4;
 
+// The screen runs on the CUDA cores (FP32 products, FP64 across K-splits) unless ACE_TC_SCREEN=1
+// asks for the BF16x3 tensor-core Gram of |phi|.
+bool tc_screen_requested() { return use_tc() && env_int("ACE_TC_SCREEN", 0) != 0; }
+
+// Workspace of the FP32 screen of n orbitals over N points (0: none needed)
+size_t screen_workspace_bytes(const float *phi, int n, long long N) {
+  if (tc_screen_requested()) return ace::tc_screen_workspace_bytes(phi, n, N - N % 32);
+  return ace::screen_syrk_workspace_bytes(n, N);
+}
+
 // Screen contribution of the columns [c0, c0 + K) of phi into O (accumulating; O zeroed by the
-// caller; only the upper triangle is used): the tensor-core Gram of |phi| where it applies (ws of
-// ace::tc_screen_workspace_bytes, non-null), else the TMA-fed FP32 kernel, else the
-// register-staged kernels.
+// caller; only the upper triangle is used): the CUDA-core kernel of FP32 products and FP64 split
+// sums (ws of screen_workspace_bytes), or the tensor-core Gram of |phi| when requested; else the
+// TMA-fed 64 x 64 tile kernel, else the register-staged kernels.
 template <typename T>
 cudaError_t screen_cols(const T *phi, int n, long long ld, long long c0, long long K, double dV, double *O, int *err,
                         void *ws, cudaStream_t st, long *launches) {
   if constexpr (sizeof(T) == 4) {
     cudaError_t e = cudaSuccess;
-    if (ws && use_tc() && env_int("ACE_NO_TC_SCREEN", 0) == 0 &&
-        ace::launch_tc_screen(phi, n, ld, c0, K, dV, O, ws, err, st, launches, &e))
+    if (ws && tc_screen_requested()) {
+      if (ace::launch_tc_screen(phi, n, ld, c0, K, dV, O, ws, err, st, launches, &e)) return e;
+    } else if (ws && env_int("ACE_SCREEN_TILES", 0) == 0 &&
+               ace::launch_screen_syrk(phi, n, ld, c0, K, dV, O, ws, err, st, launches, &e)) {
       return e;
+    }
     ++*launches;
     if (ace::launch_screen_tma(phi, n, ld, c0, K, dV, O, err, st)) return cudaGetLastError();
     return ace::launch_screen_cols(phi + c0, n, ld, K, dV, O, st);
@@ -832,7 +845,7 @@ ace_status build_begin(ace_op *op, const void *phi_in, ace_dtype dtype) {
   // workspace of the tensor-core screen (FP64 partial sums of its K-splits; sized for the whole N)
   void *screen_ws = nullptr;
   if constexpr (sizeof(T) == 4) {
-    const size_t wsb = d.rho_cut > 0.0 ? ace::tc_screen_workspace_bytes(phi, n, N - N % 32) : 0;
+    const size_t wsb = d.rho_cut > 0.0 ? screen_workspace_bytes(phi, n, N) : 0;
     if (wsb) ACE_CUDA(op_alloc(op, &screen_ws, wsb), "alloc screen workspace");
   }
   if (pipelined) {

@@ -118,6 +118,13 @@ cudaError_t launch_tc_left_mul(const float *A, int m, int n, const float *Y, lon
 // tc_screen_workspace_bytes (0: the plan does not apply).  false: nothing launched (no TMA map for
 // these operands); true: launched, *e the launch status.
 size_t tc_screen_workspace_bytes(const float *X, int n, long long K);
+// Screen contribution of the columns [c0, c0 + K) of phi on the CUDA cores (FP32 products, FP64
+// across K-splits): G += scale |X| |X|^T on the upper triangle.  ws holds
+// screen_syrk_workspace_bytes(n, N) for any K <= N.  false: nothing launched (TMA cannot map phi);
+// true: launched, *e the launch status.
+size_t screen_syrk_workspace_bytes(int n, long long K);
+bool launch_screen_syrk(const float *X, int n, long long ld, long long c0, long long K, double scale, double *G,
+                        void *ws, int *err, cudaStream_t st, long *launches, cudaError_t *e);
 bool launch_tc_screen(const float *X, int n, long long ld, long long c0, long long K, double scale, double *G,
                       void *ws, int *err, cudaStream_t st, long *launches, cudaError_t *e);
 

@@ -1080,6 +1080,209 @@ __global__ void __launch_bounds__(NT2, 2) screen_tma_kernel(const __grid_constan
   }
 }
 
+
+// ----------------------------------------------------------------------------------------
+// Screen on the CUDA cores, the default of the mixed form (section II: O_ij = dV sum_r
+// |phi_i(r) phi_j(r)|, i <= j): FP32 products, FP32 partial sums over 64 grid points added into an
+// FP32 running sum per K-split, FP64 across the K-splits in a fixed order.
+//   - A 128 x 128 block pair (bi <= bj) of O is cut into 32 x 32 warp blocks.  A diagonal block
+//     pair is one work unit of the 10 warp blocks on or above its diagonal; an off-diagonal pair is
+//     two units (its row halves) of 8 warp blocks.  One CTA (10 warps) = one unit x one split.
+//   - Boxes of 128 rows x 32 points (128-byte swizzle) arrive by TMA through a ring; every thread
+//     replaces a share of the box by |phi| in place, then the warps multiply straight out of it.
+//   - Lane (ti, tj) = (lane / 8, lane % 8) owns rows ti + 4 rr (rr < 8) and columns tj + 8 cc
+//     (cc < 4) of its warp block.  Per four grid points it loads one 16-byte run of each of its 8
+//     rows and 4 columns (every such load of a warp touches distinct bank groups: its rows differ
+//     in their low three bits, which select the swizzled position) and issues 64 packed f32x2 FMAs,
+//     each multiplying two neighbouring grid points of one (row, column) pair.
+// ----------------------------------------------------------------------------------------
+constexpr int SY_NT = 320;
+constexpr int SY_RING = 5;
+constexpr int SY_FOLD = 2;                  // K-steps per FP32 partial (64 points)
+constexpr uint32_t kSyBox = 128 * BK * 4;   // 128 rows x 32 FP32 = 16 KB
+constexpr size_t kSySmem = (size_t)SY_RING * 2 * kSyBox + 64 + 1024;
+
+__global__ void __launch_bounds__(SY_NT, 1) screen_syrk_kernel(const __grid_constant__ CUtensorMap tmX, int n,
+                                                               long long c0, long long K, int ndiag,
+                                                               double *__restrict__ partial, int *__restrict__ err) {
+  extern __shared__ unsigned char dyn[];
+  unsigned char *boxes = align1024(dyn);  // ring x {row box, column box}
+  uint64_t *full = reinterpret_cast<uint64_t *>(boxes + (size_t)SY_RING * 2 * kSyBox);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // work unit -> block pair (bi, bj), row half h (off-diagonal units)
+  int bi, bj, h = 0;
+  const int u = blockIdx.x;
+  const bool diag = u < ndiag;
+  if (diag) {
+    bi = bj = u;
+  } else {
+    int t = (u - ndiag) >> 1;
+    h = (u - ndiag) & 1;
+    bi = 0;
+    while (t >= ndiag - 1 - bi) {
+      t -= ndiag - 1 - bi;
+      ++bi;
+    }
+    bj = bi + 1 + t;
+  }
+  // this warp's 32 x 32 block (I, J) of the block pair; warps 8, 9 of an off-diagonal unit only
+  // help with the |phi| pass
+  int I, J;
+  bool computes = true;
+  if (diag) {
+    // (0,0) (0,1) (0,2) (0,3) (1,1) (1,2) (1,3) (2,2) (2,3) (3,3)
+    I = warp < 4 ? 0 : (warp < 7 ? 1 : (warp < 9 ? 2 : 3));
+    J = warp < 4 ? warp : (warp < 7 ? warp - 3 : (warp < 9 ? warp - 5 : 3));
+  } else {
+    I = 2 * h + ((warp >> 2) & 1);
+    J = warp & 3;
+    computes = warp < 8;
+  }
+  const int ti = lane >> 3, tj = lane & 7;
+  const long long KS = (K + BK - 1) / BK;
+  const long long s_lo = (long long)blockIdx.y * KS / gridDim.y, s_hi = (long long)(blockIdx.y + 1) * KS / gridDim.y;
+  const int Q = (int)(s_hi - s_lo);
+  const int nbox = diag ? 1 : 2;
+  if (tid == 0) {
+    for (int r = 0; r < SY_RING; ++r) mbar_init(smem_u32(&full[r]));
+    mbar_init_fence();
+  }
+  __syncthreads();
+  auto issue = [&](int q) {  // box(es) of step s_lo + q into ring slot q % SY_RING
+    const int slot = q % SY_RING;
+    const uint32_t mb = smem_u32(&full[slot]);
+    unsigned char *bx = boxes + (size_t)slot * 2 * kSyBox;
+    const int x = (int)(c0 + (s_lo + q) * BK);
+    mbar_expect_tx(mb, nbox * kSyBox);
+    tma_load_2d(smem_u32(bx), &tmX, x, bi * 128, mb);
+    if (!diag) tma_load_2d(smem_u32(bx + kSyBox), &tmX, x, bj * 128, mb);
+  };
+  // |phi| in place over the slot's box(es); points at or past K (only in a ragged last step) read
+  // as zero.  Row r of a box holds its logical 16-byte run k4 at position k4 ^ (r & 7).
+  auto absolute = [&](int q) {
+    unsigned char *bx = boxes + (size_t)(q % SY_RING) * 2 * kSyBox;
+    const long long k0 = (s_lo + q) * BK;
+    const bool ragged = k0 + BK > K;
+    for (int e = tid; e < nbox * 1024; e += SY_NT) {
+      uint4 *p = reinterpret_cast<uint4 *>(bx) + e;
+      uint4 v = *p;
+      v.x &= 0x7fffffffu;
+      v.y &= 0x7fffffffu;
+      v.z &= 0x7fffffffu;
+      v.w &= 0x7fffffffu;
+      if (ragged) {
+        const int row = (e >> 3) & 127, k4 = (e & 7) ^ (row & 7);
+        const long long k = k0 + 4 * k4;
+        if (k >= K) v.x = 0u;
+        if (k + 1 >= K) v.y = 0u;
+        if (k + 2 >= K) v.z = 0u;
+        if (k + 3 >= K) v.w = 0u;
+      }
+      *p = v;
+    }
+    fence_async_smem();  // these generic writes come before the TMA that refills the slot
+  };
+  int issued = Q < SY_RING ? Q : SY_RING;
+  if (tid == 0)
+    for (int q = 0; q < issued; ++q) issue(q);
+  unsigned long long part[8][4];
+  float acc[8][4];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      part[r][c] = 0ull;
+      acc[r][c] = 0.f;
+    }
+  // byte offsets inside a box: the thread's rows ti + 4 p + 8 s (p = rr & 1, s = rr >> 1) and
+  // columns tj + 8 cc; the low three row bits (ti + 4 p, tj) pick the swizzled 16-byte position
+  const uint32_t arow0 = (uint32_t)(32 * I + ti) * 128u, arow1 = arow0 + 4u * 128u;
+  const uint32_t asw0 = (uint32_t)ti, asw1 = (uint32_t)(ti + 4);
+  const uint32_t brow = (uint32_t)(32 * J + tj) * 128u + (diag ? 0u : kSyBox), bsw = (uint32_t)tj;
+  bool ok = true;
+  int fail_from = 0;  // on a timeout: the first box that every thread has not seen complete
+  for (int q = 0; q < Q; ++q) {
+    const bool got = mbar_wait(smem_u32(&full[q % SY_RING]), (uint32_t)((q / SY_RING) & 1));
+    if (got) absolute(q);
+    if (__syncthreads_or(!got)) {
+      ok = false;
+      fail_from = q;
+      break;
+    }
+    // every thread is past its products of step q - 1: refill that slot
+    if (q > 0 && issued < Q) {
+      if (tid == 0) issue(issued);
+      ++issued;
+    }
+    if (computes) {
+      const unsigned char *bx = boxes + (size_t)(q % SY_RING) * 2 * kSyBox;
+#pragma unroll 2
+      for (int k4 = 0; k4 < 8; ++k4) {
+        const unsigned char *pa0 = bx + arow0 + (((uint32_t)k4 ^ asw0) << 4);
+        const unsigned char *pa1 = bx + arow1 + (((uint32_t)k4 ^ asw1) << 4);
+        const unsigned char *pb = bx + brow + (((uint32_t)k4 ^ bsw) << 4);
+        ulonglong2 b[4], a[8];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) b[c] = *reinterpret_cast<const ulonglong2 *>(pb + c * 1024);
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+          a[r] = *reinterpret_cast<const ulonglong2 *>(((r & 1) ? pa1 : pa0) + (r >> 1) * 1024);
+        // points (k, k + 1) of every (row, column) pair, then (k + 2, k + 3): 32 independent FMAs
+        // between two updates of one accumulator
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) part[r][c] = f2fma(a[r].x, b[c].x, part[r][c]);
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) part[r][c] = f2fma(a[r].y, b[c].y, part[r][c]);
+      }
+      if ((q + 1) % SY_FOLD == 0 || q + 1 == Q) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float2 v = f2up(part[r][c]);
+            acc[r][c] += v.x + v.y;
+            part[r][c] = 0ull;
+          }
+      }
+    }
+  }
+  if (!ok) {
+    // wait (bounded) for every box still in flight before the CTA's shared memory is released
+    for (int r = fail_from; r < issued; ++r) mbar_wait(smem_u32(&full[r % SY_RING]), (uint32_t)((r / SY_RING) & 1));
+    if (tid == 0) atomicExch(err, 1);
+    return;
+  }
+  if (computes) {
+    double *dst = partial + (long long)blockIdx.y * n * n;
+    const int i0 = bi * 128 + 32 * I + ti, j0 = bj * 128 + 32 * J + tj;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = i0 + 4 * r;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int j = j0 + 8 * c;
+        if (i < n && j < n && j >= i) dst[(long long)i * n + j] = (double)acc[r][c];
+      }
+    }
+  }
+}
+
+// O_ij += scale * sum over the splits of partial[s]_ij for i <= j (FP64, fixed order)
+__global__ void screen_splits_reduce_kernel(const double *__restrict__ partial, int splits, int n, double scale,
+                                            double *__restrict__ O) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * n || e % n < e / n) return;
+  const long long ne = (long long)n * n;
+  double s = 0.0;
+#pragma unroll 8
+  for (int k = 0; k < splits; ++k) s += partial[(long long)k * ne + e];
+  O[e] += scale * s;
+}
+
 }  // namespace tc
 
 bool tc_shapes_ok(long long K) { return K % tc::BN == 0 && K % tc::BK == 0; }
@@ -1261,6 +1464,51 @@ bool launch_screen_tma(const float *X, int n, long long ld, long long c0, long l
     return false;
   }
   tc::screen_tma_kernel<<<dim3(tiles, splits), tc::NT2, smem, st>>>(map, n, c0, K, scale, ring, G, err);
+  return true;
+}
+
+// Plan of the CUDA-core screen: work units (diagonal block pairs, then two per off-diagonal
+// pair) and K-splits so that units x splits fill the SMs once.
+static void screen_syrk_plan(int n, long long K, int *ndiag, int *units, int *splits) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  *ndiag = (n + 127) / 128;
+  *units = *ndiag + (*ndiag) * (*ndiag - 1);
+  const long long ks = std::max(1LL, (K + tc::BK - 1) / tc::BK);
+  *splits = (int)std::max(1LL, std::min(ks, (long long)std::max(1, sms / *units)));
+}
+
+size_t screen_syrk_workspace_bytes(int n, long long K) {
+  int nd, un, sp;
+  screen_syrk_plan(n, K, &nd, &un, &sp);
+  return sizeof(double) * (size_t)sp * n * n;
+}
+
+bool launch_screen_syrk(const float *X, int n, long long ld, long long c0, long long K, double scale, double *G,
+                        void *ws, int *err, cudaStream_t st, long *launches, cudaError_t *e) {
+  if (!use_tma() || c0 % 4 != 0 || K <= 0 || !ws) return false;
+  CUtensorMap map;
+  if (!make_map_f32(&map, X, n, ld, 128, tc::BK, true)) return false;
+  int ndiag, units, splits;
+  screen_syrk_plan(n, K, &ndiag, &units, &splits);
+  // the shared-memory limit is a per-device attribute of the kernel: set once per device
+  static unsigned long long attr_done = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(__atomic_load_n(&attr_done, __ATOMIC_ACQUIRE) & bit)) {
+    *e = cudaFuncSetAttribute(tc::screen_syrk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSySmem);
+    if (*e != cudaSuccess) return true;
+    __atomic_fetch_or(&attr_done, bit, __ATOMIC_RELEASE);
+  }
+  double *partial = static_cast<double *>(ws);
+  tc::screen_syrk_kernel<<<dim3(units, splits), tc::SY_NT, tc::kSySmem, st>>>(map, n, c0, K, ndiag, partial, err);
+  *e = cudaGetLastError();
+  if (*e != cudaSuccess) return true;
+  tc::screen_splits_reduce_kernel<<<(n * n + 63) / 64, 64, 0, st>>>(partial, splits, n, scale, G);
+  *launches += 2;
+  *e = cudaGetLastError();
   return true;
 }
 

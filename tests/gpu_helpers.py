@@ -16,11 +16,22 @@ FP64_ARRAY_RTOL = 1e-10
 MIXED_EX_TOL_PER_ORB = 1e-6
 MIXED_KPHI_RTOL = 1e-5
 MIXED_W_RTOL = 2e-5
-# mixed-form screen values O_ij = dV sum |phi_i||phi_j| (tensor-core BF16x3 products): each product
-# carries at most 3 * 2^-16 = 4.6e-5 relative error (hi*hi + hi*lo + lo*hi of bf16 halves).  Values
-# within 1e-4 of rho_cut are recomputed with FP32 products and compensated sums before the decision,
-# so decisions may differ from the oracle's only inside the band of 1e-6 rho_cut around rho_cut.
-MIXED_SCREEN_RTOL = 5e-5
+# mixed-form xi = L^-1 W (relative Frobenius norm over the sampled points): W carries up to 2e-5 of
+# its largest entry (above), L^-1 comes from the FP64 Cholesky of an M whose tensor-core products
+# carry up to 3 * 2^-16 = 4.6e-5 relative error, and the BF16x3 product L^-1 W adds as much again;
+# for the localized sets here cond(L) = sqrt(cond(M)) is a few units, so 1e-4 bounds the sum.
+MIXED_XI_RTOL = 1e-4
+# mixed-form screen values O_ij = dV sum |phi_i||phi_j| on the CUDA cores: FP32 products of the
+# FP32-rounded orbitals (input rounding 2^-24 per factor), FP32 partial sums over 64 points (at
+# most 63 u, typically ~sqrt(64/3) u with u = 2^-24), Kahan-compensated FP32 sums across them
+# (2 u) and FP64 across K-splits, whose independent rounding errors average out: 1e-6 relative
+# bounds every value with a wide margin over the ~1e-7 seen.  Decisions may differ from the
+# oracle's only inside the band of 1e-6 rho_cut around rho_cut (values within 1e-4 of rho_cut are
+# recomputed with FP32 products and compensated sums before the decision).
+MIXED_SCREEN_RTOL = 1e-6
+# the opt-in tensor-core screen (ACE_TC_SCREEN=1): BF16x3 products, each with at most
+# 3 * 2^-16 = 4.6e-5 relative error (hi*hi + hi*lo + lo*hi of bf16 halves)
+MIXED_TC_SCREEN_RTOL = 5e-5
 SCREEN_BAND_RTOL = 1e-6
 
 

@@ -6,7 +6,7 @@ import pytest
 import oracle
 import paper_2101_03155_gb300 as ace
 from gpu_helpers import (FP64_ARRAY_RTOL, FP64_EX_TOL, MIXED_EX_TOL_PER_ORB, MIXED_KPHI_RTOL, MIXED_SCREEN_RTOL,
-                         MIXED_W_RTOL, gpu_build, rel_max, screen_band)
+                         MIXED_TC_SCREEN_RTOL, MIXED_W_RTOL, gpu_build, rel_max, screen_band)
 from workloads.generators import config1, gaussian_orbitals, loewdin, periodic_gaussian, water_like
 
 pytestmark = pytest.mark.gpu
@@ -47,6 +47,25 @@ def test_fp64_pair_chain_and_build(grid):
     assert np.abs(g["L"] - ref["L"]).max() <= FP64_ARRAY_RTOL * np.abs(ref["L"]).max()
     assert rel_max(g["xi"].reshape(ref["xi"].shape), ref["xi"]) <= FP64_ARRAY_RTOL
     assert abs(g["E_x"] - ref["E_x"]) <= FP64_EX_TOL
+
+
+@pytest.mark.parametrize("prec", [ace.ACE_FP64, ace.ACE_MIXED])
+@pytest.mark.parametrize("n1", [72, 108])
+def test_batched_config_plane_shapes(n1, prec):
+    """The 72 x 72 and 108 x 108 planes of the uneven batched set (108^2 FP32 runs 768-thread plane
+    CTAs, two per SM): W, M and E_x against the oracle, all pairs."""
+    grid = (n1, n1, n1)
+    lat = np.diag([11.0, 11.5, 12.0])
+    phi = _small(grid, lat, 4, 2, seed=n1)
+    ref = oracle.ace_build(phi, lat, 0.0, 2.0)
+    g = gpu_build(phi, lat, prec)
+    assert g["status"] == 0
+    if prec == ace.ACE_FP64:
+        assert rel_max(g["W"].reshape(ref["W"].shape), ref["W"]) <= FP64_ARRAY_RTOL
+        assert abs(g["E_x"] - ref["E_x"]) <= FP64_EX_TOL
+    else:
+        assert rel_max(g["W"].reshape(ref["W"].shape), ref["W"]) <= MIXED_W_RTOL
+        assert abs(g["E_x"] - ref["E_x"]) <= MIXED_EX_TOL_PER_ORB * 4
 
 
 def test_fp64_triclinic():
@@ -140,7 +159,7 @@ def test_screen_and_screened_build(water_small, prec):
     w = water_small
     O_ref, mask_ref = oracle.screen(w.phi, w.lattice, w.rho_cut)
     g = gpu_build(w.phi, w.lattice, prec, rho_cut=w.rho_cut)
-    # screen values: FP64 products (plain) or BF16x3 tensor-core products (mixed)
+    # screen values: FP64 products (plain) or FP32 products with FP64 split sums (mixed)
     tol = 1e-12 if prec == ace.ACE_FP64 else MIXED_SCREEN_RTOL
     assert np.all(np.abs(g["O"] - O_ref) <= tol * O_ref + 1e-14)
     band = screen_band(O_ref, w.rho_cut, prec)
@@ -157,6 +176,37 @@ def test_screen_and_screened_build(water_small, prec):
     else:
         assert abs(g["E_x"] - ref["E_x"]) <= MIXED_EX_TOL_PER_ORB * w.norb
         assert rel_max(g["W"].reshape(ref["W"].shape), ref["W"]) <= MIXED_W_RTOL
+
+
+def test_screen_beyond_one_block():
+    """136 orbitals: two 128-row blocks (the second ragged), so the screen runs its diagonal units
+    and the two row halves of the off-diagonal block pair; values and decisions against the oracle."""
+    rng = np.random.default_rng(1013)
+    w = water_like(34, 18.63 * (34 / 32) ** (1 / 3), (24, 24, 24), rng, rho_cut=1e-3, dmin=4.4)
+    O_ref, mask_ref = oracle.screen(w.phi, w.lattice, w.rho_cut)
+    g = gpu_build(w.phi, w.lattice, ace.ACE_MIXED, rho_cut=w.rho_cut)
+    assert g["status"] == 0
+    iu = np.triu_indices(w.norb)
+    assert np.all(np.abs(g["O"][iu] - O_ref[iu]) <= MIXED_SCREEN_RTOL * O_ref[iu] + 1e-14)
+    band = screen_band(O_ref, w.rho_cut)
+    assert np.array_equal(g["mask"] | band, mask_ref | band)
+    assert 0 < len(g["pairs"]) < w.norb * (w.norb + 1) // 2
+
+
+def test_tensor_core_screen_on_request(water_small, monkeypatch):
+    """ACE_TC_SCREEN=1 takes the screen to the BF16x3 tensor-core Gram of |phi|: values within the
+    split products' bound, decisions the oracle's outside the band, the build unchanged."""
+    w = water_small
+    O_ref, mask_ref = oracle.screen(w.phi, w.lattice, w.rho_cut)
+    monkeypatch.setenv("ACE_TC_SCREEN", "1")
+    g = gpu_build(w.phi, w.lattice, ace.ACE_MIXED, rho_cut=w.rho_cut)
+    monkeypatch.delenv("ACE_TC_SCREEN")
+    assert g["status"] == 0
+    assert np.all(np.abs(g["O"] - O_ref) <= MIXED_TC_SCREEN_RTOL * O_ref + 1e-14)
+    band = screen_band(O_ref, w.rho_cut)
+    assert np.array_equal(g["mask"] | band, mask_ref | band)
+    d = gpu_build(w.phi, w.lattice, ace.ACE_MIXED, rho_cut=w.rho_cut)
+    assert abs(g["E_x"] - d["E_x"]) <= 0.1 * MIXED_EX_TOL_PER_ORB * w.norb
 
 
 @pytest.mark.parametrize("side", [+1, -1])
