@@ -400,6 +400,17 @@ cudaError_t get_side_stream(int dev, int k, cudaStream_t *out) {
 }
 
 template <typename T>
+bool find_persist_ops(int n1, int n2, int n3, ace::PersistOps<T> *out);
+template <>
+bool find_persist_ops<float>(int n1, int n2, int n3, ace::PersistOps<float> *out) {
+  return ace::persist_ops_f32_small(n1, n2, n3, out) || ace::persist_ops_f32_large(n1, n2, n3, out);
+}
+template <>
+bool find_persist_ops<double>(int, int, int, ace::PersistOps<double> *) {
+  return false;
+}
+
+template <typename T>
 bool find_plane_ops(int n2, int n3, ace::PlaneOps<T> *out);
 template <>
 bool find_plane_ops<float>(int n2, int n3, ace::PlaneOps<float> *out) {
@@ -521,6 +532,146 @@ ace_status run_chain_pencil(ace_op *op, const T *phi, const T *Kd, const cpx<T> 
   return ACE_OK;
 }
 
+// Marks [base, base + bytes) as persisting in L2 for work on stream st (a per-context set-aside of
+// at most mb MB, clamped to the device's limits); bytes = 0 turns the window off.  Failures only
+// lose the hint: their error state is cleared.
+void l2_window(cudaStream_t st, int dev, void *base, size_t bytes, int mb) {
+  cudaStreamAttrValue v{};
+  if (bytes > 0 && mb > 0) {
+    int max_persist = 0, max_window = 0;
+    cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
+    cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+    const size_t limit = std::min((size_t)mb << 20, (size_t)std::max(0, max_persist));
+    if (limit == 0 || max_window <= 0) return;
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, limit);
+    v.accessPolicyWindow.base_ptr = base;
+    v.accessPolicyWindow.num_bytes = std::min({bytes, limit, (size_t)max_window});
+    v.accessPolicyWindow.hitRatio = 1.0f;
+    v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+  }
+  cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &v);
+  cudaGetLastError();
+}
+
+// Packs of a sorted pair list: two pairs that share an orbital s, written (s, i1, s, i2), so that
+// both plane passes read three planes and the W_s terms of the pack go out with one atomic.  The
+// list is taken in blocks of RB consecutive rows; inside a block, pairs with the same partner j are
+// packed together first (phi_j and W_j are then reused while they are in L2, and the block's own
+// rows stay in L2 for the whole block), then the block's remaining pairs by common row (RB = 1 gives
+// the row packs (i, j1), (i, j2) only).  Single pairs left over are packed together at the end as
+// mixed packs.  Returns the number of packs that share their first orbital (they come first).
+int form_packs(const std::vector<int2> &pr, int RB, std::vector<int4> &packs) {
+  RB = std::max(1, RB);
+  packs.clear();
+  std::vector<int2> left;
+  std::vector<int2> bp, rest;
+  size_t r0 = 0;
+  while (r0 < pr.size()) {
+    const int blk = pr[r0].x / RB;
+    size_t r1 = r0;
+    while (r1 < pr.size() && pr[r1].x / RB == blk) ++r1;
+    bp.assign(pr.begin() + r0, pr.begin() + r1);
+    rest.clear();
+    if (RB > 1) {
+      std::stable_sort(bp.begin(), bp.end(), [](int2 u, int2 v) { return u.y < v.y; });
+      for (size_t k = 0; k < bp.size();) {
+        size_t k1 = k;
+        while (k1 < bp.size() && bp[k1].y == bp[k].y) ++k1;
+        const int j = bp[k].y;
+        size_t m = k;
+        for (; m + 1 < k1; m += 2) packs.push_back(make_int4(j, bp[m].x, j, bp[m + 1].x));
+        if (m < k1) rest.push_back(bp[m]);
+        k = k1;
+      }
+      std::sort(rest.begin(), rest.end(), [](int2 u, int2 v) { return u.x < v.x || (u.x == v.x && u.y < v.y); });
+    } else {
+      rest.swap(bp);
+    }
+    for (size_t k = 0; k < rest.size();) {
+      size_t k1 = k;
+      while (k1 < rest.size() && rest[k1].x == rest[k].x) ++k1;
+      const int row = rest[k].x;
+      size_t m = k;
+      for (; m + 1 < k1; m += 2) packs.push_back(make_int4(row, rest[m].y, row, rest[m + 1].y));
+      if (m < k1) left.push_back(rest[m]);
+      k = k1;
+    }
+    r0 = r1;
+  }
+  const int nshared = (int)packs.size();
+  for (size_t k = 0; k < left.size(); k += 2) {
+    const int2 p = left[k];
+    const int2 q = (k + 1 < left.size()) ? left[k + 1] : make_int2(-1, -1);
+    packs.push_back(make_int4(p.x, p.y, q.x, q.y));
+  }
+  return nshared;
+}
+
+// Persistent chain of one or more builds on one grid: every pack of every build in one launch
+// (persistent_chain.cuh).  packs and pack_build (build of each pack, empty for one build) are on
+// the host; builds[b] holds the device pointers of build b.
+template <typename T>
+ace_status run_chain_persistent(ace_op *op, const DeviceTables *tab, const ace::PersistOps<T> &po,
+                                const std::vector<int4> &packs, const std::vector<int> &pack_build,
+                                const std::vector<ace::ChainBuild<T>> &builds, std::vector<void *> &temps,
+                                const ChainParams &cp) {
+  const long long N = op->N;
+  cudaStream_t st = op->stream;
+  const int np = (int)packs.size();
+  if (np == 0) return ACE_OK;
+  const int lag = std::max(1, env_int("ACE_PERSIST_LAG", 3));
+  const int nslots = std::min(2 * lag + 2, np);
+  // one allocation: packs, builds, pack_build, counters (3 np), ticket; then the scratch slots
+  const size_t b_packs = sizeof(int4) * np, b_builds = sizeof(ace::ChainBuild<T>) * builds.size();
+  const size_t b_pb = sizeof(int) * pack_build.size(), b_cnt = sizeof(int) * (3 * (size_t)np + 4);
+  auto up16 = [](size_t x) { return (x + 15) / 16 * 16; };
+  const size_t o_builds = up16(b_packs), o_pb = o_builds + up16(b_builds), o_cnt = o_pb + up16(b_pb);
+  const size_t meta = o_cnt + up16(b_cnt);
+  void *tmp = nullptr;
+  ACE_CUDA(cudaMallocAsync(&tmp, meta, st), "alloc pack queue");
+  temps.push_back(tmp);
+  char *m = static_cast<char *>(tmp);
+  std::vector<char> hm(o_cnt, 0);
+  std::memcpy(hm.data(), packs.data(), b_packs);
+  std::memcpy(hm.data() + o_builds, builds.data(), b_builds);
+  if (b_pb) std::memcpy(hm.data() + o_pb, pack_build.data(), b_pb);
+  ACE_CUDA(cudaMemcpyAsync(m, hm.data(), o_cnt, cudaMemcpyHostToDevice, st), "pack queue upload");
+  ACE_CUDA(cudaMemsetAsync(m + o_cnt, 0, b_cnt, st), "zero counters");
+  ACE_CUDA(cudaMallocAsync(&tmp, sizeof(cpx<T>) * (size_t)N * nslots, st), "alloc scratch");
+  temps.push_back(tmp);
+  ace::PersistArgs<T> a{};
+  a.builds = reinterpret_cast<const ace::ChainBuild<T> *>(m + o_builds);
+  a.pack_build = b_pb ? reinterpret_cast<const int *>(m + o_pb) : nullptr;
+  a.packs = reinterpret_cast<const int4 *>(m);
+  a.npacks = np;
+  a.scratch = static_cast<cpx<T> *>(tmp);
+  a.nslots = nslots;
+  a.lag = lag;
+  a.tw1 = static_cast<const cpx<T> *>(tab->tw[0]);
+  a.tw2 = static_cast<const cpx<T> *>(tab->tw[1]);
+  a.tw3 = static_cast<const cpx<T> *>(tab->tw[2]);
+  int *cnt = reinterpret_cast<int *>(m + o_cnt);
+  a.counters = cnt;
+  a.ticket = cnt + 3 * (size_t)np;
+  a.err = op->tc_err;
+  a.N = N;
+  // keep the scratch slots resident in L2 (a per-context set-aside of persisting lines)
+  const int persist_mb = cp.persist_mb;
+  if (persist_mb > 0) l2_window(st, op->dev, a.scratch, sizeof(cpx<T>) * (size_t)N * nslots, persist_mb);
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, op->dev);
+  const int per_sm = po.blocks_per_sm();
+  if (per_sm <= 0) return fail(ACE_ERR_CUDA, "persistent chain kernel does not fit on an SM");
+  const long long tasks = (long long)po.tasks_per_pack * (np + 2 * lag);
+  const int grid = (int)std::min<long long>((long long)per_sm * sms, tasks);
+  cudaError_t e = po.launch(a, grid, st);
+  if (persist_mb > 0) l2_window(st, op->dev, nullptr, 0, 0);  // window off again
+  ACE_CUDA(e, "persistent chain");
+  ++op->launches;
+  return ACE_OK;
+}
+
 // Plane, pencil, plane per batch; packs grouped by their shared first orbital.
 template <typename T>
 ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, const ace::PlaneOps<T> &pops,
@@ -532,60 +683,9 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   const int B = std::max(G, cp.B);
   const int nstreams = std::min(kSide, std::max(1, cp.streams));
   const bool acc = pops.acc_fits && G > 1;
-  // packs: two pairs that share an orbital s, written (s, i1, s, i2), so that both plane passes
-  // read three planes and the W_s terms of the pack go out with one atomic.  The sorted pair list
-  // is taken in blocks of RB consecutive rows; inside a block, pairs with the same partner j are
-  // packed together first (phi_j and W_j are then reused while they are in L2, and the block's own
-  // rows stay in L2 for the whole block), then the block's remaining pairs by common row (RB = 1
-  // gives the row packs (i, j1), (i, j2) only).  Single pairs left over are packed together at the
-  // end as mixed packs.
-  const int RB = std::max(1, cp.RB);
   std::vector<int4> packs;
   std::vector<int4> groups;
-  std::vector<int2> left;
-  {
-    const std::vector<int2> &pr = op->pairs_h;
-    std::vector<int2> bp, rest;
-    size_t r0 = 0;
-    while (r0 < pr.size()) {
-      const int blk = pr[r0].x / RB;
-      size_t r1 = r0;
-      while (r1 < pr.size() && pr[r1].x / RB == blk) ++r1;
-      bp.assign(pr.begin() + r0, pr.begin() + r1);
-      rest.clear();
-      if (RB > 1) {
-        std::stable_sort(bp.begin(), bp.end(), [](int2 u, int2 v) { return u.y < v.y; });
-        for (size_t k = 0; k < bp.size();) {
-          size_t k1 = k;
-          while (k1 < bp.size() && bp[k1].y == bp[k].y) ++k1;
-          const int j = bp[k].y;
-          size_t m = k;
-          for (; m + 1 < k1; m += 2) packs.push_back(make_int4(j, bp[m].x, j, bp[m + 1].x));
-          if (m < k1) rest.push_back(bp[m]);
-          k = k1;
-        }
-        std::sort(rest.begin(), rest.end(), [](int2 u, int2 v) { return u.x < v.x || (u.x == v.x && u.y < v.y); });
-      } else {
-        rest.swap(bp);
-      }
-      for (size_t k = 0; k < rest.size();) {
-        size_t k1 = k;
-        while (k1 < rest.size() && rest[k1].x == rest[k].x) ++k1;
-        const int row = rest[k].x;
-        size_t m = k;
-        for (; m + 1 < k1; m += 2) packs.push_back(make_int4(row, rest[m].y, row, rest[m + 1].y));
-        if (m < k1) left.push_back(rest[m]);
-        k = k1;
-      }
-      r0 = r1;
-    }
-  }
-  const int nshared = (int)packs.size();
-  for (size_t k = 0; k < left.size(); k += 2) {
-    const int2 p = left[k];
-    const int2 q = (k + 1 < left.size()) ? left[k + 1] : make_int2(-1, -1);
-    packs.push_back(make_int4(p.x, p.y, q.x, q.y));
-  }
+  const int nshared = form_packs(op->pairs_h, cp.RB, packs);
   // groups: runs of at most G consecutive packs with the same shared orbital (accumulated in
   // shared memory by the inverse pass when acc); mixed packs are groups of their own
   for (int k = 0; k < (int)packs.size();) {
@@ -637,17 +737,10 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   // set-aside of the L2 for persisting lines; ACE_L2_PERSIST_MB=0 turns it off)
   const int persist_mb = cp.persist_mb;
   if (persist_mb > 0 && nstreams > 1) {
-    size_t limit = (size_t)persist_mb << 20;
-    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, limit);
-    for (int k = 0; k < nstreams; ++k) {
-      cudaStreamAttrValue v{};
-      v.accessPolicyWindow.base_ptr = scratch_all + (size_t)k * B * N;
-      v.accessPolicyWindow.num_bytes = std::min<size_t>(limit / (size_t)nstreams, sizeof(cpx<T>) * (size_t)B * (size_t)N);
-      v.accessPolicyWindow.hitRatio = 1.0f;
-      v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-      v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
-      cudaStreamSetAttribute(side[k], cudaStreamAttributeAccessPolicyWindow, &v);
-    }
+    for (int k = 0; k < nstreams; ++k)
+      l2_window(side[k], op->dev, scratch_all + (size_t)k * B * N,
+                std::min<size_t>(((size_t)persist_mb << 20) / (size_t)nstreams, sizeof(cpx<T>) * (size_t)B * (size_t)N),
+                persist_mb);
   }
 
   ace::PlaneArgs<T> pa;
@@ -690,11 +783,7 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   }
   if (nstreams > 1) {
     for (int k = 0; k < nstreams; ++k) {
-      if (persist_mb > 0) {
-        cudaStreamAttrValue v{};
-        v.accessPolicyWindow.num_bytes = 0;  // window off again
-        cudaStreamSetAttribute(side[k], cudaStreamAttributeAccessPolicyWindow, &v);
-      }
+      if (persist_mb > 0) l2_window(side[k], op->dev, nullptr, 0, 0);  // window off again
       ACE_CUDA(cudaEventRecord(fork, side[k]), "event");
       ACE_CUDA(cudaStreamWaitEvent(st, fork, 0), "join");
     }
@@ -919,8 +1008,17 @@ ace_status build_finish(ace_op *op) {
   ACE_CUDA(op_alloc(op, &op->W, op->esz * (size_t)n * N), "alloc W");
   ACE_CUDA(cudaMemsetAsync(op->W, 0, op->esz * (size_t)n * N, st), "zero W");
   ace::PlaneOps<T> pops{};
+  ace::PersistOps<T> qops{};
   const bool plane = find_plane_ops<T>(d.n[1], d.n[2], &pops) && env_int("ACE_FORCE_PENCIL", 0) == 0;
-  if (count > 0 && plane) {
+  const bool persistent = plane && find_persist_ops<T>(d.n[0], d.n[1], d.n[2], &qops) &&
+                          env_int("ACE_PERSISTENT", 0) != 0;
+  if (count > 0 && persistent) {
+    const ChainParams cp = chain_params(d, op->fp64);
+    std::vector<int4> packs;
+    form_packs(op->pairs_h, cp.RB, packs);
+    const std::vector<ace::ChainBuild<T>> one{{phi, static_cast<T *>(op->W), static_cast<const T *>(tab->Kperm)}};
+    s = run_chain_persistent<T>(op, tab, qops, packs, {}, one, temps, cp);
+  } else if (count > 0 && plane) {
     s = run_chain_plane<T>(op, phi, tab, pops, count, temps, chain_params(d, op->fp64));
   } else if (count > 0) {
     const cpx<T> *twd[3] = {static_cast<const cpx<T> *>(tab->tw[0]), static_cast<const cpx<T> *>(tab->tw[1]),
@@ -990,7 +1088,7 @@ ace_status build_collect(ace_op *op) {
   cudaEventElapsedTime(&op->stage_ms[5], op->ev[0], op->ev[5]);
   pinned_put(op->readback, op->readback_bytes);
   op->readback = nullptr;
-  if (flags[1]) return fail(ACE_ERR_TIMEOUT, "a tensor-core kernel gave up waiting for its MMAs");
+  if (flags[1]) return fail(ACE_ERR_TIMEOUT, "a kernel gave up waiting (tensor-core pipeline, TMA copy or pair-chain task queue)");
   if (op->status >= 2000000) return fail(ACE_ERR_NONFINITE, "M has a non-finite entry");
   if (op->status >= 1000000)
     return fail(ACE_ERR_NOT_POSDEF, "-M is not positive definite: Cholesky pivot %d", op->status - 1000000);

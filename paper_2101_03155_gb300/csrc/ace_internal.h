@@ -63,6 +63,38 @@ bool plane_ops_f32_small(int n2, int n3, PlaneOps<float> *out);
 bool plane_ops_f32_large(int n2, int n3, PlaneOps<float> *out);
 bool plane_ops_f64(int n2, int n3, PlaneOps<double> *out);
 
+// Persistent pair chain (persistent_chain.cuh): one launch walks every pack of one or more builds
+// on one grid through a device-side task queue.
+template <typename T>
+struct ChainBuild {
+  const T *phi;      // [norb][N]
+  T *W;              // [norb][N], accumulated into
+  const T *Kperm;    // Coulomb table in the plane passes' permuted layout
+};
+template <typename T>
+struct PersistArgs {
+  const ChainBuild<T> *builds;  // [builds]
+  const int *pack_build;        // [npacks] build of each pack; null: every pack belongs to build 0
+  const int4 *packs;            // [npacks] (a, b, c, d), c = d = -1 for a single pair
+  int npacks;
+  cpx<T> *scratch;              // [nslots][N] complex
+  int nslots;                   // >= 2 lag + 2
+  int lag;                      // rounds between the stages of one pack in the queue
+  const cpx<T> *tw1, *tw2, *tw3;
+  int *counters;                // [3][npacks] finished F, C and I tasks per pack, zeroed
+  int *ticket;                  // next task number, zeroed
+  int *err;                     // set to 1 when a wait gives up
+  long long N;
+};
+template <typename T>
+struct PersistOps {
+  int (*blocks_per_sm)();
+  cudaError_t (*launch)(const PersistArgs<T> &, int grid, cudaStream_t);
+  int tasks_per_pack;  // F + C + I tasks
+};
+bool persist_ops_f32_small(int n1, int n2, int n3, PersistOps<float> *out);
+bool persist_ops_f32_large(int n1, int n2, int n3, PersistOps<float> *out);
+
 // Launch one pass over `npacks` packs (grid.y); returns cudaErrorInvalidValue if the axis
 // length has no compiled plan.
 template <typename T>

@@ -153,6 +153,17 @@ __device__ __forceinline__ void for_points(F &&f) {
   }
 }
 
+// Load of a complex value through L2 only (data written earlier by other CTAs of a running grid
+// must not be served from this SM's L1)
+__device__ __forceinline__ cpx<float> ldcg_cpx(const cpx<float> *p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+  return cpx<float>{v.x, v.y};
+}
+__device__ __forceinline__ cpx<double> ldcg_cpx(const cpx<double> *p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+  return cpx<double>{v.x, v.y};
+}
+
 template <typename T>
 struct Vec4;
 template <>
@@ -185,36 +196,30 @@ struct Vec4<double> {
 };
 
 // ---------------------------------------------------------------------------------------
-// Forward plane pass: one CTA per (plane i1, pack).
+// Bodies shared by the per-batch kernels below and the persistent chain kernel.
 // ---------------------------------------------------------------------------------------
+
+// Forward transform of plane i1 (offset off = i1 N2 N3) of pack pk: the pair densities
+// z = phi_a phi_b + i phi_c phi_d, axes 3 and 2, the permuted spectrum plane written to dst.
+// Uses s (N2 x PP complex) and the twiddles tw2, tw3 in shared memory; starts with a barrier-free
+// load and ends without a barrier.
 template <typename T, int N2, int N3, int NT>
-__global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, false>())) plane_fwd_kernel(PlaneArgs<T> a) {
+__device__ __forceinline__ void plane_forward(const T *__restrict__ phi, long long N, long long off, int4 pk,
+                                              cpx<T> *s, const cpx<T> *tw2, const cpx<T> *tw3, cpx<T> *dst) {
   using S = PlaneShape<N2, N3>;
   using F = PlaneStages<T, NT>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<T> *s = reinterpret_cast<cpx<T> *>(smem_raw);
-  cpx<T> *tw2 = s + N2 * S::PP;
-  cpx<T> *tw3 = tw2 + N2;
-  const int tid = threadIdx.x;
-  const int i1 = blockIdx.x;
-  const int pidx = a.pack0 + blockIdx.y;
-  const int4 pk = a.packs[pidx];
-  for (int e = tid; e < N2; e += NT) tw2[e] = a.tw2[e];
-  for (int e = tid; e < N3; e += NT) tw3[e] = a.tw3[e];
-
-  const long long off = (long long)i1 * S::NPTS;
-  const T *pa = a.phi + (long long)pk.x * a.N + off;
-  const T *pb = a.phi + (long long)pk.y * a.N + off;
+  const T *pa = phi + (long long)pk.x * N + off;
+  const T *pb = phi + (long long)pk.y * N + off;
   if (pk.z == pk.x) {
     // row pack (a, b), (a, d): z = phi_a (phi_b + i phi_d), three planes read
-    const T *pd = a.phi + (long long)pk.w * a.N + off;
+    const T *pd = phi + (long long)pk.w * N + off;
     for_points<N2, N3, NT, ACE_FWD_UNROLL>([&](int e, int si) {
       const T fa = __ldg(pa + e);
       s[si] = cpx<T>{fa * __ldg(pb + e), fa * __ldg(pd + e)};
     });
   } else if (pk.z >= 0) {
-    const T *pc = a.phi + (long long)pk.z * a.N + off;
-    const T *pd = a.phi + (long long)pk.w * a.N + off;
+    const T *pc = phi + (long long)pk.z * N + off;
+    const T *pd = phi + (long long)pk.w * N + off;
     for_points<N2, N3, NT, ACE_FWD_UNROLL>([&](int e, int si) {
       s[si] = cpx<T>{__ldg(pa + e) * __ldg(pb + e), __ldg(pc + e) * __ldg(pd + e)};
     });
@@ -232,7 +237,6 @@ __global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, false>())) pl
   // axis 2 (columns): stage 1 in shared memory, stage 2 straight to the scratch plane
   F::template stage1<N2, N3, 1, S::PP, -1, true>(s, tw2);
   __syncthreads();
-  cpx<T> *dst = a.scratch + (long long)(pidx - a.batch0) * a.N + off;
   for_tasks<N3, S::R1c, NT>([&](int p3, int k1) {
     cpx<T> x[S::R2c];
 #pragma unroll
@@ -243,6 +247,105 @@ __global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, false>())) pl
   });
 }
 
+// Inverse transform of one permuted spectrum plane src (read through L2 only: it was written
+// by other CTAs) into natural order in s: axes 2 and 3.  Ends with a barrier.
+template <typename T, int N2, int N3, int NT>
+__device__ __forceinline__ void plane_inverse(const cpx<T> *src, cpx<T> *s, const cpx<T> *tw2, const cpx<T> *tw3) {
+  using S = PlaneShape<N2, N3>;
+  using F = PlaneStages<T, NT>;
+  // axis 2 inverse, stage A straight from the scratch plane (permuted rows p2 = k1 R2c + k2);
+  // the k1 = 0 twiddles are the table's exact 1 + 0i
+  for_tasks<N3, S::R1c, NT>([&](int p3, int k1) {
+    cpx<T> x[S::R2c];
+#pragma unroll
+    for (int k2 = 0; k2 < S::R2c; ++k2) x[k2] = ldcg_cpx(src + (k1 * S::R2c + k2) * N3 + p3);
+    Dft<S::R2c, +1, T>::run(x);
+#pragma unroll
+    for (int n2 = 0; n2 < S::R2c; ++n2) {
+      cpx<T> v = x[n2];
+      if (n2 > 0) {
+        const cpx<T> w = tw2[n2 * k1];
+        v = cmul(v, cpx<T>{w.x, -w.y});
+      }
+      s[(k1 * S::R2c + n2) * S::PP + p3] = v;
+    }
+  });
+  __syncthreads();
+  F::template stage1<N2, N3, 1, S::PP, +1, false>(s, tw2);  // inverse stage B: natural rows
+  __syncthreads();
+  F::template inv_stageA<N3, N2, S::PP, 1>(s, tw3);
+  __syncthreads();
+  F::template stage1<N3, N2, S::PP, 1, +1, false>(s, tw3);  // natural columns
+  __syncthreads();
+}
+
+// W accumulation of one pack from v = v_ab + i v_cd at the natural points of plane offset off
+// (Eq. vx): W_a += v_ab phi_b (+ v_ad phi_d for a row pack), W_b += v_ab phi_a, W_c += v_cd phi_d,
+// W_d += v_cd phi_c, diagonal pairs once.  With acc (a group's shared first orbital) the W_a terms
+// are summed into acc instead.
+template <typename T, int N2, int N3, int NT>
+__device__ __forceinline__ void plane_accumulate(const T *__restrict__ phi, T *W, long long N, long long off, int4 pk,
+                                                 const cpx<T> *s, T *acc) {
+  const bool two = pk.z >= 0;
+  const bool same_a = two && pk.z == pk.x;
+  const T *fa = phi + (long long)pk.x * N + off;
+  const T *fb = phi + (long long)pk.y * N + off;
+  const T *fc = phi + (long long)(two ? pk.z : 0) * N + off;
+  const T *fd = phi + (long long)(two ? pk.w : 0) * N + off;
+  T *wa = W + (long long)pk.x * N + off;
+  T *wb = W + (long long)pk.y * N + off;
+  T *wc = W + (long long)(two ? pk.z : 0) * N + off;
+  T *wd = W + (long long)(two ? pk.w : 0) * N + off;
+  auto last = [&](auto &&epi) {
+    for_points<N2, N3, NT, ACE_INV_UNROLL>([&](int e, int si) { epi(e, s[si]); });
+  };
+  if (!acc && same_a && pk.y != pk.x && pk.w != pk.x) {
+    // row pack (a, b), (a, d) with b, d != a: W_a += v_ab phi_b + v_ad phi_d, W_b += v_ab phi_a,
+    // W_d += v_ad phi_a  (v = v_ab + i v_ad)
+    last([&](int e, cpx<T> v) {
+      const T pa_ = __ldg(fa + e), pb_ = __ldg(fb + e), pd_ = __ldg(fd + e);
+      atomicAdd(wa + e, v.x * pb_ + v.y * pd_);
+      atomicAdd(wb + e, v.x * pa_);
+      atomicAdd(wd + e, v.y * pa_);
+    });
+  } else {
+    // any pack: v = v_ab + i v_cd
+    last([&](int e, cpx<T> v) {
+      const T pa_ = __ldg(fa + e), pb_ = __ldg(fb + e);
+      const T pc_ = two ? __ldg(fc + e) : (T)0, pd_ = two ? __ldg(fd + e) : (T)0;
+      const T to_a = v.x * pb_ + (same_a ? v.y * pd_ : (T)0);
+      if (acc) {
+        acc[e] += to_a;  // pk.x == the group's row (and pk.z too when two)
+      } else {
+        atomicAdd(wa + e, to_a);
+        if (two && !same_a) atomicAdd(wc + e, v.y * pd_);
+      }
+      if (pk.y != pk.x) atomicAdd(wb + e, v.x * pa_);
+      if (two && pk.w != pk.z) atomicAdd(wd + e, v.y * pc_);
+    });
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Forward plane pass: one CTA per (plane i1, pack).
+// ---------------------------------------------------------------------------------------
+template <typename T, int N2, int N3, int NT>
+__global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, false>())) plane_fwd_kernel(PlaneArgs<T> a) {
+  using S = PlaneShape<N2, N3>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T> *s = reinterpret_cast<cpx<T> *>(smem_raw);
+  cpx<T> *tw2 = s + N2 * S::PP;
+  cpx<T> *tw3 = tw2 + N2;
+  const int tid = threadIdx.x;
+  const int i1 = blockIdx.x;
+  const int pidx = a.pack0 + blockIdx.y;
+  const int4 pk = a.packs[pidx];
+  for (int e = tid; e < N2; e += NT) tw2[e] = a.tw2[e];
+  for (int e = tid; e < N3; e += NT) tw3[e] = a.tw3[e];
+  const long long off = (long long)i1 * S::NPTS;
+  plane_forward<T, N2, N3, NT>(a.phi, a.N, off, pk, s, tw2, tw3, a.scratch + (long long)(pidx - a.batch0) * a.N + off);
+}
+
 // ---------------------------------------------------------------------------------------
 // Inverse plane pass fused with the W accumulation: one CTA per (plane i1, group).
 // Group g covers packs [gstart, gstart + glen); grow >= 0 means every pair of the group has
@@ -251,7 +354,6 @@ __global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, false>())) pl
 template <typename T, int N2, int N3, int NT, bool ACC>
 __global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, ACC>())) plane_inv_kernel(PlaneArgs<T> a) {
   using S = PlaneShape<N2, N3>;
-  using F = PlaneStages<T, NT>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T> *s = reinterpret_cast<cpx<T> *>(smem_raw);
   cpx<T> *tw2 = s + N2 * S::PP;
@@ -270,71 +372,9 @@ __global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, ACC>())) plan
   for (int q = 0; q < grp.y; ++q) {
     const int pidx = grp.x + q;
     const int4 pk = a.packs[pidx];
-    const cpx<T> *src = a.scratch + (long long)(pidx - a.batch0) * a.N + off;
     __syncthreads();  // previous pack's epilogue has finished reading s
-    // axis 2 inverse, stage A straight from the scratch plane (permuted rows p2 = k1 R2c + k2);
-    // the k1 = 0 twiddles are the table's exact 1 + 0i
-    for_tasks<N3, S::R1c, NT>([&](int p3, int k1) {
-      cpx<T> x[S::R2c];
-#pragma unroll
-      for (int k2 = 0; k2 < S::R2c; ++k2) x[k2] = src[(k1 * S::R2c + k2) * N3 + p3];
-      Dft<S::R2c, +1, T>::run(x);
-#pragma unroll
-      for (int n2 = 0; n2 < S::R2c; ++n2) {
-        cpx<T> v = x[n2];
-        if (n2 > 0) {
-          const cpx<T> w = tw2[n2 * k1];
-          v = cmul(v, cpx<T>{w.x, -w.y});
-        }
-        s[(k1 * S::R2c + n2) * S::PP + p3] = v;
-      }
-    });
-    __syncthreads();
-    F::template stage1<N2, N3, 1, S::PP, +1, false>(s, tw2);  // inverse stage B: natural rows
-    __syncthreads();
-    F::template inv_stageA<N3, N2, S::PP, 1>(s, tw3);
-    __syncthreads();
-    // epilogue: v = v_ab + i v_cd at natural points, one point per lane
-    const bool two = pk.z >= 0;
-    const bool same_a = two && pk.z == pk.x;
-    const T *fa = a.phi + (long long)pk.x * a.N + off;
-    const T *fb = a.phi + (long long)pk.y * a.N + off;
-    const T *fc = a.phi + (long long)(two ? pk.z : 0) * a.N + off;
-    const T *fd = a.phi + (long long)(two ? pk.w : 0) * a.N + off;
-    T *wa = a.W + (long long)pk.x * a.N + off;
-    T *wb = a.W + (long long)pk.y * a.N + off;
-    T *wc = a.W + (long long)(two ? pk.z : 0) * a.N + off;
-    T *wd = a.W + (long long)(two ? pk.w : 0) * a.N + off;
-    F::template stage1<N3, N2, S::PP, 1, +1, false>(s, tw3);  // natural columns
-    __syncthreads();
-    auto last = [&](auto &&epi) {
-      for_points<N2, N3, NT, ACE_INV_UNROLL>([&](int e, int si) { epi(e, s[si]); });
-    };
-    if (!use_acc && same_a && pk.y != pk.x && pk.w != pk.x) {
-      // row pack (a, b), (a, d) with b, d != a: W_a += v_ab phi_b + v_ad phi_d, W_b += v_ab phi_a,
-      // W_d += v_ad phi_a  (v = v_ab + i v_ad)
-      last([&](int e, cpx<T> v) {
-        const T pa_ = __ldg(fa + e), pb_ = __ldg(fb + e), pd_ = __ldg(fd + e);
-        atomicAdd(wa + e, v.x * pb_ + v.y * pd_);
-        atomicAdd(wb + e, v.x * pa_);
-        atomicAdd(wd + e, v.y * pa_);
-      });
-    } else {
-      // any pack: v = v_ab + i v_cd
-      last([&](int e, cpx<T> v) {
-        const T pa_ = __ldg(fa + e), pb_ = __ldg(fb + e);
-        const T pc_ = two ? __ldg(fc + e) : (T)0, pd_ = two ? __ldg(fd + e) : (T)0;
-        const T to_a = v.x * pb_ + (same_a ? v.y * pd_ : (T)0);
-        if (use_acc) {
-          acc[e] += to_a;  // pk.x == grow (and pk.z == grow when two)
-        } else {
-          atomicAdd(wa + e, to_a);
-          if (two && !same_a) atomicAdd(wc + e, v.y * pd_);
-        }
-        if (pk.y != pk.x) atomicAdd(wb + e, v.x * pa_);
-        if (two && pk.w != pk.z) atomicAdd(wd + e, v.y * pc_);
-      });
-    }
+    plane_inverse<T, N2, N3, NT>(a.scratch + (long long)(pidx - a.batch0) * a.N + off, s, tw2, tw3);
+    plane_accumulate<T, N2, N3, NT>(a.phi, a.W, a.N, off, pk, s, use_acc ? acc : nullptr);
   }
   if (use_acc) {
     __syncthreads();
