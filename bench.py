@@ -209,19 +209,14 @@ WORKLOADS = {
 
 def _batch_inputs(name):
     """List of Workload objects of a multi-build workload (one step builds all of them)."""
-    from workloads.generators import batched_set, config3, config5, water_like
+    from workloads.generators import config3, config4, config5
 
     if name == "water64":
         return [config3()]
     if name in ("enzyme8", "enzyme8_iso"):
         return config5(nsnap=8)
     if name == "batched24":
-        rng = np.random.default_rng(1004)
-        out = []
-        for n, N, cell, seed in batched_set(rng):
-            out.append(water_like(n // 4, cell, (N, N, N), np.random.default_rng(seed), rho_cut=1e-3,
-                                  name=f"water{n // 4}_{n}orb_{N}c"))
-        return out
+        return config4()
     raise ValueError(name)
 
 

@@ -16,11 +16,17 @@ FP64_ARRAY_RTOL = 1e-10
 MIXED_EX_TOL_PER_ORB = 1e-6
 MIXED_KPHI_RTOL = 1e-5
 MIXED_W_RTOL = 2e-5
-# mixed-form xi = L^-1 W (relative Frobenius norm over the sampled points): W carries up to 2e-5 of
-# its largest entry (above), L^-1 comes from the FP64 Cholesky of an M whose tensor-core products
-# carry up to 3 * 2^-16 = 4.6e-5 relative error, and the BF16x3 product L^-1 W adds as much again;
-# for the localized sets here cond(L) = sqrt(cond(M)) is a few units, so 1e-4 bounds the sum.
-MIXED_XI_RTOL = 1e-4
+# BF16x3 carries each FP32 operand as hi + lo, two bf16 halves of 8 significant bits each, so an
+# operand keeps ~16 bits (representation error <= 2^-17 relative) and a product hi*hi + hi*lo +
+# lo*hi misses up to ~2^-16 = 1.5e-5 of its value (the dropped lo*lo term and both residuals).
+# mixed-form xi = L^-1 W (relative Frobenius norm over the sampled points): W's FP32 FFT error
+# (~1e-6) plus one BF16x3 contraction whose independent product errors average over the n terms
+# of a row: 5e-5 bounds it (measured 4.9e-6 at 128 orbitals on 96^3).
+MIXED_XI_RTOL = 5e-5
+# K psi = -xi (dV xi^T psi) for an arbitrary psi: two BF16x3 contractions, 2 x 1.5e-5, where the
+# first one may cancel (psi nearly orthogonal to xi) and the second adds its own 1.5e-5: 3e-5.
+# For psi in the span of the orbitals the benchmark spec's target MIXED_KPHI_RTOL applies.
+MIXED_KPSI_RTOL = 3e-5
 # mixed-form screen values O_ij = dV sum |phi_i||phi_j| on the CUDA cores: FP32 products of the
 # FP32-rounded orbitals (input rounding 2^-24 per factor), FP32 partial sums over 64 points (at
 # most 63 u, typically ~sqrt(64/3) u with u = 2^-24), Kahan-compensated FP32 sums across them
