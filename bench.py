@@ -207,6 +207,15 @@ WORKLOADS = {
 }
 
 
+# builds of a multi-build workload with stored oracle values: (index in the step, golden key)
+GOLDEN_BUILDS = {
+    "water64": [(0, "water64_256orb_128c_rhocut1e-3")],
+    "enzyme8": [(0, "enzyme_snap0_periodic")],
+    "enzyme8_iso": [(0, "enzyme_snap0_isolated")],
+    "batched24": [(1, "batched24_b1_64orb_72c"), (15, "batched24_b15_96orb_108c"), (12, "batched24_b12_64orb_128c")],
+}
+
+
 def _batch_inputs(name):
     """List of Workload objects of a multi-build workload (one step builds all of them)."""
     from workloads.generators import config3, config4, config5
@@ -234,7 +243,6 @@ def run_multi(args):
     ws = _batch_inputs(args.workload)
     # the isolated-cell workload uses the truncated Coulomb kernel (1/r cut off at the inscribed radius)
     coulomb = ace.ACE_COULOMB_TRUNCATED if args.workload.endswith("_iso") else ace.ACE_COULOMB_PERIODIC
-    golden_key = {"enzyme8_iso": "enzyme_snap0_isolated"}.get(args.workload)
     stream = torch.cuda.current_stream()
     res = {}
     for prec, dt, steps in ((ace.ACE_MIXED, torch.float32, args.steps), (ace.ACE_FP64, torch.float64,
@@ -266,12 +274,29 @@ def run_multi(args):
         res[prec] = {"builds_per_s": len(ws) * steps / (ms / 1e3), "ms_per_step": ms / steps, "rec": rec, "clk": clk}
         del phis
     mixed, f64 = res[ace.ACE_MIXED], res[ace.ACE_FP64]
-    gold = _golden().get(golden_key) if golden_key else None
-    accuracy = None
-    if gold:
-        accuracy = {"build": ws[0].name, "E_x_oracle": gold["E_x"],
-                    "ex_err_ha_per_orb": abs(mixed["rec"]["E"][0] - gold["E_x"]) / ws[0].norb,
-                    "fp64_ex_err_ha_per_orb": abs(f64["rec"]["E"][0] - gold["E_x"]) / ws[0].norb}
+    # errors against the stored FP64-oracle values of the builds that have them (E_x; and xi, K phi,
+    # K psi at the sampled points where stored)
+    accuracy = []
+    for b, key in GOLDEN_BUILDS.get(args.workload, []):
+        gold = _golden().get(key)
+        if not gold:
+            continue
+        w = ws[b]
+        item = {"build": b, "name": w.name, "E_x_oracle": gold["E_x"],
+                "ex_err_ha_per_orb": abs(mixed["rec"]["E"][b] - gold["E_x"]) / w.norb,
+                "fp64_ex_err_ha_per_orb": abs(f64["rec"]["E"][b] - gold["E_x"]) / w.norb}
+        arrays = _golden_arrays(key)
+        if arrays is not None and "idx" in arrays:
+            for prec, dt, tag in ((ace.ACE_MIXED, torch.float32, "mixed"), (ace.ACE_FP64, torch.float64, "fp64")):
+                d = ace.make_desc(w.grid, w.lattice, w.norb, rho_cut=w.rho_cut, spin_factor=w.spin_factor,
+                                  prec=prec, coulomb=coulomb)
+                x = torch.from_numpy(w.phi).to(device="cuda", dtype=dt)
+                op = ace.ace_build(d, x, stream)
+                item[f"sampled_{tag}"] = sampled_accuracy(ace, op, w, arrays, stream)
+                op.close()
+                del x
+        accuracy.append(item)
+    accuracy = accuracy or None
     line = {
         "metric": METRIC, "value": mixed["builds_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mixed["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -517,6 +542,50 @@ def run_reference(args):
 # GPU arm
 # ------------------------------------------------------------------------------------------
 
+def _golden_arrays(key):
+    """Stored oracle arrays of a build (tests/golden/<key>.npz, written from oracle/ only), or None."""
+    entry = _golden().get(key)
+    if not entry or "arrays" not in entry:
+        return None
+    path = os.path.join(os.path.dirname(GOLDEN), entry["arrays"])
+    return dict(np.load(path)) if os.path.exists(path) else None
+
+
+def sampled_accuracy(ace, op, w, arrays, stream):
+    """Errors of a built operator against the FP64 oracle at the stored sample points: xi (every
+    row), K phi_k for every orbital and K psi of the two seeded probe vectors (section II), as
+    relative Frobenius norms; and whether the build's pair list equals the oracle's."""
+    import torch
+
+    from workloads.generators import probe_vectors
+
+    n, N = w.norb, w.npts
+    dt = torch.float64 if op.desc.prec == ace.ACE_FP64 else torch.float32
+    pairs = ace.ace.get_numpy(op, ace.ace.ACE_GET_PAIRS)
+    same = pairs.shape == arrays["pairs"].shape and bool(np.array_equal(pairs, arrays["pairs"]))
+    idx = torch.from_numpy(arrays["idx"]).cuda()
+    xi = torch.empty((n, N), dtype=dt, device="cuda")
+    ace.ace_get(op, ace.ace.ACE_GET_XI, xi, stream)
+    xi_s = xi[:, idx].double().cpu().numpy()
+    del xi
+    phi = torch.from_numpy(w.phi).to(device="cuda", dtype=dt)
+    out = torch.empty_like(phi)
+    ace.ace_apply(op, phi, out, stream)
+    kphi_s = out.reshape(n, N)[:, idx].double().cpu().numpy()
+    del phi, out
+    psi = torch.from_numpy(probe_vectors(w.phi, w.dV, int(arrays["probe_seed"]))).to(device="cuda", dtype=dt)
+    kout = torch.empty_like(psi)
+    ace.ace_apply(op, psi, kout, stream)
+    kpsi_s = kout.reshape(2, N)[:, idx].double().cpu().numpy()
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    return {"pair_list_equals_oracle": same, "samples": int(len(arrays["idx"])),
+            "xi_rel_err": rel(xi_s, arrays["xi"]), "kphi_rel_err": rel(kphi_s, arrays["kphi"]),
+            "kpsi_rel_err": max(rel(kpsi_s[c], arrays["kpsi"][c]) for c in range(2))}
+
+
 def _timed_builds(ace, desc, phi, stream, steps, collect):
     import torch
 
@@ -616,6 +685,8 @@ def run_ours(args):
     # the application of section II on the same operator: K psi = -xi (dV xi^T psi) for m = n
     # vectors (the orbitals themselves), device buffers; xi^T psi and xi C on the tensor cores
     op_a = ace.ace_build(desc, phi32, stream)
+    gold_arrays = _golden_arrays(WORKLOAD)
+    acc_mixed = sampled_accuracy(ace, op_a, w, gold_arrays, stream) if gold_arrays else None
     out_a = torch.empty_like(phi32)
     for _ in range(3):
         ace.ace_apply(op_a, phi32, out_a, stream)
@@ -640,6 +711,11 @@ def run_ours(args):
     rec64 = {"E": []}
     ms64 = _timed_builds(ace, desc64, phi64, stream, args.fp64_steps, lambda op, e: rec64["E"].append(e))
     fp64_value = args.fp64_steps / (ms64 / 1e3)
+    acc64 = None
+    if gold_arrays:
+        op64 = ace.ace_build(desc64, phi64, stream)
+        acc64 = sampled_accuracy(ace, op64, w, gold_arrays, stream)
+        op64.close()
     del phi64
 
     peaks, peak_kind = _peaks()
@@ -660,9 +736,10 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "norb": n, "grid": list(w.grid), "rho_cut": w.rho_cut,
                    "precision": "mixed", "npairs": npairs, "autotuned": tuned,
                    "l2": "inputs larger than L2 (orbitals 453 MB FP32, W and xi 453 MB each)"},
-        "accuracy": {"E_x": statistics.mean(rec["E"]), "E_x_oracle": e_ref, "ex_err_ha_per_orb": ex_err},
+        "accuracy": {"E_x": statistics.mean(rec["E"]), "E_x_oracle": e_ref, "ex_err_ha_per_orb": ex_err,
+                     **(acc_mixed or {})},
         "fp64_form": {"value": fp64_value, "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps,
-                      "steps": args.fp64_steps, "ex_err_ha_per_orb": ex_err64,
+                      "steps": args.fp64_steps, "ex_err_ha_per_orb": ex_err64, "accuracy": acc64,
                       "speedup_mixed_over_fp64": value / world / fp64_value},
         "stage_ms": stage_mean,
         "roofline": {"kernel": "pair chain (plane fwd, axis-1 pencil, plane inv+accumulate per pack batch)",

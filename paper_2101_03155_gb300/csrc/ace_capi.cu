@@ -494,6 +494,11 @@ ChainParams chain_params(const ace_desc &d, bool fp64) {
 }
 
 // Five pencil passes per batch of packs (any compiled grid).
+int form_packs(const std::vector<int2> &pr, int RB, std::vector<int4> &packs);
+std::vector<int> form_rounds(std::vector<int4> &packs, int norb);
+
+// Five pencil passes per batch of packs, one stream.  The FP64 form takes its packs in rounds on
+// disjoint orbitals (batches never span two rounds), so that W repeats bit for bit.
 template <typename T>
 ace_status run_chain_pencil(ace_op *op, const T *phi, const T *Kd, const cpx<T> *const *twd, int count,
                             std::vector<void *> &temps) {
@@ -518,17 +523,31 @@ ace_status run_chain_pencil(ace_op *op, const T *phi, const T *Kd, const cpx<T> 
   a.n1 = d.n[0];
   a.n2 = d.n[1];
   a.n3 = d.n[2];
-  for (int p0 = 0; p0 < npacks; p0 += batch) {
-    const int nb = std::min(batch, npacks - p0);
-    a.pack0 = p0;
-    const int modes[5] = {ace::PASS_FWD3_PAIR, ace::PASS_FWD2, ace::PASS_CONV1, ace::PASS_INV2, ace::PASS_INV3_ACC};
-    const int axis[5] = {2, 1, 0, 1, 2};
-    for (int k = 0; k < 5; ++k) {
-      a.tw = twd[axis[k]];
-      ACE_CUDA(ace::launch_pair_pass<T>(modes[k], a, nb, st), "pair pass");
-      ++op->launches;
-    }
+  std::vector<int> rb = {0, npacks};
+  if (op->fp64) {
+    std::vector<int4> packs;
+    form_packs(op->pairs_h, 1, packs);
+    rb = form_rounds(packs, op->n);
+    ACE_CUDA(cudaMallocAsync(&tmp, sizeof(int4) * packs.size(), st), "alloc packs");
+    temps.push_back(tmp);
+    // pageable source: the copy has read it when the call returns
+    ACE_CUDA(cudaMemcpyAsync(tmp, packs.data(), sizeof(int4) * packs.size(), cudaMemcpyHostToDevice, st),
+             "pack upload");
+    a.packs = static_cast<const int4 *>(tmp);
   }
+  for (size_t r = 0; r + 1 < rb.size(); ++r)
+    for (int p0 = rb[r]; p0 < rb[r + 1]; p0 += batch) {
+      const int nb = std::min(batch, rb[r + 1] - p0);
+      a.pack0 = p0;
+      const int modes[5] = {ace::PASS_FWD3_PAIR, ace::PASS_FWD2, ace::PASS_CONV1, ace::PASS_INV2,
+                            ace::PASS_INV3_ACC};
+      const int axis[5] = {2, 1, 0, 1, 2};
+      for (int k = 0; k < 5; ++k) {
+        a.tw = twd[axis[k]];
+        ACE_CUDA(ace::launch_pair_pass<T>(modes[k], a, nb, st), "pair pass");
+        ++op->launches;
+      }
+    }
   return ACE_OK;
 }
 
@@ -608,6 +627,40 @@ int form_packs(const std::vector<int2> &pr, int RB, std::vector<int4> &packs) {
   return nshared;
 }
 
+// Reorders packs into rounds whose packs touch disjoint orbitals (first fit in pack order) and
+// returns the start of every round in the new order, followed by the end.  Inside a round each W
+// element receives at most one addition, so a chain run round after round adds the terms of every
+// element in one fixed order: the FP64 form repeats bit for bit.
+std::vector<int> form_rounds(std::vector<int4> &packs, int norb) {
+  std::vector<std::vector<int4>> rounds;
+  std::vector<std::vector<unsigned char>> used;
+  for (const int4 &p : packs) {
+    const int rows[4] = {p.x, p.y, p.z, p.w};
+    size_t r = 0;
+    for (; r < rounds.size(); ++r) {
+      bool free_ = true;
+      for (int k = 0; k < 4 && free_; ++k)
+        if (rows[k] >= 0 && used[r][rows[k]]) free_ = false;
+      if (free_) break;
+    }
+    if (r == rounds.size()) {
+      rounds.emplace_back();
+      used.emplace_back((size_t)norb, (unsigned char)0);
+    }
+    for (int k = 0; k < 4; ++k)
+      if (rows[k] >= 0) used[r][rows[k]] = 1;
+    rounds[r].push_back(p);
+  }
+  std::vector<int> bounds;
+  packs.clear();
+  for (const auto &rd : rounds) {
+    bounds.push_back((int)packs.size());
+    packs.insert(packs.end(), rd.begin(), rd.end());
+  }
+  bounds.push_back((int)packs.size());
+  return bounds;
+}
+
 // Persistent chain of one or more builds on one grid: every pack of every build in one launch
 // (persistent_chain.cuh).  packs and pack_build (build of each pack, empty for one build) are on
 // the host; builds[b] holds the device pointers of build b.
@@ -656,6 +709,11 @@ ace_status run_chain_persistent(ace_op *op, const DeviceTables *tab, const ace::
   a.ticket = cnt + 3 * (size_t)np;
   a.err = op->tc_err;
   a.N = N;
+  // ACE_PERSIST_WAIT_NS bounds each wait (default 2 s); ACE_PERSIST_TEST_STALL=1 makes the pencil
+  // tasks wait for a word that nothing sets (a test of the give-up path)
+  const char *wn = std::getenv("ACE_PERSIST_WAIT_NS");
+  a.wait_ns = (wn && *wn) ? std::strtoull(wn, nullptr, 10) : 2000000000ull;
+  a.stall = env_int("ACE_PERSIST_TEST_STALL", 0) ? cnt + 3 * (size_t)np + 1 : nullptr;
   // keep the scratch slots resident in L2 (a per-context set-aside of persisting lines)
   const int persist_mb = cp.persist_mb;
   if (persist_mb > 0) l2_window(st, op->dev, a.scratch, sizeof(cpx<T>) * (size_t)N * nslots, persist_mb);
@@ -685,29 +743,47 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   const bool acc = pops.acc_fits && G > 1;
   std::vector<int4> packs;
   std::vector<int4> groups;
-  const int nshared = form_packs(op->pairs_h, cp.RB, packs);
+  int nshared = form_packs(op->pairs_h, cp.RB, packs);
+  // FP64 form: rounds of packs on disjoint orbitals, one pack per group, the side streams joined
+  // between rounds (deterministic W)
+  const bool rounds_on = op->fp64;
+  std::vector<int> rb;
+  if (rounds_on) {
+    rb = form_rounds(packs, op->n);
+    nshared = 0;
+  }
+  const bool acc_on = acc && !rounds_on;
   // groups: runs of at most G consecutive packs with the same shared orbital (accumulated in
   // shared memory by the inverse pass when acc); mixed packs are groups of their own
   for (int k = 0; k < (int)packs.size();) {
     int k1 = k + 1;
     if (k < nshared)
       while (k1 < nshared && k1 - k < G && packs[k1].x == packs[k].x) ++k1;
-    groups.push_back(make_int4(k, k1 - k, (acc && k < nshared) ? packs[k].x : -1, 0));
+    groups.push_back(make_int4(k, k1 - k, (acc_on && k < nshared) ? packs[k].x : -1, 0));
     k = k1;
   }
-  // batches of whole groups holding at most B packs
+  // batches of whole groups holding at most B packs (never across a round boundary); round_end[b]
+  // marks the last batch of a round
   std::vector<int2> batches;  // (first group, end group)
+  std::vector<char> round_end;
   {
+    size_t ri = 1;
     int gb = 0, cnt = 0;
     for (int g = 0; g < (int)groups.size(); ++g) {
-      if (cnt + groups[g].y > B && g > gb) {
+      const bool new_round = rounds_on && ri < rb.size() && groups[g].x == rb[ri];
+      if ((cnt + groups[g].y > B || new_round) && g > gb) {
         batches.push_back(make_int2(gb, g));
+        round_end.push_back(new_round ? 1 : 0);
         gb = g;
         cnt = 0;
       }
+      if (new_round) ++ri;
       cnt += groups[g].y;
     }
-    if (gb < (int)groups.size()) batches.push_back(make_int2(gb, (int)groups.size()));
+    if (gb < (int)groups.size()) {
+      batches.push_back(make_int2(gb, (int)groups.size()));
+      round_end.push_back(1);
+    }
   }
   void *tmp = nullptr;
   ACE_CUDA(cudaMallocAsync(&tmp, sizeof(int4) * (packs.size() + groups.size()), st), "alloc packs");
@@ -725,6 +801,9 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   cudaStream_t side[kSide];
   for (int k = 0; k < kSide; ++k) side[k] = st;
   cudaEvent_t fork = nullptr;
+  cudaEvent_t rev[kSide] = {};
+  if (nstreams > 1 && rounds_on)
+    for (int k = 0; k < nstreams; ++k) ACE_CUDA(cudaEventCreateWithFlags(&rev[k], cudaEventDisableTiming), "event");
   if (nstreams > 1) {
     ACE_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "event");
     ACE_CUDA(cudaEventRecord(fork, st), "event");
@@ -778,8 +857,15 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
     ca.pack0 = p0;
     ACE_CUDA(pops.fwd(pa, p1 - p0, side[k]), "plane forward");
     ACE_CUDA(ace::launch_conv_pass<T>(ca, p1 - p0, side[k]), "pencil pass");
-    ACE_CUDA(pops.inv(pa, b.y - b.x, acc, side[k]), "plane inverse");
+    ACE_CUDA(pops.inv(pa, b.y - b.x, acc_on, side[k]), "plane inverse");
     op->launches += 3;
+    if (rounds_on && nstreams > 1 && round_end[bi]) {
+      // every stream waits for every other one: the next round starts after this one ends
+      for (int j = 0; j < nstreams; ++j) ACE_CUDA(cudaEventRecord(rev[j], side[j]), "event");
+      for (int j = 0; j < nstreams; ++j)
+        for (int q = 0; q < nstreams; ++q)
+          if (q != j) ACE_CUDA(cudaStreamWaitEvent(side[j], rev[q], 0), "round join");
+    }
   }
   if (nstreams > 1) {
     for (int k = 0; k < nstreams; ++k) {
@@ -788,6 +874,8 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
       ACE_CUDA(cudaStreamWaitEvent(st, fork, 0), "join");
     }
     cudaEventDestroy(fork);
+    for (int k = 0; k < nstreams; ++k)
+      if (rev[k]) cudaEventDestroy(rev[k]);
   }
   return ACE_OK;
 }
@@ -808,7 +896,17 @@ cudaError_t dense_gram(const T *X, int nx, const T *Y, int ny, long long K, doub
     }
   }
   *launches += 1;
-  return ace::launch_gram<T>(X, nx, Y, ny, K, scale, false, false, G, st);
+  double *partial = nullptr;
+  if constexpr (sizeof(T) == 8) {
+    // FP64 form: chunk sums added in a fixed order, so that the result repeats bit for bit
+    void *ws = nullptr;
+    cudaError_t e = cudaMallocAsync(&ws, ace::gram_chunks_bytes(nx, ny, K), st);
+    if (e != cudaSuccess) return e;
+    temps.push_back(ws);
+    partial = static_cast<double *>(ws);
+    *launches += 1;
+  }
+  return ace::launch_gram<T>(X, nx, Y, ny, K, scale, false, false, G, st, partial);
 }
 
 // Z = A Y, A (m x n) in T
@@ -855,9 +953,10 @@ cudaError_t screen_cols(const T *phi, int n, long long ld, long long c0, long lo
     if (ace::launch_screen_tma(phi, n, ld, c0, K, dV, O, err, st)) return cudaGetLastError();
     return ace::launch_screen_cols(phi + c0, n, ld, K, dV, O, st);
   } else {
-    ++*launches;
+    *launches += ws ? 2 : 1;
     if (c0 != 0 || K != ld) return cudaErrorInvalidValue;
-    return ace::launch_gram<T>(phi, n, phi, n, K, dV, true, true, O, st);  // clears O itself
+    // clears O itself; with ws the chunk sums are added in a fixed order
+    return ace::launch_gram<T>(phi, n, phi, n, K, dV, true, true, O, st, static_cast<double *>(ws));
   }
 }
 
@@ -936,6 +1035,9 @@ ace_status build_begin(ace_op *op, const void *phi_in, ace_dtype dtype) {
   if constexpr (sizeof(T) == 4) {
     const size_t wsb = d.rho_cut > 0.0 ? screen_workspace_bytes(phi, n, N) : 0;
     if (wsb) ACE_CUDA(op_alloc(op, &screen_ws, wsb), "alloc screen workspace");
+  } else if (d.rho_cut > 0.0) {
+    ACE_CUDA(cudaMallocAsync(&screen_ws, ace::gram_chunks_bytes(n, n, N), st), "alloc screen workspace");
+    op->temps.push_back(screen_ws);
   }
   if (pipelined) {
     ACE_CUDA(cudaMemsetAsync(op->O, 0, sizeof(double) * n * n, st), "zero O");
@@ -1561,7 +1663,9 @@ ace_status ace_autotune(const ace_desc *desc, const void *phi, ace_dtype dtype, 
     if (count == 0 || !find_plane_ops<T>(desc->n[1], desc->n[2], &pops)) return ACE_OK;  // nothing to tune
     ACE_CUDA(op_alloc(op, &op->W, op->esz * (size_t)op->n * op->N), "alloc W");
     const T *phi_w = static_cast<const T *>(op->phi_work);
-    const int sample = std::min((count + 1) / 2, 96);
+    // a sample long enough (about 40% of a 128-orbital build on 96^3) for the L2 reuse of the
+    // blocked pack order and of the persisting scratch window to show in the timing
+    const int sample = std::min((count + 1) / 2, 480);
     cudaEvent_t e0, e1;
     ACE_CUDA(cudaEventCreate(&e0), "event");
     ACE_CUDA(cudaEventCreate(&e1), "event");

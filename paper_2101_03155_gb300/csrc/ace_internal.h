@@ -85,6 +85,8 @@ struct PersistArgs {
   int *ticket;                  // next task number, zeroed
   int *err;                     // set to 1 when a wait gives up
   long long N;
+  unsigned long long wait_ns;   // time limit of one wait for a pack's earlier tasks
+  const int *stall;             // null; else the pencil tasks wait for this word to reach 1 (a test)
 };
 template <typename T>
 struct PersistOps {
@@ -110,9 +112,12 @@ bool pass_length_supported(int L);
 bool axis_factors(int L, int *r1, int *r2);
 
 // Dense steps.
+// partial (gram_chunks_bytes, or null): the CUDA-core Gram of the FP64 form writes chunk sums
+// there and adds them in a fixed order (deterministic), instead of FP64 atomics across chunks.
 template <typename T>
 cudaError_t launch_gram(const T *X, int nx, const T *Y, int ny, long long K, double scale, bool abs_values,
-                        bool upper_only, double *G, cudaStream_t st);
+                        bool upper_only, double *G, cudaStream_t st, double *partial = nullptr);
+size_t gram_chunks_bytes(int nx, int ny, long long K);
 template <typename T>
 cudaError_t launch_left_mul(const T *A, int m, int n, const T *Y, long long K, T *Z, cudaStream_t st);
 

@@ -27,10 +27,13 @@ namespace ace {
 // ----------------------------------------------------------------------------------------
 constexpr int GR_BM = 64, GR_BK = 32, GR_CHUNK = 4096, GR_NT = 256;
 
+// With `partial` non-null the CTA of chunk c writes its scaled tile sums to partial[c] (no
+// atomics) and gram_chunks_reduce_kernel adds the chunks in a fixed order: the result is then
+// the same bit for bit on every run.
 template <typename T, bool ABS>
 __global__ void __launch_bounds__(GR_NT) gram_kernel(const T *__restrict__ X, int nx, const T *__restrict__ Y, int ny,
                                                      long long K, double scale, bool upper_only, int nbx,
-                                                     double *__restrict__ G) {
+                                                     double *__restrict__ G, double *__restrict__ partial) {
   __shared__ T xs[GR_BK][GR_BM + 1];
   __shared__ T ys[GR_BK][GR_BM + 1];
   int bi, bj;
@@ -110,8 +113,28 @@ __global__ void __launch_bounds__(GR_NT) gram_kernel(const T *__restrict__ X, in
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * b;
-      if (i < nx && j < ny) atomicAdd(G + (long long)i * ny + j, scale * (double)acc[a][b]);
+      if (i < nx && j < ny) {
+        if (partial)
+          partial[((long long)blockIdx.y * nx + i) * ny + j] = scale * (double)acc[a][b];
+        else
+          atomicAdd(G + (long long)i * ny + j, scale * (double)acc[a][b]);
+      }
     }
+}
+
+// G_ij = sum over the chunks of partial[c]_ij in chunk order (upper_only: j >= i only)
+__global__ void gram_chunks_reduce_kernel(const double *__restrict__ partial, long long chunks, int nx, int ny,
+                                          bool upper_only, double *__restrict__ G) {
+  const long long ne = (long long)nx * ny;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= ne || (upper_only && e % ny < e / ny)) return;
+  double s = 0.0;
+  for (long long c = 0; c < chunks; ++c) s += partial[c * ne + e];
+  G[e] = s;
+}
+
+size_t gram_chunks_bytes(int nx, int ny, long long K) {
+  return sizeof(double) * (size_t)((K + GR_CHUNK - 1) / GR_CHUNK) * nx * ny;
 }
 
 // FP32 operands: 128 x 64 output tile, 256 threads with 8 x 4 outputs each, k-tiles of 16 staged
@@ -399,7 +422,7 @@ cudaError_t launch_screen_refine(const float *phi, int n, long long N, double dV
 
 template <typename T>
 cudaError_t launch_gram(const T *X, int nx, const T *Y, int ny, long long K, double scale, bool abs_values,
-                        bool upper_only, double *G, cudaStream_t st) {
+                        bool upper_only, double *G, cudaStream_t st, double *partial) {
   if constexpr (sizeof(T) == 4) {
     if (K % 4 == 0 && X == Y && nx == ny && upper_only) {
       const int nb = (nx + GS_B - 1) / GS_B;
@@ -436,15 +459,19 @@ cudaError_t launch_gram(const T *X, int nx, const T *Y, int ny, long long K, dou
   if (e != cudaSuccess) return e;
   dim3 grid(tiles, (unsigned)chunks);
   if (abs_values)
-    gram_kernel<T, true><<<grid, GR_NT, 0, st>>>(X, nx, Y, ny, K, scale, upper_only, nbx, G);
+    gram_kernel<T, true><<<grid, GR_NT, 0, st>>>(X, nx, Y, ny, K, scale, upper_only, nbx, G, partial);
   else
-    gram_kernel<T, false><<<grid, GR_NT, 0, st>>>(X, nx, Y, ny, K, scale, upper_only, nbx, G);
+    gram_kernel<T, false><<<grid, GR_NT, 0, st>>>(X, nx, Y, ny, K, scale, upper_only, nbx, G, partial);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !partial) return e;
+  const long long ne = (long long)nx * ny;
+  gram_chunks_reduce_kernel<<<(unsigned)((ne + 127) / 128), 128, 0, st>>>(partial, chunks, nx, ny, upper_only, G);
   return cudaGetLastError();
 }
 template cudaError_t launch_gram<float>(const float *, int, const float *, int, long long, double, bool, bool,
-                                        double *, cudaStream_t);
+                                        double *, cudaStream_t, double *);
 template cudaError_t launch_gram<double>(const double *, int, const double *, int, long long, double, bool, bool,
-                                         double *, cudaStream_t);
+                                         double *, cudaStream_t, double *);
 
 // ----------------------------------------------------------------------------------------
 // Left multiply Z (m x K) = A (m x n) * Y (n x K); 64 x 64 tile, k-step 16, 4 x 4 per thread.

@@ -76,9 +76,10 @@ __device__ __forceinline__ void mbar_init_fence() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// bounded wait for the phase with the given parity; false if it never completed
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+// bounded wait for the phase with the given parity (at most `limit` polls); false if it never
+// completed
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit = kWaitLimit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -735,7 +736,8 @@ template <bool ABS>
 __global__ void __launch_bounds__(NT2, 1) tc_gram_tma_kernel(const __grid_constant__ CUtensorMap tmX,
                                                             const __grid_constant__ CUtensorMap tmY, int nx, int ny,
                                                             long long c0, long long K, int cs, int tiles_x, int ring,
-                                                            double *__restrict__ partial, int *__restrict__ err) {
+                                                            double *__restrict__ partial, int *__restrict__ err,
+                                                            uint32_t first_wait) {
   extern __shared__ unsigned char dyn[];
   unsigned char *base = align1024(dyn);
   unsigned char *ops = base;                  // 2 buffers x {A_hi, A_lo, B_hi, B_lo}
@@ -831,7 +833,9 @@ __global__ void __launch_bounds__(NT2, 1) tc_gram_tma_kernel(const __grid_consta
   uint32_t fpar = 0;
   for (; q < Q; ++q) {
     const int b = q & 1;
-    const bool got = mbar_wait(smem_u32(&full[stage]), fpar);
+    // the first wait may be given fewer polls (a test of the give-up path); the drain waits below
+    // keep the full limit, so no copy is left in flight at exit
+    const bool got = mbar_wait(smem_u32(&full[stage]), fpar, q == 0 ? first_wait : kWaitLimit);
     const bool freed = pipe.drain(mmad, b);
     if (__syncthreads_or(!(got && freed))) {
       ok = false;
@@ -1412,8 +1416,12 @@ static bool launch_gram_tma(const float *X, int nx, const float *Y, int ny, long
   *e = cudaFuncSetAttribute(tc::tc_gram_tma_kernel<ABS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (*e != cudaSuccess) return true;
   double *partial = static_cast<double *>(ws);
+  // ACE_TC_FIRST_WAIT_POLLS: polls of the kernel's first wait on a TMA box (test knob; 0 makes
+  // the kernel give up at once and report ACE_ERR_TIMEOUT after draining its copies)
+  const char *fw = std::getenv("ACE_TC_FIRST_WAIT_POLLS");
+  const uint32_t first_wait = (fw && *fw) ? (uint32_t)std::strtoul(fw, nullptr, 10) : tc::kWaitLimit;
   tc::tc_gram_tma_kernel<ABS><<<dim3(p.tiles, p.splits), tc::NT2, smem, st>>>(
-      mx, my, nx, ny, c0, K, tc_chunk() / tc::BK, p.tiles_x, p.ring, partial, err);
+      mx, my, nx, ny, c0, K, tc_chunk() / tc::BK, p.tiles_x, p.ring, partial, err, first_wait);
   *e = cudaGetLastError();
   if (*e != cudaSuccess) return true;
   const int n = nx * ny;

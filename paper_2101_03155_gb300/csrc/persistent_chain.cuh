@@ -16,7 +16,7 @@
 // unfinished task can always proceed, and the walk cannot deadlock, whatever the number of
 // resident CTAs.  With lag rounds between the stages of one pack, a task rarely finds its inputs
 // unfinished; when it does, thread 0 polls the counter with an acquire load (bounded in time:
-// after kPersistWaitNs the kernel sets the error word and every CTA leaves).
+// after wait_ns, 2 s by default, the kernel sets the error word and every CTA leaves).
 //
 // Memory order.  A task ends with a CTA barrier, then thread 0 fences and increments the pack's
 // counter; a dependent task's thread 0 reads the counter with acquire semantics before a CTA
@@ -27,7 +27,6 @@
 
 namespace ace {
 
-constexpr unsigned long long kPersistWaitNs = 2000000000ull;  // 2 s of polling before giving up
 
 // Pencil columns per C task: as many as the plane work area holds, at most ACE_PERSIST_GMAX.
 #ifndef ACE_PERSIST_GMAX
@@ -164,6 +163,7 @@ __global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, false>()))
         if (kind == 0 && p >= a.nslots) cnt = a.counters + 2 * np + (p - a.nslots), need = N1;
         if (kind == 1) cnt = a.counters + p, need = N1;
         if (kind == 2) cnt = a.counters + np + p, need = NC;
+        if (kind == 1 && a.stall) cnt = a.stall, need = 1;  // test of the give-up path
         if (cnt && ld_acquire(cnt) < need) {
           const unsigned long long t0 = global_ns();
           while (ld_acquire(cnt) < need) {
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, false>()))
               leave = 1;
               break;
             }
-            if (global_ns() - t0 > kPersistWaitNs) {
+            if (global_ns() - t0 > a.wait_ns) {
               atomicExch(a.err, 1);
               leave = 1;
               break;
