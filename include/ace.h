@@ -61,9 +61,10 @@ typedef enum {
 typedef enum {
   ACE_FP64 = 0,  /* plain form: every step in double precision                                 */
   ACE_MIXED = 1  /* mixed form: FP32 pair densities/FFTs/kernel multiply/accumulation,
-                    BF16x3 split products (FP32 accumulate within 256-point chunks, FP64
-                    across) for the screen |Phi| |Phi|^T, Phi^T W, xi^T psi and xi C; M,
-                    Cholesky, L^-1 and E_x in FP64                                               */
+                    screen |Phi| |Phi|^T as FP32 products on the CUDA cores (FP64 across
+                    K-splits), BF16x3 split products on the tensor cores (FP32 accumulate within
+                    256-point chunks, FP64 across) for Phi^T W, xi^T psi and xi C; M, Cholesky,
+                    L^-1 and E_x in FP64                                                          */
 } ace_precision;
 
 typedef enum { ACE_F32 = 0, ACE_F64 = 1 } ace_dtype;
@@ -108,6 +109,55 @@ ace_status ace_build(const ace_desc *desc, const void *phi, ace_dtype dtype, voi
  * Synchronous like ace_build; the same errors. */
 ace_status ace_build_pairs(const ace_desc *desc, const void *phi, ace_dtype dtype, const int *pairs_host,
                            long npairs, void *cuda_stream, ace_op **out);
+
+/* ---- One build over several GPUs (Eq. vx split by pairs, App. A split by grid points) ----
+ * The pairs of Eq. (vx) are independent terms, and App. A's M_kl = -dV sum_r phi_k(r) W_l(r) and
+ * xi = W L^-T (row-wise xi = L^-1 W, pointwise in r) split over disjoint slabs of grid points.  On
+ * R ranks (one GPU each, one process each):
+ *   1. rank r: ace_exchange_w on its share of the pair list       -> partial W^(r) [norb][N]
+ *   2. caller: reduce-scatter of the W^(r) over point slabs         -> W_slab [norb][N_r] on rank r
+ *   3. rank r: ace_m_partial on its slab of phi and W               -> M^(r) [norb][norb] FP64
+ *   4. caller: all-reduce of the M^(r) (sum)                        -> M on every rank
+ *   5. rank r: ace_build_from_m(M, W_slab)                          -> handle holding xi_slab, L, E_x
+ *   6. apply: ace_apply_coeffs on psi_slab, caller all-reduce of C, ace_apply_finish -> (K psi)_slab
+ * The collectives (steps 2, 4, 6) are the caller's (NCCL, or any other); the library computes.
+ * Every slab array is [norb][npts] (or [m][npts]) with rows contiguous. */
+
+/* Step 1: W = sum of the Eq. (vx) terms of the listed pairs only, W_i += v_ij phi_j and
+ * W_j += v_ij phi_i (i = j once).  pairs_host as in ace_build_pairs (no diagonal pair is added).
+ *   phi: [norb][N] host or device, dtype as given (converted to the working precision).
+ *   W:   [norb][N] in the working dtype of desc->prec (F32 mixed, F64 plain), host or device;
+ *        overwritten.
+ * Synchronous; errors as ace_build_pairs. */
+ace_status ace_exchange_w(const ace_desc *desc, const void *phi, ace_dtype dtype, const int *pairs_host,
+                          long npairs, void *W, void *cuda_stream);
+
+/* Step 3: M_partial = -dV Phi_slab^T W_slab over the npts points of a slab (App. A, M_kl summed
+ * over the slab's points), dV = Omega / N of the whole grid of desc.
+ *   phi_slab, W_slab: device [norb][npts] in the working dtype (ACE_ERR_ARG otherwise).
+ *   M: device FP64 [norb][norb], overwritten.
+ * Synchronous (reads back the tensor-core kernels' give-up flag). */
+ace_status ace_m_partial(const ace_desc *desc, const void *phi_slab, const void *W_slab, ace_dtype dtype,
+                         long long npts, double *M, void *cuda_stream);
+
+/* Step 5: the operator on a slab from the summed M (App. A): M <- (M + M^T)/2, -M = L L^T, L^-1,
+ * E_x = (f/2) tr M, and xi_slab = L^-1 W_slab (rows).  The handle behaves as one from ace_build
+ * on a grid of npts points: exchange_energy, ace_get(ACE_GET_XI / M / M_RAW / L) with
+ * [norb][npts] for xi, ace_apply_coeffs / ace_apply_finish; it holds no W and no pair list.
+ *   M: FP64 [norb][norb], host or device.  W_slab: [norb][npts], host or device, dtype as given.
+ * Synchronous; out as in ace_build (also on ACE_ERR_NOT_POSDEF / ACE_ERR_NONFINITE). */
+ace_status ace_build_from_m(const ace_desc *desc, const double *M, const void *W_slab, ace_dtype dtype,
+                            long long npts, void *cuda_stream, ace_op **out);
+
+/* Step 6, the two halves of ace_apply around the caller's all-reduce (section II, ACE
+ * application): ace_apply_coeffs writes C = dV xi^T psi (device FP64 [norb][m]) for psi of m rows
+ * of the handle's points; ace_apply_finish writes out = -xi C ([m][points], host or device, dtype
+ * as given) from the summed C (device FP64).  On one GPU the two in sequence equal ace_apply.
+ * Synchronous. */
+ace_status ace_apply_coeffs(const ace_op *op, const void *psi, ace_dtype dtype, int m, double *C,
+                            void *cuda_stream);
+ace_status ace_apply_finish(const ace_op *op, const double *C, ace_dtype dtype, int m, void *out,
+                            void *cuda_stream);
 
 /* k independent builds (replicas or snapshots) issued back to back on one stream.  desc, phi and
  * out are arrays of length k; each build is as in ace_build.  On the first failing build the

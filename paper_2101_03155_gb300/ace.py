@@ -48,6 +48,7 @@ EXPORTED = [
     "ace_build", "ace_build_batched", "ace_apply", "exchange_energy", "ace_get", "ace_pair_count",
     "ace_get_size", "ace_stage_times", "ace_kernel_launches", "ace_grid_supported", "ace_destroy",
     "ace_last_error", "ace_exchange_w_noalloc", "ace_autotune", "ace_build_pairs", "ace_scdm",
+    "ace_exchange_w", "ace_m_partial", "ace_build_from_m", "ace_apply_coeffs", "ace_apply_finish",
 ]
 
 
@@ -123,6 +124,12 @@ def load(path: str = LIB_PATH):
                                                vp, vp]
         lib.ace_scdm.argtypes = [c_int, ctypes.c_longlong, c_int, vp, c_int, vp, ctypes.POINTER(c_int),
                                  ctypes.POINTER(ctypes.c_double), vp, ctypes.POINTER(c_long)]
+        lib.ace_exchange_w.argtypes = [ctypes.POINTER(AceDesc), vp, c_int, vp, c_long, vp, vp]
+        lib.ace_m_partial.argtypes = [ctypes.POINTER(AceDesc), vp, vp, c_int, ctypes.c_longlong, vp, vp]
+        lib.ace_build_from_m.argtypes = [ctypes.POINTER(AceDesc), vp, vp, c_int, ctypes.c_longlong, vp,
+                                         ctypes.POINTER(vp)]
+        lib.ace_apply_coeffs.argtypes = [vp, vp, c_int, c_int, vp, vp]
+        lib.ace_apply_finish.argtypes = [vp, vp, c_int, c_int, vp, vp]
         lib.ace_grid_supported.argtypes = [c_int, c_int]
         lib.ace_grid_supported.restype = c_int
         lib.ace_destroy.argtypes = [vp]
@@ -130,7 +137,8 @@ def load(path: str = LIB_PATH):
         lib.ace_last_error.restype = ctypes.c_char_p
         for name in ("ace_build", "ace_build_batched", "ace_apply", "exchange_energy", "ace_get", "ace_get_size",
                      "ace_pair_count", "ace_stage_times", "ace_kernel_launches", "ace_exchange_w_noalloc",
-                     "ace_autotune", "ace_build_pairs", "ace_scdm"):
+                     "ace_autotune", "ace_build_pairs", "ace_scdm", "ace_exchange_w", "ace_m_partial",
+                     "ace_build_from_m", "ace_apply_coeffs", "ace_apply_finish"):
             getattr(lib, name).restype = c_int
         _lib = lib
         return lib
@@ -358,11 +366,79 @@ def ace_exchange_w_noalloc(desc: AceDesc, phi, pairs, W, stream=None):
     return W
 
 
+# ---- one build over several GPUs: the per-rank steps (the caller runs the collectives) ----
+
+def ace_exchange_w(desc: AceDesc, phi, pairs, W, stream=None):
+    """Partial W of Eq. (vx) over the listed pairs only, written into W ([norb][N], working dtype)."""
+    p_ptr, p_code, p_numel = _array_info(phi)
+    w_ptr, w_code, w_numel = _array_info(W)
+    N = desc.n[0] * desc.n[1] * desc.n[2]
+    if p_numel != desc.norb * N or w_numel != desc.norb * N:
+        raise ValueError("phi and W must hold norb x N values")
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    _check(load().ace_exchange_w(ctypes.byref(desc), p_ptr, p_code, pr.ctypes.data if len(pr) else None, len(pr),
+                                 w_ptr, _stream_handle(stream)))
+    return W
+
+
+def ace_m_partial(desc: AceDesc, phi_slab, W_slab, M, stream=None):
+    """M_partial = -dV Phi_slab^T W_slab (FP64 [norb][norb] device tensor M) over a slab of points."""
+    p_ptr, p_code, p_numel = _array_info(phi_slab)
+    w_ptr, w_code, w_numel = _array_info(W_slab)
+    m_ptr, m_code, m_numel = _array_info(M)
+    if p_code != w_code or p_numel != w_numel or p_numel % desc.norb or m_code != ACE_F64 or m_numel != desc.norb ** 2:
+        raise ValueError("phi_slab and W_slab: [norb][npts] of one dtype; M: FP64 [norb][norb]")
+    _check(load().ace_m_partial(ctypes.byref(desc), p_ptr, w_ptr, p_code, p_numel // desc.norb, m_ptr,
+                                _stream_handle(stream)))
+    return M
+
+
+def ace_build_from_m(desc: AceDesc, M, W_slab, stream=None, check: bool = True):
+    """Operator on a slab of points from the summed M (App. A); the handle holds xi_slab."""
+    m_ptr, m_code, m_numel = _array_info(M)
+    w_ptr, w_code, w_numel = _array_info(W_slab)
+    if m_code != ACE_F64 or m_numel != desc.norb ** 2 or w_numel % desc.norb:
+        raise ValueError("M: FP64 [norb][norb]; W_slab: [norb][npts]")
+    npts = w_numel // desc.norb
+    h = ctypes.c_void_p()
+    st = load().ace_build_from_m(ctypes.byref(desc), m_ptr, w_ptr, w_code, npts, _stream_handle(stream),
+                                 ctypes.byref(h))
+    d = AceDesc.from_buffer_copy(desc)
+    op = AceOp(h.value, d) if h.value else None
+    if op is not None:
+        op.npts = npts
+    if check:
+        _check(st, op)
+    return op if check else (st, op)
+
+
+def ace_apply_coeffs(op: AceOp, psi, C, stream=None):
+    """C = dV xi^T psi (FP64 [norb][m] device tensor) for psi of m rows of the handle's points."""
+    p_ptr, p_code, p_numel = _array_info(psi)
+    c_ptr, c_code, c_numel = _array_info(C)
+    m = c_numel // op.norb
+    if c_code != ACE_F64 or c_numel != op.norb * m or m < 1 or p_numel % m:
+        raise ValueError("C must be FP64 [norb][m] with psi of m rows")
+    _check(load().ace_apply_coeffs(op.handle, p_ptr, p_code, m, c_ptr, _stream_handle(stream)))
+    return C
+
+
+def ace_apply_finish(op: AceOp, C, out, stream=None):
+    """out = -xi C for the summed C (FP64 [norb][m] device tensor); out of m rows of the handle's points."""
+    c_ptr, c_code, c_numel = _array_info(C)
+    o_ptr, o_code, o_numel = _array_info(out)
+    m = c_numel // op.norb
+    if c_code != ACE_F64 or c_numel != op.norb * m or m < 1 or o_numel % m:
+        raise ValueError("C must be FP64 [norb][m] with out of m rows")
+    _check(load().ace_apply_finish(op.handle, c_ptr, o_code, m, o_ptr, _stream_handle(stream)))
+    return out
+
+
 # ---- convenience readers (host numpy copies) ----
 
 def get_numpy(op: AceOp, what: int) -> np.ndarray:
     n = op.norb
-    N = op.desc.n[0] * op.desc.n[1] * op.desc.n[2]
+    N = getattr(op, "npts", None) or op.desc.n[0] * op.desc.n[1] * op.desc.n[2]
     work = np.float64 if op.desc.prec == ACE_FP64 else np.float32
     if what in (ACE_GET_XI, ACE_GET_W):
         out = np.empty((n, N), dtype=work)

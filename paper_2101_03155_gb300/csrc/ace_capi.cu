@@ -1090,6 +1090,39 @@ ace_status build_begin(ace_op *op, const void *phi_in, ace_dtype dtype) {
 
 // Phase 2: with the pair list on the host, the pair chain, M, Cholesky and xi; status and E_x are
 // copied back asynchronously.  Call after op->ev[1] has completed.
+// W = sum over the listed pairs op->pairs_h of the Eq. (vx) terms, into op->W (zeroed here): the
+// persistent chain when requested, else the plane chain where the plane shape is compiled, else
+// the five pencil passes.
+template <typename T>
+ace_status run_chain(ace_op *op, const T *phi, int count) {
+  const ace_desc &d = op->desc;
+  const DeviceTables *tab = op->tab;
+  std::vector<void *> &temps = op->temps;
+  ACE_CUDA(cudaMemsetAsync(op->W, 0, op->esz * (size_t)op->n * op->N, op->stream), "zero W");
+  ace::PlaneOps<T> pops{};
+  ace::PersistOps<T> qops{};
+  const bool plane = find_plane_ops<T>(d.n[1], d.n[2], &pops) && env_int("ACE_FORCE_PENCIL", 0) == 0;
+  const bool persistent = plane && find_persist_ops<T>(d.n[0], d.n[1], d.n[2], &qops) &&
+                          env_int("ACE_PERSISTENT", 0) != 0;
+  if (count > 0 && persistent) {
+    const ChainParams cp = chain_params(d, op->fp64);
+    std::vector<int4> packs;
+    form_packs(op->pairs_h, cp.RB, packs);
+    const std::vector<ace::ChainBuild<T>> one{{phi, static_cast<T *>(op->W), static_cast<const T *>(tab->Kperm)}};
+    return run_chain_persistent<T>(op, tab, qops, packs, {}, one, temps, cp);
+  }
+  if (count > 0 && plane) return run_chain_plane<T>(op, phi, tab, pops, count, temps, chain_params(d, op->fp64));
+  if (count > 0) {
+    const cpx<T> *twd[3] = {static_cast<const cpx<T> *>(tab->tw[0]), static_cast<const cpx<T> *>(tab->tw[1]),
+                            static_cast<const cpx<T> *>(tab->tw[2])};
+    return run_chain_pencil<T>(op, phi, static_cast<const T *>(tab->K), twd, count, temps);
+  }
+  return ACE_OK;
+}
+
+template <typename T>
+ace_status factor_and_project(ace_op *op, const T *W);
+
 template <typename T>
 ace_status build_finish(ace_op *op) {
   const ace_desc &d = op->desc;
@@ -1108,25 +1141,7 @@ ace_status build_finish(ace_op *op) {
 
   // ---- pair chain (Eq. vx, Eq. e:vij): W_i = sum_j v_ij phi_j ----
   ACE_CUDA(op_alloc(op, &op->W, op->esz * (size_t)n * N), "alloc W");
-  ACE_CUDA(cudaMemsetAsync(op->W, 0, op->esz * (size_t)n * N, st), "zero W");
-  ace::PlaneOps<T> pops{};
-  ace::PersistOps<T> qops{};
-  const bool plane = find_plane_ops<T>(d.n[1], d.n[2], &pops) && env_int("ACE_FORCE_PENCIL", 0) == 0;
-  const bool persistent = plane && find_persist_ops<T>(d.n[0], d.n[1], d.n[2], &qops) &&
-                          env_int("ACE_PERSISTENT", 0) != 0;
-  if (count > 0 && persistent) {
-    const ChainParams cp = chain_params(d, op->fp64);
-    std::vector<int4> packs;
-    form_packs(op->pairs_h, cp.RB, packs);
-    const std::vector<ace::ChainBuild<T>> one{{phi, static_cast<T *>(op->W), static_cast<const T *>(tab->Kperm)}};
-    s = run_chain_persistent<T>(op, tab, qops, packs, {}, one, temps, cp);
-  } else if (count > 0 && plane) {
-    s = run_chain_plane<T>(op, phi, tab, pops, count, temps, chain_params(d, op->fp64));
-  } else if (count > 0) {
-    const cpx<T> *twd[3] = {static_cast<const cpx<T> *>(tab->tw[0]), static_cast<const cpx<T> *>(tab->tw[1]),
-                            static_cast<const cpx<T> *>(tab->tw[2])};
-    s = run_chain_pencil<T>(op, phi, static_cast<const T *>(tab->K), twd, count, temps);
-  }
+  s = run_chain<T>(op, phi, count);
   if (s != ACE_OK) return s;
   ACE_CUDA(cudaEventRecord(op->ev[2], st), "event record");
 
@@ -1140,15 +1155,27 @@ ace_status build_finish(ace_op *op) {
            "M");
   ACE_CUDA(cudaEventRecord(op->ev[3], st), "event record");
 
-  // ---- -M = L L^T, L^-1, E_x = (f/2) tr M ----
+  return factor_and_project<T>(op, static_cast<const T *>(op->W));
+}
+
+// App. A from M_raw (filled, op->M_raw): -M = L L^T with M symmetrised, L^-1 and E_x = (f/2) tr M
+// (one kernel), then xi = W L^-T stored as rows xi = L^-1 W for the op->N points of W; status and
+// E_x are copied to the readback area; the build's workspaces are released in stream order.
+template <typename T>
+ace_status factor_and_project(ace_op *op, const T *W) {
+  const int n = op->n;
+  const long long N = op->N;
+  cudaStream_t st = op->stream;
+  std::vector<void *> &temps = op->temps;
+  void *tmp = nullptr;
   double *chol_work = nullptr;
   if (n > 128) {
     ACE_CUDA(cudaMallocAsync(&tmp, sizeof(double) * ((size_t)n * n + 4 * n), st), "alloc cholesky workspace");
     temps.push_back(tmp);
     chol_work = static_cast<double *>(tmp);
   }
-  ACE_CUDA(ace::launch_cholesky(op->M_raw, n, d.spin_factor, op->M, op->L, op->Linv, op->energy_d, op->status_d,
-                                chol_work, st),
+  ACE_CUDA(ace::launch_cholesky(op->M_raw, n, op->desc.spin_factor, op->M, op->L, op->Linv, op->energy_d,
+                                op->status_d, chol_work, st),
            "cholesky");
   ++op->launches;
   ACE_CUDA(cudaEventRecord(op->ev[4], st), "event record");
@@ -1165,9 +1192,7 @@ ace_status build_finish(ace_op *op) {
     ++op->launches;
     Linv_T = static_cast<const T *>(tmp);
   }
-  ACE_CUDA(dense_left_mul<T>(Linv_T, n, n, static_cast<const T *>(op->W), N, static_cast<T *>(op->xi), op->tc_err,
-                             st, &op->launches),
-           "xi");
+  ACE_CUDA(dense_left_mul<T>(Linv_T, n, n, W, N, static_cast<T *>(op->xi), op->tc_err, st, &op->launches), "xi");
   ACE_CUDA(cudaEventRecord(op->ev[5], st), "event record");
   char *rb = static_cast<char *>(op->readback);
   ACE_CUDA(cudaMemcpyAsync(rb + 4, op->status_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, st), "status readback");
@@ -1246,25 +1271,63 @@ ace_status deliver_result(T *res, void *out, ace_dtype dtype, long long count, c
   return ACE_OK;
 }
 
+// C = dV xi^T psi (n x m FP64, device) for psi of m rows of op->N points (staged from any side)
 template <typename T>
-ace_status apply_impl(const ace_op *op, const void *psi_in, ace_dtype dtype, int m, void *out, cudaStream_t st) {
-  const int n = op->n;
-  const long long N = op->N;
-  std::vector<void *> temps;
-  struct TempGuard {
-    std::vector<void *> *v;
-    cudaStream_t s;
-    ~TempGuard() {
-      for (void *p : *v) cudaFreeAsync(p, s);
-    }
-  } guard{&temps, st};
+ace_status apply_coeffs_impl(const ace_op *op, const void *psi_in, ace_dtype dtype, int m, double *C, int *err_d,
+                             cudaStream_t st, std::vector<void *> &temps) {
   ace_op tmpop;  // only for staging on `st`
   tmpop.stream = st;
   const T *psi = nullptr;
-  ace_status s = stage_input<T>(&tmpop, psi_in, dtype, (long long)m * N, &psi, &temps);
+  ace_status s = stage_input<T>(&tmpop, psi_in, dtype, (long long)m * op->N, &psi, &temps);
   if (s != ACE_OK) return s;
+  long nl = 0;
+  ACE_CUDA(dense_gram<T>(static_cast<const T *>(op->xi), op->n, psi, m, op->N, op->dV, C, err_d, temps, st, &nl),
+           "xi^T psi");
+  return ACE_OK;
+}
+
+// out = -xi C (m rows of op->N points, any side) from C (n x m FP64, device)
+template <typename T>
+ace_status apply_finish_impl(const ace_op *op, const double *C, ace_dtype dtype, int m, void *out, int *err_d,
+                             cudaStream_t st, std::vector<void *> &temps) {
   void *tmp = nullptr;
-  // C = dV xi psi^T  (n x m, FP64 across 4096-point chunks)
+  ACE_CUDA(cudaMallocAsync(&tmp, sizeof(T) * op->n * m, st), "alloc A");
+  temps.push_back(tmp);
+  T *A = static_cast<T *>(tmp);
+  ACE_CUDA(ace::launch_transpose_scale<T>(C, op->n, m, -1.0, A, st), "transpose");
+  T *res = nullptr;
+  ace_status s = result_target<T>(out, dtype, (long long)m * op->N, st, temps, &res);
+  if (s != ACE_OK) return s;
+  long nl = 0;
+  ACE_CUDA(dense_left_mul<T>(A, m, op->n, static_cast<const T *>(op->xi), op->N, res, err_d, st, &nl), "xi C");
+  return deliver_result<T>(res, out, dtype, (long long)m * op->N, st, temps);
+}
+
+// Frees the temporaries of a call in stream order when it leaves.
+struct TempGuard {
+  std::vector<void *> *v;
+  cudaStream_t s;
+  ~TempGuard() {
+    for (void *p : *v) cudaFreeAsync(p, s);
+  }
+};
+
+// Reads the give-up flag of the call's kernels after the stream has finished them.
+ace_status finish_flag(int *err_d, cudaStream_t st, const char *what) {
+  int err_h = 0;
+  ACE_CUDA(cudaMemcpyAsync(&err_h, err_d, sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
+  ACE_CUDA(cudaStreamSynchronize(st), what);
+  if (err_h) return fail(ACE_ERR_TIMEOUT, "a kernel gave up waiting (tensor-core pipeline or TMA copy)");
+  return ACE_OK;
+}
+
+template <typename T>
+ace_status apply_impl(const ace_op *op, const void *psi_in, ace_dtype dtype, int m, void *out, cudaStream_t st) {
+  const int n = op->n;
+  std::vector<void *> temps;
+  TempGuard guard{&temps, st};
+  void *tmp = nullptr;
+  // C = dV xi psi^T  (n x m, FP64 across chunks)
   ACE_CUDA(cudaMallocAsync(&tmp, sizeof(double) * n * m, st), "alloc C");
   temps.push_back(tmp);
   double *C = static_cast<double *>(tmp);
@@ -1272,24 +1335,11 @@ ace_status apply_impl(const ace_op *op, const void *psi_in, ace_dtype dtype, int
   temps.push_back(tmp);
   int *err_d = static_cast<int *>(tmp);
   ACE_CUDA(cudaMemsetAsync(err_d, 0, sizeof(int), st), "zero flag");
-  long nl = 0;
-  ACE_CUDA(dense_gram<T>(static_cast<const T *>(op->xi), n, psi, m, N, op->dV, C, err_d, temps, st, &nl), "xi^T psi");
-  ACE_CUDA(cudaMallocAsync(&tmp, sizeof(T) * n * m, st), "alloc A");
-  temps.push_back(tmp);
-  T *A = static_cast<T *>(tmp);
-  ACE_CUDA(ace::launch_transpose_scale<T>(C, n, m, -1.0, A, st), "transpose");
-  // out = -C^T xi  (m x N)
-  T *res = nullptr;
-  ace_status s2 = result_target<T>(out, dtype, (long long)m * N, st, temps, &res);
-  if (s2 != ACE_OK) return s2;
-  ACE_CUDA(dense_left_mul<T>(A, m, n, static_cast<const T *>(op->xi), N, res, err_d, st, &nl), "xi C");
-  s2 = deliver_result<T>(res, out, dtype, (long long)m * N, st, temps);
-  if (s2 != ACE_OK) return s2;
-  int err_h = 0;
-  ACE_CUDA(cudaMemcpyAsync(&err_h, err_d, sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
-  ACE_CUDA(cudaStreamSynchronize(st), "apply");
-  if (err_h) return fail(ACE_ERR_TIMEOUT, "a tensor-core kernel gave up waiting for its MMAs");
-  return ACE_OK;
+  ace_status s = apply_coeffs_impl<T>(op, psi_in, dtype, m, C, err_d, st, temps);
+  if (s != ACE_OK) return s;
+  s = apply_finish_impl<T>(op, C, dtype, m, out, err_d, st, temps);
+  if (s != ACE_OK) return s;
+  return finish_flag(err_d, st, "apply");
 }
 
 // SCDM localisation of n orbitals of N points: pivots and Loewdin factor (scdm.cu), then
@@ -1365,6 +1415,57 @@ size_t item_bytes(const ace_op *op, int what) {
 namespace ace {
 void set_last_error(const char *msg) { g_last_error = msg; }
 }  // namespace ace
+
+namespace {
+// Sorted, checked copy of a caller's pair list: i <= j, 0 <= i, j < norb, each pair once.
+ace_status checked_pairs(const ace_desc *desc, const int *pairs_host, long npairs, std::vector<int2> &given) {
+  if (npairs < 0 || (npairs > 0 && !pairs_host)) return fail(ACE_ERR_ARG, "bad pair list");
+  const long maxp = (long)desc->norb * (desc->norb + 1) / 2;
+  if (npairs > maxp) return fail(ACE_ERR_ARG, "%ld pairs for %d orbitals", npairs, desc->norb);
+  given.assign((size_t)npairs, make_int2(0, 0));
+  for (long p = 0; p < npairs; ++p) {
+    int i = pairs_host[2 * p], j = pairs_host[2 * p + 1];
+    if (i > j) std::swap(i, j);
+    if (i < 0 || j >= desc->norb) return fail(ACE_ERR_ARG, "pair %ld = (%d, %d) outside [0, %d)", p, i, j, desc->norb);
+    given[(size_t)p] = make_int2(i, j);
+  }
+  std::sort(given.begin(), given.end(), [](int2 a, int2 b) { return a.x < b.x || (a.x == b.x && a.y < b.y); });
+  for (size_t p = 1; p < given.size(); ++p)
+    if (given[p].x == given[p - 1].x && given[p].y == given[p - 1].y)
+      return fail(ACE_ERR_ARG, "pair (%d, %d) listed twice", given[p].x, given[p].y);
+  return ACE_OK;
+}
+
+// The pair chain of a begun build with a given pair list, into W_out (the caller's buffer when it
+// is device memory, else through a device buffer and a copy); no M, no Cholesky.
+template <typename T>
+ace_status exchange_w_impl(ace_op *op, void *W_out) {
+  const int count = *static_cast<const int *>(op->readback);
+  op->npairs = count;
+  const int2 *ph = reinterpret_cast<const int2 *>(static_cast<const char *>(op->readback) + 32);
+  op->pairs_h.assign(ph, ph + count);
+  const size_t bytes = op->esz * (size_t)op->n * op->N;
+  const bool direct = is_device_pointer(W_out);
+  if (direct)
+    op->W = W_out;
+  else
+    ACE_CUDA(op_alloc(op, &op->W, bytes), "alloc W");
+  ace_status s = run_chain<T>(op, static_cast<const T *>(op->phi_work), count);
+  if (s == ACE_OK && !direct)
+    ACE_CUDA(cudaMemcpyAsync(W_out, op->W, bytes, cudaMemcpyDefault, op->stream), "W copy");
+  for (void *p : op->temps) cudaFreeAsync(p, op->stream);
+  op->temps.clear();
+  if (direct) op->W = nullptr;  // the caller's buffer
+  if (s != ACE_OK) return s;
+  return finish_flag(op->tc_err, op->stream, "exchange W");
+}
+
+ace_status working_dtype(const ace_desc *desc, ace_dtype dtype) {
+  if ((desc->prec == ACE_FP64) != (dtype == ACE_F64))
+    return fail(ACE_ERR_ARG, "dtype %d is not the working type of precision %d", (int)dtype, (int)desc->prec);
+  return ACE_OK;
+}
+}  // namespace
 
 extern "C" {
 
@@ -1444,6 +1545,155 @@ ace_status ace_build(const ace_desc *desc, const void *phi, ace_dtype dtype, voi
   return s;
 }
 
+ace_status ace_exchange_w(const ace_desc *desc, const void *phi, ace_dtype dtype, const int *pairs_host, long npairs,
+                          void *W, void *cuda_stream) {
+  ace_status s = check_desc(desc);
+  if (s != ACE_OK) return s;
+  if (!phi || !W) return fail(ACE_ERR_ARG, "NULL argument");
+  if (dtype != ACE_F32 && dtype != ACE_F64) return fail(ACE_ERR_ARG, "unknown dtype %d", (int)dtype);
+  std::vector<int2> given;
+  s = checked_pairs(desc, pairs_host, npairs, given);
+  if (s != ACE_OK) return s;
+  ace_op *op = new_op(desc, static_cast<cudaStream_t>(cuda_stream), &s);
+  if (!op) return s;
+  op->given.swap(given);
+  op->use_given = true;
+  s = begin_any(op, phi, dtype);
+  if (s == ACE_OK) {
+    cudaError_t e = cudaEventSynchronize(op->ev[1]);
+    if (e != cudaSuccess)
+      s = cuda_fail(e, "pair upload");
+    else
+      s = op->fp64 ? exchange_w_impl<double>(op, W) : exchange_w_impl<float>(op, W);
+  }
+  cudaStreamSynchronize(op->stream);
+  ace_destroy(op);
+  return s;
+}
+
+ace_status ace_m_partial(const ace_desc *desc, const void *phi_slab, const void *W_slab, ace_dtype dtype,
+                         long long npts, double *M, void *cuda_stream) {
+  ace_status s = check_desc(desc);
+  if (s != ACE_OK) return s;
+  if (!phi_slab || !W_slab || !M) return fail(ACE_ERR_ARG, "NULL argument");
+  if (npts < 1) return fail(ACE_ERR_ARG, "npts = %lld < 1", npts);
+  if ((s = working_dtype(desc, dtype)) != ACE_OK) return s;
+  if (!is_device_pointer(phi_slab) || !is_device_pointer(W_slab) || !is_device_pointer(M))
+    return fail(ACE_ERR_ARG, "phi_slab, W_slab and M must be device memory");
+  ace_op *op = new_op(desc, static_cast<cudaStream_t>(cuda_stream), &s);  // dV of the whole grid
+  if (!op) return s;
+  const double dV = op->dV;
+  const int n = op->n;
+  ace_destroy(op);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  std::vector<void *> temps;
+  TempGuard guard{&temps, st};
+  void *tmp = nullptr;
+  ACE_CUDA(cudaMallocAsync(&tmp, sizeof(int), st), "alloc flag");
+  temps.push_back(tmp);
+  int *err_d = static_cast<int *>(tmp);
+  ACE_CUDA(cudaMemsetAsync(err_d, 0, sizeof(int), st), "zero flag");
+  long nl = 0;
+  if (dtype == ACE_F64)
+    ACE_CUDA(dense_gram<double>(static_cast<const double *>(phi_slab), n, static_cast<const double *>(W_slab), n, npts,
+                                -dV, M, err_d, temps, st, &nl),
+             "M partial");
+  else
+    ACE_CUDA(dense_gram<float>(static_cast<const float *>(phi_slab), n, static_cast<const float *>(W_slab), n, npts,
+                               -dV, M, err_d, temps, st, &nl),
+             "M partial");
+  return finish_flag(err_d, st, "M partial");
+}
+
+ace_status ace_build_from_m(const ace_desc *desc, const double *M, const void *W_slab, ace_dtype dtype, long long npts,
+                            void *cuda_stream, ace_op **out) {
+  if (!out) return fail(ACE_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  ace_status s = check_desc(desc);
+  if (s != ACE_OK) return s;
+  if (!M || !W_slab) return fail(ACE_ERR_ARG, "NULL argument");
+  if (npts < 1) return fail(ACE_ERR_ARG, "npts = %lld < 1", npts);
+  if (dtype != ACE_F32 && dtype != ACE_F64) return fail(ACE_ERR_ARG, "unknown dtype %d", (int)dtype);
+  ace_op *op = new_op(desc, static_cast<cudaStream_t>(cuda_stream), &s);
+  if (!op) return s;
+  op->N = npts;  // the slab's points; dV stays that of the whole grid
+  const int n = op->n;
+  cudaStream_t st = op->stream;
+  auto run = [&]() -> ace_status {
+    for (int i = 0; i < 6; ++i) ACE_CUDA(cudaEventCreate(&op->ev[i]), "event create");
+    for (int i = 0; i < 4; ++i) ACE_CUDA(cudaEventRecord(op->ev[i], st), "event record");
+    ACE_CUDA(op_alloc(op, &op->status_d, sizeof(int) * 4), "alloc status");
+    op->tc_err = op->status_d + 1;
+    ACE_CUDA(cudaMemsetAsync(op->status_d, 0, sizeof(int) * 4, st), "zero status");
+    ACE_CUDA(op_alloc(op, &op->energy_d, sizeof(double) * 2), "alloc energy");
+    ACE_CUDA(op_alloc(op, &op->M_raw, sizeof(double) * n * n), "alloc M_raw");
+    ACE_CUDA(op_alloc(op, &op->M, sizeof(double) * n * n), "alloc M");
+    ACE_CUDA(op_alloc(op, &op->L, sizeof(double) * n * n), "alloc L");
+    ACE_CUDA(op_alloc(op, &op->Linv, sizeof(double) * n * n), "alloc Linv");
+    ACE_CUDA(pinned_get(32, &op->readback), "pinned readback");
+    op->readback_bytes = 32;
+    ACE_CUDA(cudaMemcpyAsync(op->M_raw, M, sizeof(double) * n * n, cudaMemcpyDefault, st), "M copy");
+    if (op->fp64) {
+      const double *W = nullptr;
+      ace_status r = stage_input<double>(op, W_slab, dtype, (long long)n * npts, &W, &op->temps);
+      return r != ACE_OK ? r : factor_and_project<double>(op, W);
+    }
+    const float *W = nullptr;
+    ace_status r = stage_input<float>(op, W_slab, dtype, (long long)n * npts, &W, &op->temps);
+    return r != ACE_OK ? r : factor_and_project<float>(op, W);
+  };
+  s = run();
+  if (s == ACE_OK) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    s = e == cudaSuccess ? build_collect(op) : cuda_fail(e, "build from M");
+  }
+  if (keeps_handle(s)) {
+    *out = op;
+    return s;
+  }
+  cudaStreamSynchronize(st);
+  ace_destroy(op);
+  return s;
+}
+
+ace_status ace_apply_coeffs(const ace_op *op, const void *psi, ace_dtype dtype, int m, double *C, void *cuda_stream) {
+  if (!op || !psi || !C) return fail(ACE_ERR_ARG, "NULL argument");
+  if (m < 1) return fail(ACE_ERR_ARG, "m = %d < 1", m);
+  if (dtype != ACE_F32 && dtype != ACE_F64) return fail(ACE_ERR_ARG, "unknown dtype %d", (int)dtype);
+  if (op->status != 0) return fail(ACE_ERR_NOT_POSDEF, "operator build did not complete (status %d)", op->status);
+  if (!is_device_pointer(C)) return fail(ACE_ERR_ARG, "C must be device memory");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  std::vector<void *> temps;
+  TempGuard guard{&temps, st};
+  void *tmp = nullptr;
+  ACE_CUDA(cudaMallocAsync(&tmp, sizeof(int), st), "alloc flag");
+  temps.push_back(tmp);
+  int *err_d = static_cast<int *>(tmp);
+  ACE_CUDA(cudaMemsetAsync(err_d, 0, sizeof(int), st), "zero flag");
+  ace_status s = op->fp64 ? apply_coeffs_impl<double>(op, psi, dtype, m, C, err_d, st, temps)
+                          : apply_coeffs_impl<float>(op, psi, dtype, m, C, err_d, st, temps);
+  return s != ACE_OK ? s : finish_flag(err_d, st, "apply coefficients");
+}
+
+ace_status ace_apply_finish(const ace_op *op, const double *C, ace_dtype dtype, int m, void *out, void *cuda_stream) {
+  if (!op || !C || !out) return fail(ACE_ERR_ARG, "NULL argument");
+  if (m < 1) return fail(ACE_ERR_ARG, "m = %d < 1", m);
+  if (dtype != ACE_F32 && dtype != ACE_F64) return fail(ACE_ERR_ARG, "unknown dtype %d", (int)dtype);
+  if (op->status != 0) return fail(ACE_ERR_NOT_POSDEF, "operator build did not complete (status %d)", op->status);
+  if (!is_device_pointer(C)) return fail(ACE_ERR_ARG, "C must be device memory");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  std::vector<void *> temps;
+  TempGuard guard{&temps, st};
+  void *tmp = nullptr;
+  ACE_CUDA(cudaMallocAsync(&tmp, sizeof(int), st), "alloc flag");
+  temps.push_back(tmp);
+  int *err_d = static_cast<int *>(tmp);
+  ACE_CUDA(cudaMemsetAsync(err_d, 0, sizeof(int), st), "zero flag");
+  ace_status s = op->fp64 ? apply_finish_impl<double>(op, C, dtype, m, out, err_d, st, temps)
+                          : apply_finish_impl<float>(op, C, dtype, m, out, err_d, st, temps);
+  return s != ACE_OK ? s : finish_flag(err_d, st, "apply finish");
+}
+
 ace_status ace_build_pairs(const ace_desc *desc, const void *phi, ace_dtype dtype, const int *pairs_host, long npairs,
                            void *cuda_stream, ace_op **out) {
   if (!out) return fail(ACE_ERR_ARG, "out is NULL");
@@ -1452,20 +1702,9 @@ ace_status ace_build_pairs(const ace_desc *desc, const void *phi, ace_dtype dtyp
   if (s != ACE_OK) return s;
   if (!phi) return fail(ACE_ERR_ARG, "phi is NULL");
   if (dtype != ACE_F32 && dtype != ACE_F64) return fail(ACE_ERR_ARG, "unknown dtype %d", (int)dtype);
-  if (npairs < 0 || (npairs > 0 && !pairs_host)) return fail(ACE_ERR_ARG, "bad pair list");
-  const long maxp = (long)desc->norb * (desc->norb + 1) / 2;
-  if (npairs > maxp) return fail(ACE_ERR_ARG, "%ld pairs for %d orbitals", npairs, desc->norb);
-  std::vector<int2> given((size_t)npairs);
-  for (long p = 0; p < npairs; ++p) {
-    int i = pairs_host[2 * p], j = pairs_host[2 * p + 1];
-    if (i > j) std::swap(i, j);
-    if (i < 0 || j >= desc->norb) return fail(ACE_ERR_ARG, "pair %ld = (%d, %d) outside [0, %d)", p, i, j, desc->norb);
-    given[(size_t)p] = make_int2(i, j);
-  }
-  std::sort(given.begin(), given.end(), [](int2 a, int2 b) { return a.x < b.x || (a.x == b.x && a.y < b.y); });
-  for (size_t p = 1; p < given.size(); ++p)
-    if (given[p].x == given[p - 1].x && given[p].y == given[p - 1].y)
-      return fail(ACE_ERR_ARG, "pair (%d, %d) listed twice", given[p].x, given[p].y);
+  std::vector<int2> given;
+  s = checked_pairs(desc, pairs_host, npairs, given);
+  if (s != ACE_OK) return s;
   ace_op *op = new_op(desc, static_cast<cudaStream_t>(cuda_stream), &s);
   if (!op) return s;
   op->given.swap(given);

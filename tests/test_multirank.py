@@ -95,3 +95,105 @@ def test_shard_pairs_partition():
         assert max(sizes) - min(sizes) <= 1
     with pytest.raises(ValueError):
         shard_pairs(pairs, 0)
+
+
+class _OracleSlabKernels:
+    """The per-rank steps restated with the FP64 oracle (and LAPACK for the factorisation of the
+    summed M), on numpy-backed CPU tensors."""
+
+    def __init__(self, w):
+        self.w = w
+
+    def exchange_w(self, phi, pairs):
+        import torch
+
+        import oracle
+        from paper_2101_03155_gb300.sharding import pair_mask
+
+        W = oracle.exchange_w(phi.numpy(), self.w.lattice, mask=pair_mask(pairs, self.w.norb))
+        return torch.from_numpy(W.reshape(self.w.norb, -1).copy())
+
+    def m_partial(self, phi_slab, W_slab):
+        import torch
+
+        import oracle
+
+        r = oracle.ace_from_w(phi_slab.numpy(), W_slab.numpy(), self.w.dV, want_xi=False)
+        return torch.from_numpy(r["M_raw"].copy())
+
+    def build_from_m(self, M, W_slab):
+        import scipy.linalg as sla
+
+        Ms = 0.5 * (M.numpy() + M.numpy().T)
+        L = np.linalg.cholesky(-Ms)
+        xi = sla.solve_triangular(L, W_slab.numpy(), lower=True)
+        return {"M": Ms, "L": L, "xi": xi, "E_x": 0.5 * self.w.spin_factor * np.trace(Ms)}
+
+    def apply_coeffs(self, op, psi_slab):
+        import torch
+
+        return torch.from_numpy(self.w.dV * op["xi"] @ psi_slab.numpy().T)
+
+    def apply_finish(self, op, C, m):
+        import torch
+
+        return torch.from_numpy(-(C.numpy().T @ op["xi"]))
+
+
+def _slab_worker(rank, world, port, out):
+    dist = _init(rank, world, port)
+    import torch
+
+    import oracle
+    from paper_2101_03155_gb300.sharding import Collectives, point_slabs, sharded_apply, sharded_build
+    from workloads.generators import probe_vectors, water_like
+
+    oracle.set_threads(2)
+    w = water_like(4, 9.3, (24, 24, 24), np.random.default_rng(606), rho_cut=1e-3, dmin=3.5)
+    _, mask = oracle.screen(w.phi, w.lattice, w.rho_cut)
+    iu = np.triu_indices(w.norb)
+    pairs = np.stack([iu[0][mask[iu]], iu[1][mask[iu]]], axis=1)
+    comm = Collectives(dist)
+    kern = _OracleSlabKernels(w)
+    slabs = point_slabs(w.npts, world)
+    op, (p0, p1) = sharded_build(kern, comm, torch.from_numpy(w.phi.copy()), pairs, slabs)
+    psi = probe_vectors(w.phi, w.dV, 5).reshape(2, -1)
+    kpsi_slab = sharded_apply(kern, comm, op, torch.from_numpy(psi[:, p0:p1].copy())).numpy()
+    ref = oracle.ace_build(w.phi, w.lattice, mask=mask, spin_factor=w.spin_factor)
+    xi_ref = ref["xi"].reshape(w.norb, -1)[:, p0:p1]
+    kref = oracle.ace_apply(ref["xi"], psi.reshape((2,) + w.grid), w.dV).reshape(2, -1)[:, p0:p1]
+    out[rank] = {
+        "slab": (p0, p1),
+        "M": float(np.abs(op["M"] - ref["M"]).max() / np.abs(ref["M"]).max()),
+        "L": float(np.abs(op["L"] - ref["L"]).max() / np.abs(ref["L"]).max()),
+        "xi": float(np.abs(op["xi"] - xi_ref).max() / np.abs(xi_ref).max()),
+        "E_x": abs(op["E_x"] - ref["E_x"]),
+        "kpsi": float(np.abs(kpsi_slab - kref).max() / np.abs(kref).max()),
+    }
+    dist.destroy_process_group()
+
+
+def test_slab_decomposition_matches_one_rank_build():
+    """World size 2 (gloo): pair shards -> partial W -> reduce-scatter over point slabs -> M
+    partials -> all-reduce -> replicated Cholesky and xi on each slab -> sharded application,
+    each step restated with the oracle; equals the one-rank oracle build to 1e-12."""
+    port = _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_slab_worker, args=(2, port, out), nprocs=2, join=True)
+    assert out[0]["slab"][1] == out[1]["slab"][0]
+    for r in range(2):
+        for key in ("M", "L", "xi", "kpsi"):
+            assert out[r][key] <= 1e-12, (r, key, out[r][key])
+        assert out[r]["E_x"] <= 1e-12
+
+
+def test_point_slabs_partition():
+    from paper_2101_03155_gb300.sharding import point_slabs
+
+    for npts, r in ((884736, 2), (884736, 8), (13824, 3), (1000, 4), (100, 1)):
+        s = point_slabs(npts, r)
+        assert s[0][0] == 0 and s[-1][1] == npts and len(s) == r
+        assert all(a[1] == b[0] for a, b in zip(s, s[1:]))
+        assert all(p1 % 128 == 0 for _, p1 in s[:-1])
+        sizes = [p1 - p0 for p0, p1 in s]
+        assert max(sizes) - min(sizes) <= 128
