@@ -951,6 +951,12 @@ cudaError_t screen_cols(const T *phi, int n, long long ld, long long c0, long lo
     }
     ++*launches;
     if (ace::launch_screen_tma(phi, n, ld, c0, K, dV, O, err, st)) return cudaGetLastError();
+    if (K % 4 != 0 || ld % 4 != 0 || c0 % 4 != 0) {
+      // point counts off the 16-byte grid (odd axis lengths): the general Gram kernel (clears O;
+      // such inputs are never split into column chunks)
+      if (c0 != 0 || K != ld) return cudaErrorInvalidValue;
+      return ace::launch_gram<T>(phi, n, phi, n, K, dV, true, true, O, st);
+    }
     return ace::launch_screen_cols(phi + c0, n, ld, K, dV, O, st);
   } else {
     *launches += ws ? 2 : 1;
@@ -1101,7 +1107,8 @@ ace_status run_chain(ace_op *op, const T *phi, int count) {
   ACE_CUDA(cudaMemsetAsync(op->W, 0, op->esz * (size_t)op->n * op->N, op->stream), "zero W");
   ace::PlaneOps<T> pops{};
   ace::PersistOps<T> qops{};
-  const bool plane = find_plane_ops<T>(d.n[1], d.n[2], &pops) && env_int("ACE_FORCE_PENCIL", 0) == 0;
+  const bool plane = find_plane_ops<T>(d.n[1], d.n[2], &pops) && ace::conv_length_supported(d.n[0]) &&
+                     env_int("ACE_FORCE_PENCIL", 0) == 0;
   const bool persistent = plane && find_persist_ops<T>(d.n[0], d.n[1], d.n[2], &qops) &&
                           env_int("ACE_PERSISTENT", 0) != 0;
   if (count > 0 && persistent) {
@@ -1899,7 +1906,8 @@ ace_status ace_autotune(const ace_desc *desc, const void *phi, ace_dtype dtype, 
   auto run = [&](auto tag) -> ace_status {
     using T = decltype(tag);
     ace::PlaneOps<T> pops{};
-    if (count == 0 || !find_plane_ops<T>(desc->n[1], desc->n[2], &pops)) return ACE_OK;  // nothing to tune
+    if (count == 0 || !find_plane_ops<T>(desc->n[1], desc->n[2], &pops) || !ace::conv_length_supported(desc->n[0]))
+      return ACE_OK;  // nothing to tune
     ACE_CUDA(op_alloc(op, &op->W, op->esz * (size_t)op->n * op->N), "alloc W");
     const T *phi_w = static_cast<const T *>(op->phi_work);
     // a sample long enough (about 40% of a 128-orbital build on 96^3) for the L2 reuse of the

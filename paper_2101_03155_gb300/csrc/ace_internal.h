@@ -107,6 +107,8 @@ template <typename T>
 cudaError_t launch_conv_pass(const PairPassArgs<T> &a, int npacks, cudaStream_t st);
 
 bool pass_length_supported(int L);
+// Axis-1 pass of the plane chain compiled for this length (lengths up to 160)
+bool conv_length_supported(int L);
 // Two-stage factorisation L = r1 * r2 of a compiled axis length (output index k sits at
 // position (k % r1) * r2 + k / r1 after a forward transform).
 bool axis_factors(int L, int *r1, int *r2);

@@ -278,6 +278,10 @@ template <int D, typename T> struct Dft<10, D, T> : DftPFA<2, 5, D, T> {};
 template <int D, typename T> struct Dft<12, D, T> : DftPFA<3, 4, D, T> {};
 template <int D, typename T> struct Dft<15, D, T> : DftPFA<3, 5, D, T> {};
 template <int D, typename T> struct Dft<16, D, T> : DftCT<4, 4, D, T> {};
+template <int D, typename T> struct Dft<18, D, T> : DftPFA<2, 9, D, T> {};
+template <int D, typename T> struct Dft<20, D, T> : DftPFA<4, 5, D, T> {};
+template <int D, typename T> struct Dft<25, D, T> : DftCT<5, 5, D, T> {};
+template <int D, typename T> struct Dft<27, D, T> : DftCT<3, 9, D, T> {};
 
 // ---------------------------------------------------------------------------------------
 // Factorisation L = R1 * R2 used by the two-stage pencil FFT (both factors in registers).
@@ -290,20 +294,57 @@ struct Factor;
     static constexpr int R1 = A_, R2 = B_;    \
     static_assert(A_ * B_ == L_, "factor");   \
   };
+ACE_FACTOR(2, 2, 1)
+ACE_FACTOR(3, 3, 1)
+ACE_FACTOR(4, 4, 1)
+ACE_FACTOR(5, 5, 1)
+ACE_FACTOR(6, 3, 2)
 ACE_FACTOR(8, 4, 2)
+ACE_FACTOR(9, 3, 3)
+ACE_FACTOR(10, 5, 2)
 ACE_FACTOR(12, 4, 3)
+ACE_FACTOR(15, 5, 3)
 ACE_FACTOR(16, 4, 4)
+ACE_FACTOR(18, 6, 3)
 ACE_FACTOR(20, 5, 4)
 ACE_FACTOR(24, 6, 4)
+ACE_FACTOR(25, 5, 5)
+ACE_FACTOR(27, 9, 3)
+ACE_FACTOR(30, 6, 5)
 ACE_FACTOR(32, 8, 4)
+ACE_FACTOR(36, 6, 6)
+ACE_FACTOR(40, 8, 5)
+ACE_FACTOR(45, 9, 5)
 ACE_FACTOR(48, 8, 6)
+ACE_FACTOR(50, 10, 5)
+ACE_FACTOR(54, 9, 6)
+ACE_FACTOR(60, 12, 5)
 ACE_FACTOR(64, 8, 8)
 ACE_FACTOR(72, 9, 8)
+ACE_FACTOR(75, 15, 5)
+ACE_FACTOR(80, 16, 5)
+ACE_FACTOR(81, 9, 9)
+ACE_FACTOR(90, 10, 9)
 ACE_FACTOR(96, 12, 8)
+ACE_FACTOR(100, 10, 10)
 ACE_FACTOR(108, 12, 9)
+ACE_FACTOR(120, 12, 10)
+ACE_FACTOR(125, 25, 5)
 ACE_FACTOR(128, 16, 8)
+ACE_FACTOR(135, 15, 9)
 ACE_FACTOR(144, 12, 12)
+ACE_FACTOR(150, 15, 10)
 ACE_FACTOR(160, 16, 10)
+ACE_FACTOR(162, 18, 9)
+ACE_FACTOR(180, 15, 12)
+ACE_FACTOR(192, 16, 12)
+ACE_FACTOR(200, 20, 10)
+ACE_FACTOR(216, 18, 12)
+ACE_FACTOR(225, 15, 15)
+ACE_FACTOR(240, 16, 15)
+ACE_FACTOR(243, 27, 9)
+ACE_FACTOR(250, 25, 10)
+ACE_FACTOR(256, 16, 16)
 #undef ACE_FACTOR
 
 }  // namespace ace

@@ -20,15 +20,24 @@
 #include "ace_internal.h"
 #include "fft.cuh"
 
-#define ACE_PASS_LENGTHS(X) X(8) X(12) X(16) X(20) X(24) X(32) X(48) X(64) X(72) X(96) X(108) X(128) X(144) X(160)
+// Every axis length 2^a 3^b 5^c up to 256, in four groups compiled in separate translation units
+// (pair_chain_[abcd]_f{32,64}.cu); the axis-1 pass of the plane chain (conv) takes lengths up to 160.
+#define ACE_LENGTHS_A(X) X(2) X(3) X(4) X(5) X(6) X(8) X(9) X(10) X(12) X(15) X(16) X(18) X(20) X(24) X(25) X(27) X(30) X(32) X(36)
+#define ACE_LENGTHS_B(X) X(40) X(45) X(48) X(50) X(54) X(60) X(64) X(72) X(75) X(80) X(81) X(90) X(96) X(100)
+#define ACE_LENGTHS_C(X) X(108) X(120) X(125) X(128) X(135) X(144) X(150) X(160) X(162) X(180)
+#define ACE_LENGTHS_D(X) X(192) X(200) X(216) X(225) X(240) X(243) X(250) X(256)
+#define ACE_CONV_LENGTHS_C(X) X(108) X(120) X(125) X(128) X(135) X(144) X(150) X(160)
+#define ACE_PASS_LENGTHS(X) ACE_LENGTHS_A(X) ACE_LENGTHS_B(X) ACE_LENGTHS_C(X) ACE_LENGTHS_D(X)
 
 namespace ace {
 
-template <int L>
+// Pencil tile: 16 lines of L points (odd pitch), or 8 where 16 would not fit in 48 KB of static
+// shared memory (FP64 beyond about 190 points).
+template <typename T, int L>
 struct PassShape {
   static constexpr int R1 = Factor<L>::R1;
   static constexpr int R2 = Factor<L>::R2;
-  static constexpr int TILE = 16;
+  static constexpr int TILE = (16LL * (L + 1) + L) * (long long)sizeof(cpx<T>) <= 48LL * 1024 ? 16 : 8;
   static constexpr int LP = L + 1;  // odd pitch: lanes over lines hit distinct banks
   static constexpr int NT = TILE * (R1 > R2 ? R1 : R2);
 };
@@ -41,7 +50,7 @@ __device__ __forceinline__ cpx<T> conjc(cpx<T> a) {
 // stage 1 of the two-stage transform in direction D (twiddled unless TWIDDLE is false)
 template <typename T, int L, int D, bool TWIDDLE>
 __device__ __forceinline__ void pencil_stage1(cpx<T> *s, const cpx<T> *tw, int tvalid) {
-  using S = PassShape<L>;
+  using S = PassShape<T, L>;
   for (int task = threadIdx.x; task < S::TILE * S::R2; task += S::NT) {
     const int t = task % S::TILE, n2 = task / S::TILE;
     if (t >= tvalid) continue;
@@ -64,7 +73,7 @@ __device__ __forceinline__ void pencil_stage1(cpx<T> *s, const cpx<T> *tw, int t
 
 template <typename T, int L, int D>
 __device__ __forceinline__ void pencil_stage2(cpx<T> *s, int tvalid) {
-  using S = PassShape<L>;
+  using S = PassShape<T, L>;
   for (int task = threadIdx.x; task < S::TILE * S::R1; task += S::NT) {
     const int t = task % S::TILE, k1 = task / S::TILE;
     if (t >= tvalid) continue;
@@ -80,13 +89,12 @@ __device__ __forceinline__ void pencil_stage2(cpx<T> *s, int tvalid) {
 
 template <int L>
 __device__ __forceinline__ int perm_pos(int k) {
-  using S = PassShape<L>;
-  return (k % S::R1) * S::R2 + k / S::R1;
+  return (k % Factor<L>::R1) * Factor<L>::R2 + k / Factor<L>::R1;
 }
 
 template <typename T, int L, int MODE>
-__global__ void __launch_bounds__(PassShape<L>::NT) pair_pass_kernel(PairPassArgs<T> a) {
-  using S = PassShape<L>;
+__global__ void __launch_bounds__((PassShape<T, L>::NT)) pair_pass_kernel(PairPassArgs<T> a) {
+  using S = PassShape<T, L>;
   constexpr int TILE = S::TILE, LP = S::LP, NT = S::NT;
   __shared__ cpx<T> s[TILE * LP];
   __shared__ cpx<T> tw[L];
@@ -317,20 +325,9 @@ cudaError_t launch_conv_L(const PairPassArgs<T> &a, int npacks, cudaStream_t st)
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_conv_impl(const PairPassArgs<T> &a, int npacks, cudaStream_t st) {
-  switch (a.n1) {
-#define ACE_CASE(L_) \
-  case L_: return launch_conv_L<T, L_>(a, npacks, st);
-    ACE_PASS_LENGTHS(ACE_CASE)
-#undef ACE_CASE
-    default: return cudaErrorInvalidValue;
-  }
-}
-
 template <typename T, int L>
 cudaError_t launch_pass_L(int mode, const PairPassArgs<T> &a, int npacks, cudaStream_t st) {
-  using S = PassShape<L>;
+  using S = PassShape<T, L>;
   dim3 grid;
   if (mode == PASS_FWD3_PAIR || mode == PASS_INV3_ACC) {
     grid.x = (unsigned)(((long long)a.n1 * a.n2 + S::TILE - 1) / S::TILE);
@@ -352,22 +349,31 @@ cudaError_t launch_pass_L(int mode, const PairPassArgs<T> &a, int npacks, cudaSt
 }
 
 
-template <typename T>
-cudaError_t launch_pair_pass_impl(int mode, const PairPassArgs<T> &a, int npacks, cudaStream_t st) {
-  int L;
-  switch (mode) {
-    case PASS_FWD3_PAIR:
-    case PASS_INV3_ACC: L = a.n3; break;
-    case PASS_CONV1: L = a.n1; break;
-    default: L = a.n2; break;
+// Launchers of one length group (instantiated in pair_chain_[abcd]_f{32,64}.cu): true when L
+// belongs to the group, with the launch status in *e.
+#define ACE_PASS_CASE(L_)                                 \
+  case L_:                                                \
+    *e = launch_pass_L<T, L_>(mode, a, npacks, st);       \
+    return true;
+#define ACE_CONV_CASE(L_)                                 \
+  case L_:                                                \
+    *e = launch_conv_L<T, L_>(a, npacks, st);             \
+    return true;
+#define ACE_DEFINE_GROUP(NAME, TYPE, PASS_LIST, CONV_LIST)                                                   \
+  bool pass_##NAME(int L, int mode, const PairPassArgs<TYPE> &a, int npacks, cudaStream_t st, cudaError_t *e) { \
+    using T = TYPE;                                                                                           \
+    switch (L) {                                                                                              \
+      PASS_LIST(ACE_PASS_CASE)                                                                                \
+      default: return false;                                                                                  \
+    }                                                                                                         \
+  }                                                                                                           \
+  bool conv_##NAME(int L, const PairPassArgs<TYPE> &a, int npacks, cudaStream_t st, cudaError_t *e) {           \
+    using T = TYPE;                                                                                           \
+    switch (L) {                                                                                              \
+      CONV_LIST(ACE_CONV_CASE)                                                                                \
+      default: return false;                                                                                  \
+    }                                                                                                         \
   }
-  switch (L) {
-#define ACE_CASE(L_) \
-  case L_: return launch_pass_L<T, L_>(mode, a, npacks, st);
-    ACE_PASS_LENGTHS(ACE_CASE)
-#undef ACE_CASE
-    default: return cudaErrorInvalidValue;
-  }
-}
+#define ACE_NO_LENGTHS(X)
 
 }  // namespace ace

@@ -1,0 +1,6 @@
+// Pencil-pass and axis-1 kernels (float) for the axis lengths of group B (pair_chain.cuh).
+#include "pair_chain.cuh"
+
+namespace ace {
+ACE_DEFINE_GROUP(b_f32, float, ACE_LENGTHS_B, ACE_LENGTHS_B)
+}  // namespace ace

@@ -51,7 +51,8 @@ def test_host_side_checks_without_gpu(lib):
     from paper_2101_03155_gb300 import ace
 
     ace.load()
-    assert ace.ace_grid_supported(96) and ace.ace_grid_supported(160) and not ace.ace_grid_supported(97)
+    assert ace.ace_grid_supported(96) and ace.ace_grid_supported(160) and ace.ace_grid_supported(15)
+    assert not ace.ace_grid_supported(97) and not ace.ace_grid_supported(14) and not ace.ace_grid_supported(512)
     d = ace.make_desc((96, 96, 97), np.eye(3) * 10, 4)
     with pytest.raises(ace.AceError) as e:
         ace.ace_build(d, np.zeros((4, 96, 96, 97), np.float32))
