@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -49,6 +50,32 @@ def _peaks():
             return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def measure_fp32_tflops(n: int = 8192, reps: int = 6) -> float:
+    """FP32 CUDA-core throughput of this GPU as cuBLAS reaches it: an n^3 SGEMM with TF32 off
+    (2 n^3 flops), best of `reps` after one warm-up, timed with CUDA events.  The denominator of the
+    pair chain's FFT-flop fraction (MEASURED_PEAKS.json holds no FP32 figure)."""
+    import torch
+
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        a = torch.randn(n, n, device="cuda", dtype=torch.float32)
+        b = torch.randn(n, n, device="cuda", dtype=torch.float32)
+        c = a @ b
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            c = a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        del a, b, c
+        return 2.0 * n**3 / (best * 1e-3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
 
 
 def _golden():
@@ -204,6 +231,7 @@ WORKLOADS = {
     "enzyme8_reuse": "enzyme_112orb_160x144x128_8snap_rhocut1e-3_pairlist_reuse",
     "batched24": "batched24_uneven_rhocut1e-3",
     "scdm_water32": "water32_128orb_96c_delocalised_scdm",
+    "enzyme8_mts": "enzyme_112orb_160x144x128_8snap_mts_outer_steps",
 }
 
 
@@ -404,6 +432,89 @@ def run_reuse(args):
         "pair_list_drift": drift,
         "gpu_launches": mixed["reuse"]["launches"],
         "clocks": mixed["reuse"]["clk"],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_mts(args):
+    """Outer steps of a multiple-time-step run (section II, r-RESPA with the s-ACE operator built once
+    per outer step): per snapshot of the enzyme-like set, one build (snapshot 0 screened, later
+    snapshots on its pair list) followed by `--mts-inner` applications K phi to all 112 orbitals
+    (the inner steps).  Reports the split of an outer step into construction (the paper's t_Con)
+    and application (its t_sACE), as Table 1 of the paper splits its SCF cycles."""
+    import torch
+
+    import paper_2101_03155_gb300 as ace
+    from paper_2101_03155_gb300 import ace as abi
+    from paper_2101_03155_gb300 import build as cuda_build
+    from workloads.generators import config5
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    cuda_build.build()
+    ace.ace.load()
+    ws = config5(nsnap=8)
+    stream = torch.cuda.current_stream()
+    inner = args.mts_inner
+    descs = [ace.make_desc(w.grid, w.lattice, w.norb, rho_cut=w.rho_cut, spin_factor=w.spin_factor,
+                           prec=ace.ACE_MIXED) for w in ws]
+    phis = [torch.from_numpy(w.phi.astype(np.float32)).cuda() for w in ws]
+    out = torch.empty_like(phis[0])
+
+    def outer_steps(t):
+        pairs = None
+        launches = 0
+        for k in range(len(ws)):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            if pairs is None:
+                op = ace.ace_build(descs[k], phis[k], stream)
+                pairs = abi.get_numpy(op, abi.ACE_GET_PAIRS)
+            else:
+                op = ace.ace_build_pairs(descs[k], phis[k], pairs, stream)
+            e1.record(stream)
+            for _ in range(inner):
+                ace.ace_apply(op, phis[k], out, stream)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            t["build_ms"].append(e0.elapsed_time(e1))
+            t["apply_ms"].append(e1.elapsed_time(e2) / inner)
+            launches += ace.ace.ace_kernel_launches(op) + 4 * inner
+            op.close()
+        return launches
+
+    for _ in range(args.warmup):
+        outer_steps({"build_ms": [], "apply_ms": []})
+    t = {"build_ms": [], "apply_ms": []}
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        launches += outer_steps(t)
+    end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = start.elapsed_time(end)
+    n_outer = len(ws) * args.steps
+    build_ms, apply_ms = statistics.mean(t["build_ms"]), statistics.mean(t["apply_ms"])
+    line = {
+        "metric": "MTS outer steps/s (one s-ACE build + inner applications)", "value": n_outer / (ms / 1e3),
+        "unit": "outer steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "outer_steps_per_step": len(ws), "norb": ws[0].norb,
+                   "grid": list(ws[0].grid), "inner_applications": inner, "applied_to": "all orbitals (m = n)",
+                   "precision": "mixed", "l2": "inputs larger than L2"},
+        "split": {"t_con_ms": build_ms, "t_sace_ms": apply_ms, "t_con_over_t_sace": build_ms / apply_ms,
+                  "construction_share_of_outer_step": build_ms / (build_ms + inner * apply_ms)},
+        "paper_table1_context": "32 waters, 120 cores: t_Con 6.0-23.6 s, t_sACE 0.15 s per SCF cycle",
+        "gpu_launches": launches,
+        "clocks": clk,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -719,9 +830,11 @@ def run_ours(args):
     del phi64
 
     peaks, peak_kind = _peaks()
+    fp32_tflops = measure_fp32_tflops()
     npairs = rec["npairs"]
     chain_s = statistics.mean(rec["chain_ms"]) / 1e3
     alg_bytes = 24.0 * N * npairs  # read phi_i, phi_j; read+write W_i, W_j in FP32, per grid point per pair
+    fft_flops = 2 * 5.0 * N * math.log2(N) * ((npairs + 1) // 2)
     achieved = alg_bytes / chain_s / 1e9
     stage_mean = {k: statistics.mean(s[k] for s in rec["stage"]) for k in rec["stage"][0]}
 
@@ -746,7 +859,13 @@ def run_ours(args):
                      "bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                      "frac": achieved / peaks.get("hbm_gbs"), "traffic": CHAIN_DRAM_BYTES_PER_BUILD,
                      "peak_kind": peak_kind,
-                     "algorithmic_bytes": f"24 B x N x npairs = {alg_bytes:.4g} B per build"},
+                     "algorithmic_bytes": f"24 B x N x npairs = {alg_bytes:.4g} B per build",
+                     # what bounds it: FFT arithmetic, 2 complex 3D transforms of 5 N log2 N flops per
+                     # pack of two pairs, against the FP32 rate cuBLAS SGEMM reaches on this GPU
+                     "fft_flops": {"achieved_tflops": fft_flops / chain_s / 1e12,
+                                   "peak_tflops": fp32_tflops, "frac": fft_flops / chain_s / 1e12 / fp32_tflops,
+                                   "peak_kind": "measured (cuBLAS FP32 SGEMM 8192^3, TF32 off)",
+                                   "flops_per_build": fft_flops}},
         # the dense contractions on the tensor cores are HBM-bound as well (intensity n/4 flop/B):
         # M reads Phi and W, xi reads W and writes xi (FP32, n x N each); the screen reads Phi once
         "dense_roofline": {
@@ -801,12 +920,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default chain settings")
     ap.add_argument("--workload", default="water32", choices=sorted(WORKLOADS))
+    ap.add_argument("--mts-inner", type=int, default=15, help="inner applications per outer step (enzyme8_mts)")
     args = ap.parse_args()
     if args.impl == "reference":
         args.ref_step_s = min(args.ref_step_s, max(2.0, 150.0 / max(1, args.steps + args.warmup)))
         return run_reference(args)
     if args.workload == "enzyme8_reuse":
         return run_reuse(args)
+    if args.workload == "enzyme8_mts":
+        return run_mts(args)
     if args.workload == "scdm_water32":
         return run_scdm(args)
     if args.workload != "water32":

@@ -331,9 +331,10 @@ def ace_autotune(desc: AceDesc, phi, stream=None) -> dict:
     ptr, code, numel = _array_info(phi)
     if numel != desc.norb * desc.n[0] * desc.n[1] * desc.n[2]:
         raise ValueError("phi does not match the descriptor")
-    out = (ctypes.c_int * 5)()
+    out = (ctypes.c_int * 6)()
     _check(load().ace_autotune(ctypes.byref(desc), ptr, code, _stream_handle(stream), out))
-    return {"group": out[0], "batch": out[1], "streams": out[2], "l2_mb": out[3], "row_block": out[4]}
+    return {"group": out[0], "batch": out[1], "streams": out[2], "l2_mb": out[3], "row_block": out[4],
+            "persistent_lag": out[5]}
 
 
 def ace_kernel_launches(op: AceOp) -> int:

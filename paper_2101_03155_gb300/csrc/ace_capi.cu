@@ -426,7 +426,9 @@ bool find_plane_ops<double>(int n2, int n3, ace::PlaneOps<double> *out) {
 // ace_autotune for the grid and precision; ACE_* environment variables override both.
 struct ChainParams {
   int G = 1, B = 2, streams = 4, persist_mb = 60;
-  int RB = 4;  // rows per block of the pack order
+  int RB = 4;          // rows per block of the pack order
+  int persistent = 0;  // 1: the persistent chain (one launch, device task queue)
+  int lag = 3;         // its queue lag (rounds between the stages of one pack)
 };
 
 struct TuneKey {
@@ -448,8 +450,8 @@ void tune_file_load_locked() {
   if (!f) return;
   TuneKey k;
   ChainParams c;
-  while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d", &k.n1, &k.n2, &k.n3, &k.fp64, &c.G, &c.B, &c.streams,
-                     &c.persist_mb, &c.RB) == 9)
+  while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d", &k.n1, &k.n2, &k.n3, &k.fp64, &c.G, &c.B, &c.streams,
+                     &c.persist_mb, &c.RB, &c.persistent, &c.lag) == 11)
     g_tuned.emplace_back(k, c);
   std::fclose(f);
 }
@@ -469,8 +471,9 @@ void tune_store(const TuneKey &k, const ChainParams &c) {
     FILE *f = std::fopen(path, "w");
     if (f) {
       for (const auto &e : g_tuned)
-        std::fprintf(f, "%d %d %d %d %d %d %d %d %d\n", e.first.n1, e.first.n2, e.first.n3, e.first.fp64, e.second.G,
-                     e.second.B, e.second.streams, e.second.persist_mb, e.second.RB);
+        std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d\n", e.first.n1, e.first.n2, e.first.n3, e.first.fp64,
+                     e.second.G, e.second.B, e.second.streams, e.second.persist_mb, e.second.RB, e.second.persistent,
+                     e.second.lag);
       std::fclose(f);
     }
   }
@@ -490,6 +493,8 @@ ChainParams chain_params(const ace_desc &d, bool fp64) {
   c.streams = std::min(kSide, std::max(1, env_int("ACE_STREAMS", c.streams)));
   c.persist_mb = std::max(0, env_int("ACE_L2_PERSIST_MB", c.persist_mb));
   c.RB = std::max(1, env_int("ACE_ROW_BLOCK", c.RB));
+  c.persistent = env_int("ACE_PERSISTENT", c.persistent) != 0;
+  c.lag = std::max(1, env_int("ACE_PERSIST_LAG", c.lag));
   return c;
 }
 
@@ -673,7 +678,7 @@ ace_status run_chain_persistent(ace_op *op, const DeviceTables *tab, const ace::
   cudaStream_t st = op->stream;
   const int np = (int)packs.size();
   if (np == 0) return ACE_OK;
-  const int lag = std::max(1, env_int("ACE_PERSIST_LAG", 3));
+  const int lag = std::max(1, cp.lag);
   const int nslots = std::min(2 * lag + 2, np);
   // one allocation: packs, builds, pack_build, counters (3 np), ticket; then the scratch slots
   const size_t b_packs = sizeof(int4) * np, b_builds = sizeof(ace::ChainBuild<T>) * builds.size();
@@ -1109,16 +1114,15 @@ ace_status run_chain(ace_op *op, const T *phi, int count) {
   ace::PersistOps<T> qops{};
   const bool plane = find_plane_ops<T>(d.n[1], d.n[2], &pops) && ace::conv_length_supported(d.n[0]) &&
                      env_int("ACE_FORCE_PENCIL", 0) == 0;
-  const bool persistent = plane && find_persist_ops<T>(d.n[0], d.n[1], d.n[2], &qops) &&
-                          env_int("ACE_PERSISTENT", 0) != 0;
+  const ChainParams cp = chain_params(d, op->fp64);
+  const bool persistent = plane && cp.persistent && find_persist_ops<T>(d.n[0], d.n[1], d.n[2], &qops);
   if (count > 0 && persistent) {
-    const ChainParams cp = chain_params(d, op->fp64);
     std::vector<int4> packs;
     form_packs(op->pairs_h, cp.RB, packs);
     const std::vector<ace::ChainBuild<T>> one{{phi, static_cast<T *>(op->W), static_cast<const T *>(tab->Kperm)}};
     return run_chain_persistent<T>(op, tab, qops, packs, {}, one, temps, cp);
   }
-  if (count > 0 && plane) return run_chain_plane<T>(op, phi, tab, pops, count, temps, chain_params(d, op->fp64));
+  if (count > 0 && plane) return run_chain_plane<T>(op, phi, tab, pops, count, temps, cp);
   if (count > 0) {
     const cpx<T> *twd[3] = {static_cast<const cpx<T> *>(tab->tw[0]), static_cast<const cpx<T> *>(tab->tw[1]),
                             static_cast<const cpx<T> *>(tab->tw[2])};
@@ -1945,6 +1949,36 @@ ace_status ace_autotune(const ace_desc *desc, const void *phi, ace_dtype dtype, 
             best = c;
           }
         }
+    // the persistent chain on the same sample, for a few queue lags
+    ace::PersistOps<T> qops{};
+    if (find_persist_ops<T>(desc->n[0], desc->n[1], desc->n[2], &qops)) {
+      std::vector<int4> packs;
+      form_packs(op->pairs_h, best.RB, packs);
+      packs.resize(std::min<size_t>(packs.size(), (size_t)sample));
+      const std::vector<ace::ChainBuild<T>> one{
+          {phi_w, static_cast<T *>(op->W), static_cast<const T *>(op->tab->Kperm)}};
+      for (int lag : {2, 3, 4}) {
+        ChainParams c = best;
+        c.persistent = 1;
+        c.lag = lag;
+        float t[2];
+        for (int rep = 0; rep < 2; ++rep) {
+          std::vector<void *> tmp;
+          ACE_CUDA(cudaEventRecord(e0, op->stream), "event");
+          ace_status r = run_chain_persistent<T>(op, op->tab, qops, packs, {}, one, tmp, c);
+          ACE_CUDA(cudaEventRecord(e1, op->stream), "event");
+          for (void *q : tmp) cudaFreeAsync(q, op->stream);
+          if (r != ACE_OK) return r;
+          ACE_CUDA(cudaEventSynchronize(e1), "tuning run");
+          cudaEventElapsedTime(&t[rep], e0, e1);
+        }
+        const float ms = std::min(t[0], t[1]);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = c;
+        }
+      }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     tune_store(TuneKey{desc->n[0], desc->n[1], desc->n[2], op->fp64 ? 1 : 0}, best);
@@ -1958,6 +1992,7 @@ ace_status ace_autotune(const ace_desc *desc, const void *phi, ace_dtype dtype, 
     params[2] = best.streams;
     params[3] = best.persist_mb;
     params[4] = best.RB;
+    params[5] = best.persistent ? best.lag : 0;
   }
   return ACE_OK;
 }

@@ -1,5 +1,6 @@
-"""ace_autotune: the pair-chain settings it picks are valid, are used by later builds (same
-operator within the mixed-form tolerance), and persist through ACE_TUNE_FILE."""
+"""ace_autotune: the pair-chain settings it picks (stream-batched settings, or the persistent chain
+with its queue lag) are valid, are used by later builds (same operator within the mixed-form
+tolerance), and persist through ACE_TUNE_FILE."""
 
 import os
 
@@ -35,10 +36,11 @@ def test_autotune_picks_valid_settings_and_builds_agree(tmp_path):
     finally:
         del os.environ["ACE_TUNE_FILE"]
     assert p["group"] >= 1 and p["batch"] in (1, 2, 3, 4, 6) and p["streams"] in (2, 4, 8) and p["l2_mb"] in (0, 60)
-    assert p["row_block"] in (1, 2, 4, 8)
+    assert p["row_block"] in (1, 2, 4, 8) and p["persistent_lag"] in (0, 2, 3, 4)
     fields = tune_file.read_text().split()
     assert fields[:4] == ["48", "48", "48", "0"] and [int(x) for x in fields[4:9]] == [
         p["group"], p["batch"], p["streams"], p["l2_mb"], p["row_block"]]
+    assert int(fields[9]) == (p["persistent_lag"] > 0)
     after = ace.ace_build(d, phi, stream)
     assert abs(ace.exchange_energy(after) - e0) <= MIXED_EX_TOL_PER_ORB * w.norb
     after.close()
