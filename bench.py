@@ -36,9 +36,11 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_values.json")
 # of the current chain kernels with caches not flushed (profiles/pair_chain_plane_water32_96c.md);
 # set to None whenever those kernels change.
 CHAIN_DRAM_BYTES_PER_BUILD = 14.9e9
-# DRAM bytes (read + write) per launch of the dense tensor-core kernels of the same workload, one ncu
-# capture with caches not flushed (profiles/dense_tc_water32_96c.md); None once those kernels change
-DENSE_DRAM_BYTES = {"screen": 482.8e6, "M": 929.8e6, "xi": 897.9e6}
+# DRAM bytes (read + write) per launch of the dense kernels of the same workload: M and xi from one
+# ncu capture with caches not flushed (profiles/dense_tc_water32_96c.md), the CUDA-core screen from
+# its full capture (profiles/screen_syrk_water32_96c.md: 454.2 MB read, 3.6 MB written); None once a
+# kernel changes
+DENSE_DRAM_BYTES = {"screen": 457.8e6, "M": 929.8e6, "xi": 897.9e6}
 # DRAM bytes per SCDM localisation of the 128-orbital 96^3 set: 128 selection passes at 436.1 MB
 # (ncu, profiles/scdm_water32_96c.md) + the left multiply Phi = U^T Psi (897.9 MB) + the transpose
 SCDM_DRAM_BYTES = 128 * 436.1e6 + 897.9e6 + 906e6
@@ -767,6 +769,16 @@ def run_ours(args):
     ms, value = combine_ranks(ms, args.steps, 1.0, "cuda")
     ms_per_step = ms / args.steps
 
+    if args.only_mixed:
+        # reduced run for profiler captures: the mixed builds only
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms_per_step,
+                              "gpu_launches_per_build": rec["launches"] // max(1, args.steps),
+                              "stage_ms": {k: statistics.mean(st[k] for st in rec["stage"]) for k in rec["stage"][0]},
+                              "note": "--only-mixed: reduced run for profiler captures, not a bench line"}),
+                  flush=True)
+        return 0
+
     # end to end: host (pinned) orbitals through the same C ABI call; copies inside the timed region
     host32 = torch.from_numpy(w.phi.astype(np.float32)).pin_memory()
     e2e_steps = max(1, min(args.steps, 5))
@@ -835,6 +847,7 @@ def run_ours(args):
     chain_s = statistics.mean(rec["chain_ms"]) / 1e3
     alg_bytes = 24.0 * N * npairs  # read phi_i, phi_j; read+write W_i, W_j in FP32, per grid point per pair
     fft_flops = 2 * 5.0 * N * math.log2(N) * ((npairs + 1) // 2)
+    screen_flops = 2.0 * n * (n + 1) / 2 * N
     achieved = alg_bytes / chain_s / 1e9
     stage_mean = {k: statistics.mean(s[k] for s in rec["stage"]) for k in rec["stage"][0]}
 
@@ -869,11 +882,19 @@ def run_ours(args):
         # the dense contractions on the tensor cores are HBM-bound as well (intensity n/4 flop/B):
         # M reads Phi and W, xi reads W and writes xi (FP32, n x N each); the screen reads Phi once
         "dense_roofline": {
-            k: {"bound": "hbm", "achieved": nb * 4 * n * N / (stage_mean[k] * 1e-3) / 1e9, "peak": peaks.get("hbm_gbs"),
-                "unit": "GB/s", "frac": nb * 4 * n * N / (stage_mean[k] * 1e-3) / 1e9 / peaks.get("hbm_gbs"),
-                "traffic": DENSE_DRAM_BYTES.get(k),
-                "algorithmic_bytes": f"{nb} x 4 B x n x N = {nb * 4 * n * N:.4g} B"}
-            for k, nb in (("screen", 1), ("M", 2), ("xi", 2))},
+            **{k: {"bound": "hbm", "achieved": nb * 4 * n * N / (stage_mean[k] * 1e-3) / 1e9,
+                   "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                   "frac": nb * 4 * n * N / (stage_mean[k] * 1e-3) / 1e9 / peaks.get("hbm_gbs"),
+                   "traffic": DENSE_DRAM_BYTES.get(k),
+                   "algorithmic_bytes": f"{nb} x 4 B x n x N = {nb * 4 * n * N:.4g} B"}
+               for k, nb in (("M", 2), ("xi", 2))},
+            # the screen runs FP32 FMAs on the CUDA cores: n (n + 1) / 2 x N products
+            "screen": {"bound": "fp32", "achieved": screen_flops / (stage_mean["screen"] * 1e-3) / 1e12,
+                       "peak": fp32_tflops, "unit": "TFLOP/s",
+                       "frac": screen_flops / (stage_mean["screen"] * 1e-3) / 1e12 / fp32_tflops,
+                       "traffic": DENSE_DRAM_BYTES.get("screen"),
+                       "algorithmic_flops": f"2 x n (n + 1) / 2 x N = {screen_flops:.4g}",
+                       "peak_kind": "measured (cuBLAS FP32 SGEMM 8192^3, TF32 off)"}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n * N, "d2h_bytes_per_step": 16,
                 "steps": e2e_steps},
         "apply": {"value": 1e3 / apply_ms, "unit": f"applications/s (K psi for {n} vectors)", "ms": apply_ms,
@@ -921,6 +942,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default chain settings")
     ap.add_argument("--workload", default="water32", choices=sorted(WORKLOADS))
     ap.add_argument("--mts-inner", type=int, default=15, help="inner applications per outer step (enzyme8_mts)")
+    ap.add_argument("--only-mixed", action="store_true",
+                    help="time the mixed-form builds only (a reduced run for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         args.ref_step_s = min(args.ref_step_s, max(2.0, 150.0 / max(1, args.steps + args.warmup)))
