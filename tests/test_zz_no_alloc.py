@@ -105,3 +105,53 @@ def test_noalloc_refuses_unaligned_buffers():
         ace.ace.ace_exchange_w_noalloc(desc, phi, np.array([[0, 0]], np.int32), W)
     assert e.value.status == ace.ace.ACE_ERR_ARG
     assert "aligned" in str(e.value)
+
+
+@pytest.mark.parametrize("prec", [ace.ACE_FP64, ace.ACE_MIXED])
+def test_noalloc_pair_list_beyond_one_pack_chunk(prec):
+    """130 orbitals, every pair (8,515 pairs, an odd count: 4,258 packs, more than one upload chunk
+    of the fixed array's pack list, the last pack holding a single pair): the same W as the
+    allocating per-rank entry point ace_exchange_w on the same list, on two calls in a row."""
+    import torch
+
+    from workloads.generators import gaussian_orbitals
+
+    grid, lat = (16, 16, 16), np.diag([9.0, 9.5, 10.0])
+    phi_h, _, _ = gaussian_orbitals(grid, lat, 130, 1, np.random.default_rng(77))
+    iu = np.triu_indices(130)
+    pairs = np.stack(iu, axis=1).astype(np.int32)
+    assert len(pairs) == 8515
+    dtype = torch.float64 if prec == ace.ACE_FP64 else torch.float32
+    tol = FP64_ARRAY_RTOL if prec == ace.ACE_FP64 else MIXED_W_RTOL
+    desc = ace.make_desc(grid, lat, 130, prec=prec)
+    phi = torch.from_numpy(phi_h).to(device="cuda", dtype=dtype)
+    stream = torch.cuda.current_stream()
+    W_ref = torch.empty_like(phi)
+    ace.ace.ace_exchange_w(desc, phi, pairs, W_ref, stream)
+    for _ in range(2):
+        W = torch.full_like(phi, float("nan"))
+        ace.ace.ace_exchange_w_noalloc(desc, phi, pairs, W, stream)
+        torch.cuda.synchronize()
+        assert rel_max(W.cpu().numpy(), W_ref.cpu().numpy()) <= tol
+
+
+@pytest.mark.parametrize("coulomb", [ace.ACE_COULOMB_PERIODIC, ace.ACE_COULOMB_TRUNCATED])
+def test_noalloc_triclinic_cell(coulomb):
+    """A triclinic cell: the device-built reciprocal basis and kernel table of the no-alloc path
+    against ace_build's host-built ones (FP64, both kernels)."""
+    import torch
+
+    from workloads.generators import gaussian_orbitals
+
+    lat = np.array([[7.5, 0.0, 0.0], [1.2, 7.0, 0.0], [0.6, -0.9, 6.8]])
+    grid = (12, 16, 20)
+    phi_h, _, _ = gaussian_orbitals(grid, lat, 4, 2, np.random.default_rng(5))
+    g = gpu_build(phi_h, lat, ace.ACE_FP64, coulomb=coulomb)
+    assert g["status"] == 0
+    desc = ace.make_desc(grid, lat, 4, prec=ace.ACE_FP64, coulomb=coulomb)
+    phi = torch.from_numpy(phi_h).cuda()
+    W = torch.full_like(phi, float("nan"))
+    ace.ace.ace_exchange_w_noalloc(desc, phi, g["pairs"], W, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert rel_max(W.cpu().numpy(), g["W"].reshape(phi_h.shape)) <= FP64_ARRAY_RTOL
+    g["op"].close()
