@@ -72,6 +72,12 @@ __device__ __forceinline__ void commit(uint32_t mbar) {
 __device__ __forceinline__ void mbar_init(uint32_t mbar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
 }
+__device__ __forceinline__ void mbar_init_n(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
 __device__ __forceinline__ void mbar_init_fence() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -1091,27 +1097,35 @@ __global__ void __launch_bounds__(NT2, 2) screen_tma_kernel(const __grid_constan
 // FP32 running sum per K-split, FP64 across the K-splits in a fixed order.
 //   - A 128 x 128 block pair (bi <= bj) of O is cut into 32 x 32 warp blocks.  A diagonal block
 //     pair is one work unit of the 10 warp blocks on or above its diagonal; an off-diagonal pair is
-//     two units (its row halves) of 8 warp blocks.  One CTA (10 warps) = one unit x one split.
-//   - Boxes of 128 rows x 32 points (128-byte swizzle) arrive by TMA through a ring; every thread
-//     replaces a share of the box by |phi| in place, then the warps multiply straight out of it.
+//     two units (its row halves) of 8 warp blocks.  One CTA = one unit x one split of the points.
+//   - Warp-specialised pipeline over a ring of shared-memory slots, handed on by mbarriers (no CTA
+//     barrier per step): warp 10 issues the TMA boxes (128 rows x 32 points, 128-byte swizzle) into
+//     a slot once the multiply warps have released it; warp 11 replaces each landed box by |phi| in
+//     place; warps 0-9 multiply straight out of the slot and release it.
 //   - Lane (ti, tj) = (lane / 8, lane % 8) owns rows ti + 4 rr (rr < 8) and columns tj + 8 cc
 //     (cc < 4) of its warp block.  Per four grid points it loads one 16-byte run of each of its 8
 //     rows and 4 columns (every such load of a warp touches distinct bank groups: its rows differ
 //     in their low three bits, which select the swizzled position) and issues 64 packed f32x2 FMAs,
 //     each multiplying two neighbouring grid points of one (row, column) pair.
+//   - Every wait is bounded; a wait that gives up raises a shared flag that ends every role, and
+//     the TMA warp waits (bounded) for its boxes in flight before it leaves.
 // ----------------------------------------------------------------------------------------
-constexpr int SY_NT = 320;
+constexpr int SY_MUL = 10;                  // multiply warps
+constexpr int SY_NT = 32 * (SY_MUL + 2);    // + the TMA warp and the |phi| warp
 constexpr int SY_RING = 5;
 constexpr int SY_FOLD = 2;                  // K-steps per FP32 partial (64 points)
 constexpr uint32_t kSyBox = 128 * BK * 4;   // 128 rows x 32 FP32 = 16 KB
-constexpr size_t kSySmem = (size_t)SY_RING * 2 * kSyBox + 64 + 1024;
+constexpr size_t kSySmem = (size_t)SY_RING * 2 * kSyBox + 3 * SY_RING * 8 + 16 + 1024;
 
 __global__ void __launch_bounds__(SY_NT, 1) screen_syrk_kernel(const __grid_constant__ CUtensorMap tmX, int n,
                                                                long long c0, long long K, int ndiag,
                                                                double *__restrict__ partial, int *__restrict__ err) {
   extern __shared__ unsigned char dyn[];
   unsigned char *boxes = align1024(dyn);  // ring x {row box, column box}
-  uint64_t *full = reinterpret_cast<uint64_t *>(boxes + (size_t)SY_RING * 2 * kSyBox);
+  uint64_t *full = reinterpret_cast<uint64_t *>(boxes + (size_t)SY_RING * 2 * kSyBox);  // TMA landed
+  uint64_t *ready = full + SY_RING;   // |phi| written (1 arrival)
+  uint64_t *empty = ready + SY_RING;  // multiply warps done with the slot (SY_MUL arrivals)
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + SY_RING);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // work unit -> block pair (bi, bj), row half h (off-diagonal units)
   int bi, bj, h = 0;
@@ -1129,8 +1143,88 @@ __global__ void __launch_bounds__(SY_NT, 1) screen_syrk_kernel(const __grid_cons
     }
     bj = bi + 1 + t;
   }
-  // this warp's 32 x 32 block (I, J) of the block pair; warps 8, 9 of an off-diagonal unit only
-  // help with the |phi| pass
+  const long long KS = (K + BK - 1) / BK;
+  const long long s_lo = (long long)blockIdx.y * KS / gridDim.y, s_hi = (long long)(blockIdx.y + 1) * KS / gridDim.y;
+  const int Q = (int)(s_hi - s_lo);
+  const int nbox = diag ? 1 : 2;
+  if (tid == 0) {
+    for (int r = 0; r < SY_RING; ++r) {
+      mbar_init(smem_u32(&full[r]));
+      mbar_init_n(smem_u32(&ready[r]), 1);
+      mbar_init_n(smem_u32(&empty[r]), SY_MUL);
+    }
+    *abort_flag = 0;
+    mbar_init_fence();
+  }
+  __syncthreads();
+  // bounded wait that also leaves when another role has given up; false = leave
+  auto wait = [&](uint64_t *bar, int q) -> bool {
+    const uint32_t mb = smem_u32(bar), parity = (uint32_t)((q / SY_RING) & 1);
+    for (uint32_t it = 0; it < kWaitLimit; it += 64) {
+      if (mbar_wait(mb, parity, 64)) return true;
+      if (*abort_flag) return false;
+    }
+    *abort_flag = 1;
+    atomicExch(err, 1);
+    return false;
+  };
+
+  if (warp == SY_MUL) {
+    // ---- TMA warp (one lane): box q into slot q % SY_RING once box q - SY_RING has been used ----
+    if (lane == 0) {
+      int issued = 0;
+      for (int q = 0; q < Q; ++q) {
+        const int slot = q % SY_RING;
+        if (q >= SY_RING && !wait(&empty[slot], q - SY_RING)) break;
+        const uint32_t mb = smem_u32(&full[slot]);
+        unsigned char *bx = boxes + (size_t)slot * 2 * kSyBox;
+        const int x = (int)(c0 + (s_lo + q) * BK);
+        mbar_expect_tx(mb, nbox * kSyBox);
+        tma_load_2d(smem_u32(bx), &tmX, x, bi * 128, mb);
+        if (!diag) tma_load_2d(smem_u32(bx + kSyBox), &tmX, x, bj * 128, mb);
+        issued = q + 1;
+      }
+      // no box may still be landing when the CTA ends (the other roles may leave early after a
+      // give-up): wait (bounded) for the boxes whose slots were not refilled
+      for (int q = issued > SY_RING ? issued - SY_RING : 0; q < issued; ++q)
+        mbar_wait(smem_u32(&full[q % SY_RING]), (uint32_t)((q / SY_RING) & 1));
+    }
+    return;
+  }
+  if (warp == SY_MUL + 1) {
+    // ---- |phi| warp: each landed box becomes |phi| in place; points at or past K (only in a
+    // ragged last step) read as zero.  Row r holds its logical 16-byte run k4 at position k4 ^ (r & 7).
+    for (int q = 0; q < Q; ++q) {
+      const int slot = q % SY_RING;
+      if (!wait(&full[slot], q)) return;
+      unsigned char *bx = boxes + (size_t)slot * 2 * kSyBox;
+      const long long k0 = (s_lo + q) * BK;
+      const bool ragged = k0 + BK > K;
+#pragma unroll 4
+      for (int e = lane; e < nbox * 1024; e += 32) {
+        uint4 *p = reinterpret_cast<uint4 *>(bx) + e;
+        uint4 v = *p;
+        v.x &= 0x7fffffffu;
+        v.y &= 0x7fffffffu;
+        v.z &= 0x7fffffffu;
+        v.w &= 0x7fffffffu;
+        if (ragged) {
+          const int row = (e >> 3) & 127, k4 = (e & 7) ^ (row & 7);
+          const long long k = k0 + 4 * k4;
+          if (k >= K) v.x = 0u;
+          if (k + 1 >= K) v.y = 0u;
+          if (k + 2 >= K) v.z = 0u;
+          if (k + 3 >= K) v.w = 0u;
+        }
+        *p = v;
+      }
+      fence_async_smem();  // these generic writes come before the TMA that refills the slot
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&ready[slot]));
+    }
+    return;
+  }
+  // ---- multiply warps: warp block (I, J); warps 8, 9 of an off-diagonal unit only release slots ----
   int I, J;
   bool computes = true;
   if (diag) {
@@ -1143,52 +1237,6 @@ __global__ void __launch_bounds__(SY_NT, 1) screen_syrk_kernel(const __grid_cons
     computes = warp < 8;
   }
   const int ti = lane >> 3, tj = lane & 7;
-  const long long KS = (K + BK - 1) / BK;
-  const long long s_lo = (long long)blockIdx.y * KS / gridDim.y, s_hi = (long long)(blockIdx.y + 1) * KS / gridDim.y;
-  const int Q = (int)(s_hi - s_lo);
-  const int nbox = diag ? 1 : 2;
-  if (tid == 0) {
-    for (int r = 0; r < SY_RING; ++r) mbar_init(smem_u32(&full[r]));
-    mbar_init_fence();
-  }
-  __syncthreads();
-  auto issue = [&](int q) {  // box(es) of step s_lo + q into ring slot q % SY_RING
-    const int slot = q % SY_RING;
-    const uint32_t mb = smem_u32(&full[slot]);
-    unsigned char *bx = boxes + (size_t)slot * 2 * kSyBox;
-    const int x = (int)(c0 + (s_lo + q) * BK);
-    mbar_expect_tx(mb, nbox * kSyBox);
-    tma_load_2d(smem_u32(bx), &tmX, x, bi * 128, mb);
-    if (!diag) tma_load_2d(smem_u32(bx + kSyBox), &tmX, x, bj * 128, mb);
-  };
-  // |phi| in place over the slot's box(es); points at or past K (only in a ragged last step) read
-  // as zero.  Row r of a box holds its logical 16-byte run k4 at position k4 ^ (r & 7).
-  auto absolute = [&](int q) {
-    unsigned char *bx = boxes + (size_t)(q % SY_RING) * 2 * kSyBox;
-    const long long k0 = (s_lo + q) * BK;
-    const bool ragged = k0 + BK > K;
-    for (int e = tid; e < nbox * 1024; e += SY_NT) {
-      uint4 *p = reinterpret_cast<uint4 *>(bx) + e;
-      uint4 v = *p;
-      v.x &= 0x7fffffffu;
-      v.y &= 0x7fffffffu;
-      v.z &= 0x7fffffffu;
-      v.w &= 0x7fffffffu;
-      if (ragged) {
-        const int row = (e >> 3) & 127, k4 = (e & 7) ^ (row & 7);
-        const long long k = k0 + 4 * k4;
-        if (k >= K) v.x = 0u;
-        if (k + 1 >= K) v.y = 0u;
-        if (k + 2 >= K) v.z = 0u;
-        if (k + 3 >= K) v.w = 0u;
-      }
-      *p = v;
-    }
-    fence_async_smem();  // these generic writes come before the TMA that refills the slot
-  };
-  int issued = Q < SY_RING ? Q : SY_RING;
-  if (tid == 0)
-    for (int q = 0; q < issued; ++q) issue(q);
   unsigned long long part[8][4];
   float acc[8][4];
 #pragma unroll
@@ -1203,23 +1251,11 @@ __global__ void __launch_bounds__(SY_NT, 1) screen_syrk_kernel(const __grid_cons
   const uint32_t arow0 = (uint32_t)(32 * I + ti) * 128u, arow1 = arow0 + 4u * 128u;
   const uint32_t asw0 = (uint32_t)ti, asw1 = (uint32_t)(ti + 4);
   const uint32_t brow = (uint32_t)(32 * J + tj) * 128u + (diag ? 0u : kSyBox), bsw = (uint32_t)tj;
-  bool ok = true;
-  int fail_from = 0;  // on a timeout: the first box that every thread has not seen complete
   for (int q = 0; q < Q; ++q) {
-    const bool got = mbar_wait(smem_u32(&full[q % SY_RING]), (uint32_t)((q / SY_RING) & 1));
-    if (got) absolute(q);
-    if (__syncthreads_or(!got)) {
-      ok = false;
-      fail_from = q;
-      break;
-    }
-    // every thread is past its products of step q - 1: refill that slot
-    if (q > 0 && issued < Q) {
-      if (tid == 0) issue(issued);
-      ++issued;
-    }
+    const int slot = q % SY_RING;
+    if (!wait(&ready[slot], q)) return;
     if (computes) {
-      const unsigned char *bx = boxes + (size_t)(q % SY_RING) * 2 * kSyBox;
+      const unsigned char *bx = boxes + (size_t)slot * 2 * kSyBox;
 #pragma unroll 2
       for (int k4 = 0; k4 < 8; ++k4) {
         const unsigned char *pa0 = bx + arow0 + (((uint32_t)k4 ^ asw0) << 4);
@@ -1242,23 +1278,19 @@ __global__ void __launch_bounds__(SY_NT, 1) screen_syrk_kernel(const __grid_cons
 #pragma unroll
           for (int c = 0; c < 4; ++c) part[r][c] = f2fma(a[r].y, b[c].y, part[r][c]);
       }
-      if ((q + 1) % SY_FOLD == 0 || q + 1 == Q) {
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const float2 v = f2up(part[r][c]);
-            acc[r][c] += v.x + v.y;
-            part[r][c] = 0ull;
-          }
-      }
     }
-  }
-  if (!ok) {
-    // wait (bounded) for every box still in flight before the CTA's shared memory is released
-    for (int r = fail_from; r < issued; ++r) mbar_wait(smem_u32(&full[r % SY_RING]), (uint32_t)((r / SY_RING) & 1));
-    if (tid == 0) atomicExch(err, 1);
-    return;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_u32(&empty[slot]));
+    if (computes && ((q + 1) % SY_FOLD == 0 || q + 1 == Q)) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float2 v = f2up(part[r][c]);
+          acc[r][c] += v.x + v.y;
+          part[r][c] = 0ull;
+        }
+    }
   }
   if (computes) {
     double *dst = partial + (long long)blockIdx.y * n * n;
