@@ -165,6 +165,50 @@ ace_status ace_apply_finish(const ace_op *op, const double *C, ace_dtype dtype, 
 ace_status ace_build_batched(int k, const ace_desc *desc, const void *const *phi, ace_dtype dtype,
                              void *cuda_stream, ace_op **out);
 
+/* ---- Many builds on given pair lists as one CUDA graph ----
+ * The reuse steps of a multiple-time-step run (section III) rebuild the operator on the pair lists
+ * of the last outer step while only the orbitals change; with the pair counts known on the host no
+ * build needs a host wait, so k of them (snapshots or replicas; each as in ace_build_pairs) can be
+ * recorded once and replayed with one launch.
+ *
+ * ace_graph_create records the k builds from a private stream and instantiates the graph; it runs
+ * no build.  The builds follow one another (each spreads its pair chain over side streams, with
+ * the same chain settings and L2 window as ace_build_pairs); the environment variable
+ * ACE_GRAPH_LANES (1-4, default 1) runs that many builds at a time instead.  desc, phi, pairs_host
+ * and npairs are arrays of length k.
+ *   phi[i]:        device orbitals [norb][N1][N2][N3] in the working dtype of desc[i].prec (ACE_F32
+ *                  for ACE_MIXED, ACE_F64 for ACE_FP64), 16-byte aligned (ACE_ERR_ARG otherwise).
+ *                  The graph keeps the pointers and reads the arrays at every launch: the caller
+ *                  overwrites their contents between launches, and frees them after the graph.
+ *   pairs_host[i]: the pair list of build i, checked as in ace_build_pairs and copied.
+ *   cuda_stream:   the kernel tables of every grid are made on it first (synchronously); it must
+ *                  not be capturing.
+ * The handles of the builds (ace_graph_op) exist from creation on and keep their buffers (xi, W, M,
+ * L, pair list) at fixed addresses; each launch overwrites them.  They are owned by the graph:
+ * ace_destroy ignores them and ace_graph_destroy releases them.
+ * Errors: ACE_ERR_ARG, ACE_ERR_UNSUPPORTED_GRID, ACE_ERR_OOM, ACE_ERR_CUDA (nothing is created). */
+typedef struct ace_graph ace_graph;
+ace_status ace_graph_create(int k, const ace_desc *desc, const void *const *phi, ace_dtype dtype,
+                            const int *const *pairs_host, const long *npairs, void *cuda_stream,
+                            ace_graph **out);
+
+/* Enqueue one replay of all k builds on `cuda_stream`; returns without waiting.  Work the caller
+ * queues on the same stream afterwards (ace_apply, ace_get on a handle) sees its results.  One
+ * replay runs at a time: a launch starts after the previous one has finished. */
+ace_status ace_graph_launch(ace_graph *g, void *cuda_stream);
+
+/* Wait for the last launch, then read every build's Cholesky status, give-up flag and E_x into its
+ * handle (exchange_energy).  Returns the first failing build's status (ACE_ERR_NOT_POSDEF,
+ * ACE_ERR_NONFINITE, ACE_ERR_TIMEOUT) or ACE_OK; ACE_ERR_ARG before the first launch. */
+ace_status ace_graph_sync(ace_graph *g);
+
+/* Number of builds in the graph (0 for NULL), and the handle of build i (borrowed). */
+int ace_graph_size(const ace_graph *g);
+ace_status ace_graph_op(const ace_graph *g, int i, ace_op **op);
+
+/* Waits for the last launch, then frees the graph and its handles.  NULL is a no-op. */
+void ace_graph_destroy(ace_graph *g);
+
 /* Apply the ACE operator (section II): out = -xi (dV xi^T psi) = V_X^ACE psi, dense (no screen).
  *   psi, out: [m][N1][N2][N3] of `dtype`, host or device (both on the same side), m >= 1.
  * Runs on `cuda_stream` and returns after the result is complete (it reads back a device error
@@ -249,6 +293,7 @@ ace_status ace_autotune(const ace_desc *desc, const void *phi, ace_dtype dtype, 
 /* 1 if an axis length has a compiled FFT plan for precision `prec`, else 0. */
 int ace_grid_supported(int n_axis, ace_precision prec);
 
+/* Frees a handle and everything it owns.  NULL, and handles that belong to a graph, are no-ops. */
 void ace_destroy(ace_op *op);
 
 /* W without device allocation.  The paper has no counterpart: this entry point exists for callers

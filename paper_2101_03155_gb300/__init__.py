@@ -12,6 +12,7 @@ from .ace import (  # noqa: F401
     ACE_MIXED,
     AceDesc,
     AceError,
+    AceGraph,
     AceOp,
     ace_apply,
     ace_build,
@@ -19,6 +20,7 @@ from .ace import (  # noqa: F401
     ace_build_pairs,
     ace_destroy,
     ace_get,
+    ace_graph_create,
     ace_grid_supported,
     ace_last_error,
     ace_pair_count,

@@ -49,6 +49,8 @@ EXPORTED = [
     "ace_get_size", "ace_stage_times", "ace_kernel_launches", "ace_grid_supported", "ace_destroy",
     "ace_last_error", "ace_exchange_w_noalloc", "ace_autotune", "ace_build_pairs", "ace_scdm",
     "ace_exchange_w", "ace_m_partial", "ace_build_from_m", "ace_apply_coeffs", "ace_apply_finish",
+    "ace_graph_create", "ace_graph_launch", "ace_graph_sync", "ace_graph_size", "ace_graph_op",
+    "ace_graph_destroy",
 ]
 
 
@@ -130,6 +132,15 @@ def load(path: str = LIB_PATH):
                                          ctypes.POINTER(vp)]
         lib.ace_apply_coeffs.argtypes = [vp, vp, c_int, c_int, vp, vp]
         lib.ace_apply_finish.argtypes = [vp, vp, c_int, c_int, vp, vp]
+        lib.ace_graph_create.argtypes = [c_int, ctypes.POINTER(AceDesc), ctypes.POINTER(vp), c_int,
+                                         ctypes.POINTER(vp), ctypes.POINTER(c_long), vp, ctypes.POINTER(vp)]
+        lib.ace_graph_launch.argtypes = [vp, vp]
+        lib.ace_graph_sync.argtypes = [vp]
+        lib.ace_graph_size.argtypes = [vp]
+        lib.ace_graph_size.restype = c_int
+        lib.ace_graph_op.argtypes = [vp, c_int, ctypes.POINTER(vp)]
+        lib.ace_graph_destroy.argtypes = [vp]
+        lib.ace_graph_destroy.restype = None
         lib.ace_grid_supported.argtypes = [c_int, c_int]
         lib.ace_grid_supported.restype = c_int
         lib.ace_destroy.argtypes = [vp]
@@ -138,7 +149,8 @@ def load(path: str = LIB_PATH):
         for name in ("ace_build", "ace_build_batched", "ace_apply", "exchange_energy", "ace_get", "ace_get_size",
                      "ace_pair_count", "ace_stage_times", "ace_kernel_launches", "ace_exchange_w_noalloc",
                      "ace_autotune", "ace_build_pairs", "ace_scdm", "ace_exchange_w", "ace_m_partial",
-                     "ace_build_from_m", "ace_apply_coeffs", "ace_apply_finish"):
+                     "ace_build_from_m", "ace_apply_coeffs", "ace_apply_finish", "ace_graph_create",
+                     "ace_graph_launch", "ace_graph_sync", "ace_graph_op"):
             getattr(lib, name).restype = c_int
         _lib = lib
         return lib
@@ -183,11 +195,13 @@ def _stream_handle(stream):
 
 
 class AceOp:
-    """Owner of an ace_op handle; ace_destroy runs on close() or garbage collection."""
+    """Owner of an ace_op handle; ace_destroy runs on close() or garbage collection.  A borrowed
+    handle (one build of an AceGraph) is released by its graph, never here."""
 
-    def __init__(self, handle: int, desc: AceDesc):
+    def __init__(self, handle: int, desc: AceDesc, owned: bool = True):
         self.handle = handle
         self.desc = desc
+        self.owned = owned
 
     @property
     def grid(self):
@@ -198,9 +212,9 @@ class AceOp:
         return self.desc.norb
 
     def close(self):
-        if self.handle:
+        if self.handle and self.owned:
             load().ace_destroy(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
         try:
@@ -261,6 +275,94 @@ def ace_build_batched(descs, phis, stream=None):
     outs = (ctypes.c_void_p * k)()
     _check(load().ace_build_batched(k, arr, pa, code if code is not None else ACE_F32, _stream_handle(stream), outs))
     return [AceOp(outs[i], descs[i]) for i in range(k)]
+
+
+class AceGraph:
+    """k builds on given pair lists recorded as one CUDA graph (ace_graph_create).  Holds the input
+    tensors so that they outlive the graph; overwrite their contents, then launch() again."""
+
+    def __init__(self, handle: int, descs, phis):
+        self.handle = handle
+        self.descs = list(descs)
+        self._phis = list(phis)
+        lib = load()
+        self.ops = []
+        for i in range(lib.ace_graph_size(handle)):
+            h = ctypes.c_void_p()
+            _check(lib.ace_graph_op(handle, i, ctypes.byref(h)))
+            self.ops.append(AceOp(h.value, self.descs[i], owned=False))
+
+    def launch(self, stream=None):
+        _check(load().ace_graph_launch(self.handle, _stream_handle(stream)))
+
+    def sync(self):
+        _check(load().ace_graph_sync(self.handle))
+
+    def close(self):
+        if self.handle:
+            for op in self.ops:
+                op.handle = None
+            load().ace_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def ace_graph_create(descs, phis, pairs, stream=None) -> AceGraph:
+    """ace_graph_create: phis are device tensors of the working dtype, pairs int [npairs][2] each."""
+    k = len(descs)
+    if not (len(phis) == len(pairs) == k):
+        raise ValueError("descs, phis and pairs must have one entry per build")
+    arr = (AceDesc * k)(*descs)
+    ptrs, lists = [], []
+    code = None
+    for d, p in zip(descs, phis):
+        ptr, c, numel = _array_info(p)
+        if code is not None and c != code:
+            raise TypeError("all inputs of a graph must have one dtype")
+        code = c
+        if numel != d.norb * d.n[0] * d.n[1] * d.n[2]:
+            raise ValueError("input size does not match its descriptor")
+        ptrs.append(ptr)
+    for pr in pairs:
+        lists.append(np.ascontiguousarray(np.asarray(pr, dtype=np.int32).reshape(-1, 2)))
+    pa = (ctypes.c_void_p * k)(*ptrs)
+    la = (ctypes.c_void_p * k)(*[x.ctypes.data if len(x) else None for x in lists])
+    na = (ctypes.c_long * k)(*[len(x) for x in lists])
+    h = ctypes.c_void_p()
+    _check(load().ace_graph_create(k, arr, pa, code if code is not None else ACE_F32, la, na,
+                                   _stream_handle(stream), ctypes.byref(h)))
+    return AceGraph(h.value, descs, phis)
+
+
+def ace_graph_launch(graph: AceGraph, stream=None) -> None:
+    graph.launch(stream)
+
+
+def ace_graph_sync(graph: AceGraph) -> None:
+    graph.sync()
+
+
+def ace_graph_size(graph: AceGraph) -> int:
+    return load().ace_graph_size(graph.handle)
+
+
+def ace_graph_op(graph: AceGraph, i: int) -> AceOp:
+    return graph.ops[i]
+
+
+def ace_graph_destroy(graph: AceGraph) -> None:
+    graph.close()
 
 
 def ace_apply(op: AceOp, psi, out, stream=None):

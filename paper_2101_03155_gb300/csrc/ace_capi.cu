@@ -267,14 +267,20 @@ struct ace_op {
   void *readback = nullptr;   // pinned host area for the asynchronous readbacks of a build
   size_t readback_bytes = 0;
   int lane = 0;               // stream lane of a batched build (selects its side streams)
+  bool graph = false;         // recorded into a CUDA graph: no host waits, no timing events,
+                              // uploads from pinned buffers that live as long as the handle
+  std::vector<std::pair<void *, size_t>> staged;  // those pinned upload buffers
 };
 
 namespace {
 
+// Buffers the handle owns (results and pair lists).  A handle recorded into a graph takes them
+// from cudaMalloc, outside the graph, so that they keep their addresses over every launch.
 template <typename P>
 cudaError_t op_alloc(ace_op *op, P **p, size_t bytes) {
   void *v = nullptr;
-  cudaError_t e = cudaMallocAsync(&v, bytes > 0 ? bytes : 16, op->stream);
+  cudaError_t e = op->graph ? cudaMalloc(&v, bytes > 0 ? bytes : 16)
+                            : cudaMallocAsync(&v, bytes > 0 ? bytes : 16, op->stream);
   if (e != cudaSuccess) return e;
   op->owned.push_back(v);
   *p = static_cast<P *>(v);
@@ -282,8 +288,29 @@ cudaError_t op_alloc(ace_op *op, P **p, size_t bytes) {
 }
 
 void op_free_all(ace_op *op) {
-  for (void *p : op->owned) cudaFreeAsync(p, op->stream);
+  for (void *p : op->owned) op->graph ? cudaFree(p) : cudaFreeAsync(p, op->stream);
   op->owned.clear();
+}
+
+void destroy_op(ace_op *op);
+
+// Host-to-device copy of a host temporary: directly (the call returns once the pageable source
+// has been read) or, when the op is recorded into a graph, through a pinned buffer kept with the
+// handle, since the graph reads its source again at every launch.
+cudaError_t host_upload(ace_op *op, void *dst, const void *src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  if (!op->graph) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+  void *pin = nullptr;
+  cudaError_t e = cudaHostAlloc(&pin, bytes, cudaHostAllocDefault);
+  if (e != cudaSuccess) return e;
+  std::memcpy(pin, src, bytes);
+  op->staged.emplace_back(pin, bytes);
+  return cudaMemcpyAsync(dst, pin, bytes, cudaMemcpyHostToDevice, st);
+}
+
+// Stage-timing event i of a build (not recorded inside a graph)
+cudaError_t mark(ace_op *op, int i, cudaStream_t st) {
+  return op->graph ? cudaSuccess : cudaEventRecord(op->ev[i], st);
 }
 
 ace_status check_desc(const ace_desc *d) {
@@ -535,9 +562,7 @@ ace_status run_chain_pencil(ace_op *op, const T *phi, const T *Kd, const cpx<T> 
     rb = form_rounds(packs, op->n);
     ACE_CUDA(cudaMallocAsync(&tmp, sizeof(int4) * packs.size(), st), "alloc packs");
     temps.push_back(tmp);
-    // pageable source: the copy has read it when the call returns
-    ACE_CUDA(cudaMemcpyAsync(tmp, packs.data(), sizeof(int4) * packs.size(), cudaMemcpyHostToDevice, st),
-             "pack upload");
+    ACE_CUDA(host_upload(op, tmp, packs.data(), sizeof(int4) * packs.size(), st), "pack upload");
     a.packs = static_cast<const int4 *>(tmp);
   }
   for (size_t r = 0; r + 1 < rb.size(); ++r)
@@ -556,18 +581,31 @@ ace_status run_chain_pencil(ace_op *op, const T *phi, const T *Kd, const cpx<T> 
   return ACE_OK;
 }
 
+// The per-context L2 set-aside for persisting lines, raised to mb MB (clamped to the device's
+// maximum) if it is smaller; returns the set-aside in bytes (0: none possible).
+size_t l2_set_aside(int dev, int mb) {
+  int max_persist = 0;
+  cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
+  const size_t limit = std::min((size_t)mb << 20, (size_t)std::max(0, max_persist));
+  if (limit == 0) return 0;
+  size_t now = 0;
+  cudaDeviceGetLimit(&now, cudaLimitPersistingL2CacheSize);
+  if (now < limit) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, limit);
+  cudaGetLastError();
+  return limit;
+}
+
 // Marks [base, base + bytes) as persisting in L2 for work on stream st (a per-context set-aside of
 // at most mb MB, clamped to the device's limits); bytes = 0 turns the window off.  Failures only
-// lose the hint: their error state is cleared.
+// lose the hint: their error state is cleared.  Inside a stream capture the window is copied into
+// the recorded kernels; the set-aside must then exist already (l2_set_aside before the capture).
 void l2_window(cudaStream_t st, int dev, void *base, size_t bytes, int mb) {
   cudaStreamAttrValue v{};
   if (bytes > 0 && mb > 0) {
-    int max_persist = 0, max_window = 0;
-    cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
+    int max_window = 0;
     cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev);
-    const size_t limit = std::min((size_t)mb << 20, (size_t)std::max(0, max_persist));
+    const size_t limit = l2_set_aside(dev, mb);
     if (limit == 0 || max_window <= 0) return;
-    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, limit);
     v.accessPolicyWindow.base_ptr = base;
     v.accessPolicyWindow.num_bytes = std::min({bytes, limit, (size_t)max_window});
     v.accessPolicyWindow.hitRatio = 1.0f;
@@ -694,7 +732,7 @@ ace_status run_chain_persistent(ace_op *op, const DeviceTables *tab, const ace::
   std::memcpy(hm.data(), packs.data(), b_packs);
   std::memcpy(hm.data() + o_builds, builds.data(), b_builds);
   if (b_pb) std::memcpy(hm.data() + o_pb, pack_build.data(), b_pb);
-  ACE_CUDA(cudaMemcpyAsync(m, hm.data(), o_cnt, cudaMemcpyHostToDevice, st), "pack queue upload");
+  ACE_CUDA(host_upload(op, m, hm.data(), o_cnt, st), "pack queue upload");
   ACE_CUDA(cudaMemsetAsync(m + o_cnt, 0, b_cnt, st), "zero counters");
   ACE_CUDA(cudaMallocAsync(&tmp, sizeof(cpx<T>) * (size_t)N * nslots, st), "alloc scratch");
   temps.push_back(tmp);
@@ -797,7 +835,7 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   int4 *groups_d = packs_d + packs.size();
   std::vector<int4> up(packs);
   up.insert(up.end(), groups.begin(), groups.end());
-  ACE_CUDA(cudaMemcpyAsync(packs_d, up.data(), sizeof(int4) * up.size(), cudaMemcpyHostToDevice, st), "pack upload");
+  ACE_CUDA(host_upload(op, packs_d, up.data(), sizeof(int4) * up.size(), st), "pack upload");
   ACE_CUDA(cudaMallocAsync(&tmp, sizeof(cpx<T>) * (size_t)N * B * nstreams, st), "alloc scratch");
   temps.push_back(tmp);
   cpx<T> *scratch_all = static_cast<cpx<T> *>(tmp);
@@ -980,7 +1018,7 @@ ace_status build_begin(ace_op *op, const void *phi_in, ace_dtype dtype) {
   const long long N = op->N;
   cudaStream_t st = op->stream;
   for (int i = 0; i < 6; ++i) ACE_CUDA(cudaEventCreate(&op->ev[i]), "event create");
-  ACE_CUDA(cudaEventRecord(op->ev[0], st), "event record");
+  ACE_CUDA(mark(op, 0, st), "event record");
   // FP32 host input of a screened build: copied in column chunks on a copy stream while the
   // screen adds each chunk's contribution on the build stream (the transfer hides the screen)
   const bool same = (dtype == ACE_F64) == (sizeof(T) == 8);
@@ -1033,12 +1071,8 @@ ace_status build_begin(ace_op *op, const void *phi_in, ace_dtype dtype) {
     // uploads from the pinned area, so that they stay asynchronous (the area lives until destroy)
     ACE_CUDA(cudaMemcpyAsync(op->pairs, rp, sizeof(int2) * np, cudaMemcpyHostToDevice, st), "pair upload");
     ACE_CUDA(cudaMemcpyAsync(op->count_d, op->readback, sizeof(int), cudaMemcpyHostToDevice, st), "count upload");
-    if (!pk.empty()) {
-      ACE_CUDA(cudaMemcpyAsync(op->packs, pk.data(), sizeof(int4) * pk.size(), cudaMemcpyHostToDevice, st),
-               "pack upload");
-      ACE_CUDA(cudaStreamSynchronize(st), "pack upload");  // pk is a host temporary
-    }
-    ACE_CUDA(cudaEventRecord(op->ev[1], st), "event record");
+    if (!pk.empty()) ACE_CUDA(host_upload(op, op->packs, pk.data(), sizeof(int4) * pk.size(), st), "pack upload");
+    ACE_CUDA(mark(op, 1, st), "event record");
     return ACE_OK;
   }
   // workspace of the tensor-core screen (FP64 partial sums of its K-splits; sized for the whole N)
@@ -1095,7 +1129,7 @@ ace_status build_begin(ace_op *op, const void *phi_in, ace_dtype dtype) {
   ACE_CUDA(cudaMemcpyAsync(static_cast<char *>(op->readback) + 32, op->pairs, sizeof(int2) * maxpairs,
                            cudaMemcpyDeviceToHost, st),
            "pair readback");
-  ACE_CUDA(cudaEventRecord(op->ev[1], st), "event record");
+  ACE_CUDA(mark(op, 1, st), "event record");
   return ACE_OK;
 }
 
@@ -1136,25 +1170,22 @@ ace_status factor_and_project(ace_op *op, const T *W);
 
 template <typename T>
 ace_status build_finish(ace_op *op) {
-  const ace_desc &d = op->desc;
   const int n = op->n;
   const long long N = op->N;
   cudaStream_t st = op->stream;
   const T *phi = static_cast<const T *>(op->phi_work);
-  const DeviceTables *tab = op->tab;
   const int count = *static_cast<const int *>(op->readback);
   op->npairs = count;
   const int2 *ph = reinterpret_cast<const int2 *>(static_cast<const char *>(op->readback) + 32);
   op->pairs_h.assign(ph, ph + count);
   std::vector<void *> &temps = op->temps;
-  void *tmp = nullptr;
   ace_status s = ACE_OK;
 
   // ---- pair chain (Eq. vx, Eq. e:vij): W_i = sum_j v_ij phi_j ----
   ACE_CUDA(op_alloc(op, &op->W, op->esz * (size_t)n * N), "alloc W");
   s = run_chain<T>(op, phi, count);
   if (s != ACE_OK) return s;
-  ACE_CUDA(cudaEventRecord(op->ev[2], st), "event record");
+  ACE_CUDA(mark(op, 2, st), "event record");
 
   // ---- M = -dV Phi^T W (App. A) ----
   ACE_CUDA(op_alloc(op, &op->M_raw, sizeof(double) * n * n), "alloc M_raw");
@@ -1164,7 +1195,7 @@ ace_status build_finish(ace_op *op) {
   ACE_CUDA(dense_gram<T>(phi, n, static_cast<const T *>(op->W), n, N, -op->dV, op->M_raw, op->tc_err, temps, st,
                          &op->launches),
            "M");
-  ACE_CUDA(cudaEventRecord(op->ev[3], st), "event record");
+  ACE_CUDA(mark(op, 3, st), "event record");
 
   return factor_and_project<T>(op, static_cast<const T *>(op->W));
 }
@@ -1189,7 +1220,7 @@ ace_status factor_and_project(ace_op *op, const T *W) {
                                 op->status_d, chol_work, st),
            "cholesky");
   ++op->launches;
-  ACE_CUDA(cudaEventRecord(op->ev[4], st), "event record");
+  ACE_CUDA(mark(op, 4, st), "event record");
 
   // ---- xi = W L^-T, stored as rows: xi_rows = L^-1 W_rows ----
   ACE_CUDA(op_alloc(op, &op->xi, op->esz * (size_t)n * N), "alloc xi");
@@ -1204,7 +1235,7 @@ ace_status factor_and_project(ace_op *op, const T *W) {
     Linv_T = static_cast<const T *>(tmp);
   }
   ACE_CUDA(dense_left_mul<T>(Linv_T, n, n, W, N, static_cast<T *>(op->xi), op->tc_err, st, &op->launches), "xi");
-  ACE_CUDA(cudaEventRecord(op->ev[5], st), "event record");
+  ACE_CUDA(mark(op, 5, st), "event record");
   char *rb = static_cast<char *>(op->readback);
   ACE_CUDA(cudaMemcpyAsync(rb + 4, op->status_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, st), "status readback");
   ACE_CUDA(cudaMemcpyAsync(rb + 16, op->energy_d, sizeof(double), cudaMemcpyDeviceToHost, st), "energy readback");
@@ -1222,10 +1253,12 @@ ace_status build_collect(ace_op *op) {
   std::memcpy(flags, rb + 4, sizeof flags);
   std::memcpy(&op->energy, rb + 16, sizeof(double));
   op->status = flags[0];
-  for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&op->stage_ms[i], op->ev[i], op->ev[i + 1]);
-  cudaEventElapsedTime(&op->stage_ms[5], op->ev[0], op->ev[5]);
-  pinned_put(op->readback, op->readback_bytes);
-  op->readback = nullptr;
+  if (!op->graph) {
+    for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&op->stage_ms[i], op->ev[i], op->ev[i + 1]);
+    cudaEventElapsedTime(&op->stage_ms[5], op->ev[0], op->ev[5]);
+    pinned_put(op->readback, op->readback_bytes);
+    op->readback = nullptr;
+  }
   if (flags[1]) return fail(ACE_ERR_TIMEOUT, "a kernel gave up waiting (tensor-core pipeline, TMA copy or pair-chain task queue)");
   if (op->status >= 2000000) return fail(ACE_ERR_NONFINITE, "M has a non-finite entry");
   if (op->status >= 1000000)
@@ -1632,7 +1665,7 @@ ace_status ace_build_from_m(const ace_desc *desc, const double *M, const void *W
   cudaStream_t st = op->stream;
   auto run = [&]() -> ace_status {
     for (int i = 0; i < 6; ++i) ACE_CUDA(cudaEventCreate(&op->ev[i]), "event create");
-    for (int i = 0; i < 4; ++i) ACE_CUDA(cudaEventRecord(op->ev[i], st), "event record");
+    for (int i = 0; i < 4; ++i) ACE_CUDA(mark(op, i, st), "event record");
     ACE_CUDA(op_alloc(op, &op->status_d, sizeof(int) * 4), "alloc status");
     op->tc_err = op->status_d + 1;
     ACE_CUDA(cudaMemsetAsync(op->status_d, 0, sizeof(int) * 4, st), "zero status");
@@ -1998,7 +2031,15 @@ ace_status ace_autotune(const ace_desc *desc, const void *phi, ace_dtype dtype, 
 }
 
 void ace_destroy(ace_op *op) {
-  if (!op) return;
+  if (!op || op->graph) return;  // handles of a graph belong to it (ace_graph_destroy)
+  destroy_op(op);
+}
+
+}  // extern "C"
+
+namespace {
+
+void destroy_op(ace_op *op) {
   for (void *p : op->temps) cudaFreeAsync(p, op->stream);
   op->temps.clear();
   op_free_all(op);
@@ -2008,7 +2049,188 @@ void ace_destroy(ace_op *op) {
   }
   for (int i = 0; i < 6; ++i)
     if (op->ev[i]) cudaEventDestroy(op->ev[i]);
+  for (auto &b : op->staged) cudaFreeHost(b.first);
   delete op;
+}
+
+}  // namespace
+
+// ---- many builds on given pair lists as one CUDA graph ----
+
+struct ace_graph {
+  std::vector<ace_op *> ops;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;  // private stream the builds were recorded from
+  cudaEvent_t done = nullptr;  // recorded after each launch
+  bool launched = false;
+};
+
+namespace {
+
+void graph_free(ace_graph *g) {
+  if (g->launched) cudaEventSynchronize(g->done);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  for (ace_op *op : g->ops) destroy_op(op);
+  if (g->done) cudaEventDestroy(g->done);
+  if (g->cap) cudaStreamDestroy(g->cap);
+  delete g;
+}
+
+// Records the builds of g->ops (already created, graph mode) from g->cap.  Each build is
+// build_begin + build_finish with no host wait in between (the pair count is the caller's); builds
+// are spread over stream lanes forked from g->cap and joined back.
+ace_status record_builds(ace_graph *g, const void *const *phi, ace_dtype dtype, int lanes, cudaStream_t *lane_st) {
+  cudaEvent_t ev = nullptr;
+  ACE_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+  struct EvGuard {
+    cudaEvent_t e;
+    ~EvGuard() { cudaEventDestroy(e); }
+  } guard{ev};
+  ACE_CUDA(cudaEventRecord(ev, g->cap), "event");
+  for (int l = 0; l < lanes; ++l) ACE_CUDA(cudaStreamWaitEvent(lane_st[l], ev, 0), "fork");
+  for (size_t i = 0; i < g->ops.size(); ++i) {
+    ace_status s = begin_any(g->ops[i], phi[i], dtype);
+    if (s == ACE_OK) s = finish_any(g->ops[i]);
+    if (s != ACE_OK) return fail(s, "build %zu of %zu: %s", i, g->ops.size(), g_last_error.c_str());
+  }
+  for (int l = 0; l < lanes; ++l) {
+    ACE_CUDA(cudaEventRecord(ev, lane_st[l]), "event");
+    ACE_CUDA(cudaStreamWaitEvent(g->cap, ev, 0), "join");
+  }
+  return ACE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ace_status ace_graph_create(int k, const ace_desc *desc, const void *const *phi, ace_dtype dtype,
+                            const int *const *pairs_host, const long *npairs, void *cuda_stream, ace_graph **out) {
+  if (!out) return fail(ACE_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (k < 1 || !desc || !phi || !pairs_host || !npairs) return fail(ACE_ERR_ARG, "bad graph arguments");
+  std::vector<std::vector<int2>> given(k);
+  for (int i = 0; i < k; ++i) {
+    ace_status s = check_desc(&desc[i]);
+    if (s == ACE_OK) s = working_dtype(&desc[i], dtype);
+    if (s == ACE_OK && (!phi[i] || !is_device_pointer(phi[i])))
+      s = fail(ACE_ERR_ARG, "phi is not device memory");
+    if (s == ACE_OK && reinterpret_cast<uintptr_t>(phi[i]) % 16 != 0) s = fail(ACE_ERR_ARG, "phi is not 16-byte aligned");
+    if (s == ACE_OK) s = checked_pairs(&desc[i], pairs_host[i], npairs[i], given[i]);
+    if (s != ACE_OK) return fail(s, "build %d of %d: %s", i, k, g_last_error.c_str());
+  }
+  cudaStream_t user = static_cast<cudaStream_t>(cuda_stream);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  ACE_CUDA(cudaStreamIsCapturing(user, &cs), "stream state");
+  if (cs != cudaStreamCaptureStatusNone) return fail(ACE_ERR_ARG, "cuda_stream is being captured");
+  int dev = 0;
+  ACE_CUDA(cudaGetDevice(&dev), "device");
+  // the kernel and twiddle tables are made (uploaded, then waited for) before the recording
+  for (int i = 0; i < k; ++i) {
+    const DeviceTables *tab = nullptr;
+    cudaError_t e = dtype == ACE_F64 ? get_tables<double>(dev, desc[i], user, &tab)
+                                     : get_tables<float>(dev, desc[i], user, &tab);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel and twiddle tables");
+  }
+  // the L2 set-aside for the chain's scratch windows is a context limit: made before the recording,
+  // which then only sets the windows (stream attributes, copied into the recorded kernels)
+  for (int i = 0; i < k; ++i) {
+    const int mb = chain_params(desc[i], desc[i].prec == ACE_FP64).persist_mb;
+    if (mb > 0) l2_set_aside(dev, mb);
+  }
+  ace_graph *g = new ace_graph;
+  cudaError_t e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming);
+  // one lane by default: a build's chain already fills the GPU through its side streams, and
+  // concurrent builds only share the L2 (measured: 4 lanes 25% slower on 8 builds at 96^3)
+  const int lanes = std::min(kLanes, std::max(1, std::min(k, env_int("ACE_GRAPH_LANES", 1))));
+  cudaStream_t lane_st[kLanes];
+  for (int l = 0; l < lanes && e == cudaSuccess; ++l) e = get_side_stream(dev, kSide * kLanes + l, &lane_st[l]);
+  ace_status s = e == cudaSuccess ? ACE_OK : cuda_fail(e, "graph setup");
+  for (int i = 0; i < k && s == ACE_OK; ++i) {
+    ace_op *op = new_op(&desc[i], lane_st[i % lanes], &s);
+    if (!op) break;
+    op->graph = true;
+    op->lane = i % lanes;
+    op->use_given = true;
+    op->given.swap(given[i]);
+    g->ops.push_back(op);
+  }
+  if (s == ACE_OK) {
+    // relaxed mode: the handles' buffers come from cudaMalloc while the builds are recorded
+    e = cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+      s = cuda_fail(e, "begin capture");
+    } else {
+      s = record_builds(g, phi, dtype, lanes, lane_st);
+      const std::string msg = g_last_error;
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamEndCapture(g->cap, &graph);
+      g->graph = graph;
+      if (s != ACE_OK) {
+        cudaGetLastError();
+        s = fail(s, "%s", msg.c_str());
+      } else if (e != cudaSuccess) {
+        s = cuda_fail(e, "end capture");
+      }
+    }
+    if (s != ACE_OK) {
+      // workspaces taken inside the recording belong to the discarded graph
+      for (ace_op *op : g->ops) op->temps.clear();
+    }
+  }
+  if (s == ACE_OK) {
+    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e == cudaSuccess) e = cudaGraphUpload(g->exec, user);
+    if (e != cudaSuccess) s = cuda_fail(e, "graph instantiate");
+  }
+  if (s != ACE_OK) {
+    const std::string msg = g_last_error;
+    graph_free(g);
+    return fail(s, "%s", msg.c_str());
+  }
+  *out = g;
+  return ACE_OK;
+}
+
+ace_status ace_graph_launch(ace_graph *g, void *cuda_stream) {
+  if (!g) return fail(ACE_ERR_ARG, "graph is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  ACE_CUDA(cudaGraphLaunch(g->exec, st), "graph launch");
+  ACE_CUDA(cudaEventRecord(g->done, st), "event");
+  g->launched = true;
+  return ACE_OK;
+}
+
+ace_status ace_graph_sync(ace_graph *g) {
+  if (!g) return fail(ACE_ERR_ARG, "graph is NULL");
+  if (!g->launched) return fail(ACE_ERR_ARG, "the graph has not been launched");
+  ACE_CUDA(cudaEventSynchronize(g->done), "graph");
+  ace_status first = ACE_OK;
+  std::string msg;
+  for (size_t i = 0; i < g->ops.size(); ++i) {
+    ace_status s = build_collect(g->ops[i]);
+    if (s != ACE_OK && first == ACE_OK) {
+      first = s;
+      msg = "build " + std::to_string(i) + " of " + std::to_string(g->ops.size()) + ": " + g_last_error;
+    }
+  }
+  return first == ACE_OK ? ACE_OK : fail(first, "%s", msg.c_str());
+}
+
+int ace_graph_size(const ace_graph *g) { return g ? (int)g->ops.size() : 0; }
+
+ace_status ace_graph_op(const ace_graph *g, int i, ace_op **op) {
+  if (!g || !op) return fail(ACE_ERR_ARG, "NULL argument");
+  if (i < 0 || i >= (int)g->ops.size()) return fail(ACE_ERR_ARG, "build %d of %zu", i, g->ops.size());
+  *op = g->ops[i];
+  return ACE_OK;
+}
+
+void ace_graph_destroy(ace_graph *g) {
+  if (g) graph_free(g);
 }
 
 }  // extern "C"

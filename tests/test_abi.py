@@ -65,6 +65,14 @@ def test_host_side_checks_without_gpu(lib):
     h = ctypes.c_void_p()
     assert lib.ace_build(None, None, 0, None, ctypes.byref(h)) == ace.ACE_ERR_ARG
     lib.ace_destroy(None)  # no-op
+    # graph entry points: counts and NULL handles are checked before any CUDA call
+    lib.ace_graph_create.argtypes = [ctypes.c_int] + [ctypes.c_void_p] * 7
+    assert lib.ace_graph_create(0, None, None, 0, None, None, None, ctypes.byref(h)) == ace.ACE_ERR_ARG
+    assert lib.ace_graph_create(1, None, None, 0, None, None, None, None) == ace.ACE_ERR_ARG
+    assert lib.ace_graph_launch(None, None) == ace.ACE_ERR_ARG
+    assert lib.ace_graph_sync(None) == ace.ACE_ERR_ARG
+    assert lib.ace_graph_size(None) == 0
+    lib.ace_graph_destroy(None)  # no-op
     # SCDM: orbital count, point count (at least one per orbital) and precision are checked first
     a = np.zeros((4, 3), np.float32)
     for n, npts, prec in ((0, 3, ace.ACE_MIXED), (1025, 4096, ace.ACE_MIXED), (4, 3, ace.ACE_MIXED), (4, 8, 7)):

@@ -310,6 +310,20 @@ def enzyme_like(
     return snaps
 
 
+def moved_snapshot(w: Workload, step: float, rng) -> Workload:
+    """The next snapshot of a water_like workload: every orbital centre moved by ``step`` bohr in a
+    random direction, same spreads, re-orthonormalised (the snapshot recipe of enzyme_like)."""
+    centres = np.asarray(w.meta["centres"], dtype=np.float64)
+    d = rng.standard_normal(centres.shape)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    centres = centres + step * d
+    chi = _spread_orbitals(w.grid, w.lattice, centres, w.meta["spreads"])
+    phi, _ = loewdin(chi, w.dV)
+    meta = dict(w.meta, centres=centres)
+    return Workload(name=w.name + "_moved", phi=phi, lattice=w.lattice, rho_cut=w.rho_cut,
+                    spin_factor=w.spin_factor, meta=meta)
+
+
 def batched_set(rng, nbuild=24, norbs=(64, 96, 128, 192, 256), grids=(72, 96, 108, 128), rho_cut=1e-3):
     """Descriptors (n, grid, cell) of uneven builds at water density; orbitals drawn lazily.
 
