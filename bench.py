@@ -302,6 +302,8 @@ def run_multi(args):
         clk = clocks.stop()
         ms = start.elapsed_time(end)
         res[prec] = {"builds_per_s": len(ws) * steps / (ms / 1e3), "ms_per_step": ms / steps, "rec": rec, "clk": clk}
+        if prec == ace.ACE_MIXED and not args.no_queue_legs:
+            res["legs"] = _queue_legs(ace, descs, phis, stream, steps, args.warmup)
         del phis
     mixed, f64 = res[ace.ACE_MIXED], res[ace.ACE_FP64]
     # errors against the stored FP64-oracle values of the builds that have them (E_x; and xi, K phi,
@@ -342,9 +344,62 @@ def run_multi(args):
         "gpu_launches": mixed["rec"]["launches"],
         "clocks": mixed["clk"],
     }
+    if res.get("legs"):
+        line.update(res["legs"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def _queue_legs(ace, descs, phis, stream, steps, warmup):
+    """The same builds with their pair chains in device pack queues (one persistent launch per
+    grid, no host wait between screens and chains): as one recorded CUDA graph replayed per step
+    (screening at every launch), and through ace_build_batched with ACE_BATCH_QUEUE=1.  Only where
+    the library records the screened graph (the mixed form, grids with a persistent chain plan)."""
+    import torch
+
+    try:
+        g = ace.ace_graph_create(descs, phis, None, stream)
+    except ace.AceError as err:
+        return {"graph": {"unavailable": str(err)}}
+
+    def timed(step):
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(steps):
+            energies = step()
+        end.record(stream)
+        torch.cuda.synchronize()
+        ms = start.elapsed_time(end)
+        return {"value": len(descs) * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+                "E_x": energies}
+
+    def replay():
+        g.launch(stream)
+        g.sync()
+        return [ace.exchange_energy(op) for op in g.ops]
+
+    def batched_queue():
+        ops = ace.ace_build_batched(descs, phis, stream)
+        e = [ace.exchange_energy(op) for op in ops]
+        for op in ops:
+            op.close()
+        return e
+
+    out = {"graph": timed(replay)}
+    out["graph"]["step"] = "screened builds recorded once as a CUDA graph (device pack queues), one replay"
+    out["graph"]["gpu_launches"] = sum(ace.ace.ace_kernel_launches(op) for op in g.ops) * steps
+    g.close()
+    os.environ["ACE_BATCH_QUEUE"] = "1"
+    try:
+        out["queue"] = timed(batched_queue)
+        out["queue"]["step"] = "ace_build_batched with device pack queues, one persistent chain launch per grid"
+    finally:
+        del os.environ["ACE_BATCH_QUEUE"]
+    return out
 
 
 def run_reuse(args):
@@ -969,6 +1024,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default chain settings")
     ap.add_argument("--workload", default="water32", choices=sorted(WORKLOADS))
     ap.add_argument("--mts-inner", type=int, default=15, help="inner applications per outer step (enzyme8_mts)")
+    ap.add_argument("--no-queue-legs", action="store_true",
+                    help="batched workloads: skip the device-queue and CUDA-graph legs")
     ap.add_argument("--only-mixed", action="store_true",
                     help="time the mixed-form builds only (a reduced run for profiler captures)")
     args = ap.parse_args()

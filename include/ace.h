@@ -161,15 +161,23 @@ ace_status ace_apply_finish(const ace_op *op, const double *C, ace_dtype dtype, 
 
 /* k independent builds (replicas or snapshots) issued back to back on one stream.  desc, phi and
  * out are arrays of length k; each build is as in ace_build.  On the first failing build the
- * handles already created are destroyed, every out[i] is NULL, and its status is returned. */
+ * handles already created are destroyed, every out[i] is NULL, and its status is returned.
+ * By default the builds run on up to four concurrent stream lanes, each with the pair chain of
+ * ace_build.  With the environment variable ACE_BATCH_QUEUE=1, and every build in the mixed form on
+ * a grid with a persistent chain plan (see ace_graph_create), the chains run instead as one
+ * persistent launch per grid over the builds' concatenated device pack lists, with no host wait
+ * between the screens and the chains. */
 ace_status ace_build_batched(int k, const ace_desc *desc, const void *const *phi, ace_dtype dtype,
                              void *cuda_stream, ace_op **out);
 
-/* ---- Many builds on given pair lists as one CUDA graph ----
+/* ---- Many builds as one CUDA graph ----
  * The reuse steps of a multiple-time-step run (section III) rebuild the operator on the pair lists
  * of the last outer step while only the orbitals change; with the pair counts known on the host no
  * build needs a host wait, so k of them (snapshots or replicas; each as in ace_build_pairs) can be
- * recorded once and replayed with one launch.
+ * recorded once and replayed with one launch.  Screened builds (each as in ace_build) need no host
+ * wait either when their pair chains run from device pack queues: the screen's compaction writes
+ * the packs, and one persistent chain launch per grid walks the concatenated lists of all builds on
+ * that grid, reading the counts on the device (pairs_host = NULL below).
  *
  * ace_graph_create records the k builds from a private stream and instantiates the graph; it runs
  * no build.  The builds follow one another (each spreads its pair chain over side streams, with
@@ -180,7 +188,12 @@ ace_status ace_build_batched(int k, const ace_desc *desc, const void *const *phi
  *                  for ACE_MIXED, ACE_F64 for ACE_FP64), 16-byte aligned (ACE_ERR_ARG otherwise).
  *                  The graph keeps the pointers and reads the arrays at every launch: the caller
  *                  overwrites their contents between launches, and frees them after the graph.
- *   pairs_host[i]: the pair list of build i, checked as in ace_build_pairs and copied.
+ *   pairs_host[i]: the pair list of build i, checked as in ace_build_pairs and copied; or
+ *                  pairs_host = NULL (npairs ignored): every build screens with its desc->rho_cut at
+ *                  every launch (mixed form only, ACE_ERR_ARG for ACE_FP64; grids with a persistent
+ *                  chain plan: 32^3, 48^3, 64^3, 72^3, 96^3, 108^3, 128^3, 144^3, 160x144x128, else
+ *                  ACE_ERR_UNSUPPORTED_GRID); ace_pair_count and ACE_GET_PAIRS give the last
+ *                  synchronised launch's list.
  *   cuda_stream:   the kernel tables of every grid are made on it first (synchronously); it must
  *                  not be capturing.
  * The handles of the builds (ace_graph_op) exist from creation on and keep their buffers (xi, W, M,

@@ -318,10 +318,11 @@ class AceGraph:
         self.close()
 
 
-def ace_graph_create(descs, phis, pairs, stream=None) -> AceGraph:
-    """ace_graph_create: phis are device tensors of the working dtype, pairs int [npairs][2] each."""
+def ace_graph_create(descs, phis, pairs=None, stream=None) -> AceGraph:
+    """ace_graph_create: phis are device tensors of the working dtype; pairs is one int [npairs][2]
+    list per build, or None for builds that screen on the device at every launch."""
     k = len(descs)
-    if not (len(phis) == len(pairs) == k):
+    if len(phis) != k or (pairs is not None and len(pairs) != k):
         raise ValueError("descs, phis and pairs must have one entry per build")
     arr = (AceDesc * k)(*descs)
     ptrs, lists = [], []
@@ -334,11 +335,11 @@ def ace_graph_create(descs, phis, pairs, stream=None) -> AceGraph:
         if numel != d.norb * d.n[0] * d.n[1] * d.n[2]:
             raise ValueError("input size does not match its descriptor")
         ptrs.append(ptr)
-    for pr in pairs:
+    for pr in pairs or []:
         lists.append(np.ascontiguousarray(np.asarray(pr, dtype=np.int32).reshape(-1, 2)))
     pa = (ctypes.c_void_p * k)(*ptrs)
-    la = (ctypes.c_void_p * k)(*[x.ctypes.data if len(x) else None for x in lists])
-    na = (ctypes.c_long * k)(*[len(x) for x in lists])
+    la = (ctypes.c_void_p * k)(*[x.ctypes.data if len(x) else None for x in lists]) if pairs is not None else None
+    na = (ctypes.c_long * k)(*[len(x) for x in lists]) if pairs is not None else None
     h = ctypes.c_void_p()
     _check(load().ace_graph_create(k, arr, pa, code if code is not None else ACE_F32, la, na,
                                    _stream_handle(stream), ctypes.byref(h)))

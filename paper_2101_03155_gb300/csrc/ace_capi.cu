@@ -267,6 +267,7 @@ struct ace_op {
   void *readback = nullptr;   // pinned host area for the asynchronous readbacks of a build
   size_t readback_bytes = 0;
   int lane = 0;               // stream lane of a batched build (selects its side streams)
+  bool queued = false;        // screened build whose chain ran in a device pack queue
   bool graph = false;         // recorded into a CUDA graph: no host waits, no timing events,
                               // uploads from pinned buffers that live as long as the handle
   std::vector<std::pair<void *, size_t>> staged;  // those pinned upload buffers
@@ -705,35 +706,53 @@ std::vector<int> form_rounds(std::vector<int4> &packs, int norb) {
 }
 
 // Persistent chain of one or more builds on one grid: every pack of every build in one launch
-// (persistent_chain.cuh).  packs and pack_build (build of each pack, empty for one build) are on
-// the host; builds[b] holds the device pointers of build b.
+// (persistent_chain.cuh) on stream st.  The packs are either on the host (packs, with pack_build the
+// build of each pack, empty for one build), or, with packs empty, the builds' device lists `dev`,
+// concatenated on the device (their counts are read there; maxnp bounds the total).  builds[b]
+// holds the device pointers of build b; a wait that gives up sets op->tc_err.
 template <typename T>
-ace_status run_chain_persistent(ace_op *op, const DeviceTables *tab, const ace::PersistOps<T> &po,
+ace_status run_chain_persistent(ace_op *op, cudaStream_t st, const DeviceTables *tab, const ace::PersistOps<T> &po,
                                 const std::vector<int4> &packs, const std::vector<int> &pack_build,
+                                const std::vector<ace::QueueSrc> &dev, int maxnp,
                                 const std::vector<ace::ChainBuild<T>> &builds, std::vector<void *> &temps,
                                 const ChainParams &cp) {
   const long long N = op->N;
-  cudaStream_t st = op->stream;
-  const int np = (int)packs.size();
+  const bool on_device = packs.empty() && !dev.empty();
+  const int np = on_device ? maxnp : (int)packs.size();
   if (np == 0) return ACE_OK;
   const int lag = std::max(1, cp.lag);
-  const int nslots = std::min(2 * lag + 2, np);
-  // one allocation: packs, builds, pack_build, counters (3 np), ticket; then the scratch slots
+  const int nslots = on_device ? 2 * lag + 2 : std::min(2 * lag + 2, np);
+  // one allocation: packs, builds, pack_build, device list sources, counters (3 np) with the ticket,
+  // the stall word and the device pack count; then the scratch slots
   const size_t b_packs = sizeof(int4) * np, b_builds = sizeof(ace::ChainBuild<T>) * builds.size();
-  const size_t b_pb = sizeof(int) * pack_build.size(), b_cnt = sizeof(int) * (3 * (size_t)np + 4);
+  const size_t b_pb = sizeof(int) * (on_device ? (size_t)np : pack_build.size());
+  const size_t b_src = on_device ? sizeof(ace::QueueSrc) * dev.size() : 0;
+  const size_t b_cnt = sizeof(int) * (3 * (size_t)np + 4);
   auto up16 = [](size_t x) { return (x + 15) / 16 * 16; };
-  const size_t o_builds = up16(b_packs), o_pb = o_builds + up16(b_builds), o_cnt = o_pb + up16(b_pb);
+  const size_t o_builds = up16(b_packs), o_pb = o_builds + up16(b_builds), o_src = o_pb + up16(b_pb);
+  const size_t o_cnt = o_src + up16(b_src);
   const size_t meta = o_cnt + up16(b_cnt);
   void *tmp = nullptr;
   ACE_CUDA(cudaMallocAsync(&tmp, meta, st), "alloc pack queue");
   temps.push_back(tmp);
   char *m = static_cast<char *>(tmp);
-  std::vector<char> hm(o_cnt, 0);
-  std::memcpy(hm.data(), packs.data(), b_packs);
-  std::memcpy(hm.data() + o_builds, builds.data(), b_builds);
-  if (b_pb) std::memcpy(hm.data() + o_pb, pack_build.data(), b_pb);
-  ACE_CUDA(host_upload(op, m, hm.data(), o_cnt, st), "pack queue upload");
-  ACE_CUDA(cudaMemsetAsync(m + o_cnt, 0, b_cnt, st), "zero counters");
+  int *cnt = reinterpret_cast<int *>(m + o_cnt);
+  ACE_CUDA(cudaMemsetAsync(cnt, 0, b_cnt, st), "zero counters");
+  if (on_device) {
+    ACE_CUDA(host_upload(op, m + o_builds, builds.data(), b_builds, st), "queue upload");
+    ACE_CUDA(host_upload(op, m + o_src, dev.data(), b_src, st), "queue upload");
+    ACE_CUDA(ace::launch_queue_assemble(reinterpret_cast<const ace::QueueSrc *>(m + o_src), (int)dev.size(),
+                                        reinterpret_cast<int4 *>(m), reinterpret_cast<int *>(m + o_pb),
+                                        cnt + 3 * (size_t)np + 2, st),
+             "queue assembly");
+    ++op->launches;
+  } else {
+    std::vector<char> hm(o_src, 0);
+    std::memcpy(hm.data(), packs.data(), b_packs);
+    std::memcpy(hm.data() + o_builds, builds.data(), b_builds);
+    if (b_pb) std::memcpy(hm.data() + o_pb, pack_build.data(), b_pb);
+    ACE_CUDA(host_upload(op, m, hm.data(), o_src, st), "pack queue upload");
+  }
   ACE_CUDA(cudaMallocAsync(&tmp, sizeof(cpx<T>) * (size_t)N * nslots, st), "alloc scratch");
   temps.push_back(tmp);
   ace::PersistArgs<T> a{};
@@ -741,13 +760,13 @@ ace_status run_chain_persistent(ace_op *op, const DeviceTables *tab, const ace::
   a.pack_build = b_pb ? reinterpret_cast<const int *>(m + o_pb) : nullptr;
   a.packs = reinterpret_cast<const int4 *>(m);
   a.npacks = np;
+  a.npacks_d = on_device ? cnt + 3 * (size_t)np + 2 : nullptr;
   a.scratch = static_cast<cpx<T> *>(tmp);
   a.nslots = nslots;
   a.lag = lag;
   a.tw1 = static_cast<const cpx<T> *>(tab->tw[0]);
   a.tw2 = static_cast<const cpx<T> *>(tab->tw[1]);
   a.tw3 = static_cast<const cpx<T> *>(tab->tw[2]);
-  int *cnt = reinterpret_cast<int *>(m + o_cnt);
   a.counters = cnt;
   a.ticket = cnt + 3 * (size_t)np;
   a.err = op->tc_err;
@@ -1154,7 +1173,7 @@ ace_status run_chain(ace_op *op, const T *phi, int count) {
     std::vector<int4> packs;
     form_packs(op->pairs_h, cp.RB, packs);
     const std::vector<ace::ChainBuild<T>> one{{phi, static_cast<T *>(op->W), static_cast<const T *>(tab->Kperm)}};
-    return run_chain_persistent<T>(op, tab, qops, packs, {}, one, temps, cp);
+    return run_chain_persistent<T>(op, op->stream, tab, qops, packs, {}, {}, 0, one, temps, cp);
   }
   if (count > 0 && plane) return run_chain_plane<T>(op, phi, tab, pops, count, temps, cp);
   if (count > 0) {
@@ -1167,6 +1186,8 @@ ace_status run_chain(ace_op *op, const T *phi, int count) {
 
 template <typename T>
 ace_status factor_and_project(ace_op *op, const T *W);
+template <typename T>
+ace_status build_dense(ace_op *op);
 
 template <typename T>
 ace_status build_finish(ace_op *op) {
@@ -1178,7 +1199,6 @@ ace_status build_finish(ace_op *op) {
   op->npairs = count;
   const int2 *ph = reinterpret_cast<const int2 *>(static_cast<const char *>(op->readback) + 32);
   op->pairs_h.assign(ph, ph + count);
-  std::vector<void *> &temps = op->temps;
   ace_status s = ACE_OK;
 
   // ---- pair chain (Eq. vx, Eq. e:vij): W_i = sum_j v_ij phi_j ----
@@ -1186,6 +1206,18 @@ ace_status build_finish(ace_op *op) {
   s = run_chain<T>(op, phi, count);
   if (s != ACE_OK) return s;
   ACE_CUDA(mark(op, 2, st), "event record");
+  return build_dense<T>(op);
+}
+
+// The steps after the pair chain (op->W complete on op->stream): M = -dV Phi^T W, then
+// factor_and_project.
+template <typename T>
+ace_status build_dense(ace_op *op) {
+  const int n = op->n;
+  const long long N = op->N;
+  cudaStream_t st = op->stream;
+  const T *phi = static_cast<const T *>(op->phi_work);
+  std::vector<void *> &temps = op->temps;
 
   // ---- M = -dV Phi^T W (App. A) ----
   ACE_CUDA(op_alloc(op, &op->M_raw, sizeof(double) * n * n), "alloc M_raw");
@@ -1246,6 +1278,108 @@ ace_status factor_and_project(ace_op *op, const T *W) {
   return ACE_OK;
 }
 
+// The pair chains of `group` (builds begun on one grid, screened on the device, pair counts not
+// read on the host) as one persistent launch on st over their concatenated device pack lists; the
+// W of every build is allocated and zeroed here.  The caller has joined every build's stream into
+// st.  A wait that gives up marks every build of the group.
+template <typename T>
+ace_status run_queue_chain(const std::vector<ace_op *> &group, cudaStream_t st) {
+  ace_op *op0 = group[0];
+  const ace_desc &d = op0->desc;
+  ace::PersistOps<T> qops{};
+  if (!find_persist_ops<T>(d.n[0], d.n[1], d.n[2], &qops))
+    return fail(ACE_ERR_UNSUPPORTED_GRID, "no persistent chain for the %dx%dx%d grid", d.n[0], d.n[1], d.n[2]);
+  std::vector<ace::ChainBuild<T>> builds;
+  std::vector<ace::QueueSrc> src;
+  std::vector<int *> flags;
+  long long maxnp = 0;
+  for (ace_op *op : group) {
+    const size_t bytes = op->esz * (size_t)op->n * op->N;
+    ACE_CUDA(op_alloc(op, &op->W, bytes), "alloc W");
+    ACE_CUDA(cudaMemsetAsync(op->W, 0, bytes, st), "zero W");
+    builds.push_back({static_cast<const T *>(op->phi_work), static_cast<T *>(op->W),
+                      static_cast<const T *>(op->tab->Kperm)});
+    src.push_back({op->packs, op->count_d});
+    flags.push_back(op->tc_err);
+    maxnp += ((long long)op->n * (op->n + 1) / 2 + 1) / 2;
+  }
+  if (maxnp > (1ll << 28)) return fail(ACE_ERR_ARG, "%lld packs in one queue", maxnp);
+  std::vector<void *> temps;
+  const ChainParams cp = chain_params(d, sizeof(T) == 8);
+  ace_status s = run_chain_persistent<T>(op0, st, op0->tab, qops, {}, {}, src, (int)maxnp, builds, temps, cp);
+  if (s == ACE_OK && group.size() > 1) {
+    void *tmp = nullptr;
+    cudaError_t e = cudaMallocAsync(&tmp, sizeof(int *) * flags.size(), st);
+    if (e == cudaSuccess) {
+      temps.push_back(tmp);
+      e = host_upload(op0, tmp, flags.data(), sizeof(int *) * flags.size(), st);
+    }
+    if (e == cudaSuccess) e = ace::launch_flag_fanout(op0->tc_err, static_cast<int *const *>(tmp), (int)flags.size(), st);
+    if (e != cudaSuccess) s = cuda_fail(e, "queue give-up flags");
+    ++op0->launches;
+  }
+  for (void *p : temps) cudaFreeAsync(p, st);
+  return s;
+}
+
+// Whether builds can run with their chains in device pack queues: the mixed form on grids with a
+// persistent chain plan.
+bool queue_eligible(int k, const ace_desc *desc) {
+  for (int i = 0; i < k; ++i) {
+    ace::PersistOps<float> q{};
+    if (desc[i].prec == ACE_FP64 || !find_persist_ops<float>(desc[i].n[0], desc[i].n[1], desc[i].n[2], &q))
+      return false;
+  }
+  return true;
+}
+
+// Builds screened on the device with their pair chains as one persistent launch per grid (no host
+// wait between the screen and the chain): every build's screen on its lane, then per grid the
+// queue chain on lane 0 once every build of that grid is screened, then each build's dense steps
+// on its lane.  ops[i] is new (lane stream set, working type FP32, no given pairs); phi[i] device.
+ace_status run_queued_builds(const std::vector<ace_op *> &ops, const void *const *phi, ace_dtype dtype,
+                             cudaStream_t gs) {
+  for (size_t i = 0; i < ops.size(); ++i) {
+    ops[i]->queued = true;
+    ace_status s = build_begin<float>(ops[i], phi[i], dtype);
+    if (s != ACE_OK) return fail(s, "build %zu of %zu: %s", i, ops.size(), g_last_error.c_str());
+  }
+  std::vector<std::vector<ace_op *>> groups;
+  for (ace_op *op : ops) {
+    auto same = [&](const std::vector<ace_op *> &g) {
+      return g[0]->desc.n[0] == op->desc.n[0] && g[0]->desc.n[1] == op->desc.n[1] && g[0]->desc.n[2] == op->desc.n[2];
+    };
+    auto it = std::find_if(groups.begin(), groups.end(), same);
+    if (it == groups.end())
+      groups.push_back({op});
+    else
+      it->push_back(op);
+  }
+  cudaEvent_t ev = nullptr;
+  ACE_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+  struct EvGuard {
+    cudaEvent_t e;
+    ~EvGuard() { cudaEventDestroy(e); }
+  } guard{ev};
+  for (auto &g : groups) {
+    for (ace_op *op : g)
+      if (op->stream != gs) {
+        ACE_CUDA(cudaEventRecord(ev, op->stream), "event");
+        ACE_CUDA(cudaStreamWaitEvent(gs, ev, 0), "join");
+      }
+    ace_status s = run_queue_chain<float>(g, gs);
+    if (s != ACE_OK) return s;
+    ACE_CUDA(cudaEventRecord(ev, gs), "event");
+    for (ace_op *op : g) {
+      if (op->stream != gs) ACE_CUDA(cudaStreamWaitEvent(op->stream, ev, 0), "fork");
+      ACE_CUDA(mark(op, 2, op->stream), "event record");
+      s = build_dense<float>(op);
+      if (s != ACE_OK) return s;
+    }
+  }
+  return ACE_OK;
+}
+
 // Phase 3: after the stream has completed the build.
 ace_status build_collect(ace_op *op) {
   const char *rb = static_cast<const char *>(op->readback);
@@ -1253,6 +1387,7 @@ ace_status build_collect(ace_op *op) {
   std::memcpy(flags, rb + 4, sizeof flags);
   std::memcpy(&op->energy, rb + 16, sizeof(double));
   op->status = flags[0];
+  if (op->queued) op->npairs = *reinterpret_cast<const int *>(rb);  // the pair count, read back
   if (!op->graph) {
     for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&op->stage_ms[i], op->ev[i], op->ev[i + 1]);
     cudaEventElapsedTime(&op->stage_ms[5], op->ev[0], op->ev[5]);
@@ -1799,6 +1934,7 @@ ace_status ace_build_batched(int k, const ace_desc *desc, const void *const *phi
   }
   ace_status s = ACE_OK;
   int failed = -1;
+  const bool queue = env_int("ACE_BATCH_QUEUE", 0) != 0 && queue_eligible(k, desc);
   for (int i = 0; i < k && s == ACE_OK; ++i) {
     ace_op *op = new_op(&desc[i], lane_st[i % lanes], &s);
     if (!op) {
@@ -1807,10 +1943,18 @@ ace_status ace_build_batched(int k, const ace_desc *desc, const void *const *phi
     }
     op->lane = i % lanes;
     out[i] = op;
-    s = begin_any(op, phi[i], dtype);
-    if (s != ACE_OK) failed = i;
+    if (!queue) {
+      s = begin_any(op, phi[i], dtype);
+      if (s != ACE_OK) failed = i;
+    }
   }
-  for (int i = 0; i < k && s == ACE_OK; ++i) {
+  if (queue && s == ACE_OK) {
+    // one persistent chain launch per grid over the builds' device pack lists, no host wait
+    std::vector<ace_op *> ops(out, out + k);
+    s = run_queued_builds(ops, phi, dtype, lane_st[0]);
+    if (s != ACE_OK) failed = 0;
+  }
+  for (int i = 0; i < k && s == ACE_OK && !queue; ++i) {
     cudaError_t e = cudaEventSynchronize(out[i]->ev[1]);
     s = e == cudaSuccess ? finish_any(out[i]) : cuda_fail(e, "pair list readback");
     if (s != ACE_OK) failed = i;
@@ -1998,7 +2142,7 @@ ace_status ace_autotune(const ace_desc *desc, const void *phi, ace_dtype dtype, 
         for (int rep = 0; rep < 2; ++rep) {
           std::vector<void *> tmp;
           ACE_CUDA(cudaEventRecord(e0, op->stream), "event");
-          ace_status r = run_chain_persistent<T>(op, op->tab, qops, packs, {}, one, tmp, c);
+          ace_status r = run_chain_persistent<T>(op, op->stream, op->tab, qops, packs, {}, {}, 0, one, tmp, c);
           ACE_CUDA(cudaEventRecord(e1, op->stream), "event");
           for (void *q : tmp) cudaFreeAsync(q, op->stream);
           if (r != ACE_OK) return r;
@@ -2064,6 +2208,7 @@ struct ace_graph {
   cudaStream_t cap = nullptr;  // private stream the builds were recorded from
   cudaEvent_t done = nullptr;  // recorded after each launch
   bool launched = false;
+  bool screened = false;       // builds screen on the device; chains in device pack queues
 };
 
 namespace {
@@ -2090,7 +2235,11 @@ ace_status record_builds(ace_graph *g, const void *const *phi, ace_dtype dtype, 
   } guard{ev};
   ACE_CUDA(cudaEventRecord(ev, g->cap), "event");
   for (int l = 0; l < lanes; ++l) ACE_CUDA(cudaStreamWaitEvent(lane_st[l], ev, 0), "fork");
-  for (size_t i = 0; i < g->ops.size(); ++i) {
+  if (g->screened) {
+    ace_status s = run_queued_builds(g->ops, phi, dtype, lane_st[0]);
+    if (s != ACE_OK) return s;
+  }
+  for (size_t i = 0; i < g->ops.size() && !g->screened; ++i) {
     ace_status s = begin_any(g->ops[i], phi[i], dtype);
     if (s == ACE_OK) s = finish_any(g->ops[i]);
     if (s != ACE_OK) return fail(s, "build %zu of %zu: %s", i, g->ops.size(), g_last_error.c_str());
@@ -2110,7 +2259,9 @@ ace_status ace_graph_create(int k, const ace_desc *desc, const void *const *phi,
                             const int *const *pairs_host, const long *npairs, void *cuda_stream, ace_graph **out) {
   if (!out) return fail(ACE_ERR_ARG, "out is NULL");
   *out = nullptr;
-  if (k < 1 || !desc || !phi || !pairs_host || !npairs) return fail(ACE_ERR_ARG, "bad graph arguments");
+  if (k < 1 || k > ace::kQueueMaxBuilds || !desc || !phi || (pairs_host && !npairs))
+    return fail(ACE_ERR_ARG, "bad graph arguments");
+  const bool screened = pairs_host == nullptr;
   std::vector<std::vector<int2>> given(k);
   for (int i = 0; i < k; ++i) {
     ace_status s = check_desc(&desc[i]);
@@ -2118,7 +2269,12 @@ ace_status ace_graph_create(int k, const ace_desc *desc, const void *const *phi,
     if (s == ACE_OK && (!phi[i] || !is_device_pointer(phi[i])))
       s = fail(ACE_ERR_ARG, "phi is not device memory");
     if (s == ACE_OK && reinterpret_cast<uintptr_t>(phi[i]) % 16 != 0) s = fail(ACE_ERR_ARG, "phi is not 16-byte aligned");
-    if (s == ACE_OK) s = checked_pairs(&desc[i], pairs_host[i], npairs[i], given[i]);
+    if (s == ACE_OK && !screened) s = checked_pairs(&desc[i], pairs_host[i], npairs[i], given[i]);
+    if (s == ACE_OK && screened && desc[i].prec == ACE_FP64)
+      s = fail(ACE_ERR_ARG, "screened builds in a graph run in the mixed form only");
+    if (s == ACE_OK && screened && !queue_eligible(1, &desc[i]))
+      s = fail(ACE_ERR_UNSUPPORTED_GRID, "no persistent chain for the %dx%dx%d grid", desc[i].n[0], desc[i].n[1],
+               desc[i].n[2]);
     if (s != ACE_OK) return fail(s, "build %d of %d: %s", i, k, g_last_error.c_str());
   }
   cudaStream_t user = static_cast<cudaStream_t>(cuda_stream);
@@ -2141,6 +2297,7 @@ ace_status ace_graph_create(int k, const ace_desc *desc, const void *const *phi,
     if (mb > 0) l2_set_aside(dev, mb);
   }
   ace_graph *g = new ace_graph;
+  g->screened = screened;
   cudaError_t e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming);
   // one lane by default: a build's chain already fills the GPU through its side streams, and
@@ -2154,7 +2311,7 @@ ace_status ace_graph_create(int k, const ace_desc *desc, const void *const *phi,
     if (!op) break;
     op->graph = true;
     op->lane = i % lanes;
-    op->use_given = true;
+    op->use_given = !screened;
     op->given.swap(given[i]);
     g->ops.push_back(op);
   }

@@ -77,6 +77,7 @@ struct PersistArgs {
   const int *pack_build;        // [npacks] build of each pack; null: every pack belongs to build 0
   const int4 *packs;            // [npacks] (a, b, c, d), c = d = -1 for a single pair
   int npacks;
+  const int *npacks_d;          // non-null: the pack count, read on the device (npacks bounds it)
   cpx<T> *scratch;              // [nslots][N] complex
   int nslots;                   // >= 2 lag + 2
   int lag;                      // rounds between the stages of one pack in the queue
@@ -95,6 +96,21 @@ struct PersistOps {
   int tasks_per_pack;  // F + C + I tasks
 };
 bool persist_ops_f32_small(int n1, int n2, int n3, PersistOps<float> *out);
+
+// One build's device pack list for a concatenated queue: the packs of the screen's compaction
+// (consecutive pairs two at a time) and the pair count it wrote.
+struct QueueSrc {
+  const int4 *packs;
+  const int *count;
+};
+constexpr int kQueueMaxBuilds = 1024;
+// Concatenates the pack lists of nb <= kQueueMaxBuilds builds, in build order, into packs_out,
+// with the build of each pack in pack_build and the total pack count in *np_out (all on the device;
+// the pair counts are read there).
+// *dst[i] = 1 for every i < n if *src is non-zero (a give-up flag passed on to several builds).
+cudaError_t launch_flag_fanout(const int *src, int *const *dst, int n, cudaStream_t st);
+cudaError_t launch_queue_assemble(const QueueSrc *src, int nb, int4 *packs_out, int *pack_build, int *np_out,
+                                  cudaStream_t st);
 bool persist_ops_f32_large(int n1, int n2, int n3, PersistOps<float> *out);
 
 // Launch one pass over `npacks` packs (grid.y); returns cudaErrorInvalidValue if the axis

@@ -989,6 +989,58 @@ cudaError_t launch_screen_compact(const double *O, int n, double rho_cut, int2 *
 }
 
 // ----------------------------------------------------------------------------------------
+// Queue assembly: the pack lists of several builds, concatenated in build order.  Every CTA forms
+// the prefix of the pack counts (nb is small) and copies a grid-strided share of the packs.
+// ----------------------------------------------------------------------------------------
+constexpr int QA_NT = 256;
+
+__global__ void __launch_bounds__(QA_NT) queue_assemble_kernel(const QueueSrc *__restrict__ src, int nb,
+                                                               int4 *__restrict__ out, int *__restrict__ pack_build,
+                                                               int *__restrict__ np_out) {
+  __shared__ int off[kQueueMaxBuilds + 1];
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int b = 0; b < nb; ++b) {
+      off[b] = o;
+      o += (__ldcg(src[b].count) + 1) / 2;
+    }
+    off[nb] = o;
+    if (blockIdx.x == 0) *np_out = o;
+  }
+  __syncthreads();
+  const int total = off[nb];
+  for (int q = blockIdx.x * QA_NT + threadIdx.x; q < total; q += gridDim.x * QA_NT) {
+    int lo = 0, hi = nb - 1;  // the last build whose list starts at or before q (never an empty one)
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= q)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    out[q] = src[lo].packs[q - off[lo]];
+    pack_build[q] = lo;
+  }
+}
+
+__global__ void flag_fanout_kernel(const int *src, int *const *dst, int n) {
+  if (__ldcg(src) == 0) return;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) *dst[i] = 1;
+}
+
+cudaError_t launch_flag_fanout(const int *src, int *const *dst, int n, cudaStream_t st) {
+  flag_fanout_kernel<<<1, 128, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_queue_assemble(const QueueSrc *src, int nb, int4 *packs_out, int *pack_build, int *np_out,
+                                  cudaStream_t st) {
+  if (nb < 1 || nb > kQueueMaxBuilds) return cudaErrorInvalidValue;
+  queue_assemble_kernel<<<2 * 152, QA_NT, 0, st>>>(src, nb, packs_out, pack_build, np_out);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------------
 // Elementwise precision conversion with scale.
 // ----------------------------------------------------------------------------------------
 template <typename Tin, typename Tout>

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, false>()))
     for (int e = tid; e < N2; e += NT) tw2[e] = a.tw2[e];
   if (N3 != N1 && N3 != N2)
     for (int e = tid; e < N3; e += NT) tw3[e] = a.tw3[e];
-  const int np = a.npacks;
+  const int np = a.npacks_d ? __ldcg(a.npacks_d) : a.npacks;
   const long long total = (long long)RS * (np + 2 * a.lag);
   if (tid == 0) sh[0] = atomicAdd(a.ticket, 1);
   for (;;) {
