@@ -776,6 +776,7 @@ ace_status run_chain_persistent(ace_op *op, cudaStream_t st, const DeviceTables 
   const char *wn = std::getenv("ACE_PERSIST_WAIT_NS");
   a.wait_ns = (wn && *wn) ? std::strtoull(wn, nullptr, 10) : 2000000000ull;
   a.stall = env_int("ACE_PERSIST_TEST_STALL", 0) ? cnt + 3 * (size_t)np + 1 : nullptr;
+  a.hints = env_int("ACE_L2_HINTS", 1);
   // keep the scratch slots resident in L2 (a per-context set-aside of persisting lines)
   const int persist_mb = cp.persist_mb;
   if (persist_mb > 0) l2_window(st, op->dev, a.scratch, sizeof(cpx<T>) * (size_t)N * nslots, persist_mb);
@@ -894,6 +895,7 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   pa.tw3 = static_cast<const cpx<T> *>(tab->tw[2]);
   pa.N = N;
   pa.n1 = d.n[0];
+  pa.hints = env_int("ACE_L2_HINTS", 1);
   ace::PairPassArgs<T> ca;
   ca.phi = phi;
   ca.W = static_cast<T *>(op->W);

@@ -50,6 +50,7 @@ struct PlaneArgs {
   const cpx<T> *tw3;   // [N3] e^{-2 pi i e / N3}
   long long N;
   int n1;
+  int hints;           // bit 0: drop each consumed scratch plane from L2 without writing it back
 };
 
 // Plane passes for one (N2, N3) plane shape; absent shapes fall back to the five pencil passes.
@@ -88,6 +89,7 @@ struct PersistArgs {
   long long N;
   unsigned long long wait_ns;   // time limit of one wait for a pack's earlier tasks
   const int *stall;             // null; else the pencil tasks wait for this word to reach 1 (a test)
+  int hints;                    // as PlaneArgs::hints
 };
 template <typename T>
 struct PersistOps {

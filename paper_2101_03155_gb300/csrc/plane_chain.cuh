@@ -247,10 +247,22 @@ __device__ __forceinline__ void plane_forward(const T *__restrict__ phi, long lo
   });
 }
 
+// Drops the 128-byte lines that lie wholly inside [base, base + bytes) from L2 without writing
+// them back (their contents become undefined); the CTA's threads share the lines.
+template <int NT>
+__device__ __forceinline__ void l2_discard(const void *base, size_t bytes) {
+  const unsigned long long b = reinterpret_cast<unsigned long long>(base);
+  const unsigned long long first = (b + 127) & ~127ull, end = (b + bytes) & ~127ull;
+  for (unsigned long long a = first + 128ull * threadIdx.x; a < end; a += 128ull * NT)
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
+}
+
 // Inverse transform of one permuted spectrum plane src (read through L2 only: it was written
-// by other CTAs) into natural order in s: axes 2 and 3.  Ends with a barrier.
+// by other CTAs) into natural order in s: axes 2 and 3.  Ends with a barrier.  With discard, src
+// is the plane's last use: once read, its lines leave L2 without a write-back to HBM.
 template <typename T, int N2, int N3, int NT>
-__device__ __forceinline__ void plane_inverse(const cpx<T> *src, cpx<T> *s, const cpx<T> *tw2, const cpx<T> *tw3) {
+__device__ __forceinline__ void plane_inverse(const cpx<T> *src, cpx<T> *s, const cpx<T> *tw2, const cpx<T> *tw3,
+                                              bool discard) {
   using S = PlaneShape<N2, N3>;
   using F = PlaneStages<T, NT>;
   // axis 2 inverse, stage A straight from the scratch plane (permuted rows p2 = k1 R2c + k2);
@@ -271,6 +283,7 @@ __device__ __forceinline__ void plane_inverse(const cpx<T> *src, cpx<T> *s, cons
     }
   });
   __syncthreads();
+  if (discard) l2_discard<NT>(src, sizeof(cpx<T>) * S::NPTS);
   F::template stage1<N2, N3, 1, S::PP, +1, false>(s, tw2);  // inverse stage B: natural rows
   __syncthreads();
   F::template inv_stageA<N3, N2, S::PP, 1>(s, tw3);
@@ -373,7 +386,7 @@ __global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, ACC>())) plan
     const int pidx = grp.x + q;
     const int4 pk = a.packs[pidx];
     __syncthreads();  // previous pack's epilogue has finished reading s
-    plane_inverse<T, N2, N3, NT>(a.scratch + (long long)(pidx - a.batch0) * a.N + off, s, tw2, tw3);
+    plane_inverse<T, N2, N3, NT>(a.scratch + (long long)(pidx - a.batch0) * a.N + off, s, tw2, tw3, a.hints & 1);
     plane_accumulate<T, N2, N3, NT>(a.phi, a.W, a.N, off, pk, s, use_acc ? acc : nullptr);
   }
   if (use_acc) {
