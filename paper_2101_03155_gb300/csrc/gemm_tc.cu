@@ -164,6 +164,31 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) 
 }
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// 16 consecutive FP32 columns of this thread's TMEM lane (load waits for its data)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+
 // first 1024-byte aligned address of the dynamic shared array, as an offset from it (so that the
 // compiler keeps the shared state space and emits LDS / STS rather than generic accesses)
 __device__ __forceinline__ unsigned char *align1024(unsigned char *dyn) {
@@ -724,36 +749,48 @@ __global__ void __launch_bounds__(NT2, 1) tc_left_mul_tma_kernel(const float *__
 
 // ----------------------------------------------------------------------------------------
 // Gram fed by TMA: partial[s][i][j] = sum over the chunks of split s of sum_r X[i][r] Y[j][r] for
-// one 128 x 128 tile.
-//   - X and Y boxes of 128 rows x 32 points (16 KB FP32, 128-byte swizzled) arrive by TMA in a
-//     ring of `ring` stages; one item = one 32-point K-step of both operands.
-//   - Each thread splits row `tid` of both boxes into the K-major A and B tiles (two buffers).
-//   - Each chunk of `cs` K-steps accumulates in FP32 in one of two TMEM accumulators (a longer
-//     FP32 accumulation in the tensor core loses accuracy); while the next chunk runs, the
-//     finished one is added to a running sum kept in TMEM with Kahan compensation (sum and
-//     compensation in TMEM columns 256-383 and 384-511).
-//   - At the end the split's sum minus its compensation is written in FP64; a second kernel adds
-//     the splits in FP64 in a fixed order.
-// Every wait is bounded, as in the left multiply.
+// one 128 x 128 tile, as a warp-specialised pipeline (no CTA barrier per K-step):
+//   - warp 20 (TMA): X and Y boxes of 128 rows x 32 points (16 KB FP32, 128-byte swizzled) into a
+//     ring of `ring` stages, each stage refilled once the split warps have read it;
+//   - warps 0-15 (split): warps 0-7 take the rows of the X box, warps 8-15 those of the Y box, two
+//     threads per row (16 K-values each), split them into bf16 hi/lo and store them into the
+//     K-major A or B tiles of one of `nops` operand buffers;
+//   - warp 21 (MMA, one lane): three BF16 products per 16-point K-slice into one of two TMEM
+//     accumulators; each chunk of `cs` K-steps stays in FP32 in one accumulator (a longer FP32
+//     accumulation in the tensor core loses accuracy);
+//   - warps 16-19 (fold, TMEM lane quarter warp & 3): add each finished chunk to a running sum kept
+//     in TMEM with Kahan compensation (sum and compensation in TMEM columns 256-383 and 384-511),
+//     release the accumulator, and at the end write the split's sum minus its compensation in
+//     FP64; a second kernel adds the splits in FP64 in a fixed order.
+// Every wait is bounded; a wait that gives up raises a shared flag that ends every role, the TMA
+// warp waits (bounded) for its boxes in flight and the MMA lane for its last commit before the
+// tensor memory is released.
 // ----------------------------------------------------------------------------------------
 constexpr uint32_t kGBox = BM * BK * 4;  // 128 rows x 32 FP32
+constexpr int GW_SPLIT = 16;                           // split warps: two threads per row
+constexpr int GW_FOLD0 = GW_SPLIT, GW_TMA = GW_SPLIT + 4, GW_MMA = GW_SPLIT + 5;
+constexpr int GW_NT = (GW_SPLIT + 6) * 32;             // + 4 fold warps, the TMA warp, the MMA warp
+constexpr int GW_OPS = 3;                // operand buffers (bf16 hi/lo tiles of both operands)
 
 template <bool ABS>
-__global__ void __launch_bounds__(NT2, 1) tc_gram_tma_kernel(const __grid_constant__ CUtensorMap tmX,
-                                                            const __grid_constant__ CUtensorMap tmY, int nx, int ny,
-                                                            long long c0, long long K, int cs, int tiles_x, int ring,
-                                                            double *__restrict__ partial, int *__restrict__ err,
-                                                            uint32_t first_wait) {
+__global__ void __launch_bounds__(GW_NT, 1) tc_gram_tma_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                              const __grid_constant__ CUtensorMap tmY, int nx, int ny,
+                                                              long long c0, long long K, int cs, int tiles_x,
+                                                              int ring, int nops, double *__restrict__ partial,
+                                                              int *__restrict__ err, uint32_t first_wait) {
   extern __shared__ unsigned char dyn[];
   unsigned char *base = align1024(dyn);
-  unsigned char *ops = base;                  // 2 buffers x {A_hi, A_lo, B_hi, B_lo}
-  unsigned char *boxes = ops + 2 * 4 * TILE_BYTES;  // ring x {X box, Y box}
-  uint64_t *full = reinterpret_cast<uint64_t *>(boxes + (size_t)ring * 2 * kGBox);
-  uint64_t *mmad = full + ring;
-  uint64_t *accf = mmad + 2;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accf + 2);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int quarter = warp & 3, half = warp >> 2;  // TMEM lane quarter; operand / column half
+  unsigned char *ops = base;                                       // nops x {A_hi, A_lo, B_hi, B_lo}
+  unsigned char *boxes = ops + (size_t)nops * 4 * TILE_BYTES;     // ring x {X box, Y box}
+  uint64_t *box_full = reinterpret_cast<uint64_t *>(boxes + (size_t)ring * 2 * kGBox);
+  uint64_t *box_empty = box_full + ring;  // 8 split-warp arrivals
+  uint64_t *op_full = box_empty + ring;   // 8 split-warp arrivals
+  uint64_t *op_empty = op_full + nops;    // MMA commit
+  uint64_t *acc_full = op_empty + nops;   // MMA commit after a chunk's last K-step
+  uint64_t *acc_empty = acc_full + 2;     // 4 fold-warp arrivals
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ti = blockIdx.x % tiles_x, tj = blockIdx.x / tiles_x;
   const int i0 = ti * BM, j0 = tj * BN;
   // X and Y are the same matrix (the screen) and this tile is on the diagonal: one box per K-step
@@ -764,169 +801,196 @@ __global__ void __launch_bounds__(NT2, 1) tc_gram_tma_kernel(const __grid_consta
   const long long c_lo = (long long)blockIdx.y * C / gridDim.y, c_hi = (long long)(blockIdx.y + 1) * C / gridDim.y;
   const long long ks_lo = c_lo * cs, ks_hi = min(KS, c_hi * (long long)cs);
   const int Q = (int)(ks_hi > ks_lo ? ks_hi - ks_lo : 0);
+  const int NCH = (Q + cs - 1) / cs;
 
   if (warp == 0) tmem_alloc(tmem_slot, 512);
   if (tid == 0) {
-    for (int r = 0; r < ring; ++r) mbar_init(smem_u32(&full[r]));
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(smem_u32(&mmad[b]));
-      mbar_init(smem_u32(&accf[b]));
+    for (int r = 0; r < ring; ++r) {
+      mbar_init(smem_u32(&box_full[r]));
+      mbar_init_n(smem_u32(&box_empty[r]), GW_SPLIT);
     }
+    for (int b = 0; b < nops; ++b) {
+      mbar_init_n(smem_u32(&op_full[b]), GW_SPLIT);
+      mbar_init(smem_u32(&op_empty[b]));
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&acc_full[a]));
+      mbar_init_n(smem_u32(&acc_empty[a]), 4);
+    }
+    *abort_flag = 0;
     mbar_init_fence();
   }
-  __syncthreads();
-  int p_stage = 0;
-  long long p_ks = ks_lo;
-  auto issue_next = [&]() {  // thread 0: K-step p_ks into stage p_stage
-    const uint32_t mb = smem_u32(&full[p_stage]);
-    unsigned char *bx = boxes + (size_t)p_stage * 2 * kGBox;
-    mbar_expect_tx(mb, diag ? kGBox : 2 * kGBox);
-    tma_load_2d(smem_u32(bx), &tmX, (int)(c0 + p_ks * BK), i0, mb);
-    if (!diag) tma_load_2d(smem_u32(bx + kGBox), &tmY, (int)(c0 + p_ks * BK), j0, mb);
-    if (++p_stage == ring) p_stage = 0;
-    ++p_ks;
-  };
-  int issued = Q < ring ? Q : ring;
-  if (tid == 0)
-    for (int k = 0; k < issued; ++k) issue_next();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
-  {  // running sum and compensation start at zero (each warp group its column half)
-    float z[32];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) z[c] = 0.f;
-#pragma unroll 1
-    for (int cb = 2 * half; cb < 2 * half + 2; ++cb) {
-      tmem_st32(tmem + lane_off + 256 + 32 * cb, z);
-      tmem_st32(tmem + lane_off + 384 + 32 * cb, z);
+  // bounded wait for use `use` of a barrier (parity use & 1) that also leaves when another role has
+  // given up; false = leave
+  auto wait = [&](uint64_t *bar, int use, uint32_t limit) -> bool {
+    const uint32_t mb = smem_u32(bar), parity = (uint32_t)(use & 1);
+    for (uint32_t it = 0; it < limit; it += 64) {
+      if (mbar_wait(mb, parity, 64)) return true;
+      if (*abort_flag) return false;
     }
-    tmem_st_wait();
-  }
-  Pipe pipe;
-  pipe.init();
-  bool ok = true;
-  // Kahan add of the finished chunk held in accumulator c & 1
-  auto fold = [&](int c) -> bool {
-    const int a = c & 1;
-    const bool w = mbar_wait(smem_u32(&accf[a]), (uint32_t)((c >> 1) & 1));
-    if (__syncthreads_or(!w)) return false;
-    tc_fence_after();
-#pragma unroll 1
-    for (int cb = 2 * half; cb < 2 * half + 2; ++cb) {
-      float x[32], sm[32], cp[32];
-      tmem_ld32(tmem + lane_off + (uint32_t)a * BN + 32 * cb, x);
-      tmem_ld32(tmem + lane_off + 256 + 32 * cb, sm);
-      tmem_ld32(tmem + lane_off + 384 + 32 * cb, cp);
-#pragma unroll
-      for (int e = 0; e < 32; ++e) {
-        const float y = x[e] - cp[e];
-        const float t = sm[e] + y;
-        cp[e] = (t - sm[e]) - y;
-        sm[e] = t;
-      }
-      tmem_st32(tmem + lane_off + 256 + 32 * cb, sm);
-      tmem_st32(tmem + lane_off + 384 + 32 * cb, cp);
-    }
-    tmem_st_wait();
-    tc_fence_before();
-    __syncthreads();  // accumulator a is folded before chunk c + 2 overwrites it
-    return true;
+    *abort_flag = 1;
+    atomicExch(err, 1);
+    return false;
   };
-  int q = 0, stage = 0, kin = 0, cl = 0;
-  uint32_t fpar = 0;
-  for (; q < Q; ++q) {
-    const int b = q & 1;
-    // the first wait may be given fewer polls (a test of the give-up path); the drain waits below
-    // keep the full limit, so no copy is left in flight at exit
-    const bool got = mbar_wait(smem_u32(&full[stage]), fpar, q == 0 ? first_wait : kWaitLimit);
-    const bool freed = pipe.drain(mmad, b);
-    if (__syncthreads_or(!(got && freed))) {
-      ok = false;
-      break;
-    }
-    {
-      // warps 0-3 split X, warps 4-7 split Y: row `row` of the box, whose 16-byte chunk k4 sits
-      // at position k4 ^ (row & 7) (128-byte swizzle)
-      const int row = tid & 127;
-      const unsigned char *rowp = boxes + (size_t)stage * 2 * kGBox + (size_t)(diag ? 0 : half) * kGBox + row * 128;
-      unsigned char *ob = ops + (size_t)b * 4 * TILE_BYTES + (size_t)half * 2 * TILE_BYTES;
-      Row32 r;
-#pragma unroll
-      for (int k4 = 0; k4 < 8; ++k4) {
-        const float4 t = *reinterpret_cast<const float4 *>(rowp + ((k4 ^ (row & 7)) << 4));
-        r.v[4 * k4] = ABS ? fabsf(t.x) : t.x;
-        r.v[4 * k4 + 1] = ABS ? fabsf(t.y) : t.y;
-        r.v[4 * k4 + 2] = ABS ? fabsf(t.z) : t.z;
-        r.v[4 * k4 + 3] = ABS ? fabsf(t.w) : t.w;
+
+  if (warp == GW_TMA) {
+    // ---- TMA: K-step q into stage q % ring once step q - ring has been read ----
+    if (lane == 0) {
+      int issued = 0;
+      for (int q = 0; q < Q; ++q) {
+        const int stage = q % ring;
+        if (q >= ring && !wait(&box_empty[stage], q / ring - 1, kWaitLimit)) break;
+        const uint32_t mb = smem_u32(&box_full[stage]);
+        unsigned char *bx = boxes + (size_t)stage * 2 * kGBox;
+        const int x = (int)(c0 + (ks_lo + q) * BK);
+        mbar_expect_tx(mb, diag ? kGBox : 2 * kGBox);
+        tma_load_2d(smem_u32(bx), &tmX, x, i0, mb);
+        if (!diag) tma_load_2d(smem_u32(bx + kGBox), &tmY, x, j0, mb);
+        issued = q + 1;
       }
-      store_row(r, row, ob, ob + TILE_BYTES);
+      // no box may still be landing when the CTA ends: wait (bounded) for the last ones
+      for (int q = issued > ring ? issued - ring : 0; q < issued; ++q)
+        mbar_wait(smem_u32(&box_full[q % ring]), (uint32_t)((q / ring) & 1));
     }
-    fence_async_smem();
-    __syncthreads();
-    const bool last_in_chunk = (kin == cs - 1) || (q == Q - 1);
-    if (tid == 0) {
-      if (issued < Q) {
-        issue_next();
-        ++issued;
+  } else if (warp == GW_MMA) {
+    // ---- MMA lane: three products per K-slice; a chunk per accumulator ----
+    if (lane == 0) {
+      int last = -1;  // last K-step whose MMAs were committed
+      for (int q = 0; q < Q; ++q) {
+        const int b = q % nops, kin = q % cs, cl = q / cs, a = cl & 1;
+        if (kin == 0 && cl >= 2 && !wait(&acc_empty[a], (cl >> 1) - 1, kWaitLimit)) break;
+        if (!wait(&op_full[b], q / nops, kWaitLimit)) break;
+        tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)a * BN;
+        const uint32_t a_hi = smem_u32(ops + (size_t)b * 4 * TILE_BYTES), a_lo = a_hi + TILE_BYTES;
+        const uint32_t b_hi = a_hi + 2 * TILE_BYTES, b_lo = a_hi + 3 * TILE_BYTES;
+#pragma unroll
+        for (int ks = 0; ks < BK / 16; ++ks) {
+          const uint32_t o = ks * 2 * LBO;
+          mma(acc, sdesc(a_hi + o), sdesc(b_hi + o), (kin > 0 || ks > 0) ? 1u : 0u);
+          mma(acc, sdesc(a_hi + o), sdesc(b_lo + o), 1u);
+          mma(acc, sdesc(a_lo + o), sdesc(b_hi + o), 1u);
+        }
+        commit(smem_u32(&op_empty[b]));
+        if (kin == cs - 1 || q == Q - 1) commit(smem_u32(&acc_full[a]));
+        last = q;
+      }
+      // the tensor memory is released at the end: wait (bounded) for the last MMAs
+      if (last >= 0) mbar_wait(smem_u32(&op_empty[last % nops]), (uint32_t)((last / nops) & 1));
+    }
+  } else if (warp >= GW_FOLD0) {
+    // ---- fold warps: TMEM lanes 32 (warp & 3) .. + 31, all 128 columns, 16 at a time ----
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    {
+      float z[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) z[c] = 0.f;
+#pragma unroll 1
+      for (int cb = 0; cb < 8; ++cb) {
+        tmem_st16(tmem + lane_off + 256 + 16 * cb, z);
+        tmem_st16(tmem + lane_off + 384 + 16 * cb, z);
+      }
+      tmem_st_wait();
+    }
+    bool ok = true;
+    for (int c = 0; c < NCH; ++c) {
+      const int a = c & 1;
+      // every lane polls; the lanes may leave the poll loop apart, and the TMEM loads and stores
+      // below are warp-collective (.sync.aligned): reconverge first
+      const bool got = wait(&acc_full[a], c >> 1, kWaitLimit);
+      if (!__all_sync(0xffffffffu, got)) {
+        ok = false;
+        break;
       }
       tc_fence_after();
-      const uint32_t acc = tmem + (uint32_t)(cl & 1) * BN;
-      const uint32_t a_hi = smem_u32(ops + (size_t)b * 4 * TILE_BYTES), a_lo = a_hi + TILE_BYTES;
-      const uint32_t b_hi = a_hi + 2 * TILE_BYTES, b_lo = a_hi + 3 * TILE_BYTES;
-#pragma unroll
-      for (int ks = 0; ks < BK / 16; ++ks) {
-        const uint32_t o = ks * 2 * LBO;
-        mma(acc, sdesc(a_hi + o), sdesc(b_hi + o), (kin > 0 || ks > 0) ? 1u : 0u);
-        mma(acc, sdesc(a_hi + o), sdesc(b_lo + o), 1u);
-        mma(acc, sdesc(a_lo + o), sdesc(b_hi + o), 1u);
-      }
-      commit(smem_u32(&mmad[b]));
-      if (last_in_chunk) commit(smem_u32(&accf[cl & 1]));
-    } else if (issued < Q) {
-      ++issued;
-    }
-    pipe.pending[b] = 1;
-    if (++stage == ring) {
-      stage = 0;
-      fpar ^= 1u;
-    }
-    if (kin == 0 && cl > 0 && !fold(cl - 1)) {
-      ok = false;
-      ++q;
-      break;
-    }
-    if (last_in_chunk) {
-      kin = 0;
-      ++cl;
-    } else {
-      ++kin;
-    }
-  }
-  if (ok && Q > 0) ok = fold(cl - 1);
-  if (ok) {
-    tc_fence_after();
-    const int i = i0 + 32 * quarter + (tid & 31);
-    double *dst = partial + ((long long)blockIdx.y * nx + i) * ny;
 #pragma unroll 1
-    for (int cb = 2 * half; cb < 2 * half + 2; ++cb) {
-      float sm[32], cp[32];
-      tmem_ld32(tmem + lane_off + 256 + 32 * cb, sm);
-      tmem_ld32(tmem + lane_off + 384 + 32 * cb, cp);
-      const int jb = j0 + 32 * cb;
-      if (i < nx) {
+      for (int cb = 0; cb < 8; ++cb) {
+        float x[16], sm[16], cp[16];
+        tmem_ld16(tmem + lane_off + (uint32_t)a * BN + 16 * cb, x);
+        tmem_ld16(tmem + lane_off + 256 + 16 * cb, sm);
+        tmem_ld16(tmem + lane_off + 384 + 16 * cb, cp);
 #pragma unroll
-        for (int e = 0; e < 32; ++e)
-          if (jb + e < ny) dst[jb + e] = (double)sm[e] - (double)cp[e];
+        for (int e = 0; e < 16; ++e) {
+          const float y = x[e] - cp[e];
+          const float t = sm[e] + y;
+          cp[e] = (t - sm[e]) - y;
+          sm[e] = t;
+        }
+        tmem_st16(tmem + lane_off + 256 + 16 * cb, sm);
+        tmem_st16(tmem + lane_off + 384 + 16 * cb, cp);
+      }
+      tmem_st_wait();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acc_empty[a]));
+    }
+    if (ok && !*abort_flag) {
+      const int i = i0 + 32 * (warp & 3) + lane;
+      double *dst = partial + ((long long)blockIdx.y * nx + i) * ny;
+#pragma unroll 1
+      for (int cb = 0; cb < 8; ++cb) {
+        float sm[16], cp[16];
+        tmem_ld16(tmem + lane_off + 256 + 16 * cb, sm);
+        tmem_ld16(tmem + lane_off + 384 + 16 * cb, cp);
+        const int jb = j0 + 16 * cb;
+        if (i < nx) {
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            if (jb + e < ny) dst[jb + e] = (double)sm[e] - (double)cp[e];
+        }
       }
     }
   } else {
-    for (int r = q; r < issued; ++r) mbar_wait(smem_u32(&full[r % ring]), (uint32_t)((r / ring) & 1));
-    pipe.drain(mmad, 0);
-    pipe.drain(mmad, 1);
-    if (tid == 0) atomicExch(err, 1);
+    // ---- split warps: warps 0-7 take X rows into the A tiles, warps 8-15 Y rows into the B
+    // tiles; a thread takes the K-values [16 h, 16 h + 16) of row `row` (h = bit 7 of its index);
+    // row `row` of a box holds its 16-byte chunk k4 at position k4 ^ (row & 7) ----
+    const int row = tid & 127, h = (tid >> 7) & 1, half = tid >> 8;
+    for (int q = 0; q < Q; ++q) {
+      const int stage = q % ring, b = q % nops;
+      // the first wait may be given fewer polls (a test of the give-up path)
+      if (!__all_sync(0xffffffffu, wait(&box_full[stage], q / ring, q == 0 ? first_wait : kWaitLimit))) break;
+      float v[16];
+      const unsigned char *rowp = boxes + (size_t)stage * 2 * kGBox + (size_t)(diag ? 0 : half) * kGBox + row * 128;
+#pragma unroll
+      for (int c4 = 0; c4 < 4; ++c4) {
+        const int k4 = 4 * h + c4;
+        const float4 t = *reinterpret_cast<const float4 *>(rowp + ((k4 ^ (row & 7)) << 4));
+        v[4 * c4] = ABS ? fabsf(t.x) : t.x;
+        v[4 * c4 + 1] = ABS ? fabsf(t.y) : t.y;
+        v[4 * c4 + 2] = ABS ? fabsf(t.z) : t.z;
+        v[4 * c4 + 3] = ABS ? fabsf(t.w) : t.w;
+      }
+      // the bf16 hi/lo words first, then the wait for the operand buffer (its MMAs from nops
+      // K-steps ago), then the stores
+      uint4 hi[2], lo[2];
+#pragma unroll
+      for (int c8 = 0; c8 < 2; ++c8) {
+        float x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = v[8 * c8 + e];
+        split8(x, hi[c8], lo[c8]);
+      }
+      if (q >= nops && !__all_sync(0xffffffffu, wait(&op_empty[b], q / nops - 1, kWaitLimit))) break;
+      unsigned char *ob = ops + (size_t)b * 4 * TILE_BYTES + (size_t)half * 2 * TILE_BYTES;
+#pragma unroll
+      for (int c8 = 0; c8 < 2; ++c8) {
+        const uint32_t off = tile_off(row, 16 * h + 8 * c8);
+        *reinterpret_cast<uint4 *>(ob + off) = hi[c8];
+        *reinterpret_cast<uint4 *>(ob + TILE_BYTES + off) = lo[c8];
+      }
+      fence_async_smem();  // the tiles are read by the tensor cores (async proxy)
+      __syncwarp();
+      // the box is released only now that every lane has used the values it loaded from it (a
+      // release right after the loads let the next copy land in the box while reads were pending)
+      if (lane == 0) {
+        mbar_arrive(smem_u32(&box_empty[stage]));
+        mbar_arrive(smem_u32(&op_full[b]));
+      }
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -1408,7 +1472,7 @@ static size_t gram_chunks_workspace_bytes(int nx, int ny, long long K) {
 // TMA Gram plan: splits of the K range (whole chunks) and ring depth; false when TMA cannot be
 // used for these operands (disabled, encoder missing, misaligned base, K not a multiple of 32).
 struct GramPlan {
-  int splits, ring, tiles_x, tiles;
+  int splits, ring, nops, tiles_x, tiles;
 };
 static bool gram_tma_plan(const float *X, int nx, const float *Y, int ny, long long K, GramPlan *p) {
   if (!use_tma() || !tensor_map_encoder() || (reinterpret_cast<uintptr_t>(X) & 15) ||
@@ -1422,8 +1486,11 @@ static bool gram_tma_plan(const float *X, int nx, const float *Y, int ny, long l
   const int cs = tc_chunk() / tc::BK;
   const long long chunks = (K / tc::BK + cs - 1) / cs;
   p->splits = (int)std::max(1LL, std::min(chunks, (long long)std::max(1, sms / p->tiles)));
-  const size_t fixed = 8 * (size_t)tc::TILE_BYTES + 1024 + 256;
-  p->ring = (int)std::min<size_t>(6, (227 * 1024 - fixed) / (2 * tc::kGBox));
+  // three operand buffers, the rest of shared memory for box stages (4); measured at 96^3, the
+  // split of 2-4 buffers and 2-5 stages changes nothing
+  p->nops = tc::GW_OPS;
+  const size_t fixed = (size_t)p->nops * 4 * tc::TILE_BYTES + 1024 + 256;
+  p->ring = (int)std::min<size_t>(4, (227 * 1024 - fixed) / (2 * tc::kGBox));
   return p->ring >= 2;
 }
 
@@ -1444,7 +1511,7 @@ static bool launch_gram_tma(const float *X, int nx, const float *Y, int ny, long
   if (c0 % 4 != 0 || !gram_tma_plan(X, nx, Y, ny, K, &p) || !make_map_f32(&mx, X, nx, ld, tc::BM, tc::BK, true) ||
       !make_map_f32(&my, Y, ny, ld, tc::BN, tc::BK, true))
     return false;
-  const int smem = (int)(8 * (size_t)tc::TILE_BYTES + (size_t)p.ring * 2 * tc::kGBox + 1024 + 256);
+  const int smem = (int)((size_t)p.nops * 4 * tc::TILE_BYTES + (size_t)p.ring * 2 * tc::kGBox + 1024 + 256);
   *e = cudaFuncSetAttribute(tc::tc_gram_tma_kernel<ABS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (*e != cudaSuccess) return true;
   double *partial = static_cast<double *>(ws);
@@ -1452,8 +1519,8 @@ static bool launch_gram_tma(const float *X, int nx, const float *Y, int ny, long
   // the kernel give up at once and report ACE_ERR_TIMEOUT after draining its copies)
   const char *fw = std::getenv("ACE_TC_FIRST_WAIT_POLLS");
   const uint32_t first_wait = (fw && *fw) ? (uint32_t)std::strtoul(fw, nullptr, 10) : tc::kWaitLimit;
-  tc::tc_gram_tma_kernel<ABS><<<dim3(p.tiles, p.splits), tc::NT2, smem, st>>>(
-      mx, my, nx, ny, c0, K, tc_chunk() / tc::BK, p.tiles_x, p.ring, partial, err, first_wait);
+  tc::tc_gram_tma_kernel<ABS><<<dim3(p.tiles, p.splits), tc::GW_NT, smem, st>>>(
+      mx, my, nx, ny, c0, K, tc_chunk() / tc::BK, p.tiles_x, p.ring, p.nops, partial, err, first_wait);
   *e = cudaGetLastError();
   if (*e != cudaSuccess) return true;
   const int n = nx * ny;
