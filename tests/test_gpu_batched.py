@@ -1,5 +1,6 @@
-"""ace_build_batched: uneven builds (orbital counts, grids, screening, precision) on concurrent
-stream lanes, each checked against the FP64 oracle and against its single-build result."""
+"""ace_build_batched: uneven builds (orbital counts, grids, screening, precision) on one stream lane
+(the default) and on four concurrent lanes, each checked against the FP64 oracle and against its
+single-build result."""
 
 import numpy as np
 import pytest
@@ -38,9 +39,12 @@ def _inputs():
     return cases
 
 
+@pytest.mark.parametrize("lanes", ["1", "4"])
 @pytest.mark.parametrize("prec", [ace.ACE_FP64, ace.ACE_MIXED])
-def test_batched_uneven_builds(prec):
+def test_batched_uneven_builds(prec, lanes, monkeypatch):
     import torch
+
+    monkeypatch.setenv("ACE_BATCH_LANES", lanes)
 
     cases = _inputs()
     dt = torch.float64 if prec == ace.ACE_FP64 else torch.float32
