@@ -275,11 +275,17 @@ def run_multi(args):
     coulomb = ace.ACE_COULOMB_TRUNCATED if args.workload.endswith("_iso") else ace.ACE_COULOMB_PERIODIC
     stream = torch.cuda.current_stream()
     res = {}
+    tuned = {}
     for prec, dt, steps in ((ace.ACE_MIXED, torch.float32, args.steps), (ace.ACE_FP64, torch.float64,
                                                                          max(1, args.fp64_steps))):
         descs = [ace.make_desc(w.grid, w.lattice, w.norb, rho_cut=w.rho_cut, spin_factor=w.spin_factor, prec=prec,
                                coulomb=coulomb) for w in ws]
         phis = [torch.from_numpy(w.phi).to(device="cuda", dtype=dt) for w in ws]
+        if prec == ace.ACE_MIXED and not args.no_autotune:
+            # the chain settings of each grid from the autotuner, on the largest build of that grid
+            for g in sorted({tuple(w.grid) for w in ws}):
+                b = max((i for i, w in enumerate(ws) if tuple(w.grid) == g), key=lambda i: ws[i].norb)
+                tuned[g] = ace.ace.ace_autotune(descs[b], phis[b], stream)
         for _ in range(args.warmup if prec == ace.ACE_MIXED else 1):
             for op in ace.ace_build_batched(descs, phis, stream):
                 op.close()
@@ -337,6 +343,7 @@ def run_multi(args):
                    "norb": [w.norb for w in ws], "grid": [list(w.grid) for w in ws],
                    "pairs_per_step": mixed["rec"]["pairs"] // args.steps, "precision": "mixed",
                    "coulomb": "truncated (isolated cell)" if coulomb else "periodic",
+                   "autotuned": {"x".join(map(str, g)): p for g, p in tuned.items()} or None,
                    "l2": "inputs larger than L2"},
         "accuracy": accuracy,
         "fp64_form": {"value": f64["builds_per_s"], "unit": UNIT, "ms_per_step": f64["ms_per_step"],
