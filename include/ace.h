@@ -291,16 +291,18 @@ ace_status ace_kernel_launches(const ace_op *op, long *launches);
 /* Autotuner of the pair chain; the paper has no counterpart (it is a property of this GPU code).
  * Screens `phi` as ace_build does, then times the pair chain on a sample of up to 480 of its packs
  * for each candidate setting of the stream-batched chain: packs per batch {1,2,3,4,6}, side streams
- * {2,4,8}, L2 set-aside for the scratch {0, 60 MB}, rows per block of the pack order {1,2,4,8}; and
- * the persistent chain (one launch walking the pack list through a device task queue) with queue
- * lags {2,3,4} where its grid is compiled.  The fastest setting is kept for this grid and precision
- * and used by later builds in the process; with the environment variable ACE_TUNE_FILE set, the
- * table is also read from and written to that file (one line per grid: n1 n2 n3 fp64 group batch
- * streams l2_mb row_block persistent lag).  params (optional, 6 ints) receives {group, batch,
- * streams, l2_mb, row_block, persistent lag or 0}.  Environment variables ACE_PLANE_BATCH,
- * ACE_STREAMS, ACE_L2_PERSIST_MB, ACE_GROUP, ACE_ROW_BLOCK, ACE_PERSISTENT, ACE_PERSIST_LAG
- * override the table.  Grids without a plane-pass plan keep the defaults.  Synchronous.  Errors as
- * ace_build. */
+ * {2,4,8}, L2 set-aside for the scratch {0, 60 MB}, rows per block of the pack order {1,2,4,8};
+ * then, on the best of those, the pencil tile of the axis-1 pass (FP32: 32 columns with the default
+ * or the other thread count, or 16 columns); and the persistent chain (one launch walking the pack
+ * list through a device task queue) with queue lags {2,3,4} where its grid is compiled.  The
+ * fastest setting is kept for this grid and precision and used by later builds in the process;
+ * with the environment variable ACE_TUNE_FILE set, the table is also read from and written to that
+ * file (one line per grid: n1 n2 n3 fp64 group batch streams l2_mb row_block persistent lag
+ * pencil_tile; lines without the last field read as pencil tile 0).  params (optional, 7 ints)
+ * receives {group, batch, streams, l2_mb, row_block, persistent lag or 0, pencil tile}.
+ * Environment variables ACE_PLANE_BATCH, ACE_STREAMS, ACE_L2_PERSIST_MB, ACE_GROUP, ACE_ROW_BLOCK,
+ * ACE_PERSISTENT, ACE_PERSIST_LAG, ACE_CONV_TILE override the table.  Grids without a plane-pass
+ * plan keep the defaults.  Synchronous.  Errors as ace_build. */
 ace_status ace_autotune(const ace_desc *desc, const void *phi, ace_dtype dtype, void *cuda_stream,
                         int *params);
 

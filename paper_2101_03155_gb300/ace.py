@@ -430,14 +430,15 @@ def ace_stage_times(op: AceOp):
 
 
 def ace_autotune(desc: AceDesc, phi, stream=None) -> dict:
-    """ace_autotune: pick the pair-chain batch / stream / L2 / pack-order settings for this grid and precision."""
+    """ace_autotune: pick the pair-chain batch / stream / L2 / pack-order / pencil-tile settings for this
+    grid and precision."""
     ptr, code, numel = _array_info(phi)
     if numel != desc.norb * desc.n[0] * desc.n[1] * desc.n[2]:
         raise ValueError("phi does not match the descriptor")
-    out = (ctypes.c_int * 6)()
+    out = (ctypes.c_int * 7)()
     _check(load().ace_autotune(ctypes.byref(desc), ptr, code, _stream_handle(stream), out))
     return {"group": out[0], "batch": out[1], "streams": out[2], "l2_mb": out[3], "row_block": out[4],
-            "persistent_lag": out[5]}
+            "persistent_lag": out[5], "pencil_tile": out[6]}
 
 
 def ace_kernel_launches(op: AceOp) -> int:

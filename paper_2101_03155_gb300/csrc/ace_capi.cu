@@ -457,6 +457,7 @@ struct ChainParams {
   int RB = 4;          // rows per block of the pack order
   int persistent = 0;  // 1: the persistent chain (one launch, device task queue)
   int lag = 3;         // its queue lag (rounds between the stages of one pack)
+  int conv = 0;        // pencil tile of the axis-1 pass (PairPassArgs::conv_tile)
 };
 
 struct TuneKey {
@@ -476,11 +477,17 @@ void tune_file_load_locked() {
   if (!path || !*path) return;
   FILE *f = std::fopen(path, "r");
   if (!f) return;
-  TuneKey k;
-  ChainParams c;
-  while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d", &k.n1, &k.n2, &k.n3, &k.fp64, &c.G, &c.B, &c.streams,
-                     &c.persist_mb, &c.RB, &c.persistent, &c.lag) == 11)
+  // one line per grid; the twelfth field (pencil tile) may be absent (files of eleven fields)
+  char line[256];
+  while (std::fgets(line, sizeof line, f)) {
+    TuneKey k;
+    ChainParams c;
+    const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d", &k.n1, &k.n2, &k.n3, &k.fp64, &c.G, &c.B,
+                                &c.streams, &c.persist_mb, &c.RB, &c.persistent, &c.lag, &c.conv);
+    if (got < 11) continue;
+    if (got == 11) c.conv = 0;
     g_tuned.emplace_back(k, c);
+  }
   std::fclose(f);
 }
 
@@ -499,9 +506,9 @@ void tune_store(const TuneKey &k, const ChainParams &c) {
     FILE *f = std::fopen(path, "w");
     if (f) {
       for (const auto &e : g_tuned)
-        std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d\n", e.first.n1, e.first.n2, e.first.n3, e.first.fp64,
+        std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d\n", e.first.n1, e.first.n2, e.first.n3, e.first.fp64,
                      e.second.G, e.second.B, e.second.streams, e.second.persist_mb, e.second.RB, e.second.persistent,
-                     e.second.lag);
+                     e.second.lag, e.second.conv);
       std::fclose(f);
     }
   }
@@ -523,6 +530,8 @@ ChainParams chain_params(const ace_desc &d, bool fp64) {
   c.RB = std::max(1, env_int("ACE_ROW_BLOCK", c.RB));
   c.persistent = env_int("ACE_PERSISTENT", c.persistent) != 0;
   c.lag = std::max(1, env_int("ACE_PERSIST_LAG", c.lag));
+  c.conv = std::min(2, std::max(0, env_int("ACE_CONV_TILE", c.conv)));
+  if (fp64) c.conv = 0;
   return c;
 }
 
@@ -546,7 +555,7 @@ ace_status run_chain_pencil(ace_op *op, const T *phi, const T *Kd, const cpx<T> 
   void *tmp = nullptr;
   ACE_CUDA(cudaMallocAsync(&tmp, sizeof(cpx<T>) * (size_t)N * batch, st), "alloc scratch");
   temps.push_back(tmp);
-  ace::PairPassArgs<T> a;
+  ace::PairPassArgs<T> a{};
   a.phi = phi;
   a.W = static_cast<T *>(op->W);
   a.scratch = static_cast<cpx<T> *>(tmp);
@@ -907,6 +916,7 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   ca.n1 = d.n[0];
   ca.n2 = d.n[1];
   ca.n3 = d.n[2];
+  ca.conv_tile = cp.conv;
   for (size_t bi = 0; bi < batches.size(); ++bi) {
     const int2 b = batches[bi];
     if (max_packs >= 0 && groups[b.x].x >= max_packs) break;  // autotuning sample
@@ -2131,6 +2141,30 @@ ace_status ace_autotune(const ace_desc *desc, const void *phi, ace_dtype dtype, 
             best = c;
           }
         }
+    // the pencil tile of the axis-1 pass (three compiled for the FP32 form) on the best settings
+    if (sizeof(T) == 4) {
+      const ChainParams base = best;
+      for (int v : {1, 2}) {
+        ChainParams c = base;
+        c.conv = v;
+        float t[2];
+        for (int rep = 0; rep < 2; ++rep) {
+          std::vector<void *> tmp;
+          ACE_CUDA(cudaEventRecord(e0, op->stream), "event");
+          ace_status r = run_chain_plane<T>(op, phi_w, op->tab, pops, count, tmp, c, sample);
+          ACE_CUDA(cudaEventRecord(e1, op->stream), "event");
+          for (void *q : tmp) cudaFreeAsync(q, op->stream);
+          if (r != ACE_OK) return r;
+          ACE_CUDA(cudaEventSynchronize(e1), "tuning run");
+          cudaEventElapsedTime(&t[rep], e0, e1);
+        }
+        const float ms = std::min(t[0], t[1]);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = c;
+        }
+      }
+    }
     // the persistent chain on the same sample, for a few queue lags
     ace::PersistOps<T> qops{};
     if (find_persist_ops<T>(desc->n[0], desc->n[1], desc->n[2], &qops)) {
@@ -2175,6 +2209,7 @@ ace_status ace_autotune(const ace_desc *desc, const void *phi, ace_dtype dtype, 
     params[3] = best.persist_mb;
     params[4] = best.RB;
     params[5] = best.persistent ? best.lag : 0;
+    params[6] = best.conv;
   }
   return ACE_OK;
 }

@@ -33,6 +33,8 @@ struct PairPassArgs {
   const cpx<T> *tw;         // [L] e^{-2 pi i e / L} for the axis of this pass
   long long N;              // N1 N2 N3
   int n1, n2, n3;
+  int conv_tile;            // axis-1 pencil pass of the plane chain, FP32: 0 (32 columns, default
+                            // threads), 1 (32 columns, the other thread count), 2 (16 columns, 128)
 };
 
 // Arguments of the three-pass (plane, pencil, plane) chain.

@@ -237,24 +237,29 @@ __global__ void __launch_bounds__((PassShape<T, L>::NT)) pair_pass_kernel(PairPa
 // elements straight from the scratch and the last inverse stage writes straight back (lanes
 // over the 32 columns: coalesced); only the two exchanges in between go through shared memory.
 // ---------------------------------------------------------------------------------------
-template <int L>
+template <int L, int V = 0>
 struct ConvShape {
   static constexpr int R1 = Factor<L>::R1, R2 = Factor<L>::R2;
-  static constexpr int TILE = 32;
+  // columns per CTA (lanes over columns): 32, or 16 in variant 2 (a half-warp per row, 128 bytes)
+  static constexpr int TILE = V == 2 ? 16 : 32;
   static constexpr int LP = L + 1;
   // threads: 128 up to 108 points (more CTAs per SM), 256 for the longer pencils (measured on
-  // 96, 128 and 160 points); ACE_CONV_NT overrides
+  // 96, 128 and 160 points); variant 1 takes the other count, variant 2 128; ACE_CONV_NT overrides
+  // the default
 #ifdef ACE_CONV_NT
-  static constexpr int NT = ACE_CONV_NT;
+  static constexpr int NT0 = ACE_CONV_NT;
 #else
-  static constexpr int NT = L > 108 ? 256 : 128;
+  static constexpr int NT0 = L > 108 ? 256 : 128;
 #endif
+  static constexpr int NT = V == 0 ? NT0 : (V == 1 ? (NT0 == 128 ? 256 : 128) : 128);
+  static_assert(NT % TILE == 0, "whole column tiles per pass of the threads");
 };
 
-template <typename T, int L>
-__global__ void __launch_bounds__(ConvShape<L>::NT) conv_pencil_kernel(PairPassArgs<T> a) {
-  using S = ConvShape<L>;
+template <typename T, int L, int V>
+__global__ void __launch_bounds__(ConvShape<L, V>::NT) conv_pencil_kernel(PairPassArgs<T> a) {
+  using S = ConvShape<L, V>;
   constexpr int R1 = S::R1, R2 = S::R2, TILE = S::TILE, LP = S::LP, NT = S::NT;
+  constexpr int ROWS = NT / TILE;  // task rows handled at once
   __shared__ cpx<T> s[TILE * LP];
   __shared__ cpx<T> tw[L];
   const int tid = threadIdx.x;
@@ -264,13 +269,13 @@ __global__ void __launch_bounds__(ConvShape<L>::NT) conv_pencil_kernel(PairPassA
   const int Ns = (int)cols;  // stride between consecutive i1 (fits: N < 2^31)
   cpx<T> *z = a.scratch + (long long)blockIdx.y * a.N + c0;
   const T *kc = a.kernel + c0;
-  const int t = tid & (TILE - 1);
+  const int t = tid % TILE, row = tid / TILE;
   const bool valid = c0 + t < cols;
   __syncthreads();
-  // stage 1 (forward): tasks (t, n2), n2 = warp + 4 q
+  // stage 1 (forward): tasks (t, n2), n2 = row + ROWS q
 #pragma unroll
   for (int q = 0; q < (TILE * R2 + NT - 1) / NT; ++q) {
-    const int n2 = (tid >> 5) + (NT / TILE) * q;
+    const int n2 = row + ROWS * q;
     if (n2 < R2 && valid) {
       cpx<T> x[R1];
 #pragma unroll
@@ -285,7 +290,7 @@ __global__ void __launch_bounds__(ConvShape<L>::NT) conv_pencil_kernel(PairPassA
   // stage 2 (forward), kernel multiply, inverse stage A: tasks (t, k1)
 #pragma unroll
   for (int q = 0; q < (TILE * R1 + NT - 1) / NT; ++q) {
-    const int k1 = (tid >> 5) + (NT / TILE) * q;
+    const int k1 = row + ROWS * q;
     if (k1 < R1 && valid) {
       cpx<T> *blk = s + t * LP + k1 * R2;
       cpx<T> x[R2];
@@ -303,7 +308,7 @@ __global__ void __launch_bounds__(ConvShape<L>::NT) conv_pencil_kernel(PairPassA
   // inverse stage B: tasks (t, n2); natural order i1 = n1 R2 + n2 straight to the scratch
 #pragma unroll
   for (int q = 0; q < (TILE * R2 + NT - 1) / NT; ++q) {
-    const int n2 = (tid >> 5) + (NT / TILE) * q;
+    const int n2 = row + ROWS * q;
     if (n2 < R2 && valid) {
       const cpx<T> *line = s + t * LP + n2;
       cpx<T> x[R1];
@@ -316,13 +321,23 @@ __global__ void __launch_bounds__(ConvShape<L>::NT) conv_pencil_kernel(PairPassA
   }
 }
 
-template <typename T, int L>
-cudaError_t launch_conv_L(const PairPassArgs<T> &a, int npacks, cudaStream_t st) {
-  using S = ConvShape<L>;
+template <typename T, int L, int V>
+cudaError_t launch_conv_LV(const PairPassArgs<T> &a, int npacks, cudaStream_t st) {
+  using S = ConvShape<L, V>;
   const long long cols = (long long)a.n2 * a.n3;
   dim3 grid((unsigned)((cols + S::TILE - 1) / S::TILE), npacks);
-  conv_pencil_kernel<T, L><<<grid, S::NT, 0, st>>>(a);
+  conv_pencil_kernel<T, L, V><<<grid, S::NT, 0, st>>>(a);
   return cudaGetLastError();
+}
+
+// The axis-1 pass in the pencil tile a.conv_tile selects (FP32; the FP64 form keeps the default).
+template <typename T, int L>
+cudaError_t launch_conv_L(const PairPassArgs<T> &a, int npacks, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (a.conv_tile == 1) return launch_conv_LV<T, L, 1>(a, npacks, st);
+    if (a.conv_tile == 2) return launch_conv_LV<T, L, 2>(a, npacks, st);
+  }
+  return launch_conv_LV<T, L, 0>(a, npacks, st);
 }
 
 template <typename T, int L>

@@ -196,8 +196,9 @@ __global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, false>()))
         pencil_convolve<T, N1, G, NT>(slot, bd.Kperm, S::NPTS, idx * G, s, tw1);
       } else {
         const long long off = (long long)idx * S::NPTS;
-        plane_inverse<T, N2, N3, NT>(slot + off, s, tw2, tw3, a.hints & 1);
+        plane_inverse<T, N2, N3, NT>(slot + off, s, tw2, tw3);
         plane_accumulate<T, N2, N3, NT>(bd.phi, bd.W, a.N, off, pk, s, nullptr);
+        if (a.hints & 1) l2_discard<NT>(slot + off, sizeof(cpx<T>) * S::NPTS);  // the plane's last use
       }
       __syncthreads();
       if (tid == 0) {

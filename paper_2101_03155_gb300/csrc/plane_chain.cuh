@@ -258,11 +258,10 @@ __device__ __forceinline__ void l2_discard(const void *base, size_t bytes) {
 }
 
 // Inverse transform of one permuted spectrum plane src (read through L2 only: it was written
-// by other CTAs) into natural order in s: axes 2 and 3.  Ends with a barrier.  With discard, src
-// is the plane's last use: once read, its lines leave L2 without a write-back to HBM.
+// by other CTAs) into natural order in s: axes 2 and 3.  Ends with a barrier; src is read only
+// before the first barrier.
 template <typename T, int N2, int N3, int NT>
-__device__ __forceinline__ void plane_inverse(const cpx<T> *src, cpx<T> *s, const cpx<T> *tw2, const cpx<T> *tw3,
-                                              bool discard) {
+__device__ __forceinline__ void plane_inverse(const cpx<T> *src, cpx<T> *s, const cpx<T> *tw2, const cpx<T> *tw3) {
   using S = PlaneShape<N2, N3>;
   using F = PlaneStages<T, NT>;
   // axis 2 inverse, stage A straight from the scratch plane (permuted rows p2 = k1 R2c + k2);
@@ -283,7 +282,6 @@ __device__ __forceinline__ void plane_inverse(const cpx<T> *src, cpx<T> *s, cons
     }
   });
   __syncthreads();
-  if (discard) l2_discard<NT>(src, sizeof(cpx<T>) * S::NPTS);
   F::template stage1<N2, N3, 1, S::PP, +1, false>(s, tw2);  // inverse stage B: natural rows
   __syncthreads();
   F::template inv_stageA<N3, N2, S::PP, 1>(s, tw3);
@@ -386,8 +384,11 @@ __global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, ACC>())) plan
     const int pidx = grp.x + q;
     const int4 pk = a.packs[pidx];
     __syncthreads();  // previous pack's epilogue has finished reading s
-    plane_inverse<T, N2, N3, NT>(a.scratch + (long long)(pidx - a.batch0) * a.N + off, s, tw2, tw3, a.hints & 1);
+    plane_inverse<T, N2, N3, NT>(a.scratch + (long long)(pidx - a.batch0) * a.N + off, s, tw2, tw3);
     plane_accumulate<T, N2, N3, NT>(a.phi, a.W, a.N, off, pk, s, use_acc ? acc : nullptr);
+    // the spectrum plane was this pack's last use of it: its lines leave L2 without a write-back
+    // (here, where few registers are live; every read of it ended at plane_inverse's first barrier)
+    if (a.hints & 1) l2_discard<NT>(a.scratch + (long long)(pidx - a.batch0) * a.N + off, sizeof(cpx<T>) * S::NPTS);
   }
   if (use_acc) {
     __syncthreads();
