@@ -267,6 +267,8 @@ struct ace_op {
   void *readback = nullptr;   // pinned host area for the asynchronous readbacks of a build
   size_t readback_bytes = 0;
   int lane = 0;               // stream lane of a batched build (selects its side streams)
+  float *pmax = nullptr;      // plane maxima of the working orbitals [n][N1] for the plane skip
+  float *gmax = nullptr;      // and the orbitals' maxima [n]
   bool queued = false;        // screened build whose chain ran in a device pack queue
   bool graph = false;         // recorded into a CUDA graph: no host waits, no timing events,
                               // uploads from pinned buffers that live as long as the handle
@@ -307,6 +309,31 @@ cudaError_t host_upload(ace_op *op, void *dst, const void *src, size_t bytes, cu
   std::memcpy(pin, src, bytes);
   op->staged.emplace_back(pin, bytes);
   return cudaMemcpyAsync(dst, pin, bytes, cudaMemcpyHostToDevice, st);
+}
+
+// Default plane-skip fraction of the mixed form (see plane_skip_rel).
+constexpr float kPlaneSkipDefault = 1e-7f;
+
+// Fraction of an orbital's maximum below which its planes count as negligible for the plane skip of
+// the mixed form's chain (ACE_PLANE_SKIP; 0 turns the skip off).  The FP64 form never skips.
+float plane_skip_rel(bool fp64) {
+  if (fp64) return 0.f;
+  const char *v = std::getenv("ACE_PLANE_SKIP");
+  const float r = (v && *v) ? (float)std::atof(v) : kPlaneSkipDefault;
+  return r > 0.f ? r : 0.f;
+}
+
+// The plane-maxima table of the op's working orbitals (computed once per build, on st).
+cudaError_t plane_max_table(ace_op *op, const float *phi, cudaStream_t st) {
+  if (op->pmax) return cudaSuccess;
+  cudaError_t e = op_alloc(op, &op->pmax, sizeof(float) * (size_t)op->n * op->desc.n[0]);
+  if (e == cudaSuccess) e = op_alloc(op, &op->gmax, sizeof(float) * (size_t)op->n);
+  if (e == cudaSuccess) e = cudaMemsetAsync(op->gmax, 0, sizeof(float) * (size_t)op->n, st);
+  if (e == cudaSuccess)
+    e = ace::launch_plane_max(phi, op->n, op->desc.n[0], (long long)op->desc.n[1] * op->desc.n[2], op->pmax, op->gmax,
+                              st);
+  if (e == cudaSuccess) ++op->launches;
+  return e;
 }
 
 // Stage-timing event i of a build (not recorded inside a graph)
@@ -786,6 +813,7 @@ ace_status run_chain_persistent(ace_op *op, cudaStream_t st, const DeviceTables 
   a.wait_ns = (wn && *wn) ? std::strtoull(wn, nullptr, 10) : 2000000000ull;
   a.stall = env_int("ACE_PERSIST_TEST_STALL", 0) ? cnt + 3 * (size_t)np + 1 : nullptr;
   a.hints = env_int("ACE_L2_HINTS", 1);
+  a.skip_rel = plane_skip_rel(sizeof(T) == 8);
   // keep the scratch slots resident in L2 (a per-context set-aside of persisting lines)
   const int persist_mb = cp.persist_mb;
   if (persist_mb > 0) l2_window(st, op->dev, a.scratch, sizeof(cpx<T>) * (size_t)N * nslots, persist_mb);
@@ -868,6 +896,12 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   ACE_CUDA(cudaMallocAsync(&tmp, sizeof(cpx<T>) * (size_t)N * B * nstreams, st), "alloc scratch");
   temps.push_back(tmp);
   cpx<T> *scratch_all = static_cast<cpx<T> *>(tmp);
+  // plane maxima for the plane skip (mixed form), on st before the side streams fork from it
+  float skip_rel = 0.f;
+  if constexpr (sizeof(T) == 4) {
+    skip_rel = plane_skip_rel(false);
+    if (skip_rel > 0.f) ACE_CUDA(plane_max_table(op, phi, st), "plane maxima");
+  }
   // consecutive batches alternate between side streams (own scratch each) so that one batch's
   // kernels fill the tail of the previous one; W is only touched by atomic adds
   cudaStream_t side[kSide];
@@ -905,6 +939,9 @@ ace_status run_chain_plane(ace_op *op, const T *phi, const DeviceTables *tab, co
   pa.N = N;
   pa.n1 = d.n[0];
   pa.hints = env_int("ACE_L2_HINTS", 1);
+  pa.pmax = skip_rel > 0.f ? op->pmax : nullptr;
+  pa.gmax = skip_rel > 0.f ? op->gmax : nullptr;
+  pa.skip_rel = skip_rel;
   ace::PairPassArgs<T> ca;
   ca.phi = phi;
   ca.W = static_cast<T *>(op->W);
@@ -1184,7 +1221,14 @@ ace_status run_chain(ace_op *op, const T *phi, int count) {
   if (count > 0 && persistent) {
     std::vector<int4> packs;
     form_packs(op->pairs_h, cp.RB, packs);
-    const std::vector<ace::ChainBuild<T>> one{{phi, static_cast<T *>(op->W), static_cast<const T *>(tab->Kperm)}};
+    const float *pm = nullptr, *gm = nullptr;
+    if (sizeof(T) == 4 && plane_skip_rel(false) > 0.f) {
+      ACE_CUDA(plane_max_table(op, reinterpret_cast<const float *>(phi), op->stream), "plane maxima");
+      pm = op->pmax;
+      gm = op->gmax;
+    }
+    const std::vector<ace::ChainBuild<T>> one{
+        {phi, static_cast<T *>(op->W), static_cast<const T *>(tab->Kperm), pm, gm}};
     return run_chain_persistent<T>(op, op->stream, tab, qops, packs, {}, {}, 0, one, temps, cp);
   }
   if (count > 0 && plane) return run_chain_plane<T>(op, phi, tab, pops, count, temps, cp);
@@ -1309,8 +1353,14 @@ ace_status run_queue_chain(const std::vector<ace_op *> &group, cudaStream_t st) 
     const size_t bytes = op->esz * (size_t)op->n * op->N;
     ACE_CUDA(op_alloc(op, &op->W, bytes), "alloc W");
     ACE_CUDA(cudaMemsetAsync(op->W, 0, bytes, st), "zero W");
+    const float *pm = nullptr, *gm = nullptr;
+    if (sizeof(T) == 4 && plane_skip_rel(false) > 0.f) {
+      ACE_CUDA(plane_max_table(op, reinterpret_cast<const float *>(op->phi_work), st), "plane maxima");
+      pm = op->pmax;
+      gm = op->gmax;
+    }
     builds.push_back({static_cast<const T *>(op->phi_work), static_cast<T *>(op->W),
-                      static_cast<const T *>(op->tab->Kperm)});
+                      static_cast<const T *>(op->tab->Kperm), pm, gm});
     src.push_back({op->packs, op->count_d});
     flags.push_back(op->tc_err);
     maxnp += ((long long)op->n * (op->n + 1) / 2 + 1) / 2;
@@ -2172,7 +2222,7 @@ ace_status ace_autotune(const ace_desc *desc, const void *phi, ace_dtype dtype, 
       form_packs(op->pairs_h, best.RB, packs);
       packs.resize(std::min<size_t>(packs.size(), (size_t)sample));
       const std::vector<ace::ChainBuild<T>> one{
-          {phi_w, static_cast<T *>(op->W), static_cast<const T *>(op->tab->Kperm)}};
+          {phi_w, static_cast<T *>(op->W), static_cast<const T *>(op->tab->Kperm), op->pmax, op->gmax}};
       for (int lag : {2, 3, 4}) {
         ChainParams c = best;
         c.persistent = 1;

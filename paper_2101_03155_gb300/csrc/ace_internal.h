@@ -53,6 +53,9 @@ struct PlaneArgs {
   long long N;
   int n1;
   int hints;           // bit 0: drop each consumed scratch plane from L2 without writing it back
+  const float *pmax;   // plane maxima [norb][n1] and orbital maxima [norb] for the plane skip
+  const float *gmax;
+  float skip_rel;      // > 0: planes below this fraction of the orbitals' maxima are skipped
 };
 
 // Plane passes for one (N2, N3) plane shape; absent shapes fall back to the five pencil passes.
@@ -73,6 +76,8 @@ struct ChainBuild {
   const T *phi;      // [norb][N]
   T *W;              // [norb][N], accumulated into
   const T *Kperm;    // Coulomb table in the plane passes' permuted layout
+  const float *pmax; // [norb][N1] max |phi| over each plane i1 of each orbital (plane skip), or null
+  const float *gmax; // [norb] max |phi| of each orbital
 };
 template <typename T>
 struct PersistArgs {
@@ -92,6 +97,7 @@ struct PersistArgs {
   unsigned long long wait_ns;   // time limit of one wait for a pack's earlier tasks
   const int *stall;             // null; else the pencil tasks wait for this word to reach 1 (a test)
   int hints;                    // as PlaneArgs::hints
+  float skip_rel;               // as PlaneArgs::skip_rel (plane maxima in each ChainBuild)
 };
 template <typename T>
 struct PersistOps {
@@ -111,6 +117,10 @@ constexpr int kQueueMaxBuilds = 1024;
 // Concatenates the pack lists of nb <= kQueueMaxBuilds builds, in build order, into packs_out,
 // with the build of each pack in pack_build and the total pack count in *np_out (all on the device;
 // the pair counts are read there).
+// Plane maxima of the orbitals for the plane skip: pmax[a][i1] = max |phi_a| over plane i1 (npl
+// points) and gmax[a] = max over all planes (gmax zeroed by the caller); n1 planes, norb orbitals.
+cudaError_t launch_plane_max(const float *phi, int norb, int n1, long long npl, float *pmax, float *gmax,
+                             cudaStream_t st);
 // *dst[i] = 1 for every i < n if *src is non-zero (a give-up flag passed on to several builds).
 cudaError_t launch_flag_fanout(const int *src, int *const *dst, int n, cudaStream_t st);
 cudaError_t launch_queue_assemble(const QueueSrc *src, int nb, int4 *packs_out, int *pack_build, int *np_out,

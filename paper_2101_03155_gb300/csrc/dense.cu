@@ -1023,6 +1023,42 @@ __global__ void __launch_bounds__(QA_NT) queue_assemble_kernel(const QueueSrc *_
   }
 }
 
+// One CTA per (plane i1, orbital a): the plane's max |phi|, and the orbital's max by an atomic max
+// on the bit pattern (non-negative floats order as their bits do).
+constexpr int PM_NT = 256;
+__global__ void __launch_bounds__(PM_NT) plane_max_kernel(const float *__restrict__ phi, int n1, long long npl,
+                                                         float *__restrict__ pmax, float *__restrict__ gmax) {
+  __shared__ float red[PM_NT / 32];
+  const int i1 = blockIdx.x, a = blockIdx.y;
+  const float *p = phi + ((long long)a * n1 + i1) * npl;
+  float m = 0.f;
+  if ((npl & 3) == 0 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    for (long long e = threadIdx.x; e < npl / 4; e += PM_NT) {
+      const float4 v = __ldg(q + e);
+      m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+  } else {
+    for (long long e = threadIdx.x; e < npl; e += PM_NT) m = fmaxf(m, fabsf(__ldg(p + e)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < PM_NT / 32; ++w) m = fmaxf(m, red[w]);
+    pmax[(long long)a * n1 + i1] = m;
+    atomicMax(reinterpret_cast<int *>(gmax + a), __float_as_int(m));
+  }
+}
+
+cudaError_t launch_plane_max(const float *phi, int norb, int n1, long long npl, float *pmax, float *gmax,
+                             cudaStream_t st) {
+  if (norb < 1 || norb > 65535) return cudaErrorInvalidValue;
+  plane_max_kernel<<<dim3(n1, norb), PM_NT, 0, st>>>(phi, n1, npl, pmax, gmax);
+  return cudaGetLastError();
+}
+
 __global__ void flag_fanout_kernel(const int *src, int *const *dst, int n) {
   if (__ldcg(src) == 0) return;
   for (int i = threadIdx.x; i < n; i += blockDim.x) *dst[i] = 1;

@@ -189,15 +189,21 @@ __global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, false>()))
       const ChainBuild<T> bd = a.builds[b];
       const int4 pk = a.packs[p];
       cpx<T> *slot = a.scratch + (long long)(p % a.nslots) * a.N;
+      const bool skip = a.skip_rel > 0.f && bd.pmax;
       if (kind == 0) {
         const long long off = (long long)idx * S::NPTS;
-        plane_forward<T, N2, N3, NT>(bd.phi, a.N, off, pk, s, tw2, tw3, slot + off);
+        if (skip && fwd_plane_negligible(bd.pmax, bd.gmax, N1, idx, pk, a.skip_rel))
+          zero_plane<T, S::NPTS, NT>(slot + off);
+        else
+          plane_forward<T, N2, N3, NT>(bd.phi, a.N, off, pk, s, tw2, tw3, slot + off);
       } else if (kind == 1) {
         pencil_convolve<T, N1, G, NT>(slot, bd.Kperm, S::NPTS, idx * G, s, tw1);
       } else {
         const long long off = (long long)idx * S::NPTS;
-        plane_inverse<T, N2, N3, NT>(slot + off, s, tw2, tw3);
-        plane_accumulate<T, N2, N3, NT>(bd.phi, bd.W, a.N, off, pk, s, nullptr);
+        if (!(skip && inv_plane_negligible(bd.pmax, bd.gmax, N1, idx, pk, a.skip_rel))) {
+          plane_inverse<T, N2, N3, NT>(slot + off, s, tw2, tw3);
+          plane_accumulate<T, N2, N3, NT>(bd.phi, bd.W, a.N, off, pk, s, nullptr);
+        }
         if (a.hints & 1) l2_discard<NT>(slot + off, sizeof(cpx<T>) * S::NPTS);  // the plane's last use
       }
       __syncthreads();

@@ -338,6 +338,33 @@ __device__ __forceinline__ void plane_accumulate(const T *__restrict__ phi, T *W
 }
 
 // ---------------------------------------------------------------------------------------
+// Plane skip (mixed form).  Localized orbitals leave most of the cell with negligible values.
+// On plane i1, the pair density phi_a phi_b is negligible when the product of the two orbitals'
+// plane maxima is at most rel times the product of their overall maxima: its forward transform is
+// then a zero plane.  The pack's W terms on plane i1 are products of the potential with the pack's
+// orbitals, so when every orbital of the pack is at most rel times its maximum there, the inverse
+// plane and its accumulation are skipped.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ bool fwd_plane_negligible(const float *pm, const float *gm, int n1, int i1, int4 pk,
+                                                     float rel) {
+  const bool ab = __ldg(pm + pk.x * n1 + i1) * __ldg(pm + pk.y * n1 + i1) <= rel * __ldg(gm + pk.x) * __ldg(gm + pk.y);
+  if (pk.z < 0) return ab;
+  return ab && __ldg(pm + pk.z * n1 + i1) * __ldg(pm + pk.w * n1 + i1) <= rel * __ldg(gm + pk.z) * __ldg(gm + pk.w);
+}
+__device__ __forceinline__ bool inv_plane_negligible(const float *pm, const float *gm, int n1, int i1, int4 pk,
+                                                     float rel) {
+  bool s = __ldg(pm + pk.x * n1 + i1) <= rel * __ldg(gm + pk.x) && __ldg(pm + pk.y * n1 + i1) <= rel * __ldg(gm + pk.y);
+  if (pk.z >= 0)
+    s = s && __ldg(pm + pk.z * n1 + i1) <= rel * __ldg(gm + pk.z) && __ldg(pm + pk.w * n1 + i1) <= rel * __ldg(gm + pk.w);
+  return s;
+}
+// A zero spectrum plane (the forward transform of a negligible density plane).
+template <typename T, int NPTS, int NT>
+__device__ __forceinline__ void zero_plane(cpx<T> *dst) {
+  for (int e = threadIdx.x; e < NPTS; e += NT) dst[e] = cpx<T>{(T)0, (T)0};
+}
+
+// ---------------------------------------------------------------------------------------
 // Forward plane pass: one CTA per (plane i1, pack).
 // ---------------------------------------------------------------------------------------
 template <typename T, int N2, int N3, int NT>
@@ -354,6 +381,10 @@ __global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, false>())) pl
   for (int e = tid; e < N2; e += NT) tw2[e] = a.tw2[e];
   for (int e = tid; e < N3; e += NT) tw3[e] = a.tw3[e];
   const long long off = (long long)i1 * S::NPTS;
+  if (a.skip_rel > 0.f && fwd_plane_negligible(a.pmax, a.gmax, a.n1, i1, pk, a.skip_rel)) {
+    zero_plane<T, S::NPTS, NT>(a.scratch + (long long)(pidx - a.batch0) * a.N + off);
+    return;
+  }
   plane_forward<T, N2, N3, NT>(a.phi, a.N, off, pk, s, tw2, tw3, a.scratch + (long long)(pidx - a.batch0) * a.N + off);
 }
 
@@ -384,8 +415,10 @@ __global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, ACC>())) plan
     const int pidx = grp.x + q;
     const int4 pk = a.packs[pidx];
     __syncthreads();  // previous pack's epilogue has finished reading s
-    plane_inverse<T, N2, N3, NT>(a.scratch + (long long)(pidx - a.batch0) * a.N + off, s, tw2, tw3);
-    plane_accumulate<T, N2, N3, NT>(a.phi, a.W, a.N, off, pk, s, use_acc ? acc : nullptr);
+    if (!(a.skip_rel > 0.f && inv_plane_negligible(a.pmax, a.gmax, a.n1, i1, pk, a.skip_rel))) {
+      plane_inverse<T, N2, N3, NT>(a.scratch + (long long)(pidx - a.batch0) * a.N + off, s, tw2, tw3);
+      plane_accumulate<T, N2, N3, NT>(a.phi, a.W, a.N, off, pk, s, use_acc ? acc : nullptr);
+    }
     // the spectrum plane was this pack's last use of it: its lines leave L2 without a write-back
     // (here, where few registers are live; every read of it ended at plane_inverse's first barrier)
     if (a.hints & 1) l2_discard<NT>(a.scratch + (long long)(pidx - a.batch0) * a.N + off, sizeof(cpx<T>) * S::NPTS);
