@@ -35,7 +35,7 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_values.json")
 # DRAM bytes (read + write) of the pair chain per build of the water32 workload, from one ncu capture
 # of the current chain kernels with caches not flushed (profiles/pair_chain_plane_water32_96c.md);
 # set to None whenever those kernels change.
-CHAIN_DRAM_BYTES_PER_BUILD = 9.13e9
+CHAIN_DRAM_BYTES_PER_BUILD = 8.17e9
 # DRAM bytes (read + write) per launch of the dense kernels of the same workload: M and xi from one
 # ncu capture with caches not flushed (profiles/dense_tc_water32_96c.md), the CUDA-core screen from
 # its full capture (profiles/screen_syrk_water32_96c.md: 454.2 MB read, 3.6 MB written); None once a
