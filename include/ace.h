@@ -282,7 +282,8 @@ ace_status ace_pair_count(const ace_op *op, long *npairs);
 ace_status ace_get_size(const ace_op *op, int what, size_t *bytes);
 
 /* Per-stage device times of the last build in milliseconds (CUDA events on the build stream):
- * [0] screen, [1] pair chain (W), [2] M, [3] Cholesky/L^-1/E_x, [4] xi, [5] total. */
+ * [0] screen, [1] pair chain (W), [2] M, [3] Cholesky/L^-1/E_x, [4] xi, [5] total.  The handles of
+ * a graph (ace_graph_op) record no timing events and report zeros. */
 ace_status ace_stage_times(const ace_op *op, float ms[6]);
 
 /* Number of this library's CUDA kernels that the build of `op` launched. */

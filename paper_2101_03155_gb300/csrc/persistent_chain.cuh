@@ -117,8 +117,20 @@ __device__ __forceinline__ void pencil_convolve(cpx<T> *z, const T *__restrict__
   });
 }
 
+// Resident CTAs per SM the register budget is set for: the plane kernels' count unless
+// ACE_PERSIST_MINB (a build-time setting) lowers it, which gives the pencil tasks more registers.
+template <typename T, int N2, int N3>
+constexpr int persist_min_blocks() {
+#ifdef ACE_PERSIST_MINB
+  return plane_min_blocks<T, N2, N3, false>() < ACE_PERSIST_MINB ? plane_min_blocks<T, N2, N3, false>()
+                                                                 : ACE_PERSIST_MINB;
+#else
+  return plane_min_blocks<T, N2, N3, false>();
+#endif
+}
+
 template <typename T, int N1, int N2, int N3, int NT>
-__global__ void __launch_bounds__(NT, (plane_min_blocks<T, N2, N3, false>()))
+__global__ void __launch_bounds__(NT, (persist_min_blocks<T, N2, N3>()))
     chain_persistent_kernel(PersistArgs<T> a) {
   using S = PlaneShape<N2, N3>;
   using P = PersistShape<T, N1, N2, N3>;
