@@ -674,8 +674,9 @@ __global__ void __launch_bounds__(CH_NT) cholesky_kernel(const double *__restric
 //     panel (right-looking inside the panel), a cluster barrier publishes it, every other CTA copies
 //     it from the owner's shared memory (distributed shared memory), and every CTA applies the
 //     panel's rank-CHC_B update to the columns it owns.  One cluster barrier per panel.
+//   - The owner factors its panel with one warp (__syncwarp only, no CTA barrier per column).
 //   - Afterwards every CTA holds all of L and computes its own columns of L^-1 by forward
-//     substitution (column-oriented, two CTA barriers per row).
+//     substitution, two columns per warp held in registers (a shuffle per row, no CTA barrier).
 //   - A non-positive or non-finite pivot is announced to every CTA's flag before the barrier, so all
 //     CTAs leave the panel loop together; the outputs then carry the same status codes as above.
 // All waits are hardware barriers (CTA and cluster); no CTA reads another's shared memory after the
@@ -701,13 +702,10 @@ __global__ void __cluster_dims__(CHC_C, 1, 1) __launch_bounds__(CHC_NT)
                         // cluster barrier and read only after it
   __shared__ int own[CHC_OWN];  // the columns this CTA owns, ascending (-1: none)
   __shared__ double red[CHC_NT / 32];
-  __shared__ double piv[2];     // sqrt and reciprocal of the next pivot
-  __shared__ double col[CHC_MAX_N];
   const int rank = (int)cluster.block_rank(), tid = threadIdx.x;
   const int lda = n | 1;
   double *A = dyn;                          // n x lda
-  double *X = dyn + (size_t)n * lda;        // n x CHC_OWN: own columns of L^-1
-  double *rinv = X + (size_t)n * CHC_OWN;   // n: 1 / L_kk
+  double *rinv = dyn + (size_t)n * lda;     // n: 1 / L_kk
   const int P = (n + CHC_B - 1) / CHC_B;
   if (tid == 0) {
     bad = 0;
@@ -766,38 +764,27 @@ __global__ void __cluster_dims__(CHC_C, 1, 1) __launch_bounds__(CHC_NT)
     if (bad) break;  // set before the loop: every CTA leaves at the same point
     const int c0 = p * CHC_B, c1 = min(n, c0 + CHC_B), w = c1 - c0, owner = p % CHC_C;
     if (rank == owner) {
-      // right-looking inside the panel, two barriers per column; the thread that finishes the next
-      // diagonal element takes its reciprocal square root
-      if (tid == 0) {
-        const double d = A[c0 * lda + c0];
-        if (!(d > 0.0) || !isfinite(d)) pf = 1000000 + c0;
-        piv[1] = rsqrt(d);
-        piv[0] = d * piv[1];
+      // right-looking inside the panel by one warp (rows lane, lane + 32, ...), synchronised by
+      // __syncwarp only: scale column j by 1 / sqrt(pivot), then update the panel's later columns
+      if (tid < 32) {
+        for (int j = c0; j < c1; ++j) {
+          const double d = A[j * lda + j];  // the same value in every lane
+          if (!(d > 0.0) || !isfinite(d)) {
+            if (tid == 0) pf = 1000000 + j;
+            break;
+          }
+          const double r = rsqrt(d);
+          for (int i = j + 1 + tid; i < n; i += 32) A[i * lda + j] *= r;
+          if (tid == 0) A[j * lda + j] = d * r;
+          __syncwarp();
+          for (int i = j + 1 + tid; i < n; i += 32) {
+            const double li = A[i * lda + j];
+            for (int k = j + 1; k < c1 && k <= i; ++k) A[i * lda + k] -= li * A[k * lda + j];
+          }
+          __syncwarp();
+        }
       }
       __syncthreads();
-      for (int j = c0; j < c1 && !pf; ++j) {
-        const double ri = piv[1];
-        for (int i = j + 1 + tid; i < n; i += CHC_NT) {
-          const double l = A[i * lda + j] * ri;
-          A[i * lda + j] = l;
-          col[i] = l;
-        }
-        if (tid == 0) A[j * lda + j] = piv[0];
-        __syncthreads();
-        for (int i = j + 1 + tid; i < n; i += CHC_NT) {
-          const double li = col[i];
-          for (int k = j + 1; k < c1 && k <= i; ++k) {
-            const double v = A[i * lda + k] - li * col[k];
-            A[i * lda + k] = v;
-            if (i == k && k == j + 1) {  // the next pivot
-              if (!(v > 0.0) || !isfinite(v)) pf = 1000000 + k;
-              piv[1] = rsqrt(v);
-              piv[0] = v * piv[1];
-            }
-          }
-        }
-        __syncthreads();
-      }
       if (pf && tid < CHC_C) *cluster.map_shared_rank(&fail, tid) = pf;
     }
     cluster.sync();  // panel p is final in its owner's shared memory (or the failure is announced)
@@ -837,32 +824,58 @@ __global__ void __cluster_dims__(CHC_C, 1, 1) __launch_bounds__(CHC_NT)
     if (rank == 0 && tid == 0) *status = bad ? bad : fail;
     return;
   }
-  // own columns of L^-1 by forward substitution, one barrier per row: at step k the rows i > k take
-  // X_ik -= L_ik X_kk.. and row k + 1, then final, is scaled by 1 / L_(k+1)(k+1)
+  // own columns of L^-1 by forward substitution, two columns per warp, each column held in the
+  // warp's registers (lane l: rows l, l + 32, l + 64, l + 96): at step k, X_kc (final) is broadcast
+  // by a shuffle, the rows i > k take X_ic -= L_ik X_kc, and row k + 1, then final, is scaled by
+  // 1 / L_(k+1)(k+1).  No CTA barrier: a step waits only on its shuffle.
   for (int k = tid; k < n; k += CHC_NT) rinv[k] = 1.0 / A[k * lda + k];
-  for (int e = tid; e < n * CHC_OWN; e += CHC_NT) X[e] = 0.0;
-  __syncthreads();
-  if (tid < CHC_OWN && own[tid] >= 0) X[own[tid] * CHC_OWN + tid] = rinv[own[tid]];  // X_cc = 1 / L_cc
   __syncthreads();
   {
-    const int c = own[lane16];
-    for (int k = 0; k + 1 < n; ++k) {
-      if (c >= 0 && c <= k) {
-        const double xk = X[k * CHC_OWN + lane16];
-        for (int i = k + 1 + row16; i < n; i += CHC_NT / 16) {
-          double v = X[i * CHC_OWN + lane16] - A[i * lda + k] * xk;
-          if (i == k + 1) v *= rinv[i];
-          X[i * CHC_OWN + lane16] = v;
+    const int lane = tid & 31, wp = tid >> 5;
+    static_assert(CHC_OWN == 2 * (CHC_NT / 32), "two own columns per warp");
+    static_assert(CHC_MAX_N <= 128, "four rows per lane");
+    const int ca = own[2 * wp], cb = own[2 * wp + 1];
+    double xa[4], xb[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int i = lane + 32 * m;
+      xa[m] = (ca >= 0 && i == ca) ? rinv[ca] : 0.0;
+      xb[m] = (cb >= 0 && i == cb) ? rinv[cb] : 0.0;
+    }
+    const int k0 = ca < 0 ? n : (cb < 0 ? ca : min(ca, cb));
+    for (int k = k0; k + 1 < n; ++k) {
+      const int mk = k >> 5, lk = k & 31;
+      const double va = mk == 0 ? xa[0] : (mk == 1 ? xa[1] : (mk == 2 ? xa[2] : xa[3]));
+      const double vb = mk == 0 ? xb[0] : (mk == 1 ? xb[1] : (mk == 2 ? xb[2] : xb[3]));
+      const double xka = __shfl_sync(0xffffffffu, va, lk), xkb = __shfl_sync(0xffffffffu, vb, lk);
+      const bool ua = ca >= 0 && k >= ca, ub = cb >= 0 && k >= cb;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int i = lane + 32 * m;
+        if (i > k && i < n) {
+          const double lik = A[i * lda + k];
+          if (ua) xa[m] -= lik * xka;
+          if (ub) xb[m] -= lik * xkb;
+          if (i == k + 1) {
+            if (ua) xa[m] *= rinv[i];
+            if (ub) xb[m] *= rinv[i];
+          }
         }
       }
-      __syncthreads();
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int i = lane + 32 * m;
+      if (i < n) {
+        if (ca >= 0) Linv[(long long)i * n + ca] = i >= ca ? xa[m] : 0.0;
+        if (cb >= 0) Linv[(long long)i * n + cb] = i >= cb ? xb[m] : 0.0;
+      }
     }
   }
   for (int e = tid; e < n * CHC_OWN; e += CHC_NT) {
     const int i = e / CHC_OWN, cc = e % CHC_OWN, c = own[cc];
     if (c < 0) continue;
     L[(long long)i * n + c] = (i >= c) ? A[i * lda + c] : 0.0;
-    Linv[(long long)i * n + c] = (i >= c) ? X[i * CHC_OWN + cc] : 0.0;
   }
   if (rank == 0 && tid == 0) *status = 0;
 }
@@ -883,7 +896,7 @@ cudaError_t launch_cholesky(const double *M_raw, int n, double spin_factor, doub
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && ready[dev] == 0) {
-      const size_t smax = sizeof(double) * ((size_t)CHC_MAX_N * (CHC_MAX_N | 1) + (size_t)CHC_MAX_N * (CHC_OWN + 1));
+      const size_t smax = sizeof(double) * ((size_t)CHC_MAX_N * (CHC_MAX_N | 1) + (size_t)CHC_MAX_N);
       cudaError_t e = cudaFuncSetAttribute(cholesky_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smax);
       int clusters = 0;
@@ -899,7 +912,7 @@ cudaError_t launch_cholesky(const double *M_raw, int n, double spin_factor, doub
       ready[dev] = (e == cudaSuccess && clusters > 0) ? 1 : -1;
     }
     if (dev >= 0 && dev < 64 && ready[dev] == 1) {
-      const size_t smem = sizeof(double) * ((size_t)n * (n | 1) + (size_t)n * (CHC_OWN + 1));
+      const size_t smem = sizeof(double) * ((size_t)n * (n | 1) + (size_t)n);
       cholesky_cluster_kernel<<<CHC_C, CHC_NT, smem, st>>>(M_raw, n, spin_factor, M, L, Linv, energy, status);
       return cudaGetLastError();
     }
