@@ -332,8 +332,8 @@ void ace_destroy(ace_op *op);
  * grids return ACE_ERR_ARG.  Every call on a device shares the array and finds the previous call's
  * contents in it: the call rewrites what it reads and zeroes W.  Calls whose GPU work overlaps (other
  * streams or host threads) race on the array and must be serialised by the caller.  The first call on
- * a device looks up the array's device address (cudaGetSymbolAddress, with that device current);
- * make it before any stream capture.  Stream-ordered on `cuda_stream`; pair uploads go through a
+ * a device looks up the array's device address (cudaGetSymbolAddress, with that device current)
+ * and caches it.  Stream-ordered on `cuda_stream`; pair uploads go through a
  * small pageable host buffer.  Errors: ACE_ERR_ARG, ACE_ERR_UNSUPPORTED_GRID, ACE_ERR_CUDA. */
 #define ACE_NOALLOC_SCRATCH_BYTES (32u << 20)
 ace_status ace_exchange_w_noalloc(const ace_desc *desc, const void *phi_dev, ace_dtype dtype,

@@ -18,7 +18,7 @@
 //     Calls whose work overlaps on the GPU (two streams, or two host threads) race on the array;
 //     serialise them;
 //   * the first call on a device looks up the array's device address with cudaGetSymbolAddress
-//     (with that device current) and caches it; make that first call before any stream capture.
+//     (with that device current) and caches it.
 #include <cuda_runtime.h>
 
 #include <cmath>
