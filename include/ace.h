@@ -163,8 +163,10 @@ ace_status ace_apply_finish(const ace_op *op, const double *C, ace_dtype dtype, 
  * out are arrays of length k; each build is as in ace_build.  On the first failing build the
  * handles already created are destroyed, every out[i] is NULL, and its status is returned.
  * By default the builds run one after another, each with the pair chain of ace_build (all screens
- * first, then one wait for every pair list); the environment variable ACE_BATCH_LANES (1-4) runs
- * that many at a time on concurrent stream lanes.  With the environment variable ACE_BATCH_QUEUE=1, and every build in the mixed form on
+ * first, then one wait for every pair list); each build's M, Cholesky and xi run on a second stream
+ * of its lane, beside the next build's pair chain (ACE_BATCH_TAIL=0 keeps them on the lane, after
+ * the chain).  The environment variable ACE_BATCH_LANES (1-4) runs that many builds at a time on
+ * concurrent stream lanes.  With the environment variable ACE_BATCH_QUEUE=1, and every build in the mixed form on
  * a grid with a persistent chain plan (see ace_graph_create), the chains run instead as one
  * persistent launch per grid over the builds' concatenated device pack lists, with no host wait
  * between the screens and the chains. */

@@ -267,6 +267,7 @@ struct ace_op {
   void *readback = nullptr;   // pinned host area for the asynchronous readbacks of a build
   size_t readback_bytes = 0;
   int lane = 0;               // stream lane of a batched build (selects its side streams)
+  cudaStream_t tail = nullptr;  // batched builds: stream of the steps after the pair chain
   float *pmax = nullptr;      // plane maxima of the working orbitals [n][N1] for the plane skip
   float *gmax = nullptr;      // and the orbitals' maxima [n]
   bool queued = false;        // screened build whose chain ran in a device pack queue
@@ -440,11 +441,12 @@ void pinned_put(void *p, size_t bytes) {
 std::mutex g_side_mu;
 constexpr int kLanes = 4;           // concurrent builds of one batched call
 constexpr int kSide = 8;            // pair-chain side streams per lane
-// per lane: kSide chain side streams; then the lane streams; then one input-copy stream per lane
-cudaStream_t g_side[64][(kSide + 2) * kLanes] = {};
+// per lane: kSide chain side streams; then the lane streams; then one input-copy stream per lane;
+// then one tail stream per lane (the steps after the pair chain of a batched build)
+cudaStream_t g_side[64][(kSide + 3) * kLanes] = {};
 
 cudaError_t get_side_stream(int dev, int k, cudaStream_t *out) {
-  if (dev < 0 || dev >= 64 || k < 0 || k >= (kSide + 2) * kLanes) return cudaErrorInvalidValue;
+  if (dev < 0 || dev >= 64 || k < 0 || k >= (kSide + 3) * kLanes) return cudaErrorInvalidValue;
   std::lock_guard<std::mutex> lk(g_side_mu);
   if (!g_side[dev][k]) {
     cudaError_t e = cudaStreamCreateWithFlags(&g_side[dev][k], cudaStreamNonBlocking);
@@ -1262,6 +1264,16 @@ ace_status build_finish(ace_op *op) {
   s = run_chain<T>(op, phi, count);
   if (s != ACE_OK) return s;
   ACE_CUDA(mark(op, 2, st), "event record");
+  if (op->tail) {
+    // M, the Cholesky and xi on the lane's tail stream, so that the next build's pair chain starts
+    // on the lane stream meanwhile; the handle keeps the tail stream (its last work) from here on
+    cudaEvent_t ev;
+    ACE_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+    ACE_CUDA(cudaEventRecord(ev, st), "event");
+    ACE_CUDA(cudaStreamWaitEvent(op->tail, ev, 0), "wait");
+    cudaEventDestroy(ev);
+    op->stream = op->tail;
+  }
   return build_dense<T>(op);
 }
 
@@ -1969,8 +1981,9 @@ ace_status ace_build_pairs(const ace_desc *desc, const void *phi, ace_dtype dtyp
 }
 
 // Builds go on stream lanes forked from `cuda_stream` (one by default, up to four): all screens
-// first, one wait for the pair lists, then every build's chain and dense steps on its lane, then
-// one join back into `cuda_stream`.
+// first, one wait for the pair lists, then every build's chain on its lane and its dense steps on
+// the lane's tail stream (so that they run beside the next build's chain; ACE_BATCH_TAIL=0 keeps
+// them on the lane), then one join back into `cuda_stream`.
 ace_status ace_build_batched(int k, const ace_desc *desc, const void *const *phi, ace_dtype dtype, void *cuda_stream,
                              ace_op **out) {
   if (k < 0 || (k > 0 && (!desc || !phi || !out))) return fail(ACE_ERR_ARG, "bad batched arguments");
@@ -1989,17 +2002,22 @@ ace_status ace_build_batched(int k, const ace_desc *desc, const void *const *phi
   // builds only share the L2 (measured on the 24 uneven builds: 37.5 builds/s on one lane, 35.5 on
   // four)
   const int lanes = std::min(kLanes, std::max(1, std::min(k, env_int("ACE_BATCH_LANES", 1))));
-  cudaStream_t lane_st[kLanes];
+  cudaStream_t lane_st[kLanes], tail_st[kLanes];
+  const bool queue = env_int("ACE_BATCH_QUEUE", 0) != 0 && queue_eligible(k, desc);
+  const bool tail = !queue && env_int("ACE_BATCH_TAIL", 1) != 0;
   cudaEvent_t fork = nullptr;
   ACE_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "event");
   ACE_CUDA(cudaEventRecord(fork, user), "event");
   for (int l = 0; l < lanes; ++l) {
     ACE_CUDA(get_side_stream(dev, kSide * kLanes + l, &lane_st[l]), "lane stream");
     ACE_CUDA(cudaStreamWaitEvent(lane_st[l], fork, 0), "fork");
+    if (tail) {
+      ACE_CUDA(get_side_stream(dev, (kSide + 2) * kLanes + l, &tail_st[l]), "tail stream");
+      ACE_CUDA(cudaStreamWaitEvent(tail_st[l], fork, 0), "fork");
+    }
   }
   ace_status s = ACE_OK;
   int failed = -1;
-  const bool queue = env_int("ACE_BATCH_QUEUE", 0) != 0 && queue_eligible(k, desc);
   for (int i = 0; i < k && s == ACE_OK; ++i) {
     ace_op *op = new_op(&desc[i], lane_st[i % lanes], &s);
     if (!op) {
@@ -2007,6 +2025,7 @@ ace_status ace_build_batched(int k, const ace_desc *desc, const void *const *phi
       break;
     }
     op->lane = i % lanes;
+    if (tail) op->tail = tail_st[i % lanes];
     out[i] = op;
     if (!queue) {
       s = begin_any(op, phi[i], dtype);
@@ -2027,6 +2046,10 @@ ace_status ace_build_batched(int k, const ace_desc *desc, const void *const *phi
   for (int l = 0; l < lanes; ++l) {
     cudaEventRecord(fork, lane_st[l]);
     cudaStreamWaitEvent(user, fork, 0);
+    if (tail) {
+      cudaEventRecord(fork, tail_st[l]);
+      cudaStreamWaitEvent(user, fork, 0);
+    }
   }
   for (int i = 0; i < k; ++i)
     if (out[i]) cudaStreamSynchronize(out[i]->stream);

@@ -667,18 +667,28 @@ __global__ void __launch_bounds__(CH_NT) cholesky_kernel(const double *__restric
 // ----------------------------------------------------------------------------------------
 // The same factorisation on a cluster of CHC_C CTAs, for n <= CHC_MAX_N.  This GPU retires about
 // two FP64 FMA per clock per SM, so the one-CTA kernel above is bound by one SM's FP64 pipe; here
-// the trailing updates and the inverse are spread over CHC_C SMs.
+// the work is spread over CHC_C SMs.
 //   - Every CTA holds the whole symmetrised -M in shared memory (row stride lda = n | 1, odd, so
-//     that a column walk does not hit one bank).
-//   - Columns are dealt in panels of CHC_B, panel p owned by CTA p % CHC_C.  The owner factors its
-//     panel (right-looking inside the panel), a cluster barrier publishes it, every other CTA copies
-//     it from the owner's shared memory (distributed shared memory), and every CTA applies the
-//     panel's rank-CHC_B update to the columns it owns.  One cluster barrier per panel.
-//   - The owner factors its panel with one warp (__syncwarp only, no CTA barrier per column).
-//   - Afterwards every CTA holds all of L and computes its own columns of L^-1 by forward
-//     substitution, two columns per warp held in registers (a shuffle per row, no CTA barrier).
-//   - A non-positive or non-finite pivot is announced to every CTA's flag before the barrier, so all
-//     CTAs leave the panel loop together; the outputs then carry the same status codes as above.
+//     that a column walk does not hit one bank).  Each CTA symmetrises an eighth of the elements
+//     and writes them into every CTA's copy (distributed shared memory) and into M.
+//   - Columns are dealt in panels of CHC_B, panel p owned by CTA p % CHC_C.  After panel p is
+//     published (a cluster barrier), every other CTA copies it from the owner's shared memory and
+//     applies its rank-CHC_B update to the columns it owns.
+//   - Look-ahead: the owner of panel p + 1 first updates only that panel's columns, factors it with
+//     one warp (the panel held in registers, rows lane + 32m, pivots and L_kj broadcast by
+//     shuffles) and arrives at the cluster barrier; its other columns are updated after the arrival.
+//     Every other CTA arrives right after its copy and updates its columns before it waits, so the
+//     chain from one panel to the next is a copy, an 8-column update and the panel factorisation.
+//   - Afterwards every CTA holds all of L; the columns of L^-1 are dealt in pairs, two per warp,
+//     in an order that balances the FP64 work over the CTAs.  A warp holds its two columns in
+//     registers (lane l: rows l, l + 32, l + 64, l + 96) and runs forward substitution: at step k
+//     X_kc (final) is broadcast by a shuffle, the rows i > k take X_ic -= L_ik X_kc (only the row
+//     groups below k), and row k + 1, then final, is scaled by 1 / L_(k+1)(k+1).
+//   - A non-positive or non-finite pivot is written into every CTA's flag before the barrier, so all
+//     CTAs leave the panel loop at the same point; the outputs then carry the same status codes as
+//     above.
+// The arithmetic of every element (the symmetrisation, the right-looking updates in panel order,
+// the pivots, the substitution) is that of the one-CTA kernel's cluster predecessor, step for step.
 // All waits are hardware barriers (CTA and cluster); no CTA reads another's shared memory after the
 // cluster barrier that follows the last panel.
 // ----------------------------------------------------------------------------------------
@@ -689,6 +699,73 @@ constexpr int CHC_B = 8;
 constexpr int CHC_MAX_N = 128;
 constexpr int CHC_OWN = 16;  // columns a CTA owns at most: 128 / (8 x 8) panels of 8
 static_assert(CHC_MAX_N <= CHC_C * CHC_B * (CHC_OWN / CHC_B), "own columns per CTA");
+static_assert(CHC_MAX_N <= 2 * CHC_C * (CHC_NT / 32), "two columns of L^-1 per warp");
+static_assert(CHC_MAX_N <= 128, "four rows per lane");
+
+__device__ __forceinline__ void cluster_arrive_release() {
+  asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+  asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+__device__ __forceinline__ bool finite_bits(double v) {
+  return ((__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;
+}
+
+// Panel q (columns c0 .. c0 + w - 1, rows c0 .. n - 1) factored by one warp, right-looking inside
+// the panel: scale column j by 1 / sqrt(pivot), then update the panel's later columns.  Returns 0,
+// or 1000000 + the column of a non-positive or non-finite pivot (the same in every lane).
+__device__ __forceinline__ int chc_factor_panel(double *A, int lda, int n, int c0, int w) {
+  const int lane = threadIdx.x & 31, h = n - c0;
+  double a[4][CHC_B];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int i = lane + 32 * m;
+#pragma unroll
+    for (int j = 0; j < CHC_B; ++j) a[m][j] = (i < h && j < w) ? A[(c0 + i) * lda + c0 + j] : 0.0;
+  }
+  int status = 0;
+#pragma unroll
+  for (int j = 0; j < CHC_B; ++j) {
+    if (j < w && status == 0) {
+      const double d = __shfl_sync(0xffffffffu, a[0][j], j);  // row c0 + j: lane j, group 0
+      if (!(d > 0.0) || !isfinite(d)) {
+        status = 1000000 + c0 + j;
+      } else {
+        const double r = rsqrt(d);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int i = lane + 32 * m;
+          if (32 * m < h) {
+            if (i > j) a[m][j] *= r;
+            else if (i == j) a[m][j] = d * r;
+          }
+        }
+#pragma unroll
+        for (int k = j + 1; k < CHC_B; ++k) {
+          if (k < w) {
+            const double lkj = __shfl_sync(0xffffffffu, a[0][j], k);  // row c0 + k, already scaled
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+              const int i = lane + 32 * m;
+              if (32 * m < h && i >= k) a[m][k] -= a[m][j] * lkj;
+            }
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int i = lane + 32 * m;
+    if (i < h) {
+#pragma unroll
+      for (int j = 0; j < CHC_B; ++j)
+        if (j < w) A[(c0 + i) * lda + c0 + j] = a[m][j];
+    }
+  }
+  return status;
+}
 
 __global__ void __cluster_dims__(CHC_C, 1, 1) __launch_bounds__(CHC_NT)
     cholesky_cluster_kernel(const double *__restrict__ M_raw, int n, double spin_factor, double *__restrict__ M,
@@ -696,9 +773,9 @@ __global__ void __cluster_dims__(CHC_C, 1, 1) __launch_bounds__(CHC_NT)
                             int *__restrict__ status) {
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ double dyn[];
-  __shared__ int bad;   // non-finite input: set before the panel loop, the same in every CTA
-  __shared__ int pf;    // pivot failure met by this CTA while it factors its panel
-  __shared__ int fail;  // pivot failure of the panel's owner, written into every CTA before the
+  __shared__ int bad;   // non-finite input: written into every CTA before the first barrier
+  __shared__ int pf;    // pivot failure met by this CTA while it factors a panel
+  __shared__ int fail;  // pivot failure of a panel's owner, written into every CTA before the
                         // cluster barrier and read only after it
   __shared__ int own[CHC_OWN];  // the columns this CTA owns, ascending (-1: none)
   __shared__ double red[CHC_NT / 32];
@@ -716,39 +793,44 @@ __global__ void __cluster_dims__(CHC_C, 1, 1) __launch_bounds__(CHC_NT)
       for (int c = p * CHC_B; c < min(n, (p + 1) * CHC_B); ++c) own[m++] = c;
     for (; m < CHC_OWN; ++m) own[m] = -1;
   }
-  // -M symmetrised: a coalesced copy (eight loads in flight per thread), then each pair (i < j)
-  // averaged by one thread
-  for (int base = tid; base < n * n; base += 8 * CHC_NT) {
-    double v[8];
+  cluster.sync();  // every CTA has started and cleared its flags before any write across CTAs
+  // -M symmetrised: this CTA's eighth of the elements, M_sym = (M_raw + M_raw^T) / 2 written to M
+  // and its negative into every CTA's A
+  {
+    double *Aq[CHC_C];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = base + u * CHC_NT;
-      v[u] = e < n * n ? M_raw[e] : 0.0;
-    }
+    for (int q = 0; q < CHC_C; ++q) Aq[q] = cluster.map_shared_rank(A, q);
+    constexpr int U = CHC_MAX_N * CHC_MAX_N / (CHC_NT * CHC_C);  // elements per thread at n = 128
+    const int nn = n * n;
+    double s[U];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = base + u * CHC_NT;
-      if (e < n * n) A[(e / n) * lda + e % n] = v[u];
+    for (int u = 0; u < U; ++u) {
+      const int e = (u * CHC_C + rank) * CHC_NT + tid;
+      s[u] = 0.0;
+      if (e < nn) {
+        const int i = e / n, j = e - (e / n) * n;
+        s[u] = i == j ? M_raw[e] : 0.5 * (M_raw[e] + M_raw[j * n + i]);
+      }
     }
-  }
-  __syncthreads();
-  for (int e = tid; e < n * n; e += CHC_NT) {
-    const int i = e / n, j = e % n;
-    if (i < j) {
-      const double v = 0.5 * (A[i * lda + j] + A[j * lda + i]);
-      A[i * lda + j] = -v;
-      A[j * lda + i] = -v;
-      if (!isfinite(v)) bad = 2000000;  // every CTA sees the same input
-    } else if (i == j) {
-      A[i * lda + i] = -A[i * lda + i];
-      if (!isfinite(A[i * lda + i])) bad = 2000000;
+    bool ok = true;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = (u * CHC_C + rank) * CHC_NT + tid;
+      if (e < nn) {
+        const int i = e / n, j = e - (e / n) * n;
+        M[e] = s[u];
+        ok = ok && finite_bits(s[u]);
+        const double v = __longlong_as_double(__double_as_longlong(s[u]) ^ (long long)0x8000000000000000ull);
+#pragma unroll
+        for (int q = 0; q < CHC_C; ++q) Aq[q][i * lda + j] = v;
+      }
     }
+    if (!ok)
+      for (int q = 0; q < CHC_C; ++q) *cluster.map_shared_rank(&bad, q) = 2000000;  // every CTA sees it
   }
-  __syncthreads();
   if (rank == 0) {
-    for (int e = tid; e < n * n; e += CHC_NT) M[e] = -A[(e / n) * lda + e % n];
     double part = 0.0;
-    for (int k = tid; k < n; k += CHC_NT) part -= A[k * lda + k];
+    for (int k = tid; k < n; k += CHC_NT) part += M_raw[k * n + k];
     for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
     if ((tid & 31) == 0) red[tid >> 5] = part;
     __syncthreads();
@@ -758,83 +840,89 @@ __global__ void __cluster_dims__(CHC_C, 1, 1) __launch_bounds__(CHC_NT)
       *energy = 0.5 * spin_factor * t;
     }
   }
-  cluster.sync();  // every CTA has started and cleared its flags before any shared-memory access across CTAs
-  const int lane16 = tid & 15, row16 = tid >> 4;  // (own column, row) lanes of the column-parallel loops
-  for (int p = 0; p < P; ++p) {
-    if (bad) break;  // set before the loop: every CTA leaves at the same point
-    const int c0 = p * CHC_B, c1 = min(n, c0 + CHC_B), w = c1 - c0, owner = p % CHC_C;
-    if (rank == owner) {
-      // right-looking inside the panel by one warp (rows lane, lane + 32, ...), synchronised by
-      // __syncwarp only: scale column j by 1 / sqrt(pivot), then update the panel's later columns
-      if (tid < 32) {
-        for (int j = c0; j < c1; ++j) {
-          const double d = A[j * lda + j];  // the same value in every lane
-          if (!(d > 0.0) || !isfinite(d)) {
-            if (tid == 0) pf = 1000000 + j;
-            break;
-          }
-          const double r = rsqrt(d);
-          for (int i = j + 1 + tid; i < n; i += 32) A[i * lda + j] *= r;
-          if (tid == 0) A[j * lda + j] = d * r;
-          __syncwarp();
-          for (int i = j + 1 + tid; i < n; i += 32) {
-            const double li = A[i * lda + j];
-            for (int k = j + 1; k < c1 && k <= i; ++k) A[i * lda + k] -= li * A[k * lda + j];
-          }
-          __syncwarp();
-        }
-      }
-      __syncthreads();
-      if (pf && tid < CHC_C) *cluster.map_shared_rank(&fail, tid) = pf;
+  cluster.sync();  // A complete in every CTA, bad the same everywhere
+  // panel 0 by its owner
+  if (!bad && rank == 0) {
+    if (tid < 32) {
+      const int r = chc_factor_panel(A, lda, n, 0, min(n, CHC_B));
+      if (tid == 0) pf = r;
     }
-    cluster.sync();  // panel p is final in its owner's shared memory (or the failure is announced)
-    if (fail) break;  // the same in every CTA after the barrier
+    __syncthreads();
+    if (pf && tid < CHC_C) *cluster.map_shared_rank(&fail, tid) = pf;
+  }
+  cluster.sync();  // panel 0 final in its owner's shared memory (or the failure announced)
+  const int lane16 = tid & 15, row16 = tid >> 4;  // (own column, row) lanes of the column-parallel update
+  for (int p = 0; p < P; ++p) {
+    if (bad || fail) break;  // the same in every CTA after the barrier
+    const int c0 = p * CHC_B, c1 = min(n, c0 + CHC_B), w = c1 - c0, owner = p % CHC_C;
     if (rank != owner) {  // rows c0.. of the panel's columns from the owner, four loads in flight
       const double *src = cluster.map_shared_rank(A, owner);
-      const int ne = (n - c0) * w;
+      const int ne = (n - c0) * CHC_B;
       for (int base = tid; base < ne; base += 4 * CHC_NT) {
         double v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int e = base + u * CHC_NT;
-          v[u] = e < ne ? src[(c0 + e / w) * lda + c0 + e % w] : 0.0;
+          const int e = base + u * CHC_NT, c = e & (CHC_B - 1);
+          v[u] = (e < ne && c < w) ? src[(c0 + (e >> 3)) * lda + c0 + c] : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int e = base + u * CHC_NT;
-          if (e < ne) A[(c0 + e / w) * lda + c0 + e % w] = v[u];
+          const int e = base + u * CHC_NT, c = e & (CHC_B - 1);
+          if (e < ne && c < w) A[(c0 + (e >> 3)) * lda + c0 + c] = v[u];
         }
       }
-      __syncthreads();
     }
-    // rank-w update of this CTA's columns k >= c1, rows i >= k: A_ik -= sum_j L_ij L_kj
+    __syncthreads();  // the panel, and the previous panel's updates of this CTA's columns, complete
+    const bool ahead = p + 1 < P && rank == (p + 1) % CHC_C;
+    const int c2 = min(n, c1 + CHC_B);
+    if (ahead) {
+      // rank-w update of the next panel's columns k in [c1, c2), rows i >= k, then its factorisation
+      const int col = tid & (CHC_B - 1), rl = tid >> 3, k = c1 + col;
+      if (k < c2)
+        for (int i = c1 + rl; i < n; i += CHC_NT / CHC_B) {
+          if (i < k) continue;
+          double acc = 0.0;
+          for (int j = c0; j < c1; ++j) acc += A[i * lda + j] * A[k * lda + j];
+          A[i * lda + k] -= acc;
+        }
+      __syncthreads();
+      if (tid < 32) {
+        const int r = chc_factor_panel(A, lda, n, c1, c2 - c1);
+        if (tid == 0) pf = r;
+      }
+      __syncthreads();
+      if (pf && tid < CHC_C) *cluster.map_shared_rank(&fail, tid) = pf;
+    }
+    cluster_arrive_release();  // the next panel is published once every CTA has arrived
+    // rank-w update of this CTA's other columns k >= c1 (k >= c2 for the look-ahead owner), rows i >= k
     {
       const int k = own[lane16];
-      if (k >= c1)
+      if (k >= (ahead ? c2 : c1))
         for (int i = k + row16; i < n; i += CHC_NT / 16) {
           double acc = 0.0;
           for (int j = c0; j < c1; ++j) acc += A[i * lda + j] * A[k * lda + j];
           A[i * lda + k] -= acc;
         }
     }
-    __syncthreads();
+    cluster_wait_acquire();
   }
   cluster.sync();  // no CTA reads another's shared memory past this point
   if (bad || fail) {
     if (rank == 0 && tid == 0) *status = bad ? bad : fail;
     return;
   }
-  // own columns of L^-1 by forward substitution, two columns per warp, each column held in the
-  // warp's registers (lane l: rows l, l + 32, l + 64, l + 96): at step k, X_kc (final) is broadcast
-  // by a shuffle, the rows i > k take X_ic -= L_ik X_kc, and row k + 1, then final, is scaled by
-  // 1 / L_(k+1)(k+1).  No CTA barrier: a step waits only on its shuffle.
+  for (int e = tid; e < n * CHC_OWN; e += CHC_NT) {
+    const int i = e / CHC_OWN, cc = e % CHC_OWN, c = own[cc];
+    if (c < 0) continue;
+    L[(long long)i * n + c] = (i >= c) ? A[i * lda + c] : 0.0;
+  }
   for (int k = tid; k < n; k += CHC_NT) rinv[k] = 1.0 / A[k * lda + k];
   __syncthreads();
   {
     const int lane = tid & 31, wp = tid >> 5;
-    static_assert(CHC_OWN == 2 * (CHC_NT / 32), "two own columns per warp");
-    static_assert(CHC_MAX_N <= 128, "four rows per lane");
-    const int ca = own[2 * wp], cb = own[2 * wp + 1];
+    // column pairs (2t, 2t + 1), dealt so that every CTA gets early and late columns alike
+    const int t = CHC_C * wp + ((wp & 1) ? CHC_C - 1 - rank : rank);
+    const int ca = 2 * t < n ? 2 * t : -1, cb = 2 * t + 1 < n ? 2 * t + 1 : -1;
     double xa[4], xb[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -842,23 +930,37 @@ __global__ void __cluster_dims__(CHC_C, 1, 1) __launch_bounds__(CHC_NT)
       xa[m] = (ca >= 0 && i == ca) ? rinv[ca] : 0.0;
       xb[m] = (cb >= 0 && i == cb) ? rinv[cb] : 0.0;
     }
-    const int k0 = ca < 0 ? n : (cb < 0 ? ca : min(ca, cb));
-    for (int k = k0; k + 1 < n; ++k) {
-      const int mk = k >> 5, lk = k & 31;
-      const double va = mk == 0 ? xa[0] : (mk == 1 ? xa[1] : (mk == 2 ? xa[2] : xa[3]));
-      const double vb = mk == 0 ? xb[0] : (mk == 1 ? xb[1] : (mk == 2 ? xb[2] : xb[3]));
-      const double xka = __shfl_sync(0xffffffffu, va, lk), xkb = __shfl_sync(0xffffffffu, vb, lk);
-      const bool ua = ca >= 0 && k >= ca, ub = cb >= 0 && k >= cb;
+    if (ca >= 0) {
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int i = lane + 32 * m;
-        if (i > k && i < n) {
-          const double lik = A[i * lda + k];
-          if (ua) xa[m] -= lik * xka;
-          if (ub) xb[m] -= lik * xkb;
-          if (i == k + 1) {
-            if (ua) xa[m] *= rinv[i];
-            if (ub) xb[m] *= rinv[i];
+      for (int kb = 0; kb < 4; ++kb) {
+        // steps k in this row group; the last step, n - 2, makes row n - 1 final
+        const int kbeg = max(ca, 32 * kb), kend = min(n - 1, 32 * kb + 32);
+        for (int k = kbeg; k < kend; ++k) {
+          const int lk = k & 31;
+          const double xka = __shfl_sync(0xffffffffu, xa[kb], lk), xkb = __shfl_sync(0xffffffffu, xb[kb], lk);
+          const bool ub = cb >= 0 && k >= cb;
+#pragma unroll
+          for (int m = kb; m < 4; ++m) {
+            const int i = lane + 32 * m;
+            if (i > k && i < n) {
+              const double lik = A[i * lda + k];
+              xa[m] -= lik * xka;
+              if (ub) xb[m] -= lik * xkb;
+            }
+          }
+          // row k + 1 is final: lane (k + 1) & 31 of row group kb, or lane 0 of group kb + 1
+          if (lk != 31) {
+            if (lane == lk + 1) {
+              const double s = rinv[k + 1];
+              xa[kb] *= s;
+              if (ub) xb[kb] *= s;
+            }
+          } else if (kb < 3) {
+            if (lane == 0) {
+              const double s = rinv[k + 1];
+              xa[kb + 1] *= s;
+              if (ub) xb[kb + 1] *= s;
+            }
           }
         }
       }
@@ -871,11 +973,6 @@ __global__ void __cluster_dims__(CHC_C, 1, 1) __launch_bounds__(CHC_NT)
         if (cb >= 0) Linv[(long long)i * n + cb] = i >= cb ? xb[m] : 0.0;
       }
     }
-  }
-  for (int e = tid; e < n * CHC_OWN; e += CHC_NT) {
-    const int i = e / CHC_OWN, cc = e % CHC_OWN, c = own[cc];
-    if (c < 0) continue;
-    L[(long long)i * n + c] = (i >= c) ? A[i * lda + c] : 0.0;
   }
   if (rank == 0 && tid == 0) *status = 0;
 }

@@ -1,6 +1,6 @@
 """ace_build_batched: uneven builds (orbital counts, grids, screening, precision) on one stream lane
-(the default) and on four concurrent lanes, each checked against the FP64 oracle and against its
-single-build result."""
+(the default) and on four concurrent lanes, with the steps after the pair chain on a tail stream (the
+default) or on the lane, each checked against the FP64 oracle and against its single-build result."""
 
 import numpy as np
 import pytest
@@ -39,12 +39,15 @@ def _inputs():
     return cases
 
 
-@pytest.mark.parametrize("lanes", ["1", "4"])
+@pytest.mark.parametrize("lanes,tail", [("1", "1"), ("1", "0"), ("4", "1")])
 @pytest.mark.parametrize("prec", [ace.ACE_FP64, ace.ACE_MIXED])
-def test_batched_uneven_builds(prec, lanes, monkeypatch):
+def test_batched_uneven_builds(prec, lanes, tail, monkeypatch):
+    """tail = 1 (the default): each build's M, Cholesky and xi on the lane's tail stream beside the next
+    build's chain; tail = 0: all of a build on its lane."""
     import torch
 
     monkeypatch.setenv("ACE_BATCH_LANES", lanes)
+    monkeypatch.setenv("ACE_BATCH_TAIL", tail)
 
     cases = _inputs()
     dt = torch.float64 if prec == ace.ACE_FP64 else torch.float32
@@ -71,6 +74,12 @@ def test_batched_uneven_builds(prec, lanes, monkeypatch):
         assert abi.ace_pair_count(single) == abi.ace_pair_count(op)
         tol = 1e-12 if prec == ace.ACE_FP64 else 1e-6
         assert abs(ace.exchange_energy(single) - e) <= tol * abs(e)
+        xi_b = abi.get_numpy(op, abi.ACE_GET_XI)
+        xi_s = abi.get_numpy(single, abi.ACE_GET_XI)
+        if prec == ace.ACE_FP64:
+            assert np.array_equal(xi_b, xi_s)  # the FP64 form repeats bit for bit
+        else:
+            assert rel_max(xi_b, xi_s) <= MIXED_W_RTOL
         single.close()
     for op in ops:
         op.close()
