@@ -1000,7 +1000,7 @@ template <typename T>
 cudaError_t dense_gram(const T *X, int nx, const T *Y, int ny, long long K, double scale, double *G, int *err,
                        std::vector<void *> &temps, cudaStream_t st, long *launches) {
   if constexpr (sizeof(T) == 4) {
-    if (use_tc() && ace::tc_shapes_ok(K)) {
+    if (use_tc() && ace::tc_gram_shape_ok(K)) {
       void *ws = nullptr;
       cudaError_t e = cudaMallocAsync(&ws, ace::tc_gram_workspace_bytes(X, nx, Y, ny, K), st);
       if (e != cudaSuccess) return e;
@@ -1028,7 +1028,10 @@ cudaError_t dense_left_mul(const T *A, int m, int n, const T *Y, long long K, T 
                            long *launches) {
   *launches += 1;
   if constexpr (sizeof(T) == 4) {
-    if (use_tc() && ace::tc_shapes_ok(K)) return ace::launch_tc_left_mul(A, m, n, Y, K, Z, err, st);
+    if (use_tc()) {
+      const cudaError_t e = ace::launch_tc_left_mul(A, m, n, Y, K, Z, err, st);
+      if (e != cudaErrorNotSupported) return e;  // else the CUDA-core kernel below takes the shape
+    }
   }
   return ace::launch_left_mul<T>(A, m, n, Y, K, Z, st);
 }

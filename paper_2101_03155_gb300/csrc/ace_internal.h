@@ -163,8 +163,10 @@ template <typename T>
 cudaError_t launch_transpose_scale(const double *C, int n, int m, double scale, T *A, cudaStream_t st);
 
 // Tensor-core (tcgen05) BF16x3 contractions for FP32 operands.  *err is set to 1 when a bounded
-// wait inside the kernel gave up.  K must be a multiple of 128 (tc_shapes_ok).
+// wait inside the kernel gave up.  tc_shapes_ok: K a multiple of 128 (every tensor-core kernel);
+// tc_gram_shape_ok: K a multiple of 32 (the Gram, whose last chunk may be short).
 bool tc_shapes_ok(long long K);
+bool tc_gram_shape_ok(long long K);
 // Screen contribution of columns [0, K) of X (row stride ld): G += scale |X||X|^T, upper triangle.
 cudaError_t launch_screen_cols(const float *X, int n, long long ld, long long K, double scale, double *G,
                                cudaStream_t st);
@@ -180,6 +182,9 @@ bool launch_screen_tma(const float *X, int n, long long ld, long long c0, long l
 size_t tc_gram_workspace_bytes(const float *X, int nx, const float *Y, int ny, long long K);
 cudaError_t launch_tc_gram(const float *X, int nx, const float *Y, int ny, long long K, double scale, double *G,
                            void *ws, int *err, cudaStream_t st, long *launches);
+// Z = A Y (A m x n, Y n x K, Z m x K, FP32 row-major): the TMA kernel for any K % 4 == 0 (a
+// short last column tile), else the register-staged kernel for K % 128 == 0; cudaErrorNotSupported
+// (nothing launched) for other shapes.
 cudaError_t launch_tc_left_mul(const float *A, int m, int n, const float *Y, long long K, float *Z, int *err,
                                cudaStream_t st);
 // Screen contribution of the columns [c0, c0 + K) of phi (n rows of ld points) on the tensor cores:

@@ -591,7 +591,9 @@ __global__ void __launch_bounds__(NT2, 1) tc_left_mul_tma_kernel(const float *__
   const int quarter = warp & 3, half = warp >> 2;  // TMEM lane quarter; K-half / column half
   const int col = tid & 127;                       // row of the A tile / column of the Y box
   const int i0 = blockIdx.y * BM;
-  const long long ntiles = K / BN;
+  // a last tile of fewer than BN columns reads zeros past column K (the map's bounds) and stores
+  // only its columns below K
+  const long long ntiles = (K + BN - 1) / BN;
   const long long mytiles = ntiles > (long long)blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   const long long Q = mytiles * nsteps;
 
@@ -666,8 +668,8 @@ __global__ void __launch_bounds__(NT2, 1) tc_left_mul_tma_kernel(const float *__
       fence_async_smem();
       __syncthreads();
       if (tid == 0) {
-        tma_store_2d(&tmZ, (int)(c0 + 32 * r), i0, smem_u32(epi));
-        tma_store_2d(&tmZ, (int)(c0 + 32 * (r + 2)), i0, smem_u32(epi + kEpiBox));
+        if (c0 + 32 * r < K) tma_store_2d(&tmZ, (int)(c0 + 32 * r), i0, smem_u32(epi));
+        if (c0 + 32 * (r + 2) < K) tma_store_2d(&tmZ, (int)(c0 + 32 * (r + 2)), i0, smem_u32(epi + kEpiBox));
         bulk_commit();
       }
     }
@@ -1386,6 +1388,7 @@ __global__ void screen_splits_reduce_kernel(const double *__restrict__ partial, 
 }  // namespace tc
 
 bool tc_shapes_ok(long long K) { return K % tc::BN == 0 && K % tc::BK == 0; }
+bool tc_gram_shape_ok(long long K) { return K % tc::BK == 0; }
 
 // FP32 accumulation length of the tensor-core Gram (a multiple of 32; ACE_TC_CHUNK overrides)
 static int tc_chunk() {
@@ -1621,7 +1624,7 @@ bool launch_screen_syrk(const float *X, int n, long long ld, long long c0, long 
 
 cudaError_t launch_tc_left_mul(const float *A, int m, int n, const float *Y, long long K, float *Z, int *err,
                                cudaStream_t st) {
-  if (K % tc::BN != 0) return cudaErrorInvalidValue;
+  if (K % 4 != 0) return cudaErrorNotSupported;
   if (use_tma()) {
     const int nsteps = (n + tc::BK - 1) / tc::BK;
     const size_t fixed = ((size_t)nsteps * 2 + 4) * tc::TILE_BYTES + 2 * tc::kEpiBox + 1024 + 256;
@@ -1637,14 +1640,14 @@ cudaError_t launch_tc_left_mul(const float *A, int m, int n, const float *Y, lon
       int dev = 0, sms = 152;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      const long long tiles = K / tc::BN;
+      const long long tiles = (K + tc::BN - 1) / tc::BN;
       const int rows = (m + tc::BM - 1) / tc::BM;
       const unsigned gx = (unsigned)std::max(1LL, std::min(tiles, (long long)std::max(1, sms / rows)));
       tc::tc_left_mul_tma_kernel<<<dim3(gx, rows), tc::NT2, smem, st>>>(A, m, n, map, zmap, K, ring, err);
       return cudaGetLastError();
     }
   }
-  if (K % tc::BN != 0) return cudaErrorInvalidValue;
+  if (K % tc::BN != 0) return cudaErrorNotSupported;  // the register-staged kernel stores whole tiles
   const int nsteps = (n + tc::BK - 1) / tc::BK;
   const int smem = (int)(((size_t)nsteps * 2 + 4) * tc::TILE_BYTES + 2048);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;

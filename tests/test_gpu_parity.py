@@ -6,7 +6,7 @@ import pytest
 import oracle
 import paper_2101_03155_gb300 as ace
 from gpu_helpers import (FP64_ARRAY_RTOL, FP64_EX_TOL, MIXED_EX_TOL_PER_ORB, MIXED_KPHI_RTOL, MIXED_SCREEN_RTOL,
-                         MIXED_TC_SCREEN_RTOL, MIXED_W_RTOL, gpu_build, rel_max, screen_band)
+                         MIXED_TC_SCREEN_RTOL, MIXED_W_RTOL, MIXED_XI_RTOL, gpu_build, rel_max, screen_band)
 from workloads.generators import config1, gaussian_orbitals, loewdin, periodic_gaussian, water_like
 
 pytestmark = pytest.mark.gpu
@@ -95,6 +95,32 @@ def test_general_axis_lengths(grid, prec):
         # orbital; the 1e-6 Ha per orbital target is checked on the configurations themselves
         assert rel_max(g["W"].reshape(ref["W"].shape), ref["W"]) <= MIXED_W_RTOL
         assert abs(g["E_x"] - ref["E_x"]) <= 4e-6 * 3
+
+
+# Point counts off the tensor-core kernels' 128-point column tile: M on the tensor cores whenever N is
+# a multiple of 32 (its last K chunk short), xi and the application on the TMA left multiply with a
+# short last tile (loads past N read zeros, stores past N are not issued or are clipped).  1728 and
+# 8640 leave 64 points in the last tile, 1000 leaves 104 (and its Gram runs on the CUDA cores), and
+# 216000 gives every CTA of the left multiply several tiles before the short one.
+@pytest.mark.parametrize("grid", [(12, 12, 12), (10, 10, 10), (36, 12, 20), (72, 60, 50)])
+def test_mixed_dense_steps_on_ragged_point_counts(grid):
+    import torch
+
+    lat = np.diag([6.0 + 0.1 * grid[0], 6.0 + 0.1 * grid[1], 6.0 + 0.1 * grid[2]])
+    n = 6
+    phi = _small(grid, lat, n, 2, seed=sum(grid) + 11)
+    ref = oracle.ace_build(phi, lat, 0.0, 2.0)
+    g = gpu_build(phi, lat, ace.ACE_MIXED)
+    assert g["status"] == 0
+    # E_x of small sets carries the mixed form's ~2e-6 relative error (see test_general_axis_lengths)
+    assert abs(g["E_x"] - ref["E_x"]) <= 4e-6 * n
+    xi = g["xi"].reshape(ref["xi"].shape)
+    assert np.linalg.norm(xi - ref["xi"]) <= MIXED_XI_RTOL * np.linalg.norm(ref["xi"])
+    psi = torch.from_numpy(phi.astype(np.float32)).cuda()
+    out = torch.empty_like(psi)
+    ace.ace_apply(g["op"], psi, out)
+    kref = oracle.ace_apply(ref["xi"], phi, ref["dV"])
+    assert np.linalg.norm(out.cpu().numpy().astype(np.float64) - kref) <= MIXED_KPHI_RTOL * np.linalg.norm(kref)
 
 
 def test_grid_support_covers_every_235_length_to_256():
