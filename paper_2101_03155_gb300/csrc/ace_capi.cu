@@ -1053,18 +1053,21 @@ size_t screen_workspace_bytes(const float *phi, int n, long long N) {
 // Screen contribution of the columns [c0, c0 + K) of phi into O (accumulating; O zeroed by the
 // caller; only the upper triangle is used): the CUDA-core kernel of FP32 products and FP64 split
 // sums (ws of screen_workspace_bytes), or the tensor-core Gram of |phi| when requested; else the
-// TMA-fed 64 x 64 tile kernel, else the register-staged kernels.
+// TMA-fed 64 x 64 tile kernel, else the register-staged kernels.  With pm, the CUDA-core kernel
+// also fills the plane-maxima table; *pm->done is cleared when this call did not.
 template <typename T>
 cudaError_t screen_cols(const T *phi, int n, long long ld, long long c0, long long K, double dV, double *O, int *err,
-                        void *ws, cudaStream_t st, long *launches) {
+                        void *ws, cudaStream_t st, long *launches, const ace::PlaneMaxOut *pm = nullptr) {
   if constexpr (sizeof(T) == 4) {
     cudaError_t e = cudaSuccess;
     if (ws && tc_screen_requested()) {
+      if (pm) *pm->done = false;
       if (ace::launch_tc_screen(phi, n, ld, c0, K, dV, O, ws, err, st, launches, &e)) return e;
     } else if (ws && env_int("ACE_SCREEN_TILES", 0) == 0 &&
-               ace::launch_screen_syrk(phi, n, ld, c0, K, dV, O, ws, err, st, launches, &e)) {
+               ace::launch_screen_syrk(phi, n, ld, c0, K, dV, O, ws, err, st, launches, &e, pm)) {
       return e;
     }
+    if (pm) *pm->done = false;
     ++*launches;
     if (ace::launch_screen_tma(phi, n, ld, c0, K, dV, O, err, st)) return cudaGetLastError();
     if (K % 4 != 0 || ld % 4 != 0 || c0 % 4 != 0) {
@@ -1157,6 +1160,18 @@ ace_status build_begin(ace_op *op, const void *phi_in, ace_dtype dtype) {
     ACE_CUDA(cudaMallocAsync(&screen_ws, ace::gram_chunks_bytes(n, n, N), st), "alloc screen workspace");
     op->temps.push_back(screen_ws);
   }
+  // the plane-maxima table of the mixed form's plane skip, taken by the screen on its way through phi
+  // when it can (else the chain computes it with its own pass)
+  bool pm_done = false;
+  ace::PlaneMaxOut pmo{nullptr, nullptr, (long long)d.n[1] * d.n[2], d.n[0], &pm_done};
+  if (sizeof(T) == 4 && d.rho_cut > 0.0 && plane_skip_rel(false) > 0.f && !op->pmax) {
+    ACE_CUDA(op_alloc(op, &pmo.pmax, sizeof(float) * (size_t)n * d.n[0]), "alloc plane maxima");
+    ACE_CUDA(op_alloc(op, &pmo.gmax, sizeof(float) * (size_t)n), "alloc orbital maxima");
+    ACE_CUDA(cudaMemsetAsync(pmo.pmax, 0, sizeof(float) * (size_t)n * d.n[0], st), "zero plane maxima");
+    ACE_CUDA(cudaMemsetAsync(pmo.gmax, 0, sizeof(float) * (size_t)n, st), "zero orbital maxima");
+    pm_done = true;
+  }
+  const ace::PlaneMaxOut *pm = pmo.pmax ? &pmo : nullptr;
   if (pipelined) {
     ACE_CUDA(cudaMemsetAsync(op->O, 0, sizeof(double) * n * n, st), "zero O");
     cudaStream_t cs;
@@ -1176,13 +1191,20 @@ ace_status build_begin(ace_op *op, const void *phi_in, ace_dtype dtype) {
       ACE_CUDA(cudaEventRecord(ev, cs), "event");
       ACE_CUDA(cudaStreamWaitEvent(st, ev, 0), "wait");
       cudaEventDestroy(ev);
-      ACE_CUDA(screen_cols<T>(phi, n, N, c0, wc, op->dV, op->O, op->tc_err, screen_ws, st, &op->launches), "screen");
+      ACE_CUDA(screen_cols<T>(phi, n, N, c0, wc, op->dV, op->O, op->tc_err, screen_ws, st, &op->launches, pm),
+               "screen");
     }
   } else if (d.rho_cut > 0.0) {
     ACE_CUDA(cudaMemsetAsync(op->O, 0, sizeof(double) * n * n, st), "zero O");
-    ACE_CUDA(screen_cols<T>(phi, n, N, 0, N, op->dV, op->O, op->tc_err, screen_ws, st, &op->launches), "screen");
+    ACE_CUDA(screen_cols<T>(phi, n, N, 0, N, op->dV, op->O, op->tc_err, screen_ws, st, &op->launches, pm),
+             "screen");
   } else {
     ACE_CUDA(cudaMemsetAsync(op->O, 0, sizeof(double) * n * n, st), "screen skip");
+  }
+  if (pm && pm_done) {
+    // every screen launch filled the table: the chain uses it instead of its own pass
+    op->pmax = pmo.pmax;
+    op->gmax = pmo.gmax;
   }
   if constexpr (sizeof(T) == 4) {
     // pair decisions within the tensor-core products' error of rho_cut are taken on recomputed values

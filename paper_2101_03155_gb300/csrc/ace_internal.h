@@ -196,9 +196,19 @@ size_t tc_screen_workspace_bytes(const float *X, int n, long long K);
 // across K-splits): G += scale |X| |X|^T on the upper triangle.  ws holds
 // screen_syrk_workspace_bytes(n, N) for any K <= N.  false: nothing launched (TMA cannot map phi);
 // true: launched, *e the launch status.
+// With pm (pmax of n x n1 floats and gmax of n floats, both zeroed before the first call), the
+// kernel also takes atomic maxima of |phi| per (orbital, plane of npl points) and per orbital, the
+// table of launch_plane_max, when c0 and npl are multiples of 32; *pm->done is cleared otherwise.
+struct PlaneMaxOut {
+  float *pmax, *gmax;
+  long long npl;
+  int n1;
+  bool *done;
+};
 size_t screen_syrk_workspace_bytes(int n, long long K);
 bool launch_screen_syrk(const float *X, int n, long long ld, long long c0, long long K, double scale, double *G,
-                        void *ws, int *err, cudaStream_t st, long *launches, cudaError_t *e);
+                        void *ws, int *err, cudaStream_t st, long *launches, cudaError_t *e,
+                        const PlaneMaxOut *pm = nullptr);
 bool launch_tc_screen(const float *X, int n, long long ld, long long c0, long long K, double scale, double *G,
                       void *ws, int *err, cudaStream_t st, long *launches, cudaError_t *e);
 

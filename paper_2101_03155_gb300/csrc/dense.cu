@@ -675,8 +675,9 @@ __global__ void __launch_bounds__(CH_NT) cholesky_kernel(const double *__restric
 //     published (a cluster barrier), every other CTA copies it from the owner's shared memory and
 //     applies its rank-CHC_B update to the columns it owns.
 //   - Look-ahead: the owner of panel p + 1 first updates only that panel's columns, factors it with
-//     one warp (the panel held in registers, rows lane + 32m, pivots and L_kj broadcast by
-//     shuffles) and arrives at the cluster barrier; its other columns are updated after the arrival.
+//     four warps (the panel in registers, one row group per warp and SM sub-partition, r and L_kj
+//     published by warp 0 through shared memory) and arrives at the cluster barrier; its other
+//     columns are updated after the arrival.
 //     Every other CTA arrives right after its copy and updates its columns before it waits, so the
 //     chain from one panel to the next is a copy, an 8-column update and the panel factorisation.
 //   - Afterwards every CTA holds all of L; the columns of L^-1 are dealt in pairs, two per warp,
@@ -700,7 +701,8 @@ constexpr int CHC_MAX_N = 128;
 constexpr int CHC_OWN = 16;  // columns a CTA owns at most: 128 / (8 x 8) panels of 8
 static_assert(CHC_MAX_N <= CHC_C * CHC_B * (CHC_OWN / CHC_B), "own columns per CTA");
 static_assert(CHC_MAX_N <= 2 * CHC_C * (CHC_NT / 32), "two columns of L^-1 per warp");
-static_assert(CHC_MAX_N <= 128, "four rows per lane");
+static_assert(CHC_MAX_N <= 128, "four rows per lane, four row groups in the panel factorisation");
+static_assert(CHC_NT >= 128, "four warps factor a panel");
 
 __device__ __forceinline__ void cluster_arrive_release() {
   asm volatile("barrier.cluster.arrive.release;" ::: "memory");
@@ -712,57 +714,59 @@ __device__ __forceinline__ bool finite_bits(double v) {
   return ((__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;
 }
 
-// Panel q (columns c0 .. c0 + w - 1, rows c0 .. n - 1) factored by one warp, right-looking inside
-// the panel: scale column j by 1 / sqrt(pivot), then update the panel's later columns.  Returns 0,
-// or 1000000 + the column of a non-positive or non-finite pivot (the same in every lane).
-__device__ __forceinline__ int chc_factor_panel(double *A, int lda, int n, int c0, int w) {
-  const int lane = threadIdx.x & 31, h = n - c0;
-  double a[4][CHC_B];
+// Panel (columns c0 .. c0 + w - 1, rows c0 .. n - 1) factored right-looking by the CTA's first four
+// warps, one per SM sub-partition: an FP64 warp instruction issues once per about 64 cycles on a
+// sub-partition, so one warp holding all rows would serialise four times the instructions.  Warp m
+// holds rows c0 + lane + 32 m in registers.  For column j, warp 0 takes the pivot d (lane j),
+// r = 1 / sqrt(d), scales its rows, and publishes r and the panel rows' scaled L_kj (k < CHC_B)
+// through xch (double-buffered by column parity, so one named barrier per column suffices); then
+// every warp scales its rows and updates the panel's later columns.  The arithmetic of every
+// element is that of a one-warp right-looking factorisation.  Returns 0, or 1000000 + the column of
+// a non-positive or non-finite pivot (the same in all four warps).  Call with threads 0 .. 127.
+__device__ __forceinline__ int chc_factor_panel(double *A, int lda, int n, int c0, int w, double *xch, int *xflag) {
+  const int lane = threadIdx.x & 31, wm = threadIdx.x >> 5, h = n - c0, i = lane + 32 * wm;
+  double a[CHC_B];
 #pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    const int i = lane + 32 * m;
-#pragma unroll
-    for (int j = 0; j < CHC_B; ++j) a[m][j] = (i < h && j < w) ? A[(c0 + i) * lda + c0 + j] : 0.0;
-  }
+  for (int j = 0; j < CHC_B; ++j) a[j] = (i < h && j < w) ? A[(c0 + i) * lda + c0 + j] : 0.0;
   int status = 0;
 #pragma unroll
   for (int j = 0; j < CHC_B; ++j) {
     if (j < w && status == 0) {
-      const double d = __shfl_sync(0xffffffffu, a[0][j], j);  // row c0 + j: lane j, group 0
-      if (!(d > 0.0) || !isfinite(d)) {
-        status = 1000000 + c0 + j;
-      } else {
-        const double r = rsqrt(d);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int i = lane + 32 * m;
-          if (32 * m < h) {
-            if (i > j) a[m][j] *= r;
-            else if (i == j) a[m][j] = d * r;
-          }
+      double *buf = xch + (j & 1) * (CHC_B + 1);  // [k]: scaled L_(c0+k)(c0+j), [CHC_B]: r
+      if (wm == 0) {
+        const double d = __shfl_sync(0xffffffffu, a[j], j);  // row c0 + j: lane j of warp 0
+        const long long bits = __double_as_longlong(d);
+        const bool ok = bits > 0 && ((bits >> 52) & 0x7ff) != 0x7ff;  // d > 0 and finite
+        double r = 0.0;
+        if (ok) {
+          r = rsqrt(d);
+          if (lane > j) a[j] *= r;
+          else if (lane == j) a[j] = d * r;
         }
+        if (lane < CHC_B) buf[lane] = a[j];
+        if (lane == 0) {
+          buf[CHC_B] = r;
+          xflag[j & 1] = ok ? 0 : 1000000 + c0 + j;
+        }
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      status = xflag[j & 1];
+      if (status == 0) {
+        if (wm > 0) a[j] *= buf[CHC_B];  // rows c0 + 32 and below, all past the pivot
 #pragma unroll
         for (int k = j + 1; k < CHC_B; ++k) {
           if (k < w) {
-            const double lkj = __shfl_sync(0xffffffffu, a[0][j], k);  // row c0 + k, already scaled
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-              const int i = lane + 32 * m;
-              if (32 * m < h && i >= k) a[m][k] -= a[m][j] * lkj;
-            }
+            const double lkj = buf[k];
+            if (wm > 0 || lane >= k) a[k] -= a[j] * lkj;
           }
         }
       }
     }
   }
+  if (i < h) {
 #pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    const int i = lane + 32 * m;
-    if (i < h) {
-#pragma unroll
-      for (int j = 0; j < CHC_B; ++j)
-        if (j < w) A[(c0 + i) * lda + c0 + j] = a[m][j];
-    }
+    for (int j = 0; j < CHC_B; ++j)
+      if (j < w) A[(c0 + i) * lda + c0 + j] = a[j];
   }
   return status;
 }
@@ -779,6 +783,8 @@ __global__ void __cluster_dims__(CHC_C, 1, 1) __launch_bounds__(CHC_NT)
                         // cluster barrier and read only after it
   __shared__ int own[CHC_OWN];  // the columns this CTA owns, ascending (-1: none)
   __shared__ double red[CHC_NT / 32];
+  __shared__ double xch[2 * (CHC_B + 1)];  // panel factorisation: r and the scaled panel rows
+  __shared__ int xflag[2];
   const int rank = (int)cluster.block_rank(), tid = threadIdx.x;
   const int lda = n | 1;
   double *A = dyn;                          // n x lda
@@ -843,8 +849,8 @@ __global__ void __cluster_dims__(CHC_C, 1, 1) __launch_bounds__(CHC_NT)
   cluster.sync();  // A complete in every CTA, bad the same everywhere
   // panel 0 by its owner
   if (!bad && rank == 0) {
-    if (tid < 32) {
-      const int r = chc_factor_panel(A, lda, n, 0, min(n, CHC_B));
+    if (tid < 128) {
+      const int r = chc_factor_panel(A, lda, n, 0, min(n, CHC_B), xch, xflag);
       if (tid == 0) pf = r;
     }
     __syncthreads();
@@ -886,8 +892,8 @@ __global__ void __cluster_dims__(CHC_C, 1, 1) __launch_bounds__(CHC_NT)
           A[i * lda + k] -= acc;
         }
       __syncthreads();
-      if (tid < 32) {
-        const int r = chc_factor_panel(A, lda, n, c1, c2 - c1);
+      if (tid < 128) {
+        const int r = chc_factor_panel(A, lda, n, c1, c2 - c1, xch, xflag);
         if (tid == 0) pf = r;
       }
       __syncthreads();

@@ -1185,7 +1185,9 @@ constexpr size_t kSySmem = (size_t)SY_RING * 2 * kSyBox + 3 * SY_RING * 8 + 16 +
 
 __global__ void __launch_bounds__(SY_NT, 1) screen_syrk_kernel(const __grid_constant__ CUtensorMap tmX, int n,
                                                                long long c0, long long K, int ndiag,
-                                                               double *__restrict__ partial, int *__restrict__ err) {
+                                                               double *__restrict__ partial, int *__restrict__ err,
+                                                               float *__restrict__ pmax, float *__restrict__ gmax,
+                                                               long long npl, int n1) {
   extern __shared__ unsigned char dyn[];
   unsigned char *boxes = align1024(dyn);  // ring x {row box, column box}
   uint64_t *full = reinterpret_cast<uint64_t *>(boxes + (size_t)SY_RING * 2 * kSyBox);  // TMA landed
@@ -1260,34 +1262,79 @@ __global__ void __launch_bounds__(SY_NT, 1) screen_syrk_kernel(const __grid_cons
   if (warp == SY_MUL + 1) {
     // ---- |phi| warp: each landed box becomes |phi| in place; points at or past K (only in a
     // ragged last step) read as zero.  Row r holds its logical 16-byte run k4 at position k4 ^ (r & 7).
+    // Lane l walks rows l, l + 32, l + 64, l + 96 of each box, a row's eight runs in turn.  With
+    // pmax, a diagonal unit also keeps each row's running maximum of |phi| over the current plane i1
+    // in registers (a box lies in one plane: c0 and the plane size are multiples of 32) and adds it
+    // to pmax[row][i1] and gmax[row] by atomic maxima when the plane changes and at the end.
+    const bool maxima = pmax != nullptr && diag;
+    long long cur = -1;
+    float rm[4] = {0.f, 0.f, 0.f, 0.f};
+    auto flush = [&]() {
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const int row = bi * 128 + lane + 32 * g;
+        if (row < n && cur >= 0) {
+          atomicMax(reinterpret_cast<int *>(pmax) + (long long)row * n1 + cur, __float_as_int(rm[g]));
+          atomicMax(reinterpret_cast<int *>(gmax) + row, __float_as_int(rm[g]));
+        }
+        rm[g] = 0.f;
+      }
+    };
     for (int q = 0; q < Q; ++q) {
       const int slot = q % SY_RING;
       if (!wait(&full[slot], q)) return;
       unsigned char *bx = boxes + (size_t)slot * 2 * kSyBox;
       const long long k0 = (s_lo + q) * BK;
       const bool ragged = k0 + BK > K;
-#pragma unroll 4
-      for (int e = lane; e < nbox * 1024; e += 32) {
-        uint4 *p = reinterpret_cast<uint4 *>(bx) + e;
-        uint4 v = *p;
-        v.x &= 0x7fffffffu;
-        v.y &= 0x7fffffffu;
-        v.z &= 0x7fffffffu;
-        v.w &= 0x7fffffffu;
-        if (ragged) {
-          const int row = (e >> 3) & 127, k4 = (e & 7) ^ (row & 7);
-          const long long k = k0 + 4 * k4;
-          if (k >= K) v.x = 0u;
-          if (k + 1 >= K) v.y = 0u;
-          if (k + 2 >= K) v.z = 0u;
-          if (k + 3 >= K) v.w = 0u;
+      if (maxima) {
+        const long long pl = (c0 + k0) / npl;
+        if (pl != cur) {
+          flush();
+          cur = pl;
         }
-        *p = v;
+      }
+      for (int b = 0; b < nbox; ++b) {
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const int row = lane + 32 * g;
+          const uint32_t rbase = smem_u32(bx + (size_t)b * kSyBox) + (uint32_t)row * 128u;
+          // the row's eight runs: all loads first, then the stores (logical run cl sits at position
+          // cl ^ (row & 7), so lanes 8 apart share a bank group); volatile keeps the loads after the
+          // wait on the landed box and in order with the stores
+          uint4 v[8];
+#pragma unroll
+          for (int cl = 0; cl < 8; ++cl)
+            asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                : "=r"(v[cl].x), "=r"(v[cl].y), "=r"(v[cl].z), "=r"(v[cl].w)
+                : "r"(rbase + ((uint32_t)(cl ^ (lane & 7)) << 4)));
+          float m = 0.f;
+#pragma unroll
+          for (int cl = 0; cl < 8; ++cl) {
+            v[cl].x &= 0x7fffffffu;
+            v[cl].y &= 0x7fffffffu;
+            v[cl].z &= 0x7fffffffu;
+            v[cl].w &= 0x7fffffffu;
+            if (ragged) {
+              const long long k = k0 + 4 * cl;
+              if (k >= K) v[cl].x = 0u;
+              if (k + 1 >= K) v[cl].y = 0u;
+              if (k + 2 >= K) v[cl].z = 0u;
+              if (k + 3 >= K) v[cl].w = 0u;
+            }
+            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(rbase + ((uint32_t)(cl ^ (lane & 7)) << 4)),
+                         "r"(v[cl].x), "r"(v[cl].y), "r"(v[cl].z), "r"(v[cl].w)
+                         : "memory");
+            m = fmaxf(m, fmaxf(fmaxf(__uint_as_float(v[cl].x), __uint_as_float(v[cl].y)),
+                               fmaxf(__uint_as_float(v[cl].z), __uint_as_float(v[cl].w))));
+          }
+          if (maxima && b == 0) rm[g] = fmaxf(rm[g], m);
+        }
       }
       fence_async_smem();  // these generic writes come before the TMA that refills the slot
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&ready[slot]));
     }
+    if (maxima) flush();
     return;
   }
   // ---- multiply warps: warp block (I, J); warps 8, 9 of an off-diagonal unit only release slots ----
@@ -1596,7 +1643,7 @@ size_t screen_syrk_workspace_bytes(int n, long long K) {
 }
 
 bool launch_screen_syrk(const float *X, int n, long long ld, long long c0, long long K, double scale, double *G,
-                        void *ws, int *err, cudaStream_t st, long *launches, cudaError_t *e) {
+                        void *ws, int *err, cudaStream_t st, long *launches, cudaError_t *e, const PlaneMaxOut *pm) {
   if (!use_tma() || c0 % 4 != 0 || K <= 0 || !ws) return false;
   CUtensorMap map;
   if (!make_map_f32(&map, X, n, ld, 128, tc::BK, true)) return false;
@@ -1613,7 +1660,12 @@ bool launch_screen_syrk(const float *X, int n, long long ld, long long c0, long 
     __atomic_fetch_or(&attr_done, bit, __ATOMIC_RELEASE);
   }
   double *partial = static_cast<double *>(ws);
-  tc::screen_syrk_kernel<<<dim3(units, splits), tc::SY_NT, tc::kSySmem, st>>>(map, n, c0, K, ndiag, partial, err);
+  // plane maxima along the way when every box lies in one plane
+  const bool with_max = pm && pm->pmax && pm->npl % tc::BK == 0 && c0 % tc::BK == 0;
+  tc::screen_syrk_kernel<<<dim3(units, splits), tc::SY_NT, tc::kSySmem, st>>>(
+      map, n, c0, K, ndiag, partial, err, with_max ? pm->pmax : nullptr, with_max ? pm->gmax : nullptr,
+      with_max ? pm->npl : 1, with_max ? pm->n1 : 1);
+  if (pm && pm->done) *pm->done = *pm->done && with_max;
   *e = cudaGetLastError();
   if (*e != cudaSuccess) return true;
   tc::screen_splits_reduce_kernel<<<(n * n + 63) / 64, 64, 0, st>>>(partial, splits, n, scale, G);
