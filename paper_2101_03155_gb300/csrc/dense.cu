@@ -714,20 +714,23 @@ __device__ __forceinline__ bool finite_bits(double v) {
   return ((__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;
 }
 
-// Panel (columns c0 .. c0 + w - 1, rows c0 .. n - 1) factored right-looking by the CTA's first four
-// warps, one per SM sub-partition: an FP64 warp instruction issues once per about 64 cycles on a
-// sub-partition, so one warp holding all rows would serialise four times the instructions.  Warp m
-// holds rows c0 + lane + 32 m in registers.  For column j, warp 0 takes the pivot d (lane j),
+// Panel (columns c0 .. c0 + w - 1, rows c0 .. n - 1, stored at columns s0 .. s0 + w - 1 of A) factored
+// right-looking by the CTA's first NW warps, spread over the SM sub-partitions: an FP64 warp
+// instruction issues once per about 64 cycles on a sub-partition, so one warp holding all rows would
+// serialise several times the instructions.  Warp m holds rows c0 + lane + 32 m in registers.  For column j, warp 0 takes the pivot d (lane j),
 // r = 1 / sqrt(d), scales its rows, and publishes r and the panel rows' scaled L_kj (k < CHC_B)
 // through xch (double-buffered by column parity, so one named barrier per column suffices); then
 // every warp scales its rows and updates the panel's later columns.  The arithmetic of every
 // element is that of a one-warp right-looking factorisation.  Returns 0, or 1000000 + the column of
-// a non-positive or non-finite pivot (the same in all four warps).  Call with threads 0 .. 127.
-__device__ __forceinline__ int chc_factor_panel(double *A, int lda, int n, int c0, int w, double *xch, int *xflag) {
+// a non-positive or non-finite pivot (the same in all NW warps).  Call with threads 0 .. 32 NW - 1;
+// the panel must have at most 32 NW rows.
+template <int NW>
+__device__ __forceinline__ int chc_factor_panel(double *A, int lda, int n, int c0, int s0, int w, double *xch,
+                                                int *xflag) {
   const int lane = threadIdx.x & 31, wm = threadIdx.x >> 5, h = n - c0, i = lane + 32 * wm;
   double a[CHC_B];
 #pragma unroll
-  for (int j = 0; j < CHC_B; ++j) a[j] = (i < h && j < w) ? A[(c0 + i) * lda + c0 + j] : 0.0;
+  for (int j = 0; j < CHC_B; ++j) a[j] = (i < h && j < w) ? A[(c0 + i) * lda + s0 + j] : 0.0;
   int status = 0;
 #pragma unroll
   for (int j = 0; j < CHC_B; ++j) {
@@ -749,7 +752,7 @@ __device__ __forceinline__ int chc_factor_panel(double *A, int lda, int n, int c
           xflag[j & 1] = ok ? 0 : 1000000 + c0 + j;
         }
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * NW) : "memory");
       status = xflag[j & 1];
       if (status == 0) {
         if (wm > 0) a[j] *= buf[CHC_B];  // rows c0 + 32 and below, all past the pivot
@@ -766,7 +769,7 @@ __device__ __forceinline__ int chc_factor_panel(double *A, int lda, int n, int c
   if (i < h) {
 #pragma unroll
     for (int j = 0; j < CHC_B; ++j)
-      if (j < w) A[(c0 + i) * lda + c0 + j] = a[j];
+      if (j < w) A[(c0 + i) * lda + s0 + j] = a[j];
   }
   return status;
 }
@@ -850,7 +853,7 @@ __global__ void __cluster_dims__(CHC_C, 1, 1) __launch_bounds__(CHC_NT)
   // panel 0 by its owner
   if (!bad && rank == 0) {
     if (tid < 128) {
-      const int r = chc_factor_panel(A, lda, n, 0, min(n, CHC_B), xch, xflag);
+      const int r = chc_factor_panel<4>(A, lda, n, 0, 0, min(n, CHC_B), xch, xflag);
       if (tid == 0) pf = r;
     }
     __syncthreads();
@@ -893,7 +896,7 @@ __global__ void __cluster_dims__(CHC_C, 1, 1) __launch_bounds__(CHC_NT)
         }
       __syncthreads();
       if (tid < 128) {
-        const int r = chc_factor_panel(A, lda, n, c1, c2 - c1, xch, xflag);
+        const int r = chc_factor_panel<4>(A, lda, n, c1, c1, c2 - c1, xch, xflag);
         if (tid == 0) pf = r;
       }
       __syncthreads();
@@ -983,40 +986,287 @@ __global__ void __cluster_dims__(CHC_C, 1, 1) __launch_bounds__(CHC_NT)
   if (rank == 0 && tid == 0) *status = 0;
 }
 
-static bool use_cluster_cholesky(int n) {
+// ----------------------------------------------------------------------------------------
+// The factorisation for CHC_MAX_N < n <= CHW_MAX_N on a cluster of CHC_C CTAs whose shared memory
+// holds only their own columns: all of -M does not fit one SM at these sizes.
+//   - Panel p (8 columns) is owned by CTA p % CHC_C, which keeps its panels' columns, all rows,
+//     in `own` (local column 8 (p / CHC_C) + j, odd row stride).  Each CTA symmetrises its own
+//     columns straight from M_raw and writes them to M.
+//   - The panel loop is that of the kernel above: after panel p is published, every CTA copies it
+//     (rows c0..n-1) from its owner into its panel buffer p & 1; the owner of panel p + 1 updates that
+//     panel's columns, factors it (eight warps, one row group each) and arrives at the cluster
+//     barrier; every CTA updates its other columns before it waits.
+//   - Afterwards each CTA writes its columns of L, and of L^T into the workspace (row c of L^T is
+//     column c of L); after a cluster barrier, the columns of L^-1 are dealt in groups of four, one
+//     group per warp, in an order that balances the FP64 work over the CTAs.  Forward substitution
+//     holds a warp's four columns in registers (lane l: rows l + 32 m) and reads column k of L from
+//     shared memory, where 32 rows of L^T at a time are staged (in the space of `own`).
+// Status codes as above.
+// ----------------------------------------------------------------------------------------
+constexpr int CHW_MAX_N = 256;
+constexpr int CHW_LDO = 33;  // own-column block: up to 32 columns per CTA, odd row stride
+constexpr int CHW_LDP = 9;   // panel buffer row stride
+static_assert(CHW_MAX_N <= CHC_C * CHC_B * 4, "four panels per CTA at most");
+static_assert(CHW_MAX_N <= 4 * CHC_C * (CHC_NT / 32), "four columns of L^-1 per warp");
+static_assert(CHW_MAX_N <= 32 * (CHC_NT / 32), "one row group per warp in the panel factorisation");
+static_assert(32 * CHW_MAX_N <= CHW_MAX_N * CHW_LDO, "a 32-row slab of L^T fits in the own-column block");
+
+__global__ void __cluster_dims__(CHC_C, 1, 1) __launch_bounds__(CHC_NT)
+    cholesky_cluster_wide_kernel(const double *__restrict__ M_raw, int n, double spin_factor, double *__restrict__ M,
+                                 double *__restrict__ L, double *__restrict__ Linv, double *__restrict__ energy,
+                                 int *__restrict__ status, double *__restrict__ Lt) {
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ double dyn[];
+  __shared__ int bad, pf, fail;
+  __shared__ double red[CHC_NT / 32];
+  __shared__ double xch[2 * (CHC_B + 1)];
+  __shared__ int xflag[2];
+  const int rank = (int)cluster.block_rank(), tid = threadIdx.x;
+  double *own = dyn;                              // n x CHW_LDO
+  // two n x CHW_LDP panel buffers, panel p in buffer p & 1: after arriving at the barrier a thread
+  // still reads panel p while a faster one, past the wait, may already copy panel p + 1
+  double *pbuf = own + (size_t)n * CHW_LDO;
+  double *rinv = pbuf + 2 * (size_t)n * CHW_LDP;  // n
+  const int P = (n + CHC_B - 1) / CHC_B;
+  if (tid == 0) {
+    bad = 0;
+    pf = 0;
+    fail = 0;
+  }
+  cluster.sync();  // every CTA has started and cleared its flags before any write across CTAs
+  // own columns of -M_sym (all rows), M_sym written to M: local column lc = 8 t + j holds column
+  // c = 8 (rank + CHC_C t) + j
+  {
+    bool ok = true;
+    for (int e = tid; e < n * 32; e += CHC_NT) {
+      const int i = e >> 5, lc = e & 31, c = CHC_B * (rank + CHC_C * (lc >> 3)) + (lc & 7);
+      if (c >= n) continue;
+      const double v = i == c ? M_raw[(long long)c * n + c]
+                              : 0.5 * (M_raw[(long long)i * n + c] + M_raw[(long long)c * n + i]);
+      M[(long long)i * n + c] = v;
+      ok = ok && finite_bits(v);
+      own[i * CHW_LDO + lc] = __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
+    }
+    if (!ok)
+      for (int q = 0; q < CHC_C; ++q) *cluster.map_shared_rank(&bad, q) = 2000000;
+  }
+  if (rank == 0) {
+    double part = 0.0;
+    for (int k = tid; k < n; k += CHC_NT) part += M_raw[(long long)k * n + k];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((tid & 31) == 0) red[tid >> 5] = part;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < CHC_NT / 32; ++w) t += red[w];
+      *energy = 0.5 * spin_factor * t;
+    }
+  }
+  cluster.sync();  // own columns complete, bad the same everywhere
+  if (!bad && rank == 0) {
+    const int r = chc_factor_panel<CHC_NT / 32>(own, CHW_LDO, n, 0, 0, min(n, CHC_B), xch, xflag);
+    if (tid == 0) pf = r;
+    __syncthreads();
+    if (pf && tid < CHC_C) *cluster.map_shared_rank(&fail, tid) = pf;
+  }
+  cluster.sync();  // panel 0 final in its owner's shared memory (or the failure announced)
+  for (int p = 0; p < P; ++p) {
+    if (bad || fail) break;  // the same in every CTA after the barrier
+    const int c0 = p * CHC_B, c1 = min(n, c0 + CHC_B), w = c1 - c0, owner = p % CHC_C;
+    const int s_p = CHC_B * (p / CHC_C);  // the panel's columns in its owner's block
+    double *pb = pbuf + (size_t)(p & 1) * n * CHW_LDP;
+    {
+      // rows c0.. of the panel into the panel buffer (from the owner's block; the owner's own copy
+      // is local), four loads in flight
+      const double *src = rank == owner ? own : cluster.map_shared_rank(own, owner);
+      const int ne = (n - c0) * CHC_B;
+      for (int base = tid; base < ne; base += 4 * CHC_NT) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = base + u * CHC_NT, c = e & (CHC_B - 1);
+          v[u] = (e < ne && c < w) ? src[(c0 + (e >> 3)) * CHW_LDO + s_p + c] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = base + u * CHC_NT, c = e & (CHC_B - 1);
+          if (e < ne && c < w) pb[(c0 + (e >> 3)) * CHW_LDP + c] = v[u];
+        }
+      }
+    }
+    __syncthreads();  // the panel copied, and the previous panel's updates of this CTA's columns done
+    const bool ahead = p + 1 < P && rank == (p + 1) % CHC_C;
+    const int c2 = min(n, c1 + CHC_B);
+    if (ahead) {
+      const int s_n = CHC_B * ((p + 1) / CHC_C);
+      const int col = tid & (CHC_B - 1), rl = tid >> 3, k = c1 + col;
+      if (k < c2)
+        for (int i = c1 + rl; i < n; i += CHC_NT / CHC_B) {
+          if (i < k) continue;
+          double acc = 0.0;
+          for (int j = 0; j < w; ++j) acc += pb[i * CHW_LDP + j] * pb[k * CHW_LDP + j];
+          own[i * CHW_LDO + s_n + col] -= acc;
+        }
+      __syncthreads();
+      const int r = chc_factor_panel<CHC_NT / 32>(own, CHW_LDO, n, c1, s_n, c2 - c1, xch, xflag);
+      if (tid == 0) pf = r;
+      __syncthreads();
+      if (pf && tid < CHC_C) *cluster.map_shared_rank(&fail, tid) = pf;
+    }
+    cluster_arrive_release();  // the next panel is published once every CTA has arrived
+    {
+      // rank-w update of this CTA's other columns k >= c1 (k >= c2 for the look-ahead owner), rows i >= k
+      const int lc = tid & 31, rl = tid >> 5;
+      const int k = CHC_B * (rank + CHC_C * (lc >> 3)) + (lc & 7);
+      if (k < n && k >= (ahead ? c2 : c1))
+        for (int i = k + rl; i < n; i += CHC_NT / 32) {
+          double acc = 0.0;
+          for (int j = 0; j < w; ++j) acc += pb[i * CHW_LDP + j] * pb[k * CHW_LDP + j];
+          own[i * CHW_LDO + lc] -= acc;
+        }
+    }
+    cluster_wait_acquire();
+  }
+  cluster.sync();  // no CTA reads another's shared memory past this point
+  if (bad || fail) {
+    if (rank == 0 && tid == 0) *status = bad ? bad : fail;
+    return;
+  }
+  // this CTA's columns of L (row-major, zeros above the diagonal) and of L^T (row c = column c of L)
+  for (int e = tid; e < n * 32; e += CHC_NT) {
+    const int i = e >> 5, lc = e & 31, c = CHC_B * (rank + CHC_C * (lc >> 3)) + (lc & 7);
+    if (c >= n) continue;
+    const double v = own[i * CHW_LDO + lc];
+    L[(long long)i * n + c] = i >= c ? v : 0.0;
+    if (i >= c) Lt[(long long)c * n + i] = v;
+  }
+  __threadfence();
+  cluster.sync();  // every column of L^T written
+  for (int k = tid; k < n; k += CHC_NT) rinv[k] = 1.0 / __ldcg(Lt + (long long)k * n + k);
+  {
+    double *S = own;  // 32 rows of L^T at a time
+    const int lane = tid & 31, wp = tid >> 5;
+    const int t = CHC_C * wp + ((wp & 1) ? CHC_C - 1 - rank : rank);  // group of columns 4t .. 4t + 3
+    int cq[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cq[q] = 4 * t + q < n ? 4 * t + q : -1;
+    __syncthreads();  // rinv complete
+    double x[4][8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int m = 0; m < 8; ++m) x[q][m] = (cq[q] >= 0 && lane + 32 * m == cq[q]) ? rinv[cq[q]] : 0.0;
+#pragma unroll
+    for (int kb = 0; kb < 8; ++kb) {
+      const int k_lo = 32 * kb, k_hi = min(n, 32 * kb + 32);
+      if (k_lo >= n) break;  // the same in every thread
+      __syncthreads();      // the previous slab is no longer read
+      for (int e = tid; e < (k_hi - k_lo) * n; e += CHC_NT) {
+        const int kk = e / n, i = e - kk * n;
+        S[e] = i > k_lo + kk ? __ldcg(Lt + (long long)(k_lo + kk) * n + i) : 0.0;
+      }
+      __syncthreads();
+      if (cq[0] >= 0) {
+        // steps k in this slab; the last step, n - 2, makes row n - 1 final
+        for (int k = max(cq[0], k_lo); k < min(n - 1, k_hi); ++k) {
+          const int lk = k & 31;
+          double xk[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) xk[q] = __shfl_sync(0xffffffffu, x[q][kb], lk);
+          const double *Sk = S + (k - k_lo) * n;
+#pragma unroll
+          for (int m = kb; m < 8; ++m) {
+            const int i = lane + 32 * m;
+            if (i > k && i < n) {
+              const double lik = Sk[i];
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                if (cq[q] >= 0 && k >= cq[q]) x[q][m] -= lik * xk[q];
+            }
+          }
+          // row k + 1 is final: lane (k + 1) & 31 of row group kb, or lane 0 of group kb + 1
+          if (lk != 31) {
+            if (lane == lk + 1) {
+              const double sc = rinv[k + 1];
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                if (cq[q] >= 0 && k >= cq[q]) x[q][kb] *= sc;
+            }
+          } else if (kb < 7) {
+            if (lane == 0) {
+              const double sc = rinv[k + 1];
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                if (cq[q] >= 0 && k >= cq[q]) x[q][kb + 1] *= sc;
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int i = lane + 32 * m;
+      if (i < n) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (cq[q] >= 0) Linv[(long long)i * n + cq[q]] = i >= cq[q] ? x[q][m] : 0.0;
+      }
+    }
+  }
+  if (rank == 0 && tid == 0) *status = 0;
+}
+
+static bool cluster_cholesky_off() {
   static const bool off = [] {
     const char *v = std::getenv("ACE_CHOLESKY_ONE_CTA");
     return v && *v && *v != '0';
   }();
-  return !off && n <= CHC_MAX_N;
+  return off;
+}
+
+// Once per device and kernel: the shared-memory limit for the largest n, and whether such a cluster
+// fits (state[dev]: 0 unknown, 1 usable, -1 not).
+template <typename K>
+static bool cluster_ready(K kernel, size_t smax, int *state, cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return false;
+  if (state[dev] == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+    int clusters = 0;
+    if (e == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(CHC_C);
+      cfg.blockDim = dim3(CHC_NT);
+      cfg.dynamicSmemBytes = smax;
+      cfg.stream = st;
+      e = cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg);
+    }
+    cudaGetLastError();
+    state[dev] = (e == cudaSuccess && clusters > 0) ? 1 : -1;
+  }
+  return state[dev] == 1;
 }
 
 cudaError_t launch_cholesky(const double *M_raw, int n, double spin_factor, double *M, double *L, double *Linv,
                             double *energy, int *status, double *gwork, cudaStream_t st) {
-  if (use_cluster_cholesky(n)) {
-    // once per device: the shared-memory limit for the largest n, and whether such a cluster fits
-    static int ready[64] = {};  // 0 unknown, 1 usable, -1 not
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && ready[dev] == 0) {
-      const size_t smax = sizeof(double) * ((size_t)CHC_MAX_N * (CHC_MAX_N | 1) + (size_t)CHC_MAX_N);
-      cudaError_t e = cudaFuncSetAttribute(cholesky_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smax);
-      int clusters = 0;
-      if (e == cudaSuccess) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(CHC_C);
-        cfg.blockDim = dim3(CHC_NT);
-        cfg.dynamicSmemBytes = smax;
-        cfg.stream = st;
-        e = cudaOccupancyMaxActiveClusters(&clusters, cholesky_cluster_kernel, &cfg);
-      }
-      cudaGetLastError();
-      ready[dev] = (e == cudaSuccess && clusters > 0) ? 1 : -1;
-    }
-    if (dev >= 0 && dev < 64 && ready[dev] == 1) {
+  if (!cluster_cholesky_off() && n <= CHC_MAX_N) {
+    static int state[64] = {};
+    const size_t smax = sizeof(double) * ((size_t)CHC_MAX_N * (CHC_MAX_N | 1) + (size_t)CHC_MAX_N);
+    if (cluster_ready(cholesky_cluster_kernel, smax, state, st)) {
       const size_t smem = sizeof(double) * ((size_t)n * (n | 1) + (size_t)n);
       cholesky_cluster_kernel<<<CHC_C, CHC_NT, smem, st>>>(M_raw, n, spin_factor, M, L, Linv, energy, status);
+      return cudaGetLastError();
+    }
+  }
+  if (!cluster_cholesky_off() && n > CHC_MAX_N && n <= CHW_MAX_N && gwork != nullptr) {
+    // columns spread over the cluster; gwork (n x n doubles at least) holds L^T
+    static int state[64] = {};
+    const size_t smax = sizeof(double) * (size_t)CHW_MAX_N * (CHW_LDO + 2 * CHW_LDP + 1);
+    if (cluster_ready(cholesky_cluster_wide_kernel, smax, state, st)) {
+      const size_t smem = sizeof(double) * (size_t)n * (CHW_LDO + 2 * CHW_LDP + 1);
+      cholesky_cluster_wide_kernel<<<CHC_C, CHC_NT, smem, st>>>(M_raw, n, spin_factor, M, L, Linv, energy, status,
+                                                                 gwork);
       return cudaGetLastError();
     }
   }

@@ -66,6 +66,60 @@ np.savez(sys.argv[1], L=g["L"], M=g["M"], E=np.array(g["E_x"]))
 """
 
 
+CHILD_CHOL_WIDE = r"""
+import sys
+import numpy as np, torch
+sys.path.insert(0, {root!r})
+sys.path.insert(0, {tests!r})
+import paper_2101_03155_gb300 as ace
+from gpu_helpers import gpu_build
+from workloads.generators import water_like
+w = water_like({nmol}, {cell!r}, (48, 48, 48), np.random.default_rng(1011), rho_cut=1e-3)
+g = gpu_build(w.phi, w.lattice, ace.ACE_FP64, rho_cut=w.rho_cut)
+np.savez(sys.argv[1], L=g["L"], M=g["M"], E=np.array(g["E_x"]), xi=g["xi"], W=g["W"])
+"""
+
+
+@pytest.mark.parametrize("nmol", [48, 64])
+def test_wide_cluster_cholesky_matches_one_cta(tmp_path, nmol):
+    """Above 128 orbitals (192 and 256 here) the cluster kernel with columns spread over its CTAs and
+    the one-CTA kernel (ACE_CHOLESKY_ONE_CTA=1) both factor -M = L L^T to FP64 rounding, and
+    xi = L^-1 W holds with the GPU's own W and L (the FP64 left multiply adds no error of note)."""
+    cell = 23.47 * (nmol / 64.0) ** (1.0 / 3.0)  # water density
+    outs = {}
+    for name, flag in (("cluster", "0"), ("one_cta", "1")):
+        f = tmp_path / f"{name}.npz"
+        env = dict(os.environ, ACE_CHOLESKY_ONE_CTA=flag)
+        code = CHILD_CHOL_WIDE.format(root=ROOT, tests=os.path.join(ROOT, "tests"), nmol=nmol, cell=cell)
+        r = subprocess.run([sys.executable, "-c", code, str(f)], env=env, capture_output=True, text=True,
+                           timeout=900, cwd=ROOT)
+        assert r.returncode == 0, r.stderr[-2000:]
+        outs[name] = np.load(f)
+    a, b = outs["cluster"], outs["one_cta"]
+    assert a["L"].shape == (4 * nmol, 4 * nmol)
+    assert np.abs(a["M"] - b["M"]).max() <= 1e-13 * np.abs(b["M"]).max()
+    assert abs(float(a["E"]) - float(b["E"])) <= 1e-12 * abs(float(b["E"]))
+    eps = np.finfo(np.float64).eps
+    for o in (a, b):
+        L, M = o["L"], o["M"]
+        assert np.all(np.triu(L, 1) == 0.0)
+        # backward error of the factorisation: L L^T = -M to rounding (n eps |M|, with margin)
+        assert np.abs(L @ L.T + M).max() <= 1e-12 * np.abs(M).max()
+        # forward error against LAPACK's factor of the same M: a multiple of cond(-M) eps (the
+        # orbitals of a coarse 48^3 grid leave -M with cond ~ 1e6 at 256 orbitals)
+        cond = np.linalg.cond(-M)
+        L_ref = np.linalg.cholesky(-M)
+        assert np.abs(L - L_ref).max() <= max(1e-12, 10 * cond * eps) * np.abs(L_ref).max()
+        # xi = L^-1 W through L^-1 (forward substitution): a multiple of cond(L) eps
+        W = o["W"].reshape(L.shape[0], -1)
+        xi_ref = np.linalg.solve(L, W)
+        tol = max(1e-10, 10 * np.sqrt(cond) * eps)
+        assert np.abs(o["xi"].reshape(xi_ref.shape) - xi_ref).max() <= tol * np.abs(xi_ref).max()
+    # the two kernels' factors agree to the same forward bound
+    cond = np.linalg.cond(-b["M"])
+    assert np.abs(a["L"] - b["L"]).max() <= max(1e-12, 20 * cond * eps) * np.abs(b["L"]).max()
+
+
 def test_one_cta_cholesky_matches_cluster_cholesky(tmp_path):
     """The cluster Cholesky (default for n <= 128) and the one-CTA kernel (ACE_CHOLESKY_ONE_CTA=1)
     factor the same M to FP64 rounding, and both L L^T = -M."""
