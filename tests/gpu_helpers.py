@@ -25,7 +25,7 @@ MIXED_W_RTOL = 2e-5
 MIXED_XI_RTOL = 5e-5
 # K psi = -xi (dV xi^T psi) for an arbitrary psi: two BF16x3 contractions, 2 x 1.5e-5, where the
 # first one may cancel (psi nearly orthogonal to xi) and the second adds its own 1.5e-5: 3e-5.
-# For psi in the span of the orbitals the benchmark spec's target MIXED_KPHI_RTOL applies.
+# For psi in the span of the orbitals the K phi target MIXED_KPHI_RTOL (1e-5) applies.
 MIXED_KPSI_RTOL = 3e-5
 # mixed-form screen values O_ij = dV sum |phi_i||phi_j| on the CUDA cores: FP32 products of the
 # FP32-rounded orbitals (input rounding 2^-24 per factor), FP32 partial sums over 64 points (at
