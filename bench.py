@@ -38,9 +38,9 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_values.json")
 CHAIN_DRAM_BYTES_PER_BUILD = 8.17e9
 # DRAM bytes (read + write) per launch of the dense kernels of the same workload: M and xi from one
 # ncu capture with caches not flushed (profiles/dense_tc_water32_96c.md), the CUDA-core screen from
-# its full capture (profiles/screen_syrk_water32_96c.md: 454.2 MB read, 3.6 MB written); None once a
-# kernel changes
-DENSE_DRAM_BYTES = {"screen": 457.8e6, "M": 929.8e6, "xi": 897.9e6}
+# its capture with the plane maxima (profiles/screen_syrk_water32_96c.md: 950.9 GB/s over 482.0 us,
+# 458.3 MB); None once a kernel changes
+DENSE_DRAM_BYTES = {"screen": 458.3e6, "M": 929.8e6, "xi": 897.9e6}
 # DRAM bytes per SCDM localisation of the 128-orbital 96^3 set: 128 selection passes at 436.1 MB
 # (ncu, profiles/scdm_water32_96c.md) + the left multiply Phi = U^T Psi (897.9 MB) + the transpose
 SCDM_DRAM_BYTES = 128 * 436.1e6 + 897.9e6 + 906e6
