@@ -39,8 +39,9 @@ CHAIN_DRAM_BYTES_PER_BUILD = 8.17e9
 # DRAM bytes (read + write) per launch of the dense kernels of the same workload: M and xi from one
 # ncu capture with caches not flushed (profiles/dense_tc_water32_96c.md), the CUDA-core screen from
 # its capture with the plane maxima (profiles/screen_syrk_water32_96c.md: 950.9 GB/s over 482.0 us,
-# 458.3 MB); None once a kernel changes
-DENSE_DRAM_BYTES = {"screen": 458.3e6, "M": 929.8e6, "xi": 897.9e6}
+# 458.3 MB), xi from the capture of the left multiply with its short-last-tile support (4.22 TB/s
+# over 207.8 us, 876.5 MB); None once a kernel changes
+DENSE_DRAM_BYTES = {"screen": 458.3e6, "M": 929.8e6, "xi": 876.5e6}
 # DRAM bytes per SCDM localisation of the 128-orbital 96^3 set: 128 selection passes at 436.1 MB
 # (ncu, profiles/scdm_water32_96c.md) + the left multiply Phi = U^T Psi (897.9 MB) + the transpose
 SCDM_DRAM_BYTES = 128 * 436.1e6 + 897.9e6 + 906e6
