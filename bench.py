@@ -43,8 +43,8 @@ CHAIN_DRAM_BYTES_PER_BUILD = 8.17e9
 # over 207.8 us, 876.5 MB); None once a kernel changes
 DENSE_DRAM_BYTES = {"screen": 458.3e6, "M": 929.8e6, "xi": 876.5e6}
 # DRAM bytes per SCDM localisation of the 128-orbital 96^3 set: 128 selection passes at 436.1 MB
-# (ncu, profiles/scdm_water32_96c.md) + the left multiply Phi = U^T Psi (897.9 MB) + the transpose
-SCDM_DRAM_BYTES = 128 * 436.1e6 + 897.9e6 + 906e6
+# (ncu, profiles/scdm_water32_96c.md) + the left multiply Phi = U^T Psi (876.5 MB) + the transpose
+SCDM_DRAM_BYTES = 128 * 436.1e6 + 876.5e6 + 906e6
 
 
 def _peaks():
