@@ -688,8 +688,9 @@ __global__ void __launch_bounds__(CH_NT) cholesky_kernel(const double *__restric
 //   - A non-positive or non-finite pivot is written into every CTA's flag before the barrier, so all
 //     CTAs leave the panel loop at the same point; the outputs then carry the same status codes as
 //     above.
-// The arithmetic of every element (the symmetrisation, the right-looking updates in panel order,
-// the pivots, the substitution) is that of the one-CTA kernel's cluster predecessor, step for step.
+// Every element's arithmetic is fixed by the algorithm, not by the schedule: the panel updates of an
+// element are applied in panel order (each a sum over the panel's columns in order, then one
+// subtraction), and the substitution takes the steps k in order, so the result repeats bit for bit.
 // All waits are hardware barriers (CTA and cluster); no CTA reads another's shared memory after the
 // cluster barrier that follows the last panel.
 // ----------------------------------------------------------------------------------------
